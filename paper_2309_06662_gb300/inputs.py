@@ -1,0 +1,267 @@
+"""Seeded synthetic inputs for the hydrostatic free-surface ocean step.
+
+This module is shared by the CUDA library's tests and benchmark and by the CPU
+oracle's tests.  It holds none of the method's arithmetic: it only places the
+vertical levels, draws the random-field bathymetry, evaluates the surface wind
+stress and the initial temperature/salinity fields, and collects the run
+parameters.  Every random number comes from one counter-based generator
+(SplitMix64, Steele, Lea & Flood 2014) followed by the Box-Muller transform, so
+the same seed gives the same arrays on every machine.
+
+The paper (Sec. "How performance was measured") forces its realistic domains with
+ECCO2 fields over real bathymetry; neither is available here, so the recipes
+below are synthetic stand-ins with the same shapes, depth range and forcing
+magnitude.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Dict, Optional
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_STREAM = np.uint64(0xD1B54A32D192ED03)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function applied elementwise to uint64 words."""
+    z = z.copy()
+    z ^= z >> np.uint64(30)
+    z *= _M1
+    z ^= z >> np.uint64(27)
+    z *= _M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def random_u64(seed: int, stream: int, start: int, n: int) -> np.ndarray:
+    """Words start..start+n-1 of the SplitMix64 sequence keyed by (seed, stream)."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([np.uint64(seed) ^ (np.uint64(stream) * _STREAM)],
+                              dtype=np.uint64))[0]
+        ctr = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        return _mix64(key + ctr * _GAMMA)
+
+
+def random_normal(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
+    """n standard normal draws (Box-Muller on consecutive word pairs)."""
+    with np.errstate(over="ignore"):
+        w = random_u64(seed, stream, 2 * start, 2 * n).reshape(n, 2)
+    u1 = ((w[:, 0] >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+    u2 = (w[:, 1] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def random_uniform(seed: int, stream: int, n: int) -> np.ndarray:
+    """n uniform draws in [0, 1)."""
+    w = random_u64(seed, stream, 0, n)
+    return (w >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+# ----------------------------------------------------------------------------- levels
+
+def uniform_z_faces(nz: int, depth: float) -> np.ndarray:
+    """nz+1 level faces from -depth (bottom) to 0 (top), evenly spaced."""
+    return np.linspace(-depth, 0.0, nz + 1)
+
+
+def stretched_z_faces(nz: int, depth: float = 5000.0, stretch: float = 3.0) -> np.ndarray:
+    """nz+1 faces, bottom to top, thin near the surface.
+
+    Face m below the surface sits at depth d(m) = H (exp(s m/nz) - 1)/(exp(s) - 1).
+    """
+    m = np.arange(nz + 1, dtype=np.float64)
+    d = depth * (np.exp(stretch * m / nz) - 1.0) / (math.exp(stretch) - 1.0)
+    d[-1] = depth
+    return -d[::-1].copy()
+
+
+# ----------------------------------------------------------------------------- bathymetry
+
+def _gauss_filter_periodic(a: np.ndarray, sigma: float, axis: int) -> np.ndarray:
+    n = a.shape[axis]
+    k = np.fft.fftfreq(n) * 2.0 * math.pi
+    h = np.exp(-0.5 * (sigma * k) ** 2)
+    shape = [1] * a.ndim
+    shape[axis] = n
+    return np.real(np.fft.ifft(np.fft.fft(a, axis=axis) * h.reshape(shape), axis=axis))
+
+
+def _gauss_filter_reflect(a: np.ndarray, sigma: float, axis: int) -> np.ndarray:
+    n = a.shape[axis]
+    b = np.concatenate([a, np.flip(a, axis=axis)], axis=axis)   # even extension
+    b = _gauss_filter_periodic(b, sigma, axis)
+    return np.take(b, np.arange(n), axis=axis)
+
+
+def random_field_depth(nx: int, ny: int, dx_deg: float, dy_deg: float, seed: int,
+                       corr_deg: float = 10.0, max_depth: float = 5500.0,
+                       min_depth: float = 50.0, periodic_x: bool = True,
+                       walls_y: bool = True) -> np.ndarray:
+    """Seeded Gaussian random-field bathymetry (depth >= 0, metres), [ny, nx].
+
+    White N(0,1) noise is smoothed by a Gaussian of standard deviation corr_deg
+    (periodic in x when the domain is periodic, reflecting otherwise), min-max
+    normalised to [0, max_depth]; columns shallower than min_depth become land
+    (depth 0), and with walls_y the first and last rows are land.
+    """
+    noise = random_normal(seed, 1, nx * ny).reshape(ny, nx)
+    f = noise
+    if periodic_x:
+        f = _gauss_filter_periodic(f, corr_deg / dx_deg, axis=1)
+    else:
+        f = _gauss_filter_reflect(f, corr_deg / dx_deg, axis=1)
+    f = _gauss_filter_reflect(f, corr_deg / dy_deg, axis=0)
+    f = (f - f.min()) / (f.max() - f.min())
+    d = f * max_depth
+    d[d < min_depth] = 0.0
+    if walls_y:
+        d[0, :] = 0.0
+        d[-1, :] = 0.0
+    return d
+
+
+# ----------------------------------------------------------------------------- parameters
+
+def default_params() -> Dict[str, float]:
+    """Physical constants and scheme switches (the readings of the paper's unnamed constants)."""
+    return dict(
+        dt=600.0, n_substeps=30, chi=0.1,
+        g=9.80665, rho0=1026.0, alpha=2e-4, beta_s=8e-4, T0=10.0, S0=35.0,
+        f0=1e-4, beta_plane=2e-11, omega=7.292115e-5, radius=6.371e6,
+        nu0=1e-2, ri_a=5.0, nu_b=1e-4, kappa_b=1e-5, kappa_conv=0.1,
+        weno_eps=1e-30, weno_linear=0, min_depth=50.0,
+    )
+
+
+@dataclass
+class Case:
+    """A complete seeded initial-value problem: grid, bathymetry, forcing, state, params."""
+    name: str
+    kind: int                 # 0 = Cartesian beta-plane box (metres), 1 = lat-lon (degrees)
+    nx: int
+    ny: int
+    nz: int
+    periodic_x: bool
+    periodic_y: bool
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    z_faces: np.ndarray       # nz+1, bottom to top
+    depth: np.ndarray         # [ny, nx], metres, >= 0
+    taux: np.ndarray          # [ny, nx] on u-faces, N/m^2
+    tauy: np.ndarray          # [ny, nx] on v-faces, N/m^2
+    T: np.ndarray             # [nz, ny, nx]
+    S: np.ndarray             # [nz, ny, nx]
+    params: Dict[str, float] = field(default_factory=default_params)
+    steps: int = 100
+    u: Optional[np.ndarray] = None
+    v: Optional[np.ndarray] = None
+    eta: Optional[np.ndarray] = None
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def with_params(self, **kw) -> "Case":
+        p = dict(self.params)
+        p.update(kw)
+        return replace(self, params=p)
+
+
+def _zc(zf: np.ndarray) -> np.ndarray:
+    return 0.5 * (zf[1:] + zf[:-1])
+
+
+def _stratified(zf: np.ndarray, ny: int, nx: int, seed: int, t_top: float, t_bot: float,
+                s_top: float, s_bot: float, noise: float) -> tuple:
+    nz = len(zf) - 1
+    H = -zf[0]
+    zc = _zc(zf)
+    frac = (zc + H) / H                      # 0 at the bottom, 1 at the top
+    T = np.empty((nz, ny, nx))
+    S = np.empty((nz, ny, nx))
+    n2 = ny * nx
+    for k in range(nz):
+        T[k] = t_bot + (t_top - t_bot) * frac[k]
+        S[k] = s_bot + (s_top - s_bot) * frac[k]
+        if noise > 0:
+            T[k] += noise * random_normal(seed, 2, n2, start=k * n2).reshape(ny, nx)
+            if s_top != s_bot:
+                S[k] += noise * random_normal(seed, 3, n2, start=k * n2).reshape(ny, nx)
+    return T, S
+
+
+def box_case(nx: int = 32, ny: int = 32, nz: int = 8, seed: int = 1) -> Case:
+    """Closed 1000 km x 1000 km beta-plane box, flat 4 km bottom, double-gyre wind.
+
+    T is linear from 20 C (top) to 2 C (bottom) plus N(0, 0.01 C) noise; S = 35.
+    """
+    L = 1.0e6
+    zf = uniform_z_faces(nz, 4000.0)
+    depth = np.full((ny, nx), 4000.0)
+    yc = (np.arange(ny) + 0.5) * (L / ny)
+    taux = np.repeat((0.1 * np.cos(math.pi * yc / L))[:, None], nx, axis=1)
+    tauy = np.zeros((ny, nx))
+    T, S = _stratified(zf, ny, nx, seed, 20.0, 2.0, 35.0, 35.0, 0.01)
+    p = default_params()
+    p.update(dt=600.0, n_substeps=30)
+    return Case("box", 0, nx, ny, nz, False, False, 0.0, L, 0.0, L, zf, depth, taux, tauy,
+                T, S, p, steps=100)
+
+
+def latlon_case(nx: int, ny: int, nz: int, lat: float, seed: int, dt: float, n_substeps: int,
+                steps: int, name: str, noise: float = 0.05, corr_deg: float = 10.0) -> Case:
+    """Global lat-lon channel from -lat to +lat, periodic in longitude, walls at both ends.
+
+    Stretched levels to 5000 m, random-field bathymetry, zonal wind 0.1 cos(3 phi) N/m^2,
+    T linear 20 -> 2 C and S linear 34.5 -> 35 with depth, each with `noise`-amplitude
+    N(0,1) perturbations.
+    """
+    zf = stretched_z_faces(nz, 5000.0, 3.0)
+    dlon = 360.0 / nx
+    dlat = 2.0 * lat / ny
+    depth = random_field_depth(nx, ny, dlon, dlat, seed, corr_deg=corr_deg)
+    phi = np.deg2rad(-lat + (np.arange(ny) + 0.5) * dlat)
+    taux = np.repeat((0.1 * np.cos(3.0 * phi))[:, None], nx, axis=1)
+    tauy = np.zeros((ny, nx))
+    T, S = _stratified(zf, ny, nx, seed, 20.0, 2.0, 34.5, 35.0, noise)
+    p = default_params()
+    p.update(dt=dt, n_substeps=n_substeps)
+    return Case(name, 1, nx, ny, nz, True, False, 0.0, 360.0, -lat, lat, zf, depth, taux,
+                tauy, T, S, p, steps=steps)
+
+
+def latlon_1deg_case(seed: int = 2) -> Case:
+    """1-degree, 360 x 160 x 32, 80S-80N, dt = 1200 s, 40 substeps, 1000 steps."""
+    return latlon_case(360, 160, 32, 80.0, seed, 1200.0, 40, 1000, "latlon_1deg")
+
+
+def latlon_12th_case(seed: int = 3) -> Case:
+    """1/12-degree, 4320 x 1680 x 48, 70S-70N, dt = 300 s, 60 substeps, 200 steps."""
+    return latlon_case(4320, 1680, 48, 70.0, seed, 300.0, 60, 200, "latlon_12th")
+
+
+def latlon_half_case(seed: int = 4, lat: float = 80.0) -> Case:
+    """1/2-degree, 720 x 320 x 48, 80S-80N, dt = 900 s, 60 substeps."""
+    return latlon_case(720, 320, 48, lat, seed, 900.0, 60, 2000, "latlon_half")
+
+
+def latlon_small_case(nx: int = 72, ny: int = 40, nz: int = 12, seed: int = 7,
+                      lat: float = 70.0, dt: float = 1800.0, n_substeps: int = 20) -> Case:
+    """A small lat-lon case (5 degree) with the same recipe, for fast parity runs."""
+    return latlon_case(nx, ny, nz, lat, seed, dt, n_substeps, 50, "latlon_small",
+                       corr_deg=20.0)
+
+
+def latlon_window(case_nx: int, case_ny: int, lat: float, i0: int, j0: int, wx: int,
+                  wy: int) -> tuple:
+    """Lon/lat bounds of the sub-window [i0, i0+wx) x [j0, j0+wy) of a global lat-lon grid."""
+    dlon = 360.0 / case_nx
+    dlat = 2.0 * lat / case_ny
+    return (i0 * dlon, (i0 + wx) * dlon, -lat + j0 * dlat, -lat + (j0 + wy) * dlat)
