@@ -638,11 +638,13 @@ static void cadd(csum_t* a, double x) {
 /*
  * out[0] = sum T V over wet cells, out[1] = sum S V, out[2] = sum eta A over wet
  * columns (compensated), out[3] = kinetic energy 1/2 sum u^2 V_u + 1/2 sum v^2 V_v,
- * out[4] = max advective CFL number, out[5] = 1 if any state value is not finite,
+ * out[4] = max advective CFL number (w of the current state), out[5] = 1 if any state
+ * value is not finite,
  * out[6] = wet volume, out[7] = step counter.
  */
-void ora_diagnostics(const ora_t* m, double* out) {
+void ora_diagnostics(ora_t* m, double* out) {
     int nx = m->nx, ny = m->ny, nz = m->nz;
+    diagnose(m);   /* w of the state being reported, for the vertical CFL number */
     csum_t st = {0, 0}, ss = {0, 0}, se = {0, 0}, ke = {0, 0}, vol = {0, 0};
     double cfl = 0.0;
     int bad = 0;
