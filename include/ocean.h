@@ -1,0 +1,207 @@
+/*
+ * ocean.h -- C ABI of the GB300 hydrostatic free-surface ocean step (libocean.so).
+ *
+ * The library advances one explicit baroclinic time step of the hydrostatic
+ * Boussinesq equations on an Arakawa C-grid (arXiv 2309.06662, Sec. "New numerical
+ * methods for finite volume fluid dynamics on the sphere": finite volumes on a
+ * staggered C-grid, implicit-explicit second-order Adams-Bashforth stepping,
+ * backward-Euler vertical diffusion with a tridiagonal solve, adaptive-order WENO
+ * advection of momentum and tracers; Sec. "Optimization of ocean free surface
+ * dynamics": split-explicit barotropic sub-cycling; Sec. "How performance was
+ * measured": Richardson-number vertical mixing, no explicit horizontal diffusion).
+ * Every step runs in CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *  - Return codes: OCEAN_OK (0) or a negative OCEAN_ERR_* code; the message is
+ *    available from ocean_last_error(handle) (or ocean_last_error(NULL) when no
+ *    handle exists yet).  No C++ exception crosses this boundary.
+ *  - Indexing: i is the zonal (x) index, j the meridional (y) index, k the level;
+ *    k = 0 is the BOTTOM level, k = nz-1 the top.  3-D host arrays are [nz][ny][nx]
+ *    (i fastest), 2-D host arrays [ny][nx].  No halo on the host side.
+ *  - Staggering: u(i,j,k) lives on the west face of cell (i,j,k), v(i,j,k) on its
+ *    south face, w(i,j,k) on its bottom face, T, S, p at the cell centre; kappa and
+ *    nu on the bottom (w-)face.
+ *  - Host arrays cross the ABI as double, whatever the internal precision.  Values on
+ *    dry cells/faces are ignored on input and returned as 0.
+ *  - Ownership: the library copies every host input; the caller owns its buffers.
+ *    Device memory belongs to the handle (or to the caller, with ocean_create_in).
+ *  - Threads: a handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef OCEAN_H
+#define OCEAN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCEAN_OK 0
+#define OCEAN_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad id) */
+#define OCEAN_ERR_CUDA (-2)      /* a CUDA call failed */
+#define OCEAN_ERR_NONFINITE (-3) /* the health check found a NaN/Inf or CFL > 1 */
+#define OCEAN_ERR_TIMEOUT (-4)   /* a bounded device wait gave up */
+#define OCEAN_ERR_OOM (-5)       /* device allocation failed or arena too small */
+#define OCEAN_ERR_STATE (-6)     /* call not valid in the handle's current state */
+
+#define OCEAN_FP64 0             /* every field and stencil in FP64 */
+#define OCEAN_MIXED 1            /* FP32 fields and stencils, FP64 free surface,
+                                    barotropic averages and conservation sums */
+
+#define OCEAN_CLOSURE_RI 0       /* Richardson-number closure */
+#define OCEAN_CLOSURE_LEARNED 1  /* column MLP, with the Ri closure as fallback */
+
+/* field ids for ocean_set_field / ocean_get_field */
+#define OCEAN_U 0
+#define OCEAN_V 1
+#define OCEAN_T 2
+#define OCEAN_S 3
+#define OCEAN_ETA 4        /* 2-D free-surface height, m */
+#define OCEAN_GU_PREV 5    /* tendencies of the last completed step (AB2 memory) */
+#define OCEAN_GV_PREV 6
+#define OCEAN_GT_PREV 7
+#define OCEAN_GS_PREV 8
+#define OCEAN_W 9          /* diagnostics of the last ocean_tendencies call (read only) */
+#define OCEAN_P 10
+#define OCEAN_KAPPA 11
+#define OCEAN_NU 12
+#define OCEAN_GU 13        /* tendencies G^n of the last ocean_tendencies call (read only) */
+#define OCEAN_GV 14
+#define OCEAN_GT 15
+#define OCEAN_GS 16
+#define OCEAN_HU 17        /* 2-D depth of the u- and v-columns (read only) */
+#define OCEAN_HV 18
+#define OCEAN_T_ANOM 19    /* the stored anomalies T - Tref(k), S - Sref(k): what a bitwise */
+#define OCEAN_S_ANOM 20    /* checkpoint saves (with the profiles of ocean_get_reference) */
+
+typedef struct ocean_s* ocean_t;
+
+/* Grid.  kind 0: Cartesian beta-plane, x0..x1 and y0..y1 in metres.  kind 1: latitude-
+ * longitude, x0..x1 longitude and y0..y1 latitude in degrees.  z_faces holds nz+1
+ * level faces, increasing from the sea floor (-H) to the surface (0); copied. */
+typedef struct {
+    int kind;
+    int nx, ny, nz;
+    int periodic_x, periodic_y;
+    double x0, x1, y0, y1;
+    const double* z_faces;
+} ocean_grid;
+
+/* Parameters.  taux/tauy: surface wind stress on u-/v-faces, [ny][nx], N/m^2; copied
+ * (NULL = no wind).  check_every: run the non-finite/CFL health check every that many
+ * steps inside ocean_step (0 = never). */
+typedef struct {
+    double dt;              /* baroclinic time step, s */
+    int n_substeps;         /* barotropic substeps N_s >= 1 */
+    double chi;             /* quasi-AB2 offset (0.1) */
+    double g, rho0;         /* gravity, reference density */
+    double alpha, beta_s;   /* linear EOS: b = g[alpha (T - T0) - beta_s (S - S0)] */
+    double T0, S0;
+    double f0, beta_plane;  /* Cartesian Coriolis f = f0 + beta (y - (y0+y1)/2) */
+    double omega, radius;   /* lat-lon: f = 2 omega sin(phi), planet radius */
+    double nu0, ri_a, nu_b, kappa_b, kappa_conv; /* Richardson-number closure */
+    double weno_eps;        /* WENO-Z epsilon */
+    int weno_linear;        /* 1: ideal (linear) weights, a test switch */
+    double min_depth;       /* columns shallower than this are land, m */
+    int precision;          /* OCEAN_FP64 or OCEAN_MIXED */
+    int closure;            /* OCEAN_CLOSURE_RI or OCEAN_CLOSURE_LEARNED */
+    int check_every;
+    const double* taux;
+    const double* tauy;
+} ocean_params;
+
+typedef struct {
+    long step;              /* completed steps */
+    double tracer_T;        /* sum T dV over wet cells (compensated FP64) */
+    double tracer_S;        /* sum S dV */
+    double volume_eta;      /* sum eta dA over wet columns */
+    double ke;              /* 1/2 sum u^2 dV_u + 1/2 sum v^2 dV_v */
+    double max_cfl;         /* max advective CFL number |u| dt/dx, |v| dt/dy, |w| dt/dz */
+    double wet_volume;      /* sum dV over wet cells */
+    int nonfinite;          /* 1 if any prognostic value is NaN/Inf */
+} ocean_diag;
+
+/* Device bytes ocean_create_in needs for this grid and these parameters. */
+int ocean_arena_bytes(const ocean_grid* grid, const ocean_params* params, size_t* bytes);
+
+/* Build a model: validates the grid, builds metrics and masks from depth ([ny][nx], m,
+ * >= 0; copied), allocates its device memory with cudaMalloc on the current device and
+ * creates its own stream.  State starts at rest: u = v = eta = 0, T = T0, S = S0. */
+int ocean_create(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                 ocean_t* out);
+
+/* As ocean_create, but inside caller-owned device memory d_arena (at least
+ * ocean_arena_bytes, 256-byte aligned) and on the caller's cudaStream_t `stream` (NULL =
+ * legacy default stream).  The caller keeps the memory alive until ocean_destroy. */
+int ocean_create_in(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                    void* d_arena, size_t arena_bytes, void* stream, ocean_t* out);
+
+void ocean_destroy(ocean_t h);
+const char* ocean_last_error(ocean_t h);
+
+/* Copy a host field in (count must equal the field's element count) or out.  Setting
+ * u or v leaves the AB2 memory alone; setting T or S also resets the horizontally
+ * uniform reference profiles the library subtracts before the pressure integral. */
+int ocean_set_field(ocean_t h, int field, const double* host, size_t count);
+int ocean_get_field(ocean_t h, int field, double* host, size_t count);
+
+/* The horizontally uniform reference profiles Tref[k], Sref[k] (nz values each, host).
+ * The library stores T and S as anomalies from them (in the mixed form this keeps the
+ * buoyancy resolution that drives the horizontal pressure gradient).  By default
+ * ocean_set_field(T or S) resets the profile to the mean of the given field over the wet
+ * cells of each level; after ocean_set_reference the profiles stay fixed, and the stored
+ * state is re-expressed so that T and S themselves do not change.  A checkpoint that
+ * saves the profiles and restores them before the fields resumes bit for bit. */
+int ocean_get_reference(ocean_t h, double* Tref, double* Sref);
+int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref);
+
+/* Replace the surface wind stress (host arrays [ny][nx], copied). */
+int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy);
+
+/* Advance n >= 0 steps and wait for them; runs the health check when check_every > 0. */
+int ocean_step(ocean_t h, int n);
+
+/* Enqueue n steps on the handle's stream and return without waiting. */
+int ocean_step_async(ocean_t h, int n);
+
+/* Wait for all work queued on the handle's stream. */
+int ocean_sync(ocean_t h);
+
+/* Compute the diagnostics (w, p, kappa, nu) and the tendencies G^n of the current
+ * state without stepping (fields OCEAN_W .. OCEAN_GS). */
+int ocean_tendencies(ocean_t h);
+
+/* Conservation and health diagnostics of the current state (synchronous). */
+int ocean_diagnostics(ocean_t h, ocean_diag* out);
+
+long ocean_get_step(ocean_t h);
+int ocean_set_step(ocean_t h, long step);
+
+/* The handle's stream (a cudaStream_t). */
+void* ocean_stream(ocean_t h);
+
+/* ---- component entry points (device pointers, caller-owned, on `stream`) ---- */
+
+/* Adaptive-order WENO-Z reconstruction on a periodic 1-D row (Sec. "New numerical
+ * methods", adaptive-order WENO): for each face f in [0, n) between cells f-1 and f,
+ * out[f] = reconstruction upwind by the sign of vel[f] (vel >= 0 takes cell f-1 as the
+ * upwind cell), using the fifth-order stencil when all five cells have inside[] != 0,
+ * else the third-order one, else the upwind value.  q, vel, out: n values of the given
+ * precision (double for OCEAN_FP64, float for OCEAN_MIXED); inside: n bytes (NULL =
+ * all inside). */
+int ocean_weno_faces(const void* d_q, const void* d_vel, const unsigned char* d_inside, int n,
+                     void* d_out, int precision, double eps, int linear, void* stream);
+
+/* Batched tridiagonal solve (Sec. "New numerical methods": backward Euler + tridiagonal
+ * solver): for each of nsys systems s, a[k] x[k-1] + b[k] x[k] + c[k] x[k+1] = d[k],
+ * k = 0..n-1 (a[0], c[n-1] ignored), by the Thomas algorithm without pivoting (the
+ * caller guarantees diagonal dominance).  Arrays are level-major: element (k, s) at
+ * k*nsys + s, of the given precision.  1 <= n <= 256. */
+int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, const void* d_d,
+                          void* d_x, int n, int nsys, int precision, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCEAN_H */

@@ -1,0 +1,834 @@
+// ocean_api.cu -- host side of libocean's C ABI: validation, metrics and masks, the
+// device arena, field transfer and the per-step launch sequence.  All arithmetic of the
+// step itself runs in the kernels of ocean_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ocean.h"
+#include "ocean_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr double kPi = 3.14159265358979323846;
+
+inline double deg2rad(double d) { return d * (kPi / 180.0); }
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct ocean_s {
+    // configuration
+    int kind = 0, nx = 0, ny = 0, nz = 0, px = 0, py = 0;
+    double x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    std::vector<double> zf, zc, dz;
+    ocean_params prm{};
+    int prec = OCEAN_FP64;
+    size_t esz = 8;
+    int pitch = 0;
+    long plane = 0, n2pad = 0;
+    // device memory
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device pointers (3-D fields of element size esz)
+    void *u[2] = {}, *v[2] = {}, *T[2] = {}, *S[2] = {};
+    void *Gu = nullptr, *Gv = nullptr, *GT = nullptr, *GS = nullptr;
+    void *w = nullptr, *p = nullptr, *kap = nullptr, *nu = nullptr;
+    // 2-D of element size esz
+    void *taux_s = nullptr, *tauy_s = nullptr, *Un = nullptr, *Vn = nullptr, *GU = nullptr,
+         *GV = nullptr, *Su = nullptr, *Sv = nullptr, *Ub = nullptr, *Vb = nullptr,
+         *dE = nullptr, *paccE = nullptr, *paccU = nullptr, *paccV = nullptr, *gxe = nullptr,
+         *gye = nullptr, *corrU = nullptr, *corrV = nullptr, *Hu = nullptr, *Hv = nullptr,
+         *rHu = nullptr, *rHv = nullptr;
+    double *eta = nullptr, *accE = nullptr, *accU = nullptr, *accV = nullptr;
+    short *kb = nullptr, *kbu = nullptr, *kbv = nullptr, *kbz = nullptr, *kbzin = nullptr;
+    void* rowm = nullptr;   // 7 row arrays of (ny + 2H) elements
+    void* levm = nullptr;   // 8 level arrays of nz elements
+    double *drow = nullptr, *dlev = nullptr;
+    double *diag_part = nullptr, *diag_out = nullptr;
+    // host-side copies
+    std::vector<short> h_kb, h_kbu, h_kbv;
+    std::vector<double> h_rows[8];   // dxc rdxc dxv rAc rAz fu fv Ac
+    std::vector<double> Tref, Sref, h_Hu, h_Hv;
+    bool ref_locked = false;   // reference profiles fixed by ocean_set_reference
+    double dy = 0;
+    int cur = 0;
+    long nstep = 0;
+    bool tend_valid = false;
+    std::string err;
+};
+
+namespace {
+
+int fail(ocean_t h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    g_last_error = buf;
+    return code;
+}
+
+#define OC_CUDA(h, call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, OCEAN_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int validate(const ocean_grid* g, const ocean_params* p) {
+    if (!g || !p) return fail(nullptr, OCEAN_ERR_ARG, "null grid or params");
+    if (g->kind != 0 && g->kind != 1) return fail(nullptr, OCEAN_ERR_ARG, "grid kind must be 0 or 1");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+        return fail(nullptr, OCEAN_ERR_ARG, "grid sizes must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz);
+    if (g->nz > OC_NZMAX) return fail(nullptr, OCEAN_ERR_ARG, "nz = %d exceeds the maximum %d", g->nz, OC_NZMAX);
+    if ((long)g->nx * g->ny > (1L << 30)) return fail(nullptr, OCEAN_ERR_ARG, "too many columns");
+    if (g->periodic_x && g->nx < OC_H) return fail(nullptr, OCEAN_ERR_ARG, "periodic x needs nx >= %d", OC_H);
+    if (g->periodic_y && g->ny < OC_H) return fail(nullptr, OCEAN_ERR_ARG, "periodic y needs ny >= %d", OC_H);
+    if (g->periodic_y && g->kind == 1) return fail(nullptr, OCEAN_ERR_ARG, "lat-lon grids cannot be periodic in y");
+    if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return fail(nullptr, OCEAN_ERR_ARG, "empty domain extent");
+    if (g->kind == 1 && (g->y0 <= -90.0 || g->y1 >= 90.0))
+        return fail(nullptr, OCEAN_ERR_ARG, "latitudes must lie strictly inside (-90, 90)");
+    if (!g->z_faces) return fail(nullptr, OCEAN_ERR_ARG, "null z_faces");
+    for (int k = 0; k < g->nz; ++k)
+        if (!(g->z_faces[k + 1] > g->z_faces[k]))
+            return fail(nullptr, OCEAN_ERR_ARG, "z_faces must increase from the bottom to the top");
+    if (!(p->dt > 0)) return fail(nullptr, OCEAN_ERR_ARG, "dt must be > 0");
+    if (p->n_substeps < 1) return fail(nullptr, OCEAN_ERR_ARG, "n_substeps must be >= 1");
+    if (p->precision != OCEAN_FP64 && p->precision != OCEAN_MIXED)
+        return fail(nullptr, OCEAN_ERR_ARG, "precision must be OCEAN_FP64 or OCEAN_MIXED");
+    if (p->closure != OCEAN_CLOSURE_RI && p->closure != OCEAN_CLOSURE_LEARNED)
+        return fail(nullptr, OCEAN_ERR_ARG, "unknown closure");
+    if (p->check_every < 0) return fail(nullptr, OCEAN_ERR_ARG, "check_every must be >= 0");
+    return OCEAN_OK;
+}
+
+void configure(ocean_t m, const ocean_grid* g, const ocean_params* p) {
+    m->kind = g->kind; m->nx = g->nx; m->ny = g->ny; m->nz = g->nz;
+    m->px = g->periodic_x ? 1 : 0; m->py = g->periodic_y ? 1 : 0;
+    m->x0 = g->x0; m->x1 = g->x1; m->y0 = g->y0; m->y1 = g->y1;
+    m->zf.assign(g->z_faces, g->z_faces + g->nz + 1);
+    m->zc.resize(g->nz); m->dz.resize(g->nz);
+    for (int k = 0; k < g->nz; ++k) {
+        m->zc[k] = 0.5 * (m->zf[k] + m->zf[k + 1]);
+        m->dz[k] = m->zf[k + 1] - m->zf[k];
+    }
+    m->prm = *p;
+    m->prm.taux = nullptr;
+    m->prm.tauy = nullptr;
+    m->prec = p->precision;
+    m->esz = p->precision == OCEAN_FP64 ? sizeof(double) : sizeof(float);
+    int w = g->nx + 2 * OC_H;
+    m->pitch = (w + 31) & ~31;
+    m->n2pad = (long)m->pitch * (g->ny + 2 * OC_H);
+    m->plane = m->n2pad;
+    m->Tref.assign(g->nz, p->T0);
+    m->Sref.assign(g->nz, p->S0);
+}
+
+// lays out (base == nullptr: sizes) every device array; returns the total bytes
+size_t layout(ocean_t m, char* base) {
+    Carver c{base};
+    const size_t n3 = (size_t)m->plane * m->nz, n2 = (size_t)m->n2pad, e = m->esz;
+    auto f3 = [&]() { return (void*)c.take<char>(n3 * e); };
+    auto f2 = [&]() { return (void*)c.take<char>(n2 * e); };
+    for (int b = 0; b < 2; ++b) { m->u[b] = f3(); m->v[b] = f3(); m->T[b] = f3(); m->S[b] = f3(); }
+    m->Gu = f3(); m->Gv = f3(); m->GT = f3(); m->GS = f3();
+    m->w = f3(); m->p = f3(); m->kap = f3(); m->nu = f3();
+    void** two[] = {&m->taux_s, &m->tauy_s, &m->Un, &m->Vn, &m->GU, &m->GV, &m->Su, &m->Sv,
+                    &m->Ub, &m->Vb, &m->dE, &m->paccE, &m->paccU, &m->paccV, &m->gxe, &m->gye,
+                    &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv};
+    for (void** q : two) *q = f2();
+    m->eta = c.take<double>(n2); m->accE = c.take<double>(n2);
+    m->accU = c.take<double>(n2); m->accV = c.take<double>(n2);
+    m->kb = c.take<short>(n2); m->kbu = c.take<short>(n2); m->kbv = c.take<short>(n2);
+    m->kbz = c.take<short>(n2); m->kbzin = c.take<short>(n2);
+    const size_t nr = (size_t)m->ny + 2 * OC_H;
+    m->rowm = c.take<char>(7 * nr * e);
+    m->levm = c.take<char>(8 * (size_t)m->nz * e);
+    m->drow = c.take<double>(3 * nr);
+    m->dlev = c.take<double>(3 * (size_t)m->nz);
+    m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes()));
+    m->diag_out = c.take<double>(8);
+    return c.off + 256;
+}
+
+inline long hix2(const ocean_t m, int i, int j) {
+    return (long)(j + OC_H) * m->pitch + (i + OC_H);
+}
+
+// wrap a padded column index onto the interior; false when it lies beyond a wall
+inline bool wrap(const ocean_t m, int& i, int& j) {
+    if (m->px) { i %= m->nx; if (i < 0) i += m->nx; }
+    else if (i < 0 || i >= m->nx) return false;
+    if (m->py) { j %= m->ny; if (j < 0) j += m->ny; }
+    else if (j < 0 || j >= m->ny) return false;
+    return true;
+}
+
+// host -> device copy on the handle's stream, complete on return
+void upload_bytes(ocean_t m, void* dst, const void* src, size_t bytes) {
+    cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->stream);
+    cudaStreamSynchronize(m->stream);
+}
+
+template <typename R>
+void upload_conv(ocean_t m, const std::vector<double>& src, void* dst) {
+    std::vector<R> t(src.size());
+    for (size_t q = 0; q < src.size(); ++q) t[q] = (R)src[q];
+    upload_bytes(m, dst, t.data(), t.size() * sizeof(R));
+}
+
+void upload_real(ocean_t m, const std::vector<double>& src, void* dst) {
+    if (m->prec == OCEAN_FP64) upload_conv<double>(m, src, dst);
+    else upload_conv<float>(m, src, dst);
+}
+
+void upload_levels(ocean_t m) {
+    const int nz = m->nz;
+    std::vector<double> lv(8 * (size_t)nz, 0.0), dl(3 * (size_t)nz);
+    for (int k = 0; k < nz; ++k) {
+        lv[k] = m->dz[k];
+        lv[nz + k] = 1.0 / m->dz[k];
+        lv[2 * nz + k] = k > 0 ? m->zc[k] - m->zc[k - 1] : 0.0;
+        lv[3 * nz + k] = k > 0 ? 1.0 / (m->zc[k] - m->zc[k - 1]) : 0.0;
+        lv[4 * nz + k] = m->Tref[k];
+        lv[5 * nz + k] = m->Sref[k];
+        lv[6 * nz + k] = k > 0 ? m->Tref[k] - m->Tref[k - 1] : 0.0;
+        lv[7 * nz + k] = k > 0 ? m->Sref[k] - m->Sref[k - 1] : 0.0;
+        dl[k] = m->dz[k];
+        dl[nz + k] = m->Tref[k];
+        dl[2 * nz + k] = m->Sref[k];
+    }
+    upload_real(m, lv, m->levm);
+    upload_bytes(m, m->dlev, dl.data(), dl.size() * sizeof(double));
+}
+
+// metrics, masks, column depths; host FP64, uploaded once
+int build_geometry(ocean_t m, const double* depth) {
+    const int nx = m->nx, ny = m->ny, nz = m->nz, H = OC_H;
+    const int nr = ny + 2 * H;
+    const ocean_params& p = m->prm;
+    // ---- rows
+    for (auto& r : m->h_rows) r.assign(nr, 0.0);
+    double dy;
+    if (m->kind == 0) {
+        const double dx = (m->x1 - m->x0) / nx;
+        dy = (m->y1 - m->y0) / ny;
+        const double ymid = 0.5 * (m->y0 + m->y1);
+        for (int jj = 0; jj < nr; ++jj) {
+            const int j = jj - H;
+            m->h_rows[0][jj] = dx;
+            m->h_rows[2][jj] = dx;
+            m->h_rows[5][jj] = p.f0 + p.beta_plane * (m->y0 + (j + 0.5) * dy - ymid);
+            m->h_rows[6][jj] = p.f0 + p.beta_plane * (m->y0 + j * dy - ymid);
+        }
+    } else {
+        const double dlam = deg2rad((m->x1 - m->x0) / nx), dphi = (m->y1 - m->y0) / ny;
+        dy = p.radius * deg2rad(dphi);
+        for (int jj = 0; jj < nr; ++jj) {
+            const int j = jj - H;
+            const double pc = deg2rad(m->y0 + (j + 0.5) * dphi), pf = deg2rad(m->y0 + j * dphi);
+            m->h_rows[0][jj] = p.radius * std::fmax(std::cos(pc), 1e-12) * dlam;
+            m->h_rows[2][jj] = p.radius * std::fmax(std::cos(pf), 1e-12) * dlam;
+            m->h_rows[5][jj] = 2.0 * p.omega * std::sin(pc);
+            m->h_rows[6][jj] = 2.0 * p.omega * std::sin(pf);
+        }
+    }
+    m->dy = dy;
+    for (int jj = 0; jj < nr; ++jj) {
+        m->h_rows[1][jj] = 1.0 / m->h_rows[0][jj];
+        m->h_rows[7][jj] = m->h_rows[0][jj] * dy;
+        m->h_rows[3][jj] = 1.0 / m->h_rows[7][jj];
+        m->h_rows[4][jj] = 1.0 / (m->h_rows[2][jj] * dy);
+    }
+    std::vector<double> rows(7 * (size_t)nr);
+    for (int a = 0; a < 7; ++a)
+        for (int jj = 0; jj < nr; ++jj) rows[(size_t)a * nr + jj] = m->h_rows[a][jj];
+    upload_real(m, rows, m->rowm);
+    std::vector<double> drow(3 * (size_t)nr);
+    for (int jj = 0; jj < nr; ++jj) {
+        drow[jj] = m->h_rows[7][jj];
+        drow[nr + jj] = m->h_rows[2][jj];
+        drow[2 * nr + jj] = m->h_rows[1][jj];
+    }
+    upload_bytes(m, m->drow, drow.data(), drow.size() * sizeof(double));
+    upload_levels(m);
+    // ---- masks
+    const long n2 = m->n2pad;
+    std::vector<short> kbi((size_t)nx * ny);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const double d = depth[(size_t)j * nx + i];
+            if (!(d >= 0.0) || !std::isfinite(d))
+                return fail(nullptr, OCEAN_ERR_ARG, "depth must be finite and >= 0 (column %d,%d)", i, j);
+            int kb = nz;
+            if (d >= p.min_depth)
+                for (int k = nz - 1; k >= 0 && m->zc[k] > -d; --k) kb = k;
+            kbi[(size_t)j * nx + i] = (short)kb;
+        }
+    auto KB = [&](int i, int j) -> int {
+        if (!wrap(m, i, j)) return nz;
+        return kbi[(size_t)j * nx + i];
+    };
+    m->h_kb.assign(n2, (short)nz);
+    m->h_kbu.assign(n2, (short)nz);
+    m->h_kbv.assign(n2, (short)nz);
+    std::vector<short> kbz(n2, (short)nz), kbzin(n2, (short)nz);
+    for (int j = -H; j < ny + H; ++j)
+        for (int i = -H; i < nx + H; ++i) {
+            const long c = hix2(m, i, j);
+            const int a = KB(i, j), b = KB(i - 1, j), cc = KB(i, j - 1), d = KB(i - 1, j - 1);
+            m->h_kb[c] = (short)a;
+            m->h_kbu[c] = (short)std::max(a, b);
+            m->h_kbv[c] = (short)std::max(a, cc);
+            kbz[c] = (short)std::max(std::max(a, b), std::max(cc, d));
+            kbzin[c] = (short)std::min(std::min(a, b), std::min(cc, d));
+        }
+    upload_bytes(m, m->kb, m->h_kb.data(), n2 * sizeof(short));
+    upload_bytes(m, m->kbu, m->h_kbu.data(), n2 * sizeof(short));
+    upload_bytes(m, m->kbv, m->h_kbv.data(), n2 * sizeof(short));
+    upload_bytes(m, m->kbz, kbz.data(), n2 * sizeof(short));
+    upload_bytes(m, m->kbzin, kbzin.data(), n2 * sizeof(short));
+    // ---- column depths
+    m->h_Hu.assign(n2, 0.0);
+    m->h_Hv.assign(n2, 0.0);
+    std::vector<double> rHu(n2, 0.0), rHv(n2, 0.0);
+    for (long c = 0; c < n2; ++c) {
+        double hu = 0, hv = 0;
+        for (int k = m->h_kbu[c]; k < nz; ++k) hu += m->dz[k];
+        for (int k = m->h_kbv[c]; k < nz; ++k) hv += m->dz[k];
+        m->h_Hu[c] = hu; m->h_Hv[c] = hv;
+        rHu[c] = hu > 0 ? 1.0 / hu : 0.0;
+        rHv[c] = hv > 0 ? 1.0 / hv : 0.0;
+    }
+    upload_real(m, m->h_Hu, m->Hu);
+    upload_real(m, m->h_Hv, m->Hv);
+    upload_real(m, rHu, m->rHu);
+    upload_real(m, rHv, m->rHv);
+    return OCEAN_OK;
+}
+
+int set_wind(ocean_t m, const double* taux, const double* tauy) {
+    const long n2 = m->n2pad;
+    std::vector<double> tx(n2, 0.0), ty(n2, 0.0);
+    const double s = 1.0 / (m->prm.rho0 * m->dz[m->nz - 1]);
+    for (int j = 0; j < m->ny; ++j)
+        for (int i = 0; i < m->nx; ++i) {
+            const long c = hix2(m, i, j);
+            if (taux) tx[c] = taux[(size_t)j * m->nx + i] * s;
+            if (tauy) ty[c] = tauy[(size_t)j * m->nx + i] * s;
+        }
+    upload_real(m, tx, m->taux_s);
+    upload_real(m, ty, m->tauy_s);
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK
+                                             : fail(m, OCEAN_ERR_CUDA, "wind stress upload failed");
+}
+
+// field location and mask: which lowest-wet-level array applies (0 cell, 1 u, 2 v)
+struct FieldRef {
+    void* ptr = nullptr;
+    bool is2d = false, is_double = false, readonly = false;
+    int mask = 0;
+};
+
+FieldRef field_ref(ocean_t m, int id) {
+    FieldRef r;
+    const int c = m->cur, n = 1 - m->cur;
+    switch (id) {
+        case OCEAN_U: r.ptr = m->u[c]; r.mask = 1; break;
+        case OCEAN_V: r.ptr = m->v[c]; r.mask = 2; break;
+        case OCEAN_T: r.ptr = m->T[c]; break;
+        case OCEAN_S: r.ptr = m->S[c]; break;
+        case OCEAN_ETA: r.ptr = m->eta; r.is2d = true; r.is_double = true; break;
+        case OCEAN_GU_PREV: r.ptr = m->Gu; r.mask = 1; break;
+        case OCEAN_GV_PREV: r.ptr = m->Gv; r.mask = 2; break;
+        case OCEAN_GT_PREV: r.ptr = m->GT; break;
+        case OCEAN_GS_PREV: r.ptr = m->GS; break;
+        case OCEAN_W: r.ptr = m->w; r.readonly = true; break;
+        case OCEAN_P: r.ptr = m->p; r.readonly = true; break;
+        case OCEAN_KAPPA: r.ptr = m->kap; r.readonly = true; break;
+        case OCEAN_NU: r.ptr = m->nu; r.readonly = true; break;
+        case OCEAN_GU: r.ptr = m->u[n]; r.mask = 1; r.readonly = true; break;
+        case OCEAN_GV: r.ptr = m->v[n]; r.mask = 2; r.readonly = true; break;
+        case OCEAN_GT: r.ptr = m->T[n]; r.readonly = true; break;
+        case OCEAN_GS: r.ptr = m->S[n]; r.readonly = true; break;
+        case OCEAN_HU: r.ptr = m->Hu; r.is2d = true; r.readonly = true; break;
+        case OCEAN_HV: r.ptr = m->Hv; r.is2d = true; r.readonly = true; break;
+        case OCEAN_T_ANOM: r.ptr = m->T[c]; break;
+        case OCEAN_S_ANOM: r.ptr = m->S[c]; break;
+        default: break;
+    }
+    return r;
+}
+
+// kinematic pressure of the reference profiles, added back on output
+std::vector<double> reference_pressure(const ocean_t m) {
+    const int nz = m->nz;
+    const ocean_params& p = m->prm;
+    std::vector<double> P(nz), b(nz);
+    for (int k = 0; k < nz; ++k)
+        b[k] = p.g * (p.alpha * (m->Tref[k] - p.T0) - p.beta_s * (m->Sref[k] - p.S0));
+    P[nz - 1] = -b[nz - 1] * (m->zf[nz] - m->zc[nz - 1]);
+    for (int k = nz - 2; k >= 0; --k) P[k] = P[k + 1] - 0.5 * (b[k] + b[k + 1]) * (m->zc[k + 1] - m->zc[k]);
+    return P;
+}
+
+template <typename R>
+KP<R> make_kp(const ocean_t m, bool first) {
+    KP<R> k{};
+    GeoD& g = k.g;
+    g.nx = m->nx; g.ny = m->ny; g.nz = m->nz; g.px = m->px; g.py = m->py; g.pitch = m->pitch;
+    g.plane = m->plane;
+    g.kb = m->kb; g.kbu = m->kbu; g.kbv = m->kbv; g.kbz = m->kbz; g.kbzin = m->kbzin;
+    const size_t nr = (size_t)m->ny + 2 * OC_H;
+    const R* rows = reinterpret_cast<const R*>(m->rowm);
+    k.dxc = rows; k.rdxc = rows + nr; k.dxv = rows + 2 * nr; k.rAc = rows + 3 * nr;
+    k.rAz = rows + 4 * nr; k.fu = rows + 5 * nr; k.fv = rows + 6 * nr;
+    const R* lv = reinterpret_cast<const R*>(m->levm);
+    const int nz = m->nz;
+    k.dz = lv; k.rdz = lv + nz; k.dzf = lv + 2 * nz; k.rdzf = lv + 3 * nz;
+    k.Tref = lv + 4 * nz; k.Sref = lv + 5 * nz; k.dTref = lv + 6 * nz; k.dSref = lv + 7 * nz;
+    const ocean_params& p = m->prm;
+    k.dy = (R)m->dy; k.rdy = (R)(1.0 / m->dy); k.dt = (R)p.dt;
+    k.ca = first ? R(1) : (R)(1.5 + p.chi);
+    k.cb = first ? R(0) : (R)(0.5 + p.chi);
+    k.grav = (R)p.g; k.alpha = (R)p.alpha; k.beta_s = (R)p.beta_s;
+    k.nu0 = (R)p.nu0; k.ri_a = (R)p.ri_a; k.nu_b = (R)p.nu_b; k.kappa_b = (R)p.kappa_b;
+    k.kappa_conv = (R)p.kappa_conv; k.eps = (R)p.weno_eps;
+    k.ptop = (R)(m->zf[nz] - m->zc[nz - 1]);
+    k.linear = p.weno_linear;
+    return k;
+}
+
+template <typename R>
+StepBuffers<R> make_bufs(const ocean_t m) {
+    StepBuffers<R> b{};
+    const int c = m->cur, n = 1 - m->cur;
+    auto P = [](void* q) { return reinterpret_cast<R*>(q); };
+    b.u = P(m->u[c]); b.v = P(m->v[c]); b.T = P(m->T[c]); b.S = P(m->S[c]);
+    b.un = P(m->u[n]); b.vn = P(m->v[n]); b.Tn = P(m->T[n]); b.Sn = P(m->S[n]);
+    b.Gu = P(m->Gu); b.Gv = P(m->Gv); b.GT = P(m->GT); b.GS = P(m->GS);
+    b.w = P(m->w); b.p = P(m->p); b.kap = P(m->kap); b.nu = P(m->nu);
+    b.taux_s = P(m->taux_s); b.tauy_s = P(m->tauy_s);
+    b.Un = P(m->Un); b.Vn = P(m->Vn); b.GU = P(m->GU); b.GV = P(m->GV); b.Su = P(m->Su); b.Sv = P(m->Sv);
+    b.Ub = P(m->Ub); b.Vb = P(m->Vb); b.dE = P(m->dE); b.paccE = P(m->paccE);
+    b.paccU = P(m->paccU); b.paccV = P(m->paccV); b.gxe = P(m->gxe); b.gye = P(m->gye);
+    b.corrU = P(m->corrU); b.corrV = P(m->corrV);
+    b.Hu = P(m->Hu); b.Hv = P(m->Hv); b.rHu = P(m->rHu); b.rHv = P(m->rHv);
+    b.eta = m->eta; b.accE = m->accE; b.accU = m->accU; b.accV = m->accV;
+    return b;
+}
+
+template <typename R>
+void enqueue_step(ocean_t m) {
+    const bool first = m->nstep == 0;
+    const KP<R> k = make_kp<R>(m, first);
+    const StepBuffers<R> b = make_bufs<R>(m);
+    cudaStream_t s = m->stream;
+    launch_diag<R>(k, b, s);
+    launch_tracer<R>(k, b, true, s);
+    launch_momentum<R>(k, b, true, s);
+    launch_barotropic<R>(k, b, m->prm.n_substeps, m->prm.dt, (R)m->prm.g, s);
+    launch_correct<R>(k, b, s);
+    if (m->px || m->py) {
+        R* f[4] = {b.un, b.vn, b.Tn, b.Sn};
+        launch_halo3<R>(k.g, f, 4, s);
+    }
+    m->cur = 1 - m->cur;
+    m->nstep += 1;
+    m->tend_valid = false;
+}
+
+template <typename R>
+void enqueue_tendencies(ocean_t m) {
+    const KP<R> k = make_kp<R>(m, m->nstep == 0);
+    const StepBuffers<R> b = make_bufs<R>(m);
+    launch_diag<R>(k, b, m->stream);
+    launch_tracer<R>(k, b, false, m->stream);
+    launch_momentum<R>(k, b, false, m->stream);
+    m->tend_valid = true;
+}
+
+template <typename R>
+void enqueue_diagnostics(ocean_t m) {
+    const KP<R> k = make_kp<R>(m, m->nstep == 0);
+    const StepBuffers<R> b = make_bufs<R>(m);
+    launch_diag<R>(k, b, m->stream);   // w of the current state for the CFL number
+    const size_t nr = (size_t)m->ny + 2 * OC_H;
+    DiagMetrics dm{m->drow, m->drow + nr, m->drow + 2 * nr, m->dlev, m->dlev + m->nz,
+                   m->dlev + 2 * m->nz, m->dy, 1.0 / m->dy, m->prm.dt};
+    launch_diagnostics<R>(k.g, dm, b.u, b.v, b.T, b.S, b.w, m->eta, m->diag_part, m->diag_out,
+                          m->stream);
+}
+
+int run_diagnostics(ocean_t m, double out[8]) {
+    if (m->prec == OCEAN_FP64) enqueue_diagnostics<double>(m);
+    else enqueue_diagnostics<float>(m);
+    OC_CUDA(m, cudaGetLastError());
+    OC_CUDA(m, cudaMemcpyAsync(out, m->diag_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    OC_CUDA(m, cudaStreamSynchronize(m->stream));
+    return OCEAN_OK;
+}
+
+int create_common(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                  void* d_arena, size_t arena_bytes, void* stream, bool own, ocean_t* out) {
+    if (!out) return fail(nullptr, OCEAN_ERR_ARG, "null output handle");
+    *out = nullptr;
+    int rc = validate(grid, params);
+    if (rc) return rc;
+    if (!depth) return fail(nullptr, OCEAN_ERR_ARG, "null depth");
+    ocean_t m = new ocean_s();
+    configure(m, grid, params);
+    const size_t need = layout(m, nullptr);
+    if (own) {
+        cudaError_t e = cudaMalloc(&d_arena, need);
+        if (e != cudaSuccess) {
+            delete m;
+            return fail(nullptr, OCEAN_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", need, cudaGetErrorString(e));
+        }
+        arena_bytes = need;
+        m->own_arena = true;
+        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaFree(d_arena);
+            delete m;
+            return fail(nullptr, OCEAN_ERR_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+        }
+        m->own_stream = true;
+    } else {
+        if (!d_arena) { delete m; return fail(nullptr, OCEAN_ERR_ARG, "null arena"); }
+        if (((uintptr_t)d_arena & 255) != 0) { delete m; return fail(nullptr, OCEAN_ERR_ARG, "arena must be 256-byte aligned"); }
+        if (arena_bytes < need) {
+            delete m;
+            return fail(nullptr, OCEAN_ERR_OOM, "arena of %zu bytes is smaller than the %zu needed", arena_bytes, need);
+        }
+        m->stream = (cudaStream_t)stream;
+    }
+    m->arena = (char*)d_arena;
+    m->arena_bytes = arena_bytes;
+    layout(m, m->arena);
+    cudaError_t e = cudaMemsetAsync(m->arena, 0, need - 256, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        int r = fail(nullptr, OCEAN_ERR_CUDA, "arena clear failed: %s", cudaGetErrorString(e));
+        ocean_destroy(m);
+        return r;
+    }
+    int se = m->prec == OCEAN_FP64 ? setup_kernel_attributes<double>(m->nz)
+                                   : setup_kernel_attributes<float>(m->nz);
+    if (se != 0) {
+        int r = fail(nullptr, OCEAN_ERR_CUDA, "kernel attribute setup failed: %s", cudaGetErrorString((cudaError_t)se));
+        ocean_destroy(m);
+        return r;
+    }
+    rc = build_geometry(m, depth);
+    if (rc == OCEAN_OK) rc = set_wind(m, params->taux, params->tauy);
+    if (rc != OCEAN_OK) {
+        ocean_destroy(m);
+        return rc;
+    }
+    // state at rest with T = T0, S = S0 on wet cells
+    std::vector<double> t((size_t)m->nx * m->ny * m->nz, params->T0);
+    rc = ocean_set_field(m, OCEAN_T, t.data(), t.size());
+    if (rc == OCEAN_OK) {
+        std::fill(t.begin(), t.end(), params->S0);
+        rc = ocean_set_field(m, OCEAN_S, t.data(), t.size());
+    }
+    if (rc == OCEAN_OK) {
+        cudaError_t e2 = cudaDeviceSynchronize();
+        if (e2 != cudaSuccess) rc = fail(m, OCEAN_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
+    }
+    if (rc != OCEAN_OK) {
+        ocean_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return OCEAN_OK;
+}
+
+// reference profile stored-value offset of a field (T and S are kept as anomalies)
+const std::vector<double>* field_reference(const ocean_t m, int id) {
+    if (id == OCEAN_T) return &m->Tref;
+    if (id == OCEAN_S) return &m->Sref;
+    return nullptr;
+}
+
+template <typename R>
+void scatter_field(const ocean_t m, const double* src, std::vector<R>& dst, bool is2d, int mask,
+                   int id) {
+    const std::vector<double>* ref = field_reference(m, id);
+    const int nx = m->nx, ny = m->ny, nzl = is2d ? 1 : m->nz;
+    dst.assign((size_t)(is2d ? m->n2pad : m->plane * m->nz), R(0));
+    const std::vector<short>& kbm = mask == 1 ? m->h_kbu : mask == 2 ? m->h_kbv : m->h_kb;
+    for (int k = 0; k < nzl; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long c = hix2(m, i, j);
+                const bool wet = is2d ? m->h_kb[c] < m->nz : k >= kbm[c];
+                const double off = ref ? (*ref)[k] : 0.0;
+                dst[(size_t)k * (is2d ? 0 : m->plane) + c] =
+                    wet ? (R)(src[((size_t)k * ny + j) * nx + i] - off) : R(0);
+            }
+}
+
+template <typename R>
+int set_field_t(ocean_t m, const FieldRef& r, int id, const double* host) {
+    std::vector<R> buf;
+    scatter_field<R>(m, host, buf, r.is2d, r.mask, id);
+    OC_CUDA(m, cudaMemcpyAsync(r.ptr, buf.data(), buf.size() * sizeof(R), cudaMemcpyHostToDevice, m->stream));
+    OC_CUDA(m, cudaStreamSynchronize(m->stream));
+    return OCEAN_OK;
+}
+
+template <typename R>
+int get_field_t(ocean_t m, const FieldRef& r, int id, double* host) {
+    const size_t n = (size_t)(r.is2d ? m->n2pad : m->plane * m->nz);
+    std::vector<R> buf(n);
+    OC_CUDA(m, cudaMemcpyAsync(buf.data(), r.ptr, n * sizeof(R), cudaMemcpyDeviceToHost, m->stream));
+    OC_CUDA(m, cudaStreamSynchronize(m->stream));
+    const int nx = m->nx, ny = m->ny, nzl = r.is2d ? 1 : m->nz;
+    std::vector<double> pref;
+    if (id == OCEAN_P) pref = reference_pressure(m);
+    if (id == OCEAN_T) pref = m->Tref;
+    if (id == OCEAN_S) pref = m->Sref;
+    const bool addref = id == OCEAN_P || id == OCEAN_T || id == OCEAN_S;
+    for (int k = 0; k < nzl; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const long c = hix2(m, i, j);
+                double val = (double)buf[(size_t)k * (r.is2d ? 0 : m->plane) + c];
+                if (addref && k >= m->h_kb[c]) val += pref[k];
+                host[((size_t)k * ny + j) * nx + i] = val;
+            }
+    return OCEAN_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+
+extern "C" {
+
+int ocean_arena_bytes(const ocean_grid* grid, const ocean_params* params, size_t* bytes) {
+    if (!bytes) return fail(nullptr, OCEAN_ERR_ARG, "null bytes");
+    int rc = validate(grid, params);
+    if (rc) return rc;
+    ocean_s tmp;
+    configure(&tmp, grid, params);
+    *bytes = layout(&tmp, nullptr);
+    return OCEAN_OK;
+}
+
+int ocean_create(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                 ocean_t* out) {
+    return create_common(grid, depth, params, nullptr, 0, nullptr, true, out);
+}
+
+int ocean_create_in(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                    void* d_arena, size_t arena_bytes, void* stream, ocean_t* out) {
+    return create_common(grid, depth, params, d_arena, arena_bytes, stream, false, out);
+}
+
+void ocean_destroy(ocean_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->own_arena && h->arena) cudaFree(h->arena);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char* ocean_last_error(ocean_t h) {
+    return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+int ocean_set_field(ocean_t h, int field, const double* host, size_t count) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!host) return fail(h, OCEAN_ERR_ARG, "null host buffer");
+    FieldRef r = field_ref(h, field);
+    if (!r.ptr) return fail(h, OCEAN_ERR_ARG, "unknown field id %d", field);
+    if (r.readonly) return fail(h, OCEAN_ERR_ARG, "field %d is read-only", field);
+    const size_t need = (size_t)h->nx * h->ny * (r.is2d ? 1 : h->nz);
+    if (count != need) return fail(h, OCEAN_ERR_ARG, "field %d needs %zu values, got %zu", field, need, count);
+    for (size_t q = 0; q < count; ++q)
+        if (!std::isfinite(host[q])) return fail(h, OCEAN_ERR_ARG, "non-finite input value at %zu", q);
+    if ((field == OCEAN_T || field == OCEAN_S) && !h->ref_locked) {
+        // horizontally uniform reference profile: mean over the wet cells of each level
+        std::vector<double>& ref = field == OCEAN_T ? h->Tref : h->Sref;
+        const double dflt = field == OCEAN_T ? h->prm.T0 : h->prm.S0;
+        for (int k = 0; k < h->nz; ++k) {
+            double s = 0;
+            long n = 0;
+            for (int j = 0; j < h->ny; ++j)
+                for (int i = 0; i < h->nx; ++i)
+                    if (k >= h->h_kb[hix2(h, i, j)]) { s += host[((size_t)k * h->ny + j) * h->nx + i]; ++n; }
+            ref[k] = n ? s / n : dflt;
+        }
+        upload_levels(h);
+    }
+    int rc;
+    if (r.is_double) rc = set_field_t<double>(h, r, field, host);
+    else if (h->prec == OCEAN_FP64) rc = set_field_t<double>(h, r, field, host);
+    else rc = set_field_t<float>(h, r, field, host);
+    if (rc) return rc;
+    if ((h->px || h->py) && !r.is2d) {
+        if (h->prec == OCEAN_FP64) {
+            KP<double> k = make_kp<double>(h, true);
+            double* f[1] = {reinterpret_cast<double*>(r.ptr)};
+            launch_halo3<double>(k.g, f, 1, h->stream);
+        } else {
+            KP<float> k = make_kp<float>(h, true);
+            float* f[1] = {reinterpret_cast<float*>(r.ptr)};
+            launch_halo3<float>(k.g, f, 1, h->stream);
+        }
+        OC_CUDA(h, cudaGetLastError());
+        OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    h->tend_valid = false;
+    return OCEAN_OK;
+}
+
+int ocean_get_field(ocean_t h, int field, double* host, size_t count) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!host) return fail(h, OCEAN_ERR_ARG, "null host buffer");
+    FieldRef r = field_ref(h, field);
+    if (!r.ptr) return fail(h, OCEAN_ERR_ARG, "unknown field id %d", field);
+    const size_t need = (size_t)h->nx * h->ny * (r.is2d ? 1 : h->nz);
+    if (count != need) return fail(h, OCEAN_ERR_ARG, "field %d needs %zu values, got %zu", field, need, count);
+    if (field >= OCEAN_GU && field <= OCEAN_GS && !h->tend_valid)
+        return fail(h, OCEAN_ERR_STATE, "tendencies are not available: call ocean_tendencies first");
+    if (r.is_double) return get_field_t<double>(h, r, field, host);
+    if (h->prec == OCEAN_FP64) return get_field_t<double>(h, r, field, host);
+    return get_field_t<float>(h, r, field, host);
+}
+
+int ocean_get_reference(ocean_t h, double* Tref, double* Sref) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!Tref || !Sref) return fail(h, OCEAN_ERR_ARG, "null output");
+    std::copy(h->Tref.begin(), h->Tref.end(), Tref);
+    std::copy(h->Sref.begin(), h->Sref.end(), Sref);
+    return OCEAN_OK;
+}
+
+int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!Tref || !Sref) return fail(h, OCEAN_ERR_ARG, "null profile");
+    for (int k = 0; k < h->nz; ++k)
+        if (!std::isfinite(Tref[k]) || !std::isfinite(Sref[k]))
+            return fail(h, OCEAN_ERR_ARG, "non-finite reference value at level %d", k);
+    // re-express the stored anomalies against the new profiles
+    const size_t n = (size_t)h->nx * h->ny * h->nz;
+    std::vector<double> T(n), S(n);
+    int rc = ocean_get_field(h, OCEAN_T, T.data(), n);
+    if (rc == OCEAN_OK) rc = ocean_get_field(h, OCEAN_S, S.data(), n);
+    if (rc) return rc;
+    h->Tref.assign(Tref, Tref + h->nz);
+    h->Sref.assign(Sref, Sref + h->nz);
+    h->ref_locked = true;
+    upload_levels(h);
+    rc = ocean_set_field(h, OCEAN_T, T.data(), n);
+    if (rc == OCEAN_OK) rc = ocean_set_field(h, OCEAN_S, S.data(), n);
+    return rc;
+}
+
+int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    return set_wind(h, taux, tauy);
+}
+
+int ocean_step_async(ocean_t h, int n) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (n < 0) return fail(h, OCEAN_ERR_ARG, "n must be >= 0");
+    for (int q = 0; q < n; ++q) {
+        if (h->prec == OCEAN_FP64) enqueue_step<double>(h);
+        else enqueue_step<float>(h);
+    }
+    OC_CUDA(h, cudaGetLastError());
+    return OCEAN_OK;
+}
+
+int ocean_sync(ocean_t h) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return OCEAN_OK;
+}
+
+int ocean_step(ocean_t h, int n) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (n < 0) return fail(h, OCEAN_ERR_ARG, "n must be >= 0");
+    const int every = h->prm.check_every;
+    for (int q = 0; q < n; ++q) {
+        int rc = ocean_step_async(h, 1);
+        if (rc) return rc;
+        if (every > 0 && h->nstep % every == 0) {
+            double d[8];
+            rc = run_diagnostics(h, d);
+            if (rc) return rc;
+            if (d[5] != 0.0) return fail(h, OCEAN_ERR_NONFINITE, "non-finite state after step %ld", h->nstep);
+            if (d[4] > 1.0) return fail(h, OCEAN_ERR_NONFINITE, "CFL number %.3g > 1 after step %ld", d[4], h->nstep);
+        }
+    }
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return OCEAN_OK;
+}
+
+int ocean_tendencies(ocean_t h) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (h->prec == OCEAN_FP64) enqueue_tendencies<double>(h);
+    else enqueue_tendencies<float>(h);
+    OC_CUDA(h, cudaGetLastError());
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return OCEAN_OK;
+}
+
+int ocean_diagnostics(ocean_t h, ocean_diag* out) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!out) return fail(h, OCEAN_ERR_ARG, "null output");
+    double d[8];
+    int rc = run_diagnostics(h, d);
+    if (rc) return rc;
+    out->step = h->nstep;
+    out->tracer_T = d[0];
+    out->tracer_S = d[1];
+    out->volume_eta = d[2];
+    out->ke = d[3];
+    out->max_cfl = d[4];
+    out->nonfinite = d[5] != 0.0;
+    out->wet_volume = d[6];
+    return OCEAN_OK;
+}
+
+long ocean_get_step(ocean_t h) { return h ? h->nstep : -1; }
+
+int ocean_set_step(ocean_t h, long step) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (step < 0) return fail(h, OCEAN_ERR_ARG, "step must be >= 0");
+    h->nstep = step;
+    return OCEAN_OK;
+}
+
+void* ocean_stream(ocean_t h) { return h ? (void*)h->stream : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// ocean_components.cu -- standalone kernels over caller-owned device buffers: the
+// adaptive-order WENO-Z face reconstruction and the batched Thomas solve, the same
+// device functions the step kernels use, exposed for component-level checks.
+#include <string>
+
+#include "ocean.h"
+#include "ocean_internal.cuh"
+
+namespace {
+
+template <typename R>
+__global__ void k_weno_faces(const R* __restrict__ q, const R* __restrict__ vel,
+                             const unsigned char* __restrict__ inside, int n, R* __restrict__ out,
+                             R eps, int linear) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const bool pos = vel[f] >= R(0);
+    R s[5];
+    unsigned in = 0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        int c = pos ? f - 3 + m : f + 2 - m;
+        c %= n;
+        if (c < 0) c += n;
+        s[m] = q[c];
+        in |= ((inside ? inside[c] != 0 : true) ? 1u : 0u) << m;
+    }
+    out[f] = weno_adaptive(s, in, eps, linear);
+}
+
+template <typename R>
+__global__ void k_tridiag(const R* __restrict__ a, const R* __restrict__ b, const R* __restrict__ c,
+                          const R* __restrict__ d, R* __restrict__ x, int n, int nsys) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    // forward elimination writes c' into x's slots' companion (kept in registers via a
+    // local array bounded by n <= 256) and d' into x; back substitution in place
+    R cp[256];
+    R inv = R(1) / b[s];
+    cp[0] = c[s] * inv;
+    x[s] = d[s] * inv;
+    for (int k = 1; k < n; ++k) {
+        const long e = (long)k * nsys + s;
+        const R ak = a[e];
+        inv = R(1) / (b[e] - ak * cp[k - 1]);
+        cp[k] = c[e] * inv;
+        x[e] = (d[e] - ak * x[e - nsys]) * inv;
+    }
+    for (int k = n - 2; k >= 0; --k) {
+        const long e = (long)k * nsys + s;
+        x[e] = x[e] - cp[k] * x[e + nsys];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ocean_weno_faces(const void* d_q, const void* d_vel, const unsigned char* d_inside, int n,
+                     void* d_out, int precision, double eps, int linear, void* stream) {
+    if (!d_q || !d_vel || !d_out || n < 5) return OCEAN_ERR_ARG;
+    const int tpb = 256, nb = (n + tpb - 1) / tpb;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == OCEAN_FP64)
+        k_weno_faces<double><<<nb, tpb, 0, s>>>((const double*)d_q, (const double*)d_vel, d_inside,
+                                                n, (double*)d_out, eps, linear);
+    else if (precision == OCEAN_MIXED)
+        k_weno_faces<float><<<nb, tpb, 0, s>>>((const float*)d_q, (const float*)d_vel, d_inside, n,
+                                               (float*)d_out, (float)eps, linear);
+    else
+        return OCEAN_ERR_ARG;
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : OCEAN_ERR_CUDA;
+}
+
+int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, const void* d_d,
+                          void* d_x, int n, int nsys, int precision, void* stream) {
+    if (!d_a || !d_b || !d_c || !d_d || !d_x || n < 1 || n > 256 || nsys < 1) return OCEAN_ERR_ARG;
+    const int tpb = 128, nb = (nsys + tpb - 1) / tpb;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == OCEAN_FP64)
+        k_tridiag<double><<<nb, tpb, 0, s>>>((const double*)d_a, (const double*)d_b,
+                                             (const double*)d_c, (const double*)d_d, (double*)d_x,
+                                             n, nsys);
+    else if (precision == OCEAN_MIXED)
+        k_tridiag<float><<<nb, tpb, 0, s>>>((const float*)d_a, (const float*)d_b, (const float*)d_c,
+                                            (const float*)d_d, (float*)d_x, n, nsys);
+    else
+        return OCEAN_ERR_ARG;
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : OCEAN_ERR_CUDA;
+}
+
+}  // extern "C"

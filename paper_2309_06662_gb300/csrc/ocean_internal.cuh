@@ -1,0 +1,164 @@
+// ocean_internal.cuh -- device-side layout, kernel parameters and shared device
+// functions of the GB300 ocean step.  Included by the kernel and host translation units
+// of libocean only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Horizontal halo width of every padded field: five-point WENO stencils reach three
+// cells beyond a face, staggered averages one more.
+#define OC_H 4
+// Largest number of levels the column kernels accept.
+#define OC_NZMAX 192
+
+// Geometry and masks shared by all kernels.  Padded 2-D index of column (i, j):
+// (j + OC_H) * pitch + (i + OC_H), for i in [-OC_H, nx + OC_H), j in [-OC_H, ny + OC_H).
+// 3-D index: k * plane + that.
+struct GeoD {
+    int nx, ny, nz, px, py, pitch;
+    long plane;
+    const short* kb;     // lowest wet level of each column (nz = land)
+    const short* kbu;    // lowest wet level of the u-face on the west side of the column
+    const short* kbv;    // lowest wet level of the v-face on the south side
+    const short* kbz;    // corner (SW of the column) active, all four cells wet, for k >= kbz
+    const short* kbzin;  // corner touches the fluid (one cell wet) for k >= kbzin
+};
+
+__device__ __forceinline__ long ix2(const GeoD& g, int i, int j) {
+    return (long)(j + OC_H) * g.pitch + (i + OC_H);
+}
+
+// Metrics, constants and switches passed by value to every kernel.  R is the storage
+// and arithmetic type of the 3-D fields (double, or float in the mixed form).
+template <typename R>
+struct KP {
+    GeoD g;
+    // per-row metrics, indexed j + OC_H
+    const R *dxc, *rdxc, *dxv, *rAc, *rAz, *fu, *fv;
+    // per-level metrics: dz[k], 1/dz[k], dzf[k] = zc[k] - zc[k-1], 1/dzf[k]; the
+    // horizontally uniform reference profiles Tref, Sref (T and S are stored as anomalies
+    // T - Tref(k), S - Sref(k)) and their level differences dTref[k] = Tref[k] - Tref[k-1]
+    const R *dz, *rdz, *dzf, *rdzf, *Tref, *Sref, *dTref, *dSref;
+    R dy, rdy, dt, ca, cb;
+    R grav, alpha, beta_s;
+    R nu0, ri_a, nu_b, kappa_b, kappa_conv;
+    R eps, ptop;
+    int linear;
+};
+
+// ----------------------------------------------------------------------- WENO-Z
+
+// In FP32 the ratio tau/(beta + eps) can exceed sqrt(FLT_MAX) when a stencil is
+// exactly flat; above 1e18 every stencil it is compared with is smooth to far below
+// FP32 resolution, so clamping leaves the reconstructed value unchanged.
+template <typename R> struct WenoRatio {
+    static __device__ __forceinline__ R clamp(R r) { return r; }
+};
+template <> struct WenoRatio<float> {
+    static __device__ __forceinline__ float clamp(float r) { return fminf(r, 1e18f); }
+};
+
+// Fifth-order WENO-Z value at the face downstream of q2 (q0..q4 upwind to downwind):
+// Jiang-Shu candidates and smoothness indicators, ideal weights (1, 6, 3)/10,
+// alpha_r = d_r (1 + (tau5 / (beta_r + eps))^2), tau5 = |beta_0 - beta_2|.
+template <typename R>
+__device__ __forceinline__ R weno5(R q0, R q1, R q2, R q3, R q4, R eps, int linear) {
+    const R s6 = R(1) / R(6);
+    R p0 = (R(2) * q0 - R(7) * q1 + R(11) * q2) * s6;
+    R p1 = (-q1 + R(5) * q2 + R(2) * q3) * s6;
+    R p2 = (R(2) * q2 + R(5) * q3 - q4) * s6;
+    if (linear) return R(0.1) * p0 + R(0.6) * p1 + R(0.3) * p2;
+    const R c13 = R(13) / R(12);
+    R a = q0 - R(2) * q1 + q2, b = q0 - R(4) * q1 + R(3) * q2;
+    R b0 = c13 * a * a + R(0.25) * b * b;
+    a = q1 - R(2) * q2 + q3; b = q1 - q3;
+    R b1 = c13 * a * a + R(0.25) * b * b;
+    a = q2 - R(2) * q3 + q4; b = R(3) * q2 - R(4) * q3 + q4;
+    R b2 = c13 * a * a + R(0.25) * b * b;
+    R tau = fabs(b0 - b2);
+    R r0 = WenoRatio<R>::clamp(tau / (b0 + eps));
+    R r1 = WenoRatio<R>::clamp(tau / (b1 + eps));
+    R r2 = WenoRatio<R>::clamp(tau / (b2 + eps));
+    R a0 = R(0.1) * (R(1) + r0 * r0);
+    R a1 = R(0.6) * (R(1) + r1 * r1);
+    R a2 = R(0.3) * (R(1) + r2 * r2);
+    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
+// Third-order WENO-Z at the face downstream of q1 (q0..q2 upwind to downwind).
+template <typename R>
+__device__ __forceinline__ R weno3(R q0, R q1, R q2, R eps, int linear) {
+    R p0 = R(0.5) * (-q0 + R(3) * q1);
+    R p1 = R(0.5) * (q1 + q2);
+    const R d0 = R(1) / R(3), d1 = R(2) / R(3);
+    if (linear) return d0 * p0 + d1 * p1;
+    R b0 = (q1 - q0) * (q1 - q0);
+    R b1 = (q2 - q1) * (q2 - q1);
+    R tau = fabs(b0 - b1);
+    R r0 = WenoRatio<R>::clamp(tau / (b0 + eps));
+    R r1 = WenoRatio<R>::clamp(tau / (b1 + eps));
+    R a0 = d0 * (R(1) + r0 * r0);
+    R a1 = d1 * (R(1) + r1 * r1);
+    return (a0 * p0 + a1 * p1) / (a0 + a1);
+}
+
+// Adaptive order: bit n of `in` says whether stencil point n lies in the fluid.  All
+// five: WENO5; the central three: WENO3; otherwise the upwind value q2.
+template <typename R>
+__device__ __forceinline__ R weno_adaptive(const R* q, unsigned in, R eps, int linear) {
+    if (in == 31u) return weno5(q[0], q[1], q[2], q[3], q[4], eps, linear);
+    if ((in & 14u) == 14u) return weno3(q[1], q[2], q[3], eps, linear);
+    return q[2];
+}
+
+// ----------------------------------------------------------------------- launchers
+// Implemented in ocean_kernels.cu, instantiated for double and float.
+
+template <typename R> struct StepBuffers {
+    // state n (read) and n+1 (written)
+    const R *u, *v, *T, *S;
+    R *un, *vn, *Tn, *Sn;
+    R *Gu, *Gv, *GT, *GS;      // G^{n-1} in, G^n out
+    R *w, *p, *kap, *nu;       // diagnostics
+    const R *taux_s, *tauy_s;  // wind stress / (rho0 dz_top)
+    R *Un, *Vn, *GU, *GV, *Su, *Sv;         // column sums (2-D)
+    R *Ub, *Vb, *dE, *paccE, *paccU, *paccV, *gxe, *gye, *corrU, *corrV;
+    const R *Hu, *Hv, *rHu, *rHv;
+    double *eta, *accE, *accU, *accV;
+};
+
+template <typename R>
+void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s);
+template <typename R>
+void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s);
+template <typename R>
+void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s);
+template <typename R>
+void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double dt, R grav,
+                       cudaStream_t s);
+template <typename R>
+void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s);
+template <typename R>
+void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s);
+template <typename R>
+void launch_halo2(const GeoD& g, R* f, cudaStream_t s);
+template <typename R>
+int setup_kernel_attributes(int nz);
+
+// FP64 metrics of the conservation reductions (row arrays indexed j + OC_H).
+struct DiagMetrics {
+    const double *Ac, *dxv, *rdxc, *dz, *Tref, *Sref;
+    double dy, rdy, dt;
+};
+
+// Conservation/health reduction; `partials` is device scratch of at least
+// diag_partials_bytes() bytes; `out` (device) receives 8 doubles:
+// {sum T dV, sum S dV, sum eta dA, KE, max CFL, nonfinite, wet volume, 0}.
+#define OC_DIAG_BLOCKS 1024
+#define OC_DIAG_THREADS 256
+size_t diag_partials_bytes();
+template <typename R>
+void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v,
+                        const R* T, const R* S, const R* w, const double* eta,
+                        double* partials, double* out, cudaStream_t s);

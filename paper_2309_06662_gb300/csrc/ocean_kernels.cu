@@ -1,0 +1,843 @@
+// ocean_kernels.cu -- CUDA kernels of one baroclinic step (sm_103a), instantiated for
+// FP64 (R = double) and the mixed form (R = float).
+//
+// Step n -> n+1 (arXiv 2309.06662, Sec. "New numerical methods ..." and
+// Sec. "Optimization of ocean free surface dynamics"):
+//   k_diag      hydrostatic pressure (top -> bottom), w from continuity (bottom -> top),
+//               Richardson-number kappa and nu: the two intermediates the paper's fused
+//               tendency kernels depend on (pressure and vertical diffusivity)
+//   k_tracer    WENO-Z flux-form T and S tendencies, quasi-AB2 predictor and the
+//               backward-Euler vertical diffusion (Thomas) of the same column, fused
+//   k_momentum  vector-invariant u and v tendencies (WENO-Z vorticity flux, Coriolis,
+//               kinetic-energy and pressure gradients, vertical advection, wind),
+//               quasi-AB2, vertical viscosity solve, column sums for the barotropic mode
+//   k_baro_*    split-explicit barotropic sub-cycle with equal-weight averaging
+//   k_correct   barotropic correction of u and v
+//   k_halo*     periodic halo copies
+// One thread owns one water column in the column kernels; threads of a warp hold
+// neighbouring columns of a row, so every level access is coalesced.
+#include "ocean_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 128;
+
+// multiplications that the compiler may not fuse into a neighbouring add
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+
+inline int nblocks(long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+// T and S are stored as anomalies T' = T - Tref(k), S' = S - Sref(k) from horizontally
+// uniform reference profiles; in FP32 this keeps ~1e-9 instead of ~1e-6 of absolute
+// resolution in the buoyancy that drives the horizontal pressure gradients.
+// Buoyancy anomaly b' = g (alpha T' - beta_s S'): its pressure integral differs from the
+// full one by a function of k alone, which has no horizontal gradient.
+// Explicitly rounded: columns of different depth run this in loops of different trip
+// counts, and identical inputs must give identical bits at every level whatever code
+// the compiler generates for each trip (the lake-at-rest state depends on it).
+template <typename R>
+__device__ __forceinline__ R buoy_anom(const KP<R>& p, R Ta, R Sa) {
+    return rmul(p.grav, fma(p.alpha, Ta, -rmul(p.beta_s, Sa)));
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
+                                              const R* __restrict__ v, const R* __restrict__ T,
+                                              const R* __restrict__ S, R* __restrict__ w,
+                                              R* __restrict__ pr, R* __restrict__ kap,
+                                              R* __restrict__ nu) {
+    const GeoD& g = p.g;
+    const int W = g.nx + 2;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)W * (g.ny + 2)) return;
+    const int i = (int)(c % W) - 1, j = (int)(c / W) - 1;
+    const long c2 = ix2(g, i, j);
+    const int kb = g.kb[c2], nz = g.nz;
+    if (kb >= nz) return;
+    const long P = g.plane;
+    // pressure anomaly, integrated downward from the surface
+    R bup = buoy_anom(p, T[(nz - 1) * P + c2], S[(nz - 1) * P + c2]);
+    R pk = -rmul(bup, p.ptop);
+    pr[(nz - 1) * P + c2] = pk;
+#pragma unroll 1
+    for (int k = nz - 2; k >= kb; --k) {
+        R bk = buoy_anom(p, T[k * P + c2], S[k * P + c2]);
+        pk = fma(-rmul(R(0.5), bk + bup), p.dzf[k + 1], pk);
+        pr[k * P + c2] = pk;
+        bup = bk;
+    }
+    // vertical velocity on bottom faces, integrated upward from the sea floor
+    const R dy = p.dy, dxvS = p.dxv[j + OC_H], dxvN = p.dxv[j + 1 + OC_H], rac = p.rAc[j + OC_H];
+    R wk = R(0);
+    w[kb * P + c2] = wk;
+    for (int k = kb; k < nz - 1; ++k) {
+        const long ck = k * P + c2;
+        R div = dy * p.dz[k] * (u[ck + 1] - u[ck])
+              + p.dz[k] * (dxvN * v[ck + g.pitch] - dxvS * v[ck]);
+        wk = wk - div * rac;
+        w[ck + P] = wk;
+    }
+    // Richardson-number closure on the interior w-faces
+    for (int k = kb + 1; k < nz; ++k) {
+        const long ck = k * P + c2, cm = ck - P;
+        R rz = p.rdzf[k];
+        R n2 = p.grav * (p.alpha * ((T[ck] - T[cm]) + p.dTref[k])
+                         - p.beta_s * ((S[ck] - S[cm]) + p.dSref[k])) * rz;
+        R ua = R(0.5) * (u[ck] + u[ck + 1]), ub = R(0.5) * (u[cm] + u[cm + 1]);
+        R va = R(0.5) * (v[ck] + v[ck + g.pitch]), vb = R(0.5) * (v[cm] + v[cm + g.pitch]);
+        R s2 = ((ua - ub) * (ua - ub) + (va - vb) * (va - vb)) * rz * rz;
+        R kk, nn;
+        if (n2 < R(0)) {
+            kk = p.kappa_conv; nn = p.kappa_conv;
+        } else {
+            R ri = n2 / (s2 > R(1e-14) ? s2 : R(1e-14));
+            R q = R(1) + p.ri_a * ri;
+            nn = p.nu0 / (q * q) + p.nu_b;
+            kk = nn / q + p.kappa_b;
+        }
+        kap[ck] = kk;
+        nu[ck] = nn;
+    }
+}
+
+// ------------------------------------------------------------------ tracers
+
+// Horizontal advective fluxes through the u-face (i, j, k): the transport U = u dy dz and
+// U T'~, U S'~.  WENO is translation-equivariant (candidates have unit coefficient sums,
+// indicators see differences only), so reconstructing the anomalies along a level and
+// adding U Tref(k) is the same flux as reconstructing T itself.
+template <typename R>
+__device__ __forceinline__ void xflux(const KP<R>& p, const R* __restrict__ u,
+                                      const R* __restrict__ T, const R* __restrict__ S, int i,
+                                      int j, int k, R& fU, R& fT, R& fS) {
+    const GeoD& g = p.g;
+    const long c2 = ix2(g, i, j);
+    if (k < g.kbu[c2]) { fU = R(0); fT = R(0); fS = R(0); return; }
+    const long ck = k * g.plane + c2;
+    const R ut = u[ck];
+    R qT[5], qS[5];
+    unsigned in = 0;
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+        const int o = ut >= R(0) ? n - 3 : 2 - n;
+        qT[n] = T[ck + o];
+        qS[n] = S[ck + o];
+        in |= (k >= g.kb[c2 + o] ? 1u : 0u) << n;
+    }
+    const R U = ut * p.dy * p.dz[k];
+    fU = U;
+    fT = U * weno_adaptive(qT, in, p.eps, p.linear);
+    fS = U * weno_adaptive(qS, in, p.eps, p.linear);
+}
+
+template <typename R>
+__device__ __forceinline__ void yflux(const KP<R>& p, const R* __restrict__ v,
+                                      const R* __restrict__ T, const R* __restrict__ S, int i,
+                                      int j, int k, R& fV, R& fT, R& fS) {
+    const GeoD& g = p.g;
+    const long c2 = ix2(g, i, j);
+    if (k < g.kbv[c2]) { fV = R(0); fT = R(0); fS = R(0); return; }
+    const long ck = k * g.plane + c2;
+    const R vt = v[ck];
+    R qT[5], qS[5];
+    unsigned in = 0;
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+        const long o = (long)(vt >= R(0) ? n - 3 : 2 - n) * g.pitch;
+        qT[n] = T[ck + o];
+        qS[n] = S[ck + o];
+        in |= (k >= g.kb[c2 + o] ? 1u : 0u) << n;
+    }
+    const R V = vt * p.dxv[j + OC_H] * p.dz[k];
+    fV = V;
+    fT = V * weno_adaptive(qT, in, p.eps, p.linear);
+    fS = V * weno_adaptive(qS, in, p.eps, p.linear);
+}
+
+// w T~ and w S~ through the bottom face of cell k (kb < k < nz) of column c2; the
+// reference profile varies along the column, so the stencil holds full values
+template <typename R>
+__device__ __forceinline__ void zflux(const KP<R>& p, const R* __restrict__ w,
+                                      const R* __restrict__ T, const R* __restrict__ S, long c2,
+                                      int k, int kb, R& fT, R& fS) {
+    const GeoD& g = p.g;
+    const long P = g.plane;
+    const R wt = w[k * P + c2];
+    R qT[5], qS[5];
+    unsigned in = 0;
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+        const int kk = wt >= R(0) ? k - 3 + n : k + 2 - n;
+        const bool ok = kk >= kb && kk < g.nz;
+        qT[n] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
+        qS[n] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
+        in |= (ok ? 1u : 0u) << n;
+    }
+    fT = wt * weno_adaptive(qT, in, p.eps, p.linear);
+    fS = wt * weno_adaptive(qS, in, p.eps, p.linear);
+}
+
+// STEP = false: write G^n of T, S into Tn, Sn.  STEP = true: quasi-AB2 predictor
+// T* = T + dt (ca G^n - cb G^{n-1}), G^{n-1} <- G^n, then the backward-Euler diffusion
+//   T_k - T*_k = dt/dz_k [kap_{k+1} (T_{k+1} - T_k)/dzf_{k+1} - kap_k (T_k - T_{k-1})/dzf_k]
+// with zero flux at the sea floor and the surface, by the Thomas algorithm: forward
+// elimination from the bottom while the column is swept upward, back substitution down.
+template <typename R, bool STEP>
+__global__ void __launch_bounds__(TPB) k_tracer(KP<R> p, const R* __restrict__ u,
+                                                const R* __restrict__ v, const R* __restrict__ w,
+                                                const R* __restrict__ T, const R* __restrict__ S,
+                                                const R* __restrict__ kap, R* __restrict__ GTp,
+                                                R* __restrict__ GSp, R* __restrict__ Tn,
+                                                R* __restrict__ Sn) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GeoD& g = p.g;
+    const int nz = g.nz, tid = threadIdx.x, nb = blockDim.x;
+    R* cp = reinterpret_cast<R*>(smem_raw);
+    R* dT = cp + nz * nb;
+    R* dS = dT + nz * nb;
+    long c = (long)blockIdx.x * blockDim.x + tid;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j), P = g.plane;
+    const int kb = g.kb[c2];
+    if (kb >= nz) return;
+    const R rac = p.rAc[j + OC_H];
+    R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
+    for (int k = kb; k < nz; ++k) {
+        const long ck = k * P + c2;
+        R fwU, fwT, fwS, feU, feT, feS, fsV, fsT, fsS, fnV, fnT, fnS, ftT = R(0), ftS = R(0);
+        xflux(p, u, T, S, i, j, k, fwU, fwT, fwS);
+        xflux(p, u, T, S, i + 1, j, k, feU, feT, feS);
+        yflux(p, v, T, S, i, j, k, fsV, fsT, fsS);
+        yflux(p, v, T, S, i, j + 1, k, fnV, fnT, fnS);
+        if (k + 1 < nz) zflux(p, w, T, S, c2, k + 1, kb, ftT, ftS);
+        const R rdz = p.rdz[k];
+        const R divU = feU - fwU + fnV - fsV;
+        const R GT = -((p.Tref[k] * divU + (feT - fwT + fnT - fsT)) * rac + (ftT - fzT)) * rdz;
+        const R GS = -((p.Sref[k] * divU + (feS - fwS + fnS - fsS)) * rac + (ftS - fzS)) * rdz;
+        fzT = ftT;
+        fzS = ftS;
+        if (!STEP) {
+            Tn[ck] = GT;
+            Sn[ck] = GS;
+            continue;
+        }
+        const R gT = p.ca * GT - p.cb * GTp[ck];
+        const R gS = p.ca * GS - p.cb * GSp[ck];
+        GTp[ck] = GT;
+        GSp[ck] = GS;
+        const R lo = k > kb ? p.dt * kap[ck] * rdz * p.rdzf[k] : R(0);
+        const R hi = k < nz - 1 ? p.dt * kap[ck + P] * rdz * p.rdzf[k + 1] : R(0);
+        // the diffusion of the reference profile moves to the right-hand side of the
+        // anomaly system: (I - dt D) T'^{n+1} = T'* + dt D Tref
+        const R Ts = T[ck] + p.dt * gT
+                   + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
+        const R Ss = S[ck] + p.dt * gS
+                   + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
+        const R den = (R(1) + lo + hi) + lo * cprev;   // b_k - a_k c'_{k-1}, a_k = -lo
+        const R inv = R(1) / den;
+        cprev = -hi * inv;
+        dTprev = (Ts + lo * dTprev) * inv;
+        dSprev = (Ss + lo * dSprev) * inv;
+        cp[k * nb + tid] = cprev;
+        dT[k * nb + tid] = dTprev;
+        dS[k * nb + tid] = dSprev;
+    }
+    if (!STEP) return;
+    R xT = dT[(nz - 1) * nb + tid], xS = dS[(nz - 1) * nb + tid];
+    Tn[(nz - 1) * P + c2] = xT;
+    Sn[(nz - 1) * P + c2] = xS;
+    for (int k = nz - 2; k >= kb; --k) {
+        const R cc = cp[k * nb + tid];
+        xT = dT[k * nb + tid] - cc * xT;
+        xS = dS[k * nb + tid] - cc * xS;
+        Tn[k * P + c2] = xT;
+        Sn[k * P + c2] = xS;
+    }
+}
+
+// ------------------------------------------------------------------ momentum
+
+// relative vorticity at the SW corner of column (i, j), zero unless all four cells wet
+template <typename R>
+__device__ __forceinline__ R zeta_at(const KP<R>& p, const R* __restrict__ u,
+                                     const R* __restrict__ v, int i, int j, int k) {
+    const GeoD& g = p.g;
+    const long c2 = ix2(g, i, j);
+    if (k < g.kbz[c2]) return R(0);
+    const long ck = k * g.plane + c2;
+    const R circ = p.dy * (v[ck] - v[ck - 1])
+                 - (p.dxc[j + OC_H] * u[ck] - p.dxc[j - 1 + OC_H] * u[ck - g.pitch]);
+    return circ * p.rAz[j + OC_H];
+}
+
+// kinetic energy at the centre of the cell at index ck
+template <typename R>
+__device__ __forceinline__ R kin_at(const R* __restrict__ u, const R* __restrict__ v, long ck,
+                                    int pitch) {
+    const R a = u[ck], b = u[ck + 1], c = v[ck], d = v[ck + pitch];
+    return R(0.25) * (a * a + b * b) + R(0.25) * (c * c + d * d);
+}
+
+template <typename R, bool STEP>
+__global__ void __launch_bounds__(TPB) k_momentum(
+    KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
+    const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
+    const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
+    R* __restrict__ vn, R* __restrict__ Un, R* __restrict__ Vn, R* __restrict__ GU,
+    R* __restrict__ GV, R* __restrict__ Su, R* __restrict__ Sv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GeoD& g = p.g;
+    const int nz = g.nz, tid = threadIdx.x, nb = blockDim.x;
+    R* cpu = reinterpret_cast<R*>(smem_raw);
+    R* du = cpu + nz * nb;
+    R* cpv = du + nz * nb;
+    R* dv = cpv + nz * nb;
+    long c = (long)blockIdx.x * blockDim.x + tid;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j), P = g.plane;
+    const int pitch = g.pitch;
+    const int ku = g.kbu[c2], kv = g.kbv[c2];
+    const int k0 = ku < kv ? ku : kv;
+    if (k0 >= nz) return;
+    const R rdxc = p.rdxc[j + OC_H], fu = p.fu[j + OC_H], fv = p.fv[j + OC_H];
+    R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
+    R cu = 0, dup = 0, cv = 0, dvp = 0;
+    for (int k = k0; k < nz; ++k) {
+        const long ck = k * P + c2;
+        const R rdz = p.rdz[k];
+        if (k >= ku) {   // ---------------- u at the west face of column (i, j)
+            const R u0 = u[ck];
+            const R vh = R(0.25) * (v[ck - 1] + v[ck] + v[ck - 1 + pitch] + v[ck + pitch]);
+            R q[5];
+            unsigned in = 0;
+#pragma unroll
+            for (int n = 0; n < 5; ++n) {
+                const int jj = vh >= R(0) ? j - 2 + n : j + 3 - n;
+                q[n] = zeta_at(p, u, v, i, jj, k);
+                in |= (k >= g.kbzin[ix2(g, i, jj)] ? 1u : 0u) << n;
+            }
+            const R zt = weno_adaptive(q, in, p.eps, p.linear);
+            const R dK = (kin_at(u, v, ck, pitch) - kin_at(u, v, ck - 1, pitch)) * rdxc;
+            const R dP = (pr[ck] - pr[ck - 1]) * rdxc;
+            R up = R(0), dn = R(0);
+            if (k + 1 < nz)
+                up = R(0.5) * (w[ck + P - 1] + w[ck + P]) * (u[ck + P] - u0) * p.rdzf[k + 1];
+            if (k - 1 >= ku)
+                dn = R(0.5) * (w[ck - 1] + w[ck]) * (u0 - u[ck - P]) * p.rdzf[k];
+            const R wind = k == nz - 1 ? taux_s[c2] : R(0);
+            const R G = (zt + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
+            if (!STEP) {
+                un[ck] = G;
+            } else {
+                const R gh = p.ca * G - p.cb * Gup[ck];
+                Gup[ck] = G;
+                sUn += p.dz[k] * u0;
+                sGU += p.dz[k] * gh;
+                const R us = u0 + p.dt * gh;
+                const R lo = k > ku ? p.dt * R(0.5) * (nu[ck - 1] + nu[ck]) * rdz * p.rdzf[k] : R(0);
+                const R hi = k < nz - 1
+                    ? p.dt * R(0.5) * (nu[ck + P - 1] + nu[ck + P]) * rdz * p.rdzf[k + 1] : R(0);
+                const R inv = R(1) / ((R(1) + lo + hi) + lo * cu);
+                cu = -hi * inv;
+                dup = (us + lo * dup) * inv;
+                cpu[k * nb + tid] = cu;
+                du[k * nb + tid] = dup;
+            }
+        }
+        if (k >= kv) {   // ---------------- v at the south face of column (i, j)
+            const R v0 = v[ck];
+            const R uh = R(0.25) * (u[ck - pitch] + u[ck + 1 - pitch] + u[ck] + u[ck + 1]);
+            R q[5];
+            unsigned in = 0;
+#pragma unroll
+            for (int n = 0; n < 5; ++n) {
+                const int ii = uh >= R(0) ? i - 2 + n : i + 3 - n;
+                q[n] = zeta_at(p, u, v, ii, j, k);
+                in |= (k >= g.kbzin[ix2(g, ii, j)] ? 1u : 0u) << n;
+            }
+            const R zt = weno_adaptive(q, in, p.eps, p.linear);
+            const R dK = (kin_at(u, v, ck, pitch) - kin_at(u, v, ck - pitch, pitch)) * p.rdy;
+            const R dP = (pr[ck] - pr[ck - pitch]) * p.rdy;
+            R up = R(0), dn = R(0);
+            if (k + 1 < nz)
+                up = R(0.5) * (w[ck + P - pitch] + w[ck + P]) * (v[ck + P] - v0) * p.rdzf[k + 1];
+            if (k - 1 >= kv)
+                dn = R(0.5) * (w[ck - pitch] + w[ck]) * (v0 - v[ck - P]) * p.rdzf[k];
+            const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
+            const R G = -(zt + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
+            if (!STEP) {
+                vn[ck] = G;
+            } else {
+                const R gh = p.ca * G - p.cb * Gvp[ck];
+                Gvp[ck] = G;
+                sVn += p.dz[k] * v0;
+                sGV += p.dz[k] * gh;
+                const R vs = v0 + p.dt * gh;
+                const R lo = k > kv
+                    ? p.dt * R(0.5) * (nu[ck - pitch] + nu[ck]) * rdz * p.rdzf[k] : R(0);
+                const R hi = k < nz - 1
+                    ? p.dt * R(0.5) * (nu[ck + P - pitch] + nu[ck + P]) * rdz * p.rdzf[k + 1] : R(0);
+                const R inv = R(1) / ((R(1) + lo + hi) + lo * cv);
+                cv = -hi * inv;
+                dvp = (vs + lo * dvp) * inv;
+                cpv[k * nb + tid] = cv;
+                dv[k * nb + tid] = dvp;
+            }
+        }
+    }
+    if (!STEP) return;
+    if (ku < nz) {
+        R x = du[(nz - 1) * nb + tid];
+        un[(nz - 1) * P + c2] = x;
+        R s = p.dz[nz - 1] * x;
+        for (int k = nz - 2; k >= ku; --k) {
+            x = du[k * nb + tid] - cpu[k * nb + tid] * x;
+            un[k * P + c2] = x;
+            s += p.dz[k] * x;
+        }
+        Un[c2] = sUn;
+        GU[c2] = sGU;
+        Su[c2] = s;
+    }
+    if (kv < nz) {
+        R x = dv[(nz - 1) * nb + tid];
+        vn[(nz - 1) * P + c2] = x;
+        R s = p.dz[nz - 1] * x;
+        for (int k = nz - 2; k >= kv; --k) {
+            x = dv[k * nb + tid] - cpv[k * nb + tid] * x;
+            vn[k * P + c2] = x;
+            s += p.dz[k] * x;
+        }
+        Vn[c2] = sVn;
+        GV[c2] = sGV;
+        Sv[c2] = s;
+    }
+}
+
+// ------------------------------------------------------------------ barotropic mode
+
+// start of the sub-cycle: U^0 = U^n, deta^0 = 0, accumulators cleared, the gradient of
+// the FP64 free surface eta^n formed once (in R)
+template <typename R>
+__global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restrict__ Vn,
+                             const double* __restrict__ eta, const R* __restrict__ Hu,
+                             const R* __restrict__ Hv, R* Ub, R* Vb, R* dE, R* paccE, R* paccU,
+                             R* paccV, double* accE, double* accU, double* accV, R* gxe, R* gye) {
+    const GeoD& g = p.g;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j);
+    Ub[c2] = Un[c2];
+    Vb[c2] = Vn[c2];
+    dE[c2] = R(0);
+    paccE[c2] = R(0);
+    paccU[c2] = R(0);
+    paccV[c2] = R(0);
+    accE[c2] = 0.0;
+    accU[c2] = 0.0;
+    accV[c2] = 0.0;
+    gxe[c2] = Hu[c2] > R(0) ? R(eta[c2] - eta[c2 - 1]) : R(0);
+    gye[c2] = Hv[c2] > R(0) ? R(eta[c2] - eta[c2 - g.pitch]) : R(0);
+}
+
+// deta^m = deta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]^{m-1}
+template <typename R>
+__global__ void k_baro_eta(KP<R> p, const R* __restrict__ Ub, const R* __restrict__ Vb, R* dE,
+                           R* paccE, R dtau) {
+    const GeoD& g = p.g;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j);
+    if (g.kb[c2] >= g.nz) return;
+    const R div = p.dy * (Ub[c2 + 1] - Ub[c2])
+                + p.dxv[j + 1 + OC_H] * Vb[c2 + g.pitch] - p.dxv[j + OC_H] * Vb[c2];
+    const R e = dE[c2] - dtau * p.rAc[j + OC_H] * div;
+    dE[c2] = e;
+    paccE[c2] += e;
+}
+
+// U^m = U^{m-1} + dtau [-g H_u (eta^m_i - eta^m_{i-1})/dx_c + G_U] (and V); partial sums
+// of deta, U - U^n, V - V^n are flushed into the FP64 accumulators when `flush`
+template <typename R>
+__global__ void k_baro_uv(KP<R> p, const R* __restrict__ dE, const R* __restrict__ gxe,
+                          const R* __restrict__ gye, const R* __restrict__ Hu,
+                          const R* __restrict__ Hv, const R* __restrict__ GU,
+                          const R* __restrict__ GV, const R* __restrict__ Un,
+                          const R* __restrict__ Vn, R* Ub, R* Vb, R* paccE, R* paccU, R* paccV,
+                          double* accE, double* accU, double* accV, R dtau, R grav, int flush) {
+    const GeoD& g = p.g;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j);
+    const R hu = Hu[c2], hv = Hv[c2];
+    R pu = paccU[c2], pv = paccV[c2];
+    if (hu > R(0)) {
+        const R Unew = Ub[c2] + dtau * (-grav * hu * (gxe[c2] + (dE[c2] - dE[c2 - 1])) * p.rdxc[j + OC_H]
+                                        + GU[c2]);
+        Ub[c2] = Unew;
+        pu += Unew - Un[c2];
+    }
+    if (hv > R(0)) {
+        const R Vnew = Vb[c2] + dtau * (-grav * hv * (gye[c2] + (dE[c2] - dE[c2 - g.pitch])) * p.rdy
+                                        + GV[c2]);
+        Vb[c2] = Vnew;
+        pv += Vnew - Vn[c2];
+    }
+    if (flush) {
+        accE[c2] += (double)paccE[c2];
+        accU[c2] += (double)pu;
+        accV[c2] += (double)pv;
+        paccE[c2] = R(0);
+        pu = R(0);
+        pv = R(0);
+    }
+    paccU[c2] = pu;
+    paccV[c2] = pv;
+}
+
+// eta^{n+1} = eta^n + mean(deta) in FP64; correction of the depth-integrated velocity
+// (Ubar - sum dz u**)/H_u with Ubar = U^n + mean(U - U^n)
+template <typename R>
+__global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE,
+                           const double* __restrict__ accU, const double* __restrict__ accV,
+                           const R* __restrict__ Un, const R* __restrict__ Vn,
+                           const R* __restrict__ Su, const R* __restrict__ Sv,
+                           const R* __restrict__ rHu, const R* __restrict__ rHv, R* corrU,
+                           R* corrV, double rns) {
+    const GeoD& g = p.g;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j);
+    if (g.kb[c2] < g.nz) eta[c2] = eta[c2] + accE[c2] * rns;
+    corrU[c2] = rHu[c2] > R(0) ? (R(accU[c2] * rns) + (Un[c2] - Su[c2])) * rHu[c2] : R(0);
+    corrV[c2] = rHv[c2] > R(0) ? (R(accV[c2] * rns) + (Vn[c2] - Sv[c2])) * rHv[c2] : R(0);
+}
+
+template <typename R>
+__global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
+                          const R* __restrict__ corrU, const R* __restrict__ corrV) {
+    const GeoD& g = p.g;
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    const long c2 = ix2(g, i, j), P = g.plane;
+    const int ku = g.kbu[c2], kv = g.kbv[c2];
+    const R cu = corrU[c2], cv = corrV[c2];
+    for (int k = ku; k < g.nz; ++k) un[k * P + c2] += cu;
+    for (int k = kv; k < g.nz; ++k) vn[k * P + c2] += cv;
+}
+
+// ------------------------------------------------------------------ halos
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+// Column kernels keep the Thomas coefficients of every level in shared memory:
+// per thread 3 (tracers) or 4 (momentum) values per level.  The block shrinks (in whole
+// warps) so that the block's share stays within 200 KB.
+static int column_tpb(int nz, int vals, size_t esz) {
+    const size_t per = (size_t)vals * nz * esz;
+    int t = (int)((200u * 1024u) / per) / 32 * 32;
+    return t > TPB ? TPB : (t < 32 ? 32 : t);
+}
+template <typename R>
+static size_t tracer_smem(int nz) { return (size_t)3 * nz * column_tpb(nz, 3, sizeof(R)) * sizeof(R); }
+template <typename R>
+static size_t momentum_smem(int nz) { return (size_t)4 * nz * column_tpb(nz, 4, sizeof(R)) * sizeof(R); }
+
+template <typename R>
+int setup_kernel_attributes(int nz) {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_tracer<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tracer_smem<R>(nz));
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_tracer<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tracer_smem<R>(nz));
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_momentum<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)momentum_smem<R>(nz));
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_momentum<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)momentum_smem<R>(nz));
+    return (int)e;
+}
+
+template <typename R>
+void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
+    const long n = (long)(p.g.nx + 2) * (p.g.ny + 2);
+    k_diag<R><<<nblocks(n, TPB), TPB, 0, s>>>(p, b.u, b.v, b.T, b.S, b.w, b.p, b.kap, b.nu);
+}
+
+template <typename R>
+void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
+    const long n = (long)p.g.nx * p.g.ny;
+    const size_t sm = tracer_smem<R>(p.g.nz);
+    const int tpb = column_tpb(p.g.nz, 3, sizeof(R));
+    if (step)
+        k_tracer<R, true><<<nblocks(n, tpb), tpb, sm, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap,
+                                                          b.GT, b.GS, b.Tn, b.Sn);
+    else
+        k_tracer<R, false><<<nblocks(n, tpb), tpb, sm, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap,
+                                                           b.GT, b.GS, b.Tn, b.Sn);
+}
+
+template <typename R>
+void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
+    const long n = (long)p.g.nx * p.g.ny;
+    const size_t sm = momentum_smem<R>(p.g.nz);
+    const int tpb = column_tpb(p.g.nz, 4, sizeof(R));
+    if (step)
+        k_momentum<R, true><<<nblocks(n, tpb), tpb, sm, s>>>(
+            p, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.Un, b.Vn,
+            b.GU, b.GV, b.Su, b.Sv);
+    else
+        k_momentum<R, false><<<nblocks(n, tpb), tpb, sm, s>>>(
+            p, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.Un, b.Vn,
+            b.GU, b.GV, b.Su, b.Sv);
+}
+
+// flush the FP32 partial sums into the FP64 accumulators every this many substeps
+#define OC_BARO_FLUSH 8
+
+template <typename R>
+void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double dt, R grav,
+                       cudaStream_t s) {
+    const GeoD& g = p.g;
+    const long n = (long)g.nx * g.ny;
+    const int nbk = nblocks(n, TPB);
+    const R dtau = (R)(2.0 * dt / (ns + 1.0));
+    if (g.px || g.py) launch_halo2<double>(g, b.eta, s);
+    k_baro_begin<R><<<nbk, TPB, 0, s>>>(p, b.Un, b.Vn, b.eta, b.Hu, b.Hv, b.Ub, b.Vb, b.dE,
+                                       b.paccE, b.paccU, b.paccV, b.accE, b.accU, b.accV, b.gxe,
+                                       b.gye);
+    for (int m = 1; m <= ns; ++m) {
+        if (g.px || g.py) {
+            launch_halo2<R>(g, b.Ub, s);
+            launch_halo2<R>(g, b.Vb, s);
+        }
+        k_baro_eta<R><<<nbk, TPB, 0, s>>>(p, b.Ub, b.Vb, b.dE, b.paccE, dtau);
+        if (g.px || g.py) launch_halo2<R>(g, b.dE, s);
+        const int flush = (m % OC_BARO_FLUSH == 0) || m == ns;
+        k_baro_uv<R><<<nbk, TPB, 0, s>>>(p, b.dE, b.gxe, b.gye, b.Hu, b.Hv, b.GU, b.GV, b.Un,
+                                        b.Vn, b.Ub, b.Vb, b.paccE, b.paccU, b.paccV, b.accE,
+                                        b.accU, b.accV, dtau, grav, flush);
+    }
+    k_baro_end<R><<<nbk, TPB, 0, s>>>(p, b.eta, b.accE, b.accU, b.accV, b.Un, b.Vn, b.Su, b.Sv,
+                                     b.rHu, b.rHv, b.corrU, b.corrV, 1.0 / ns);
+}
+
+template <typename R>
+void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
+    const long n = (long)p.g.nx * p.g.ny;
+    k_correct<R><<<nblocks(n, TPB), TPB, 0, s>>>(p, b.un, b.vn, b.corrU, b.corrV);
+}
+
+// up to four field pointers passed by value, so a halo launch needs no device table
+template <typename R> struct PtrPack { R* f[4]; };
+
+// periodic copies: x halo columns of the interior rows, then y halo rows of the full
+// padded width (so the corners come out right)
+
+template <typename R>
+__global__ void k_halo_x_pack(GeoD g, PtrPack<R> pk, int nf, int nlev) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long per = (long)2 * OC_H * g.ny;
+    if (t >= per * nlev * nf) return;
+    const int f = (int)(t / (per * nlev));
+    t -= (long)f * per * nlev;
+    const int k = (int)(t / per);
+    t -= (long)k * per;
+    const int j = (int)(t / (2 * OC_H)), h = (int)(t % (2 * OC_H));
+    const int i = h < OC_H ? h - OC_H : g.nx + (h - OC_H);
+    const int isrc = h < OC_H ? i + g.nx : i - g.nx;
+    R* F = pk.f[f];
+    F[k * g.plane + ix2(g, i, j)] = F[k * g.plane + ix2(g, isrc, j)];
+}
+
+template <typename R>
+__global__ void k_halo_y_pack(GeoD g, PtrPack<R> pk, int nf, int nlev) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int W = g.nx + 2 * OC_H;
+    const long per = (long)2 * OC_H * W;
+    if (t >= per * nlev * nf) return;
+    const int f = (int)(t / (per * nlev));
+    t -= (long)f * per * nlev;
+    const int k = (int)(t / per);
+    t -= (long)k * per;
+    const int h = (int)(t / W), i = (int)(t % W) - OC_H;
+    const int j = h < OC_H ? h - OC_H : g.ny + (h - OC_H);
+    const int jsrc = h < OC_H ? j + g.ny : j - g.ny;
+    R* F = pk.f[f];
+    F[k * g.plane + ix2(g, i, j)] = F[k * g.plane + ix2(g, i, jsrc)];
+}
+
+template <typename R>
+static void halo_pack(const GeoD& g, R* const* f, int nf, int nlev, cudaStream_t s) {
+    PtrPack<R> pk{};
+    for (int q = 0; q < nf && q < 4; ++q) pk.f[q] = f[q];
+    if (g.px) {
+        const long n = (long)2 * OC_H * g.ny * nlev * nf;
+        k_halo_x_pack<R><<<nblocks(n, 256), 256, 0, s>>>(g, pk, nf, nlev);
+    }
+    if (g.py) {
+        const long n = (long)2 * OC_H * (g.nx + 2 * OC_H) * nlev * nf;
+        k_halo_y_pack<R><<<nblocks(n, 256), 256, 0, s>>>(g, pk, nf, nlev);
+    }
+}
+
+template <typename R>
+void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s) {
+    for (int q = 0; q < nf; q += 4) halo_pack<R>(g, f + q, nf - q < 4 ? nf - q : 4, g.nz, s);
+}
+
+template <typename R>
+void launch_halo2(const GeoD& g, R* f, cudaStream_t s) {
+    halo_pack<R>(g, &f, 1, 1, s);
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+namespace {
+
+// Neumaier-compensated pair (s, c)
+struct CSum {
+    double s, c;
+};
+__device__ __forceinline__ void cs_add(CSum& a, double x) {
+    const double t = a.s + x;
+    if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x;
+    else a.c += (x - t) + a.s;
+    a.s = t;
+}
+__device__ __forceinline__ void cs_merge(CSum& a, const CSum& b) {
+    cs_add(a, b.s);
+    a.c += b.c;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
+    GeoD g, DiagMetrics m, const R* __restrict__ u, const R* __restrict__ v,
+    const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ w,
+    const double* __restrict__ eta, double* __restrict__ partials) {
+    CSum sT{0, 0}, sS{0, 0}, sE{0, 0}, sK{0, 0}, sV{0, 0};
+    double cfl = 0.0;
+    int bad = 0;
+    const long ncol = (long)g.nx * g.ny;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncol;
+         c += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+        const long c2 = ix2(g, i, j);
+        const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
+        const double ac = m.Ac[j + OC_H], av = m.dxv[j + OC_H] * m.dy;
+        const double rdx = m.rdxc[j + OC_H];
+        for (int k = 0; k < g.nz; ++k) {
+            const long ck = k * g.plane + c2;
+            const double dz = m.dz[k];
+            const double tv = (double)T[ck] + m.Tref[k], sv = (double)S[ck] + m.Sref[k];
+            const double uv = (double)u[ck], vv = (double)v[ck];
+            if (!isfinite(tv) || !isfinite(sv) || !isfinite(uv) || !isfinite(vv)) bad = 1;
+            if (k >= kb) {
+                const double vol = ac * dz;
+                cs_add(sT, tv * vol);
+                cs_add(sS, sv * vol);
+                cs_add(sV, vol);
+                cfl = fmax(cfl, fabs((double)w[ck]) * m.dt / dz);
+            }
+            if (k >= ku) {
+                cs_add(sK, 0.5 * uv * uv * ac * dz);
+                cfl = fmax(cfl, fabs(uv) * m.dt * rdx);
+            }
+            if (k >= kv) {
+                cs_add(sK, 0.5 * vv * vv * av * dz);
+                cfl = fmax(cfl, fabs(vv) * m.dt * m.rdy);
+            }
+        }
+        if (kb < g.nz) cs_add(sE, eta[c2] * ac);
+        if (!isfinite(eta[c2])) bad = 1;
+    }
+    // block reduction in a fixed order
+    __shared__ CSum red[5][OC_DIAG_THREADS];
+    __shared__ double rc[OC_DIAG_THREADS];
+    __shared__ int rb[OC_DIAG_THREADS];
+    const int t = threadIdx.x;
+    red[0][t] = sT; red[1][t] = sS; red[2][t] = sE; red[3][t] = sK; red[4][t] = sV;
+    rc[t] = cfl;
+    rb[t] = bad;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int q = 0; q < 5; ++q) cs_merge(red[q][t], red[q][t + h]);
+            rc[t] = fmax(rc[t], rc[t + h]);
+            rb[t] |= rb[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double* o = partials + (long)blockIdx.x * 12;
+        for (int q = 0; q < 5; ++q) { o[2 * q] = red[q][0].s; o[2 * q + 1] = red[q][0].c; }
+        o[10] = rc[0];
+        o[11] = (double)rb[0];
+    }
+}
+
+__global__ void k_diag_final(const double* __restrict__ partials, int nblk, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    CSum a[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    double cfl = 0.0, bad = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        const double* o = partials + (long)b * 12;
+        for (int q = 0; q < 5; ++q) cs_merge(a[q], CSum{o[2 * q], o[2 * q + 1]});
+        cfl = fmax(cfl, o[10]);
+        bad = fmax(bad, o[11]);
+    }
+    out[0] = a[0].s + a[0].c;
+    out[1] = a[1].s + a[1].c;
+    out[2] = a[2].s + a[2].c;
+    out[3] = a[3].s + a[3].c;
+    out[4] = cfl;
+    out[5] = bad;
+    out[6] = a[4].s + a[4].c;
+    out[7] = 0.0;
+}
+
+}  // namespace
+
+size_t diag_partials_bytes() { return (size_t)OC_DIAG_BLOCKS * 12 * sizeof(double); }
+
+template <typename R>
+void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v, const R* T,
+                        const R* S, const R* w, const double* eta, double* partials,
+                        double* out, cudaStream_t s) {
+    k_diag_sums<R><<<OC_DIAG_BLOCKS, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, w, eta, partials);
+    k_diag_final<<<1, 32, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
+}
+
+// ------------------------------------------------------------------ instantiations
+
+#define OC_INST(R)                                                                          \
+    template int setup_kernel_attributes<R>(int);                                           \
+    template void launch_diag<R>(const KP<R>&, const StepBuffers<R>&, cudaStream_t);        \
+    template void launch_tracer<R>(const KP<R>&, const StepBuffers<R>&, bool, cudaStream_t); \
+    template void launch_momentum<R>(const KP<R>&, const StepBuffers<R>&, bool,             \
+                                     cudaStream_t);                                         \
+    template void launch_barotropic<R>(const KP<R>&, const StepBuffers<R>&, int, double, R, \
+                                       cudaStream_t);                                       \
+    template void launch_correct<R>(const KP<R>&, const StepBuffers<R>&, cudaStream_t);     \
+    template void launch_halo3<R>(const GeoD&, R* const*, int, cudaStream_t);               \
+    template void launch_halo2<R>(const GeoD&, R*, cudaStream_t);                           \
+    template void launch_diagnostics<R>(const GeoD&, const DiagMetrics&, const R*, const R*, \
+                                        const R*, const R*, const R*, const double*,        \
+                                        double*, double*, cudaStream_t);
+
+OC_INST(double)
+OC_INST(float)

@@ -1,0 +1,334 @@
+"""Thin Python binding of libocean (include/ocean.h): argument marshalling only.
+
+The functions below carry the C names and call straight into the CUDA library; every
+step of the ocean model runs in its kernels.  PyTorch supplies device memory (the
+arena passed to ocean_create_in) and the CUDA stream.  There is no CPU fallback: if
+the library cannot be loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from ctypes import POINTER, c_double, c_int, c_long, c_size_t, c_void_p
+from typing import Dict, Optional
+
+import numpy as np
+
+from . import build as _build
+
+OCEAN_OK = 0
+OCEAN_ERR = {-1: "OCEAN_ERR_ARG", -2: "OCEAN_ERR_CUDA", -3: "OCEAN_ERR_NONFINITE",
+             -4: "OCEAN_ERR_TIMEOUT", -5: "OCEAN_ERR_OOM", -6: "OCEAN_ERR_STATE"}
+OCEAN_FP64, OCEAN_MIXED = 0, 1
+OCEAN_CLOSURE_RI, OCEAN_CLOSURE_LEARNED = 0, 1
+
+FIELD = dict(u=0, v=1, T=2, S=3, eta=4, Gu_prev=5, Gv_prev=6, GT_prev=7, GS_prev=8, w=9, p=10,
+             kappa=11, nu=12, Gu=13, Gv=14, GT=15, GS=16, Hu=17, Hv=18, T_anom=19, S_anom=20)
+# everything a bitwise restart needs, besides the reference profiles and the step count
+CHECKPOINT_FIELDS = ["u", "v", "T_anom", "S_anom", "eta", "Gu_prev", "Gv_prev", "GT_prev",
+                     "GS_prev"]
+FIELDS_2D = {"eta", "Hu", "Hv"}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "ocean.h")
+
+
+class OceanGrid(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("periodic_x", c_int), ("periodic_y", c_int), ("x0", c_double), ("x1", c_double),
+                ("y0", c_double), ("y1", c_double), ("z_faces", POINTER(c_double))]
+
+
+class OceanParams(ctypes.Structure):
+    _fields_ = [("dt", c_double), ("n_substeps", c_int), ("chi", c_double), ("g", c_double),
+                ("rho0", c_double), ("alpha", c_double), ("beta_s", c_double), ("T0", c_double),
+                ("S0", c_double), ("f0", c_double), ("beta_plane", c_double),
+                ("omega", c_double), ("radius", c_double), ("nu0", c_double),
+                ("ri_a", c_double), ("nu_b", c_double), ("kappa_b", c_double),
+                ("kappa_conv", c_double), ("weno_eps", c_double), ("weno_linear", c_int),
+                ("min_depth", c_double), ("precision", c_int), ("closure", c_int),
+                ("check_every", c_int), ("taux", POINTER(c_double)), ("tauy", POINTER(c_double))]
+
+
+class OceanDiag(ctypes.Structure):
+    _fields_ = [("step", c_long), ("tracer_T", c_double), ("tracer_S", c_double),
+                ("volume_eta", c_double), ("ke", c_double), ("max_cfl", c_double),
+                ("wet_volume", c_double), ("nonfinite", c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+class OceanError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{OCEAN_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load libocean.so (building it in-tree first when sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed and _build.needs_build():
+            _build.build()
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libocean.so not built ({path}); run paper_2309_06662_gb300.build")
+        L = ctypes.CDLL(path)
+        pv, pd = c_void_p, POINTER(c_double)
+        sig = {
+            "ocean_arena_bytes": (c_int, [POINTER(OceanGrid), POINTER(OceanParams), POINTER(c_size_t)]),
+            "ocean_create": (c_int, [POINTER(OceanGrid), pd, POINTER(OceanParams), POINTER(pv)]),
+            "ocean_create_in": (c_int, [POINTER(OceanGrid), pd, POINTER(OceanParams), pv, c_size_t,
+                                        pv, POINTER(pv)]),
+            "ocean_destroy": (None, [pv]),
+            "ocean_last_error": (ctypes.c_char_p, [pv]),
+            "ocean_set_field": (c_int, [pv, c_int, pd, c_size_t]),
+            "ocean_get_field": (c_int, [pv, c_int, pd, c_size_t]),
+            "ocean_set_wind_stress": (c_int, [pv, pd, pd]),
+            "ocean_get_reference": (c_int, [pv, pd, pd]),
+            "ocean_set_reference": (c_int, [pv, pd, pd]),
+            "ocean_step": (c_int, [pv, c_int]),
+            "ocean_step_async": (c_int, [pv, c_int]),
+            "ocean_sync": (c_int, [pv]),
+            "ocean_tendencies": (c_int, [pv]),
+            "ocean_diagnostics": (c_int, [pv, POINTER(OceanDiag)]),
+            "ocean_get_step": (c_long, [pv]),
+            "ocean_set_step": (c_int, [pv, c_long]),
+            "ocean_stream": (pv, [pv]),
+            "ocean_weno_faces": (c_int, [pv, pv, pv, c_int, pv, c_int, c_double, c_int, pv]),
+            "ocean_tridiag_batched": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/ocean.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ocean_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(rc: int, h=None) -> None:
+    if rc != OCEAN_OK:
+        msg = load().ocean_last_error(h)
+        raise OceanError(rc, msg.decode() if msg else "")
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libocean needs a CUDA device; none is visible")
+    return torch
+
+
+def make_grid(case):
+    zf = np.ascontiguousarray(case.z_faces, dtype=np.float64)
+    g = OceanGrid(case.kind, case.nx, case.ny, case.nz, int(case.periodic_x),
+                  int(case.periodic_y), case.x0, case.x1, case.y0, case.y1, _dp(zf))
+    return g, zf
+
+
+def make_params(p: Dict[str, float], precision: int, taux=None, tauy=None, closure: int = 0,
+                check_every: int = 0):
+    keep = []
+    tx = ty = None
+    if taux is not None:
+        tx = np.ascontiguousarray(taux, dtype=np.float64)
+        keep.append(tx)
+    if tauy is not None:
+        ty = np.ascontiguousarray(tauy, dtype=np.float64)
+        keep.append(ty)
+    prm = OceanParams(
+        p["dt"], int(p["n_substeps"]), p["chi"], p["g"], p["rho0"], p["alpha"], p["beta_s"],
+        p["T0"], p["S0"], p["f0"], p["beta_plane"], p["omega"], p["radius"], p["nu0"], p["ri_a"],
+        p["nu_b"], p["kappa_b"], p["kappa_conv"], p["weno_eps"], int(p["weno_linear"]),
+        p["min_depth"], precision, closure, check_every,
+        _dp(tx) if tx is not None else None, _dp(ty) if ty is not None else None)
+    return prm, keep
+
+
+class Ocean:
+    """One model handle on the current CUDA device, in a torch-allocated arena."""
+
+    def __init__(self, case, precision: int = OCEAN_FP64, params: Optional[dict] = None,
+                 check_every: int = 0, own_memory: bool = False):
+        torch = _torch_cuda()
+        L = load()
+        p = dict(case.params)
+        if params:
+            p.update(params)
+        self.params = p
+        self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
+        self.precision = precision
+        grid, self._zf = make_grid(case)
+        prm, self._keep = make_params(p, precision, case.taux, case.tauy,
+                                      check_every=check_every)
+        depth = np.ascontiguousarray(case.depth, dtype=np.float64)
+        h = c_void_p()
+        self._arena = None
+        if own_memory:
+            _check(L.ocean_create(ctypes.byref(grid), _dp(depth), ctypes.byref(prm), ctypes.byref(h)))
+        else:
+            nbytes = c_size_t()
+            _check(L.ocean_arena_bytes(ctypes.byref(grid), ctypes.byref(prm), ctypes.byref(nbytes)))
+            self._arena = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+            base = self._arena.data_ptr()
+            aligned = (base + 255) & ~255
+            stream = torch.cuda.current_stream().cuda_stream
+            _check(L.ocean_create_in(ctypes.byref(grid), _dp(depth), ctypes.byref(prm),
+                                     c_void_p(aligned), nbytes.value, c_void_p(stream),
+                                     ctypes.byref(h)))
+        self._h = h
+        self.set("T", case.T)
+        self.set("S", case.S)
+        if case.u is not None:
+            self.set("u", case.u)
+        if case.v is not None:
+            self.set("v", case.v)
+        if case.eta is not None:
+            self.set("eta", case.eta)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().ocean_destroy(h)
+            self._h = None
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shape(self, name: str):
+        return (self.ny, self.nx) if name in FIELDS_2D else (self.nz, self.ny, self.nx)
+
+    def set(self, name: str, arr) -> None:
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        assert a.shape == self.shape(name), (name, a.shape)
+        _check(load().ocean_set_field(self._h, FIELD[name], _dp(a), a.size), self._h)
+
+    def get(self, name: str) -> np.ndarray:
+        out = np.zeros(self.shape(name))
+        _check(load().ocean_get_field(self._h, FIELD[name], _dp(out), out.size), self._h)
+        return out
+
+    def step(self, n: int = 1) -> None:
+        _check(load().ocean_step(self._h, int(n)), self._h)
+
+    def step_async(self, n: int = 1) -> None:
+        _check(load().ocean_step_async(self._h, int(n)), self._h)
+
+    def sync(self) -> None:
+        _check(load().ocean_sync(self._h), self._h)
+
+    def tendencies(self) -> None:
+        _check(load().ocean_tendencies(self._h), self._h)
+
+    def get_reference(self):
+        T = np.zeros(self.nz)
+        S = np.zeros(self.nz)
+        _check(load().ocean_get_reference(self._h, _dp(T), _dp(S)), self._h)
+        return T, S
+
+    def set_reference(self, Tref, Sref) -> None:
+        T = np.ascontiguousarray(Tref, dtype=np.float64)
+        S = np.ascontiguousarray(Sref, dtype=np.float64)
+        assert T.shape == (self.nz,) and S.shape == (self.nz,)
+        _check(load().ocean_set_reference(self._h, _dp(T), _dp(S)), self._h)
+
+    def checkpoint(self) -> Dict[str, np.ndarray]:
+        """The complete restart state (host arrays)."""
+        d = {f: self.get(f) for f in CHECKPOINT_FIELDS}
+        d["Tref"], d["Sref"] = self.get_reference()
+        d["step"] = np.array(self.nstep)
+        return d
+
+    def restore(self, d: Dict[str, np.ndarray]) -> None:
+        """Resume from checkpoint(): the continuation is the same bit for bit."""
+        self.set_reference(d["Tref"], d["Sref"])
+        for f in CHECKPOINT_FIELDS:
+            self.set(f, d[f])
+        self.nstep = int(d["step"])
+
+    def set_wind_stress(self, taux, tauy) -> None:
+        tx = np.ascontiguousarray(taux, dtype=np.float64)
+        ty = np.ascontiguousarray(tauy, dtype=np.float64)
+        _check(load().ocean_set_wind_stress(self._h, _dp(tx), _dp(ty)), self._h)
+
+    def diagnostics(self) -> Dict[str, float]:
+        d = OceanDiag()
+        _check(load().ocean_diagnostics(self._h, ctypes.byref(d)), self._h)
+        return dict(step=d.step, tracer_T=d.tracer_T, tracer_S=d.tracer_S,
+                    volume_eta=d.volume_eta, ke=d.ke, max_cfl=d.max_cfl,
+                    wet_volume=d.wet_volume, nonfinite=bool(d.nonfinite))
+
+    @property
+    def nstep(self) -> int:
+        return load().ocean_get_step(self._h)
+
+    @nstep.setter
+    def nstep(self, n: int) -> None:
+        _check(load().ocean_set_step(self._h, int(n)), self._h)
+
+    @property
+    def stream(self) -> int:
+        return load().ocean_stream(self._h) or 0
+
+
+def weno_faces(q, vel, inside=None, precision: int = OCEAN_FP64, eps: float = 1e-30,
+               linear: bool = False):
+    """ocean_weno_faces on torch CUDA tensors (returns a new tensor)."""
+    torch = _torch_cuda()
+    dt = torch.float64 if precision == OCEAN_FP64 else torch.float32
+    q = q.to(device="cuda", dtype=dt).contiguous()
+    vel = vel.to(device="cuda", dtype=dt).contiguous()
+    out = torch.empty_like(q)
+    ins = None
+    if inside is not None:
+        ins = inside.to(device="cuda", dtype=torch.uint8).contiguous()
+    s = torch.cuda.current_stream().cuda_stream
+    rc = load().ocean_weno_faces(c_void_p(q.data_ptr()), c_void_p(vel.data_ptr()),
+                                 c_void_p(ins.data_ptr()) if ins is not None else None,
+                                 q.numel(), c_void_p(out.data_ptr()), precision, eps, int(linear),
+                                 c_void_p(s))
+    _check(rc)
+    return out
+
+
+def tridiag_batched(a, b, c, d, precision: int = OCEAN_FP64):
+    """ocean_tridiag_batched on level-major [n, nsys] torch CUDA tensors."""
+    torch = _torch_cuda()
+    dt = torch.float64 if precision == OCEAN_FP64 else torch.float32
+    a, b, c, d = (t.to(device="cuda", dtype=dt).contiguous() for t in (a, b, c, d))
+    x = torch.empty_like(d)
+    n, nsys = d.shape
+    s = torch.cuda.current_stream().cuda_stream
+    rc = load().ocean_tridiag_batched(*(c_void_p(t.data_ptr()) for t in (a, b, c, d)),
+                                      c_void_p(x.data_ptr()), n, nsys, precision, c_void_p(s))
+    _check(rc)
+    return x

@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every symbol
+the public headers declare (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+from paper_2309_06662_gb300 import build, ocean
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b([a-z][a-z0-9_]+)\s*\([^;{]*\)\s*;", txt))
+    return sorted(n for n in names if not n.startswith(("sizeof", "if", "for")))
+
+
+def test_library_exports_every_declared_function():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert "ocean_step" in names and "ocean_create" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    L = ocean.load()
+    for n in ocean.header_functions():
+        assert getattr(L, n).argtypes is not None, n
+
+
+def test_arena_size_and_argument_errors_without_gpu():
+    # host-side validation paths run without touching a device
+    from paper_2309_06662_gb300 import inputs
+    c = inputs.box_case()
+    L = ocean.load()
+    g, _zf = ocean.make_grid(c)
+    prm, _keep = ocean.make_params(c.params, ocean.OCEAN_MIXED, c.taux, c.tauy)
+    nb = ctypes.c_size_t()
+    assert L.ocean_arena_bytes(ctypes.byref(g), ctypes.byref(prm), ctypes.byref(nb)) == 0
+    assert nb.value > 16 * 32 * 32 * 8 * 4
+    prm64, _k = ocean.make_params(c.params, ocean.OCEAN_FP64, c.taux, c.tauy)
+    nb64 = ctypes.c_size_t()
+    L.ocean_arena_bytes(ctypes.byref(g), ctypes.byref(prm64), ctypes.byref(nb64))
+    assert nb64.value > nb.value
+    bad = ocean.OceanGrid(0, 0, 4, 4, 0, 0, 0.0, 1.0, 0.0, 1.0, g.z_faces)
+    assert L.ocean_arena_bytes(ctypes.byref(bad), ctypes.byref(prm), ctypes.byref(nb)) == -1
+    assert b"grid sizes" in L.ocean_last_error(None)
+    prm.n_substeps = 0
+    assert L.ocean_arena_bytes(ctypes.byref(g), ctypes.byref(prm), ctypes.byref(nb)) == -1
+    prm.n_substeps = 30
+    h = ctypes.c_void_p()
+    assert L.ocean_create(ctypes.byref(g), None, ctypes.byref(prm), ctypes.byref(h)) == -1
+    assert L.ocean_step(None, 1) == -1
+    assert L.ocean_get_step(None) == -1
