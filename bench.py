@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of one baroclinic time step of the hydrostatic free-surface ocean on GB300.
+
+Workload (default): the 1/12-degree lat-lon configuration, 4320 x 1680 x 48 cells
+(70S-70N), dt = 300 s, 60 barotropic substeps, in the mixed-precision form (FP32 fields
+and stencils; FP64 free surface, barotropic averages and conservation sums).  Inputs are
+seeded and synthetic: random-field bathymetry and stratified T/S with noise stand in for
+the ECCO2-forced realistic domain of the paper (Sec. "How performance was measured").
+
+Prints one JSON line.  `value` is whole-job cell-updates/s (grid cells, land included,
+times steps, summed over ranks, over the max-over-ranks device time), state resident in
+HBM.  `e2e` is the same metric through the C ABI with host buffers: every step uploads
+the surface wind stress from host memory and reads the diagnostics back.  `--impl
+reference` times the CPU oracle instead, on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+import numpy as np  # noqa: E402
+
+from paper_2309_06662_gb300 import inputs, metrics, roofline  # noqa: E402
+
+WORKLOADS = {
+    "latlon_12th": (inputs.latlon_12th_case, "latlon_1/12deg_4320x1680x48"),
+    "latlon_quarter": (inputs.latlon_quarter_case, "latlon_1/4deg_1440x560x48"),
+    "latlon_1deg": (inputs.latlon_1deg_case, "latlon_1deg_360x160x32"),
+    "box": (inputs.box_case, "box_32x32x8"),
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for name in ("ocean_kernels.cu", "ocean_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2309_06662_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.flush()
+        with open(self.out.name) as f:
+            rows = [ln.strip().split(",") for ln in f if ln.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def window_case(case, i0: int, j0: int, wx: int, wy: int):
+    """The sub-window [i0, i0+wx) x [j0, j0+wy) of a lat-lon case (walls at its edges)."""
+    lat = case.y1
+    x0, x1, y0, y1 = inputs.latlon_window(case.nx, case.ny, lat, i0, j0, wx, wy)
+    sl = (slice(j0, j0 + wy), slice(i0, i0 + wx))
+    return inputs.Case(f"{case.name}_window", case.kind, wx, wy, case.nz, False, False,
+                       x0, x1, y0, y1, case.z_faces, case.depth[sl].copy(),
+                       case.taux[sl].copy(), case.tauy[sl].copy(),
+                       case.T[(slice(None),) + sl].copy(), case.S[(slice(None),) + sl].copy(),
+                       dict(case.params), steps=case.steps)
+
+
+def oracle_sample(case):
+    """The bounded sample of the workload the CPU oracle runs: a 96 x 96 column window of
+    a large lat-lon grid (walls at the window edges), or the whole grid when small."""
+    if case.kind == 1 and case.nx >= 200:
+        wx, wy = 96, 96
+        i0, j0 = case.nx // 2, case.ny // 2
+        desc = (f"{wx}x{wy}x{case.nz} window of the {case.nx}x{case.ny}x{case.nz} workload at "
+                f"(i0={i0}, j0={j0}), walls at the window edges")
+        return window_case(case, i0, j0, wx, wy), desc
+    return case, f"the full {case.nx}x{case.ny}x{case.nz} workload"
+
+
+def run_oracle_sample(case, seconds: float, warmup: int = 1, steps_cap: int = 10_000):
+    """Time the CPU oracle on the bounded sample for about `seconds`; cell-updates/s."""
+    import oracle
+    sample, desc = oracle_sample(case)
+    m = oracle.OracleModel(sample)
+    m.step(warmup)   # the forward-Euler first step stays outside the timing
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_cap:
+        m.step(1)
+        n += 1
+        if time.perf_counter() - t0 >= seconds and n >= 2:
+            break
+    dt = time.perf_counter() - t0
+    cells = sample.nx * sample.ny * sample.nz
+    return {"value": cells * n / dt, "unit": "cell-updates/s", "kind": "oracle",
+            "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+            "sample": f"{desc}; {n} steps in {dt:.1f} s (plain FP64 C, OpenMP over rows)",
+            "s_per_step": dt / n}
+
+
+# ----------------------------------------------------------------------------- main
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="latlon_12th")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def reference_arm(args, rank: int):
+    """The oracle on the host cores, on the same workload's config, metric and unit: W
+    untimed steps, then K timed steps of the bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    make, wname = WORKLOADS[args.workload]
+    case = make()
+    sample, desc = oracle_sample(case)
+    m = oracle.OracleModel(sample)
+    m.step(max(1, args.warmup))
+    t0 = time.perf_counter()
+    m.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sample.nx * sample.ny * sample.nz * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    line = {
+        "impl": "reference", "metric": "cell_updates_per_s", "value": value,
+        "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(case, wname, "FP64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "kind": "oracle",
+                         "cores": cores,
+                         "sample": f"{desc}; {args.steps} steps in {dt:.1f} s (plain FP64 C, "
+                                   f"OpenMP over rows)"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(case, wname, precision):
+    p = case.params
+    return {"workload": wname, "nx": case.nx, "ny": case.ny, "nz": case.nz,
+            "cells": case.cells, "dt_s": p["dt"], "n_substeps": int(p["n_substeps"]),
+            "precision": precision, "parallelism": "replicas (one full model per GPU)",
+            "l2": "inputs larger than L2 (every 3-D field > 1 GB)"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    from paper_2309_06662_gb300 import ocean
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    make, wname = WORKLOADS[args.workload]
+    case = make()
+    p = case.params
+    wet = roofline.wet_cells(case.depth, case.z_faces, p["min_depth"])
+    wet_cols = roofline.wet_columns(case.depth, p["min_depth"], case.z_faces)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- mixed, device-resident
+    m = ocean.Ocean(case, precision=ocean.OCEAN_MIXED)
+    m.step_async(args.warmup)
+    m.sync()
+    barrier()
+    launches0 = m.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        m.profile(True)
+        barrier()
+        ev0.record()
+        m.step_async(args.steps)
+        ev1.record()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phases, nprof = m.phase_times()
+    m.profile(False)
+    launches = m.launches - launches0
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = metrics.cell_updates_per_s(case.nx, case.ny, case.nz, ms_all / 1e3, replicas=world)
+
+    # ---------------------------------------------------------------- roofline of the top kernel
+    peak, peak_src = measured_peaks()
+    esz = 4
+    single = {k: phases[k] / nprof for k in roofline.KERNEL_WORDS}
+    top = max(single, key=single.get)
+    top_ms = single[top]
+    algo = roofline.KERNEL_WORDS[top] * esz * wet
+    achieved = algo / (top_ms / 1e3) / 1e9
+    traffic = roofline.load_traffic(os.path.join(ROOT, "profiles", "traffic.txt"), wname,
+                                    source_digest())
+    tr = traffic.get(top) * wet if traffic and top in traffic else None
+    step_bytes = roofline.STEP_WORDS_PER_CELL * esz * wet + \
+        roofline.barotropic_bytes_per_column(esz, int(p["n_substeps"])) * wet_cols
+    phase_frac = {}
+    for k in roofline.KERNEL_WORDS:
+        t = phases[k] / nprof
+        phase_frac[k] = {"ms": round(t, 4),
+                         "GBs": round(roofline.KERNEL_WORDS[k] * esz * wet / (t / 1e3) / 1e9, 1),
+                         "frac": round(roofline.KERNEL_WORDS[k] * esz * wet / (t / 1e3) / 1e9 / peak, 3)}
+    tb = phases["barotropic"] / nprof
+    bb = roofline.barotropic_bytes_per_column(esz, int(p["n_substeps"])) * wet_cols
+    phase_frac["barotropic"] = {"ms": round(tb, 4), "GBs": round(bb / (tb / 1e3) / 1e9, 1),
+                                "frac": round(bb / (tb / 1e3) / 1e9 / peak, 3),
+                                "kernels": 2 * int(p["n_substeps"]) + 2}
+
+    # ---------------------------------------------------------------- end to end, host buffers
+    taux = torch.from_numpy(np.ascontiguousarray(case.taux)).pin_memory().numpy()
+    tauy = torch.from_numpy(np.ascontiguousarray(case.tauy)).pin_memory().numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        m.set_wind_stress(taux, tauy)
+        m.step_async(1)
+        d = m.diagnostics()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = metrics.cell_updates_per_s(case.nx, case.ny, case.nz, e2e_s, replicas=world)
+    healthy = not d["nonfinite"] and d["max_cfl"] < 1.0
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- plain FP64 path
+    fp64 = None
+    if args.fp64_steps > 0:
+        m64 = ocean.Ocean(case, precision=ocean.OCEAN_FP64)
+        m64.step_async(1)
+        m64.sync()
+        barrier()
+        ev0.record()
+        m64.step_async(args.fp64_steps)
+        ev1.record()
+        barrier()
+        ms64 = ev0.elapsed_time(ev1) / args.fp64_steps
+        m64.close()
+        del m64
+        torch.cuda.empty_cache()
+        v64 = metrics.cell_updates_per_s(case.nx, case.ny, case.nz, ms64 / 1e3, replicas=world)
+        fp64 = {"value": v64, "ms_per_step": ms64, "steps": args.fp64_steps,
+                "mixed_over_fp64": value / v64}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_sample(case, args.cpu_seconds)
+        cpu.pop("s_per_step", None)
+
+    if rank == 0:
+        line = {
+            "metric": "cell_updates_per_s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded random-field bathymetry, stratified T/S with noise, "
+                    "zonal wind 0.1 cos(3 lat); stands in for the ECCO2-forced domains)",
+            "config": config_block(case, wname, "mixed (FP32 fields and stencils; FP64 free "
+                                                 "surface, barotropic averages, sums)"),
+            "sypd": metrics.sypd(p["dt"], ms_all / 1e3),
+            "sim_days_per_day": metrics.sim_days_per_day(p["dt"], ms_all / 1e3),
+            "wet_cells": wet,
+            "step_hbm": {"algorithmic_bytes": step_bytes,
+                         "GBs": step_bytes / (ms_all / 1e3) / 1e9,
+                         "frac": step_bytes / (ms_all / 1e3) / 1e9 / peak,
+                         "of": peak_src},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+                         "algorithmic_bytes_per_launch": algo, "ms_per_launch": top_ms,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "phases": phase_frac,
+            "fp64": fp64,
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": int(taux.nbytes + tauy.nbytes),
+                    "d2h_bytes_per_step": 8 * 8, "healthy": healthy,
+                    "what": "per step: wind stress host->device, one step, diagnostics "
+                            "(conservation sums, CFL, NaN check) device->host"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

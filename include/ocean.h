@@ -180,6 +180,23 @@ int ocean_set_step(ocean_t h, long step);
 /* The handle's stream (a cudaStream_t). */
 void* ocean_stream(ocean_t h);
 
+/* Per-phase timing of ocean_step: with profiling on, every step records CUDA events on
+ * the handle's stream between its phases.  enable = 1 clears the totals and starts,
+ * 0 stops (both wait for queued work).  ocean_phase_times waits for the stream and
+ * returns in ms[0..n) the summed device time of each phase over the steps timed so far
+ * (*steps).  Phases: */
+#define OCEAN_PHASE_DIAG 0         /* pressure, w, Richardson-number closure */
+#define OCEAN_PHASE_TRACER 1       /* T, S tendencies + AB2 + vertical diffusion */
+#define OCEAN_PHASE_MOMENTUM 2     /* u, v tendencies + AB2 + vertical viscosity */
+#define OCEAN_PHASE_BAROTROPIC 3   /* split-explicit sub-cycle and averaging */
+#define OCEAN_PHASE_CORRECT 4      /* barotropic correction and halo copies */
+#define OCEAN_NPHASE 5
+int ocean_profile(ocean_t h, int enable);
+int ocean_phase_times(ocean_t h, double* ms, int n, long* steps);
+
+/* Number of kernels this handle has enqueued so far (all entry points). */
+long ocean_kernel_launches(ocean_t h);
+
 /* ---- component entry points (device pointers, caller-owned, on `stream`) ---- */
 
 /* Adaptive-order WENO-Z reconstruction on a periodic 1-D row (Sec. "New numerical

@@ -71,6 +71,12 @@ struct ocean_s {
     std::vector<double> h_rows[8];   // dxc rdxc dxv rAc rAz fu fv Ac
     std::vector<double> Tref, Sref, h_Hu, h_Hv;
     bool ref_locked = false;   // reference profiles fixed by ocean_set_reference
+    // per-phase timing: events recorded on the stream around each phase of a step
+    bool prof = false;
+    std::vector<std::vector<cudaEvent_t>> prof_pending;
+    double phase_ms[OCEAN_NPHASE] = {};
+    long prof_steps = 0;
+    long launches = 0;         // kernels enqueued by this handle
     double dy = 0;
     int cur = 0;
     long nstep = 0;
@@ -442,21 +448,44 @@ StepBuffers<R> make_bufs(const ocean_t m) {
     return b;
 }
 
+// kernels one step enqueues (each periodic direction adds one halo kernel per halo fill)
+long launches_per_step(const ocean_t m) {
+    const long hk = (m->px ? 1 : 0) + (m->py ? 1 : 0);
+    const long ns = m->prm.n_substeps;
+    return 3 + (hk + 1 + ns * (2 + 3 * hk) + 1) + 1 + hk;
+}
+
 template <typename R>
 void enqueue_step(ocean_t m) {
     const bool first = m->nstep == 0;
     const KP<R> k = make_kp<R>(m, first);
     const StepBuffers<R> b = make_bufs<R>(m);
     cudaStream_t s = m->stream;
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&]() {
+        if (!m->prof) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    };
+    mark();
     launch_diag<R>(k, b, s);
+    mark();
     launch_tracer<R>(k, b, true, s);
+    mark();
     launch_momentum<R>(k, b, true, s);
+    mark();
     launch_barotropic<R>(k, b, m->prm.n_substeps, m->prm.dt, (R)m->prm.g, s);
+    mark();
     launch_correct<R>(k, b, s);
     if (m->px || m->py) {
         R* f[4] = {b.un, b.vn, b.Tn, b.Sn};
         launch_halo3<R>(k.g, f, 4, s);
     }
+    mark();
+    if (m->prof) m->prof_pending.push_back(ev);
+    m->launches += launches_per_step(m);
     m->cur = 1 - m->cur;
     m->nstep += 1;
     m->tend_valid = false;
@@ -655,6 +684,8 @@ int ocean_create_in(const ocean_grid* grid, const double* depth, const ocean_par
 void ocean_destroy(ocean_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& ev : h->prof_pending)
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (h->own_arena && h->arena) cudaFree(h->arena);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -819,6 +850,41 @@ int ocean_diagnostics(ocean_t h, ocean_diag* out) {
     out->wet_volume = d[6];
     return OCEAN_OK;
 }
+
+int ocean_profile(ocean_t h, int enable) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto& ev : h->prof_pending)
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    h->prof_pending.clear();
+    if (enable) {
+        for (double& x : h->phase_ms) x = 0.0;
+        h->prof_steps = 0;
+    }
+    h->prof = enable != 0;
+    return OCEAN_OK;
+}
+
+int ocean_phase_times(ocean_t h, double* ms, int n, long* steps) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!ms || n < 0) return fail(h, OCEAN_ERR_ARG, "bad output");
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto& ev : h->prof_pending) {
+        for (size_t q = 0; q + 1 < ev.size() && q < OCEAN_NPHASE; ++q) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+            h->phase_ms[q] += t;
+        }
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        h->prof_steps += 1;
+    }
+    h->prof_pending.clear();
+    for (int q = 0; q < n && q < OCEAN_NPHASE; ++q) ms[q] = h->phase_ms[q];
+    if (steps) *steps = h->prof_steps;
+    return OCEAN_OK;
+}
+
+long ocean_kernel_launches(ocean_t h) { return h ? h->launches : -1; }
 
 long ocean_get_step(ocean_t h) { return h ? h->nstep : -1; }
 

@@ -16,6 +16,7 @@ magnitude.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field, replace
 from typing import Dict, Optional
 
@@ -178,22 +179,62 @@ def _zc(zf: np.ndarray) -> np.ndarray:
     return 0.5 * (zf[1:] + zf[:-1])
 
 
+def _noise_on_grid(seed: int, stream: int, level: int, ny: int, nx: int, lon0: float,
+                   dlon: float, lat0: float, dlat: float, noise_deg: Optional[float],
+                   periodic_x: bool) -> np.ndarray:
+    """N(0,1) noise for one level.  With noise_deg, the draws sit on a noise_deg grid
+    (periodic in longitude) and are interpolated bilinearly to the cell centres, which
+    gives them a correlation length of about noise_deg; without, one draw per cell."""
+    if noise_deg is None:
+        return random_normal(seed, stream, ny * nx, start=level * ny * nx).reshape(ny, nx)
+    nxc = max(1, int(round(nx * dlon / noise_deg)))
+    nyc = max(2, int(round(ny * dlat / noise_deg)) + 1)
+    base = random_normal(seed, stream, nyc * nxc, start=level * nyc * nxc).reshape(nyc, nxc)
+    fy = (lat0 + (np.arange(ny) + 0.5) * dlat - lat0) / noise_deg - 0.5
+    fy = np.clip(fy, 0.0, nyc - 1.0)
+    jy0 = np.minimum(np.floor(fy).astype(int), nyc - 2)
+    wy = (fy - jy0)[:, None]
+    rows = (1.0 - wy) * base[jy0] + wy * base[jy0 + 1]
+    fx = ((np.arange(nx) + 0.5) * dlon) / noise_deg - 0.5
+    ix0 = np.floor(fx).astype(int)
+    wx = (fx - ix0)[None, :]
+    if periodic_x:
+        i0, i1 = ix0 % nxc, (ix0 + 1) % nxc
+    else:
+        i0, i1 = np.clip(ix0, 0, nxc - 1), np.clip(ix0 + 1, 0, nxc - 1)
+    return (1.0 - wx) * rows[:, i0] + wx * rows[:, i1]
+
+
 def _stratified(zf: np.ndarray, ny: int, nx: int, seed: int, t_top: float, t_bot: float,
-                s_top: float, s_bot: float, noise: float) -> tuple:
+                s_top: float, s_bot: float, noise: float, grid=None,
+                noise_deg: Optional[float] = None) -> tuple:
+    """T and S linear in depth (top and bottom values) plus `noise` times N(0,1) noise.
+    `grid` = (lon0, dlon, lat0, dlat, periodic_x) places the noise for noise_deg."""
     nz = len(zf) - 1
     H = -zf[0]
     zc = _zc(zf)
     frac = (zc + H) / H                      # 0 at the bottom, 1 at the top
     T = np.empty((nz, ny, nx))
     S = np.empty((nz, ny, nx))
-    n2 = ny * nx
-    for k in range(nz):
+    lon0, dlon, lat0, dlat, px = grid if grid is not None else (0.0, 1.0, 0.0, 1.0, True)
+
+    def level(k):
         T[k] = t_bot + (t_top - t_bot) * frac[k]
         S[k] = s_bot + (s_top - s_bot) * frac[k]
         if noise > 0:
-            T[k] += noise * random_normal(seed, 2, n2, start=k * n2).reshape(ny, nx)
+            T[k] += noise * _noise_on_grid(seed, 2, k, ny, nx, lon0, dlon, lat0, dlat,
+                                           noise_deg, px)
             if s_top != s_bot:
-                S[k] += noise * random_normal(seed, 3, n2, start=k * n2).reshape(ny, nx)
+                S[k] += noise * _noise_on_grid(seed, 3, k, ny, nx, lon0, dlon, lat0, dlat,
+                                               noise_deg, px)
+
+    if ny * nx * nz >= 1 << 22:      # large grids: levels in parallel (numpy releases the GIL)
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(level, range(nz)))
+    else:
+        for k in range(nz):
+            level(k)
     return T, S
 
 
@@ -216,12 +257,14 @@ def box_case(nx: int = 32, ny: int = 32, nz: int = 8, seed: int = 1) -> Case:
 
 
 def latlon_case(nx: int, ny: int, nz: int, lat: float, seed: int, dt: float, n_substeps: int,
-                steps: int, name: str, noise: float = 0.05, corr_deg: float = 10.0) -> Case:
+                steps: int, name: str, noise: float = 0.05, corr_deg: float = 10.0,
+                noise_deg: Optional[float] = 1.0) -> Case:
     """Global lat-lon channel from -lat to +lat, periodic in longitude, walls at both ends.
 
     Stretched levels to 5000 m, random-field bathymetry, zonal wind 0.1 cos(3 phi) N/m^2,
     T linear 20 -> 2 C and S linear 34.5 -> 35 with depth, each with `noise`-amplitude
-    N(0,1) perturbations.
+    N(0,1) perturbations drawn on a noise_deg grid (1 degree: one draw per cell of the
+    1-degree grid, a mesoscale correlation length on finer grids).
     """
     zf = stretched_z_faces(nz, 5000.0, 3.0)
     dlon = 360.0 / nx
@@ -230,7 +273,8 @@ def latlon_case(nx: int, ny: int, nz: int, lat: float, seed: int, dt: float, n_s
     phi = np.deg2rad(-lat + (np.arange(ny) + 0.5) * dlat)
     taux = np.repeat((0.1 * np.cos(3.0 * phi))[:, None], nx, axis=1)
     tauy = np.zeros((ny, nx))
-    T, S = _stratified(zf, ny, nx, seed, 20.0, 2.0, 34.5, 35.0, noise)
+    T, S = _stratified(zf, ny, nx, seed, 20.0, 2.0, 34.5, 35.0, noise,
+                       grid=(0.0, dlon, -lat, dlat, True), noise_deg=noise_deg)
     p = default_params()
     p.update(dt=dt, n_substeps=n_substeps)
     return Case(name, 1, nx, ny, nz, True, False, 0.0, 360.0, -lat, lat, zf, depth, taux,
@@ -242,9 +286,21 @@ def latlon_1deg_case(seed: int = 2) -> Case:
     return latlon_case(360, 160, 32, 80.0, seed, 1200.0, 40, 1000, "latlon_1deg")
 
 
-def latlon_12th_case(seed: int = 3) -> Case:
-    """1/12-degree, 4320 x 1680 x 48, 70S-70N, dt = 300 s, 60 substeps, 200 steps."""
-    return latlon_case(4320, 1680, 48, 70.0, seed, 300.0, 60, 200, "latlon_12th")
+def latlon_12th_case(seed: int = 3, dt: float = 180.0) -> Case:
+    """1/12-degree, 4320 x 1680 x 48, 70S-70N, 60 substeps, 200 steps.
+
+    dt = 180 s, the paper's own step for its 1/12-degree, 48-level run (table of GPU
+    model performance).  At 300 s the explicit quasi-AB2 step is past its internal
+    gravity-wave limit next to 70 degrees (dx = 3.2 km, first-mode speed ~4.4 m/s with
+    this stratification: omega dt ~ 0.88 for the shortest waves, while chi = 0.1 damps
+    only below ~0.63) and the state diverges within about 30 steps."""
+    return latlon_case(4320, 1680, 48, 70.0, seed, dt, 60, 200, "latlon_12th")
+
+
+def latlon_quarter_case(seed: int = 6) -> Case:
+    """1/4-degree, 1440 x 560 x 48, 70S-70N, dt = 900 s, 60 substeps (a profiling-size
+    member of the same recipe: every 3-D FP32 field is larger than L2)."""
+    return latlon_case(1440, 560, 48, 70.0, seed, 900.0, 60, 200, "latlon_quarter")
 
 
 def latlon_half_case(seed: int = 4, lat: float = 80.0) -> Case:

@@ -105,6 +105,9 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_get_step": (c_long, [pv]),
             "ocean_set_step": (c_int, [pv, c_long]),
             "ocean_stream": (pv, [pv]),
+            "ocean_profile": (c_int, [pv, c_int]),
+            "ocean_phase_times": (c_int, [pv, pd, c_int, POINTER(c_long)]),
+            "ocean_kernel_launches": (c_long, [pv]),
             "ocean_weno_faces": (c_int, [pv, pv, pv, c_int, pv, c_int, c_double, c_int, pv]),
             "ocean_tridiag_batched": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
         }
@@ -294,6 +297,21 @@ class Ocean:
     @nstep.setter
     def nstep(self, n: int) -> None:
         _check(load().ocean_set_step(self._h, int(n)), self._h)
+
+    PHASES = ["diag", "tracer", "momentum", "barotropic", "correct"]
+
+    def profile(self, enable: bool) -> None:
+        _check(load().ocean_profile(self._h, int(enable)), self._h)
+
+    def phase_times(self):
+        ms = np.zeros(len(self.PHASES))
+        n = c_long()
+        _check(load().ocean_phase_times(self._h, _dp(ms), len(ms), ctypes.byref(n)), self._h)
+        return dict(zip(self.PHASES, ms.tolist())), n.value
+
+    @property
+    def launches(self) -> int:
+        return load().ocean_kernel_launches(self._h)
 
     @property
     def stream(self) -> int:

@@ -1,0 +1,72 @@
+"""Algorithmic byte counts of the step's kernels (host-side bookkeeping for the roofline).
+
+"Algorithmic" means every field a kernel must read is read once and every field it must
+write is written once, per wet cell (3-D kernels) or per wet column (barotropic), at the
+storage size `esz` of the path (4 bytes in the mixed form, 8 in FP64).  Neighbour reads
+of a stencil are cache hits by construction and are not counted again.
+
+Whole step (the compulsory traffic of the method): read u, v, T, S and the four
+tendencies of the previous step, write u, v, T, S and the four new tendencies: 16
+words per cell, plus the 2-D barotropic state once per step.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+STEP_WORDS_PER_CELL = 16
+
+# per wet cell, in words of the path's storage size
+KERNEL_WORDS = {
+    # reads T, S, u, v; writes w, p, kappa, nu
+    "diag": 8,
+    # reads T, S, u, v, w, kappa, G_T, G_S; writes G_T, G_S, T, S
+    "tracer": 12,
+    # reads u, v, w, p, nu, G_u, G_v; writes G_u, G_v, u, v
+    "momentum": 11,
+    # reads and writes u, v
+    "correct": 4,
+}
+
+
+def barotropic_bytes_per_column(esz: int, n_substeps: int, flush_every: int = 8) -> float:
+    """Bytes the split-explicit sub-cycle moves per wet column and step, as written:
+    begin (U^n, V^n, H_u, H_v, eta^n in; U, V, deta, partial sums, gradients and the
+    FP64 accumulators out), per substep the deta kernel (U, V, deta, partial in; deta,
+    partial out) and the U/V kernel (14 words in, 4 out), a flush of the partial sums
+    into the FP64 accumulators every `flush_every` substeps, and the end kernel."""
+    begin = 12 * esz + 8 + 24
+    sub = 24 * esz
+    flushes = -(-n_substeps // flush_every)
+    end = 8 * esz + 40
+    return begin + n_substeps * sub + flushes * (48 + esz) + end
+
+
+def wet_cells(depth: np.ndarray, z_faces: np.ndarray, min_depth: float) -> int:
+    """Number of wet cells under the full-cell rule (centre above the sea floor)."""
+    zc = 0.5 * (z_faces[1:] + z_faces[:-1])
+    d = np.where(depth >= min_depth, depth, 0.0)
+    return int(sum(np.count_nonzero(zc[k] > -d) for k in range(len(zc))))
+
+
+def wet_columns(depth: np.ndarray, min_depth: float, z_faces: np.ndarray) -> int:
+    zc_top = 0.5 * (z_faces[-1] + z_faces[-2])
+    return int(np.count_nonzero((depth >= min_depth) & (zc_top > -depth)))
+
+
+def load_traffic(path: str, workload: str, source_digest: str) -> Optional[Dict[str, float]]:
+    """Per-kernel DRAM bytes per wet cell of `workload` from a committed ncu summary
+    (lines "traffic_json: {...}"), or None when none matches or the summary was taken on
+    a different kernel source (its digest no longer matches)."""
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic_json:"):
+                d = json.loads(line.split(":", 1)[1])
+                if d.get("workload") == workload and d.get("source_digest") == source_digest:
+                    return d.get("bytes_per_wet_cell")
+    return None
