@@ -53,7 +53,7 @@ struct ocean_s {
     // device pointers (3-D fields of element size esz)
     void *u[2] = {}, *v[2] = {}, *T[2] = {}, *S[2] = {};
     void *Gu = nullptr, *Gv = nullptr, *GT = nullptr, *GS = nullptr;
-    void *w = nullptr, *p = nullptr, *kap = nullptr, *nu = nullptr;
+    void *w = nullptr, *p = nullptr, *kap = nullptr, *nu = nullptr, *wk = nullptr;
     // 2-D of element size esz
     void *taux_s = nullptr, *tauy_s = nullptr, *Un = nullptr, *Vn = nullptr, *GU = nullptr,
          *GV = nullptr, *Su = nullptr, *Sv = nullptr, *Ub = nullptr, *Vb = nullptr,
@@ -162,7 +162,7 @@ size_t layout(ocean_t m, char* base) {
     auto f2 = [&]() { return (void*)c.take<char>(n2 * e); };
     for (int b = 0; b < 2; ++b) { m->u[b] = f3(); m->v[b] = f3(); m->T[b] = f3(); m->S[b] = f3(); }
     m->Gu = f3(); m->Gv = f3(); m->GT = f3(); m->GS = f3();
-    m->w = f3(); m->p = f3(); m->kap = f3(); m->nu = f3();
+    m->w = f3(); m->p = f3(); m->kap = f3(); m->nu = f3(); m->wk = f3();
     void** two[] = {&m->taux_s, &m->tauy_s, &m->Un, &m->Vn, &m->GU, &m->GV, &m->Su, &m->Sv,
                     &m->Ub, &m->Vb, &m->dE, &m->paccE, &m->paccU, &m->paccV, &m->gxe, &m->gye,
                     &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv};
@@ -437,7 +437,7 @@ StepBuffers<R> make_bufs(const ocean_t m) {
     b.u = P(m->u[c]); b.v = P(m->v[c]); b.T = P(m->T[c]); b.S = P(m->S[c]);
     b.un = P(m->u[n]); b.vn = P(m->v[n]); b.Tn = P(m->T[n]); b.Sn = P(m->S[n]);
     b.Gu = P(m->Gu); b.Gv = P(m->Gv); b.GT = P(m->GT); b.GS = P(m->GS);
-    b.w = P(m->w); b.p = P(m->p); b.kap = P(m->kap); b.nu = P(m->nu);
+    b.w = P(m->w); b.p = P(m->p); b.kap = P(m->kap); b.nu = P(m->nu); b.wk = P(m->wk);
     b.taux_s = P(m->taux_s); b.tauy_s = P(m->tauy_s);
     b.Un = P(m->Un); b.Vn = P(m->Vn); b.GU = P(m->GU); b.GV = P(m->GV); b.Su = P(m->Su); b.Sv = P(m->Sv);
     b.Ub = P(m->Ub); b.Vb = P(m->Vb); b.dE = P(m->dE); b.paccE = P(m->paccE);

@@ -120,7 +120,8 @@ template <typename R> struct StepBuffers {
     const R *u, *v, *T, *S;
     R *un, *vn, *Tn, *Sn;
     R *Gu, *Gv, *GT, *GS;      // G^{n-1} in, G^n out
-    R *w, *p, *kap, *nu;       // diagnostics
+    R *w, *p, *kap, *nu;       // diagnostics (kap also holds the tracers' Thomas c')
+    R *wk;                     // 3-D scratch (the v-viscosity Thomas c')
     const R *taux_s, *tauy_s;  // wind stress / (rho0 dz_top)
     R *Un, *Vn, *GU, *GV, *Su, *Sv;         // column sums (2-D)
     R *Ub, *Vb, *dE, *paccE, *paccU, *paccV, *gxe, *gye, *corrU, *corrV;

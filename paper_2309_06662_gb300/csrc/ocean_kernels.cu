@@ -7,15 +7,17 @@
 //               Richardson-number kappa and nu: the two intermediates the paper's fused
 //               tendency kernels depend on (pressure and vertical diffusivity)
 //   k_tracer    WENO-Z flux-form T and S tendencies, quasi-AB2 predictor and the
-//               backward-Euler vertical diffusion (Thomas) of the same column, fused
+//               backward-Euler vertical diffusion (Thomas) of the same column, fused;
+//               2.5-D tiled (see "tile layout")
 //   k_momentum  vector-invariant u and v tendencies (WENO-Z vorticity flux, Coriolis,
 //               kinetic-energy and pressure gradients, vertical advection, wind),
-//               quasi-AB2, vertical viscosity solve, column sums for the barotropic mode
+//               quasi-AB2, vertical viscosity solve, column sums for the barotropic mode;
+//               2.5-D tiled
 //   k_baro_*    split-explicit barotropic sub-cycle with equal-weight averaging
 //   k_correct   barotropic correction of u and v
 //   k_halo*     periodic halo copies
-// One thread owns one water column in the column kernels; threads of a warp hold
-// neighbouring columns of a row, so every level access is coalesced.
+// One thread owns one water column; threads of a warp hold neighbouring columns of a
+// row, so every level access is coalesced.
 #include "ocean_internal.cuh"
 
 namespace {
@@ -103,301 +105,455 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
     }
 }
 
+// ------------------------------------------------------------------ tile layout
+
+// The tracer and momentum kernels are 2.5-D tiled: a block of TX x TY threads owns a
+// TX x TY patch of columns and marches up through the levels.  At each level it stages
+// the patch (plus the halo its stencils reach) in shared memory, computes every face
+// flux / corner vorticity once, then each thread finishes its own cell.  Vertical
+// stencils use a per-thread register window.  The Thomas coefficients of the implicit
+// solve go to global scratch (one value per level and column, written and read back by
+// the same thread, so they stay in L2), which keeps shared memory small and occupancy
+// bounded by registers only.
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+
+// padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
+// the domain stage a few columns beyond it, whose values only feed threads that are
+// themselves outside the domain
+__device__ __forceinline__ long tix(const GeoD& g, int i, int j) {
+    i = i < g.nx + OC_H - 1 ? i : g.nx + OC_H - 1;
+    j = j < g.ny + OC_H - 1 ? j : g.ny + OC_H - 1;
+    return ix2(g, i, j);
+}
+
 // ------------------------------------------------------------------ tracers
 
-// Horizontal advective fluxes through the u-face (i, j, k): the transport U = u dy dz and
-// U T'~, U S'~.  WENO is translation-equivariant (candidates have unit coefficient sums,
-// indicators see differences only), so reconstructing the anomalies along a level and
-// adding U Tref(k) is the same flux as reconstructing T itself.
 template <typename R>
-__device__ __forceinline__ void xflux(const KP<R>& p, const R* __restrict__ u,
-                                      const R* __restrict__ T, const R* __restrict__ S, int i,
-                                      int j, int k, R& fU, R& fT, R& fS) {
-    const GeoD& g = p.g;
-    const long c2 = ix2(g, i, j);
-    if (k < g.kbu[c2]) { fU = R(0); fT = R(0); fS = R(0); return; }
-    const long ck = k * g.plane + c2;
-    const R ut = u[ck];
-    R qT[5], qS[5];
-    unsigned in = 0;
-#pragma unroll
-    for (int n = 0; n < 5; ++n) {
-        const int o = ut >= R(0) ? n - 3 : 2 - n;
-        qT[n] = T[ck + o];
-        qS[n] = S[ck + o];
-        in |= (k >= g.kb[c2 + o] ? 1u : 0u) << n;
-    }
-    const R U = ut * p.dy * p.dz[k];
-    fU = U;
-    fT = U * weno_adaptive(qT, in, p.eps, p.linear);
-    fS = U * weno_adaptive(qS, in, p.eps, p.linear);
-}
+struct TracerSmem {
+    R T[TY + 6][TX + 6], S[TY + 6][TX + 6];           // anomalies of level k, halo 3
+    short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
+    short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
+    R fxU[TY][TX + 1], fxT[TY][TX + 1], fxS[TY][TX + 1];   // x-face transport and fluxes
+    R fyV[TY + 1][TX], fyT[TY + 1][TX], fyS[TY + 1][TX];   // y-face transport and fluxes
+    int kmin;
+};
 
-template <typename R>
-__device__ __forceinline__ void yflux(const KP<R>& p, const R* __restrict__ v,
-                                      const R* __restrict__ T, const R* __restrict__ S, int i,
-                                      int j, int k, R& fV, R& fT, R& fS) {
-    const GeoD& g = p.g;
-    const long c2 = ix2(g, i, j);
-    if (k < g.kbv[c2]) { fV = R(0); fT = R(0); fS = R(0); return; }
-    const long ck = k * g.plane + c2;
-    const R vt = v[ck];
-    R qT[5], qS[5];
-    unsigned in = 0;
-#pragma unroll
-    for (int n = 0; n < 5; ++n) {
-        const long o = (long)(vt >= R(0) ? n - 3 : 2 - n) * g.pitch;
-        qT[n] = T[ck + o];
-        qS[n] = S[ck + o];
-        in |= (k >= g.kb[c2 + o] ? 1u : 0u) << n;
-    }
-    const R V = vt * p.dxv[j + OC_H] * p.dz[k];
-    fV = V;
-    fT = V * weno_adaptive(qT, in, p.eps, p.linear);
-    fS = V * weno_adaptive(qS, in, p.eps, p.linear);
-}
-
-// w T~ and w S~ through the bottom face of cell k (kb < k < nz) of column c2; the
-// reference profile varies along the column, so the stencil holds full values
-template <typename R>
-__device__ __forceinline__ void zflux(const KP<R>& p, const R* __restrict__ w,
-                                      const R* __restrict__ T, const R* __restrict__ S, long c2,
-                                      int k, int kb, R& fT, R& fS) {
-    const GeoD& g = p.g;
-    const long P = g.plane;
-    const R wt = w[k * P + c2];
-    R qT[5], qS[5];
-    unsigned in = 0;
-#pragma unroll
-    for (int n = 0; n < 5; ++n) {
-        const int kk = wt >= R(0) ? k - 3 + n : k + 2 - n;
-        const bool ok = kk >= kb && kk < g.nz;
-        qT[n] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
-        qS[n] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
-        in |= (ok ? 1u : 0u) << n;
-    }
-    fT = wt * weno_adaptive(qT, in, p.eps, p.linear);
-    fS = wt * weno_adaptive(qS, in, p.eps, p.linear);
-}
-
-// STEP = false: write G^n of T, S into Tn, Sn.  STEP = true: quasi-AB2 predictor
+// STEP = false: G^n of T, S into Tn, Sn.  STEP = true: quasi-AB2 predictor
 // T* = T + dt (ca G^n - cb G^{n-1}), G^{n-1} <- G^n, then the backward-Euler diffusion
 //   T_k - T*_k = dt/dz_k [kap_{k+1} (T_{k+1} - T_k)/dzf_{k+1} - kap_k (T_k - T_{k-1})/dzf_k]
 // with zero flux at the sea floor and the surface, by the Thomas algorithm: forward
-// elimination from the bottom while the column is swept upward, back substitution down.
+// elimination from the bottom while the column is swept upward (c' overwrites kap, d'
+// goes to Tn, Sn), back substitution down.  Horizontal fluxes reconstruct the anomalies
+// (WENO is translation-equivariant, so adding U Tref(k) gives the flux of T itself);
+// vertical ones reconstruct full values, since the reference varies along the column.
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(TPB) k_tracer(KP<R> p, const R* __restrict__ u,
-                                                const R* __restrict__ v, const R* __restrict__ w,
-                                                const R* __restrict__ T, const R* __restrict__ S,
-                                                const R* __restrict__ kap, R* __restrict__ GTp,
-                                                R* __restrict__ GSp, R* __restrict__ Tn,
-                                                R* __restrict__ Sn) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
+                                               const R* __restrict__ v, const R* __restrict__ w,
+                                               const R* __restrict__ T, const R* __restrict__ S,
+                                               R* __restrict__ kap, R* __restrict__ GTp,
+                                               R* __restrict__ GSp, R* __restrict__ Tn,
+                                               R* __restrict__ Sn) {
+    __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
-    const int nz = g.nz, tid = threadIdx.x, nb = blockDim.x;
-    R* cp = reinterpret_cast<R*>(smem_raw);
-    R* dT = cp + nz * nb;
-    R* dS = dT + nz * nb;
-    long c = (long)blockIdx.x * blockDim.x + tid;
-    if (c >= (long)g.nx * g.ny) return;
-    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    const long c2 = ix2(g, i, j), P = g.plane;
-    const int kb = g.kb[c2];
-    if (kb >= nz) return;
-    const R rac = p.rAc[j + OC_H];
-    R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
-    for (int k = kb; k < nz; ++k) {
-        const long ck = k * P + c2;
-        R fwU, fwT, fwS, feU, feT, feS, fsV, fsT, fsS, fnV, fnT, fnS, ftT = R(0), ftS = R(0);
-        xflux(p, u, T, S, i, j, k, fwU, fwT, fwS);
-        xflux(p, u, T, S, i + 1, j, k, feU, feT, feS);
-        yflux(p, v, T, S, i, j, k, fsV, fsT, fsS);
-        yflux(p, v, T, S, i, j + 1, k, fnV, fnT, fnS);
-        if (k + 1 < nz) zflux(p, w, T, S, c2, k + 1, kb, ftT, ftS);
-        const R rdz = p.rdz[k];
-        const R divU = feU - fwU + fnV - fsV;
-        const R GT = -((p.Tref[k] * divU + (feT - fwT + fnT - fsT)) * rac + (ftT - fzT)) * rdz;
-        const R GS = -((p.Sref[k] * divU + (feS - fwS + fnS - fsS)) * rac + (ftS - fzS)) * rdz;
-        fzT = ftT;
-        fzS = ftS;
-        if (!STEP) {
-            Tn[ck] = GT;
-            Sn[ck] = GS;
-            continue;
-        }
-        const R gT = p.ca * GT - p.cb * GTp[ck];
-        const R gS = p.ca * GS - p.cb * GSp[ck];
-        GTp[ck] = GT;
-        GSp[ck] = GS;
-        const R lo = k > kb ? p.dt * kap[ck] * rdz * p.rdzf[k] : R(0);
-        const R hi = k < nz - 1 ? p.dt * kap[ck + P] * rdz * p.rdzf[k + 1] : R(0);
-        // the diffusion of the reference profile moves to the right-hand side of the
-        // anomaly system: (I - dt D) T'^{n+1} = T'* + dt D Tref
-        const R Ts = T[ck] + p.dt * gT
-                   + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
-        const R Ss = S[ck] + p.dt * gS
-                   + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
-        const R den = (R(1) + lo + hi) + lo * cprev;   // b_k - a_k c'_{k-1}, a_k = -lo
-        const R inv = R(1) / den;
-        cprev = -hi * inv;
-        dTprev = (Ts + lo * dTprev) * inv;
-        dSprev = (Ss + lo * dSprev) * inv;
-        cp[k * nb + tid] = cprev;
-        dT[k * nb + tid] = dTprev;
-        dS[k * nb + tid] = dSprev;
+    const int nz = g.nz;
+    const long P = g.plane;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool mine = i < g.nx && j < g.ny;
+    const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
+    // ---- 2-D masks of the patch, and the lowest wet level of the whole patch
+    if (tid == 0) sm.kmin = nz;
+    for (int q = tid; q < (TY + 6) * (TX + 6); q += NT) {
+        const int a = q / (TX + 6), b = q % (TX + 6);
+        sm.kb[a][b] = g.kb[tix(g, i0 - 3 + b, j0 - 3 + a)];
     }
-    if (!STEP) return;
-    R xT = dT[(nz - 1) * nb + tid], xS = dS[(nz - 1) * nb + tid];
-    Tn[(nz - 1) * P + c2] = xT;
-    Sn[(nz - 1) * P + c2] = xS;
+    for (int q = tid; q < TY * (TX + 1); q += NT) {
+        const int a = q / (TX + 1), b = q % (TX + 1);
+        const int fi = i0 + b, fj = j0 + a;
+        sm.kbu[a][b] = (fi <= g.nx && fj < g.ny) ? g.kbu[ix2(g, fi, fj)] : (short)nz;
+    }
+    for (int q = tid; q < (TY + 1) * TX; q += NT) {
+        const int a = q / TX, b = q % TX;
+        const int fi = i0 + b, fj = j0 + a;
+        sm.kbv[a][b] = (fi < g.nx && fj <= g.ny) ? g.kbv[ix2(g, fi, fj)] : (short)nz;
+    }
+    __syncthreads();
+    const int kb = mine ? (int)sm.kb[ty + 3][tx + 3] : nz;
+    if (kb < nz) atomicMin(&sm.kmin, kb);
+    __syncthreads();
+    const int kstart = sm.kmin;
+    if (kstart >= nz) return;   // the whole patch is land
+
+    const R rac = p.rAc[(mine ? j : 0) + OC_H];
+    // register window of full values at levels k-2 .. k+3 (0 outside the column)
+    R wT[6], wS[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int kk = kstart - 2 + q;
+        const bool ok = mine && kk >= kb && kk < nz;
+        wT[q] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
+        wS[q] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
+    }
+    R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
+
+    for (int k = kstart; k < nz; ++k) {
+        const long Pk = k * P;
+        // ---- stage the anomalies of level k (halo 3)
+        for (int q = tid; q < (TY + 6) * (TX + 6); q += NT) {
+            const int a = q / (TX + 6), b = q % (TX + 6);
+            const long c = Pk + tix(g, i0 - 3 + b, j0 - 3 + a);
+            sm.T[a][b] = T[c];
+            sm.S[a][b] = S[c];
+        }
+        __syncthreads();
+        const R dzk = p.dz[k];
+        // ---- x-face fluxes, each face once
+        for (int q = tid; q < TY * (TX + 1); q += NT) {
+            const int a = q / (TX + 1), b = q % (TX + 1);
+            R fU = R(0), fT = R(0), fS = R(0);
+            if (k >= sm.kbu[a][b]) {
+                const R ut = u[Pk + ix2(g, i0 + b, j0 + a)];
+                R qT[5], qS[5];
+                unsigned in = 0;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int col = ut >= R(0) ? b + n : b + 5 - n;
+                    qT[n] = sm.T[a + 3][col];
+                    qS[n] = sm.S[a + 3][col];
+                    in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
+                }
+                fU = ut * p.dy * dzk;
+                fT = fU * weno_adaptive(qT, in, p.eps, p.linear);
+                fS = fU * weno_adaptive(qS, in, p.eps, p.linear);
+            }
+            sm.fxU[a][b] = fU;
+            sm.fxT[a][b] = fT;
+            sm.fxS[a][b] = fS;
+        }
+        // ---- y-face fluxes
+        for (int q = tid; q < (TY + 1) * TX; q += NT) {
+            const int a = q / TX, b = q % TX;
+            R fV = R(0), fT = R(0), fS = R(0);
+            if (k >= sm.kbv[a][b]) {
+                const int fj = j0 + a;
+                const R vt = v[Pk + ix2(g, i0 + b, fj)];
+                R qT[5], qS[5];
+                unsigned in = 0;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int row = vt >= R(0) ? a + n : a + 5 - n;
+                    qT[n] = sm.T[row][b + 3];
+                    qS[n] = sm.S[row][b + 3];
+                    in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                }
+                fV = vt * p.dxv[fj + OC_H] * dzk;
+                fT = fV * weno_adaptive(qT, in, p.eps, p.linear);
+                fS = fV * weno_adaptive(qS, in, p.eps, p.linear);
+            }
+            sm.fyV[a][b] = fV;
+            sm.fyT[a][b] = fT;
+            sm.fyS[a][b] = fS;
+        }
+        __syncthreads();
+        // ---- own cell
+        if (mine && k >= kb) {
+            const long ck = Pk + c2;
+            R ftT = R(0), ftS = R(0);
+            if (k + 1 < nz) {   // flux through the top face (bottom face of cell k+1)
+                const R wt = w[ck + P];
+                const bool pos = wt >= R(0);
+                R qT[5], qS[5];
+                unsigned in = 0;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    // window index n (level k-2+n) upward, 5-n (level k+3-n) downward; both
+                    // compile-time so the window stays in registers
+                    qT[n] = pos ? wT[n] : wT[5 - n];
+                    qS[n] = pos ? wS[n] : wS[5 - n];
+                    const int kk = pos ? k - 2 + n : k + 3 - n;
+                    in |= (kk >= kb && kk < nz ? 1u : 0u) << n;
+                }
+                ftT = wt * weno_adaptive(qT, in, p.eps, p.linear);
+                ftS = wt * weno_adaptive(qS, in, p.eps, p.linear);
+            }
+            const R rdz = p.rdz[k];
+            const R divU = sm.fxU[ty][tx + 1] - sm.fxU[ty][tx] + sm.fyV[ty + 1][tx] - sm.fyV[ty][tx];
+            const R hT = sm.fxT[ty][tx + 1] - sm.fxT[ty][tx] + sm.fyT[ty + 1][tx] - sm.fyT[ty][tx];
+            const R hS = sm.fxS[ty][tx + 1] - sm.fxS[ty][tx] + sm.fyS[ty + 1][tx] - sm.fyS[ty][tx];
+            const R GT = -((p.Tref[k] * divU + hT) * rac + (ftT - fzT)) * rdz;
+            const R GS = -((p.Sref[k] * divU + hS) * rac + (ftS - fzS)) * rdz;
+            fzT = ftT;
+            fzS = ftS;
+            if (!STEP) {
+                Tn[ck] = GT;
+                Sn[ck] = GS;
+            } else {
+                const R gT = p.ca * GT - p.cb * GTp[ck];
+                const R gS = p.ca * GS - p.cb * GSp[ck];
+                GTp[ck] = GT;
+                GSp[ck] = GS;
+                const R lo = k > kb ? p.dt * kap[ck] * rdz * p.rdzf[k] : R(0);
+                const R hi = k < nz - 1 ? p.dt * kap[ck + P] * rdz * p.rdzf[k + 1] : R(0);
+                // the diffusion of the reference profile moves to the right-hand side:
+                // (I - dt D) T'^{n+1} = T'* + dt D Tref
+                const R Ts = T[ck] + p.dt * gT
+                           + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
+                const R Ss = S[ck] + p.dt * gS
+                           + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
+                const R inv = R(1) / ((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
+                cprev = -hi * inv;
+                dTprev = (Ts + lo * dTprev) * inv;
+                dSprev = (Ss + lo * dSprev) * inv;
+                kap[ck] = cprev;
+                Tn[ck] = dTprev;
+                Sn[ck] = dSprev;
+            }
+        }
+        // ---- slide the vertical window up one level
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            wT[q] = wT[q + 1];
+            wS[q] = wS[q + 1];
+        }
+        {
+            const int kk = k + 4;
+            const bool ok = mine && kk >= kb && kk < nz;
+            wT[5] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
+            wS[5] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
+        }
+        __syncthreads();   // the staged level and fluxes are reused by the next level
+    }
+    if (!STEP || !mine || kb >= nz) return;
+    R xT = dTprev, xS = dSprev;   // level nz-1: x = d'
     for (int k = nz - 2; k >= kb; --k) {
-        const R cc = cp[k * nb + tid];
-        xT = dT[k * nb + tid] - cc * xT;
-        xS = dS[k * nb + tid] - cc * xS;
-        Tn[k * P + c2] = xT;
-        Sn[k * P + c2] = xS;
+        const long ck = k * P + c2;
+        const R cc = kap[ck];
+        xT = Tn[ck] - cc * xT;
+        xS = Sn[ck] - cc * xS;
+        Tn[ck] = xT;
+        Sn[ck] = xS;
     }
 }
 
 // ------------------------------------------------------------------ momentum
 
-// relative vorticity at the SW corner of column (i, j), zero unless all four cells wet
 template <typename R>
-__device__ __forceinline__ R zeta_at(const KP<R>& p, const R* __restrict__ u,
-                                     const R* __restrict__ v, int i, int j, int k) {
-    const GeoD& g = p.g;
-    const long c2 = ix2(g, i, j);
-    if (k < g.kbz[c2]) return R(0);
-    const long ck = k * g.plane + c2;
-    const R circ = p.dy * (v[ck] - v[ck - 1])
-                 - (p.dxc[j + OC_H] * u[ck] - p.dxc[j - 1 + OC_H] * u[ck - g.pitch]);
-    return circ * p.rAz[j + OC_H];
-}
+struct MomentumSmem {
+    R u[TY + 6][TX + 5];      // u(k) at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3)
+    R v[TY + 5][TX + 6];      // v(k) at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
+    R z[TY + 5][TX + 5];      // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3)
+    R K[TY + 1][TX + 1];      // kinetic energy at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
+    R p[TY + 1][TX + 1];      // pressure anomaly, same centres
+    R w[2][TY + 1][TX + 1];   // w on the bottom faces of levels k and k+1, same centres
+    R nu[2][TY + 1][TX + 1];  // nu on those faces
+    short kbz[TY + 5][TX + 5], kbzin[TY + 5][TX + 5];
+    int kmin;
+};
 
-// kinetic energy at the centre of the cell at index ck
-template <typename R>
-__device__ __forceinline__ R kin_at(const R* __restrict__ u, const R* __restrict__ v, long ck,
-                                    int pitch) {
-    const R a = u[ck], b = u[ck + 1], c = v[ck], d = v[ck + pitch];
-    return R(0.25) * (a * a + b * b) + R(0.25) * (c * c + d * d);
-}
-
+// STEP = false: G^n of u, v into un, vn.  STEP = true: quasi-AB2 predictor, G^{n-1} <-
+// G^n, the column sums U^n = sum dz u^n and G_U = sum dz G^ of the barotropic mode, the
+// backward-Euler vertical viscosity (Thomas: c' in cu/cv scratch, d' in un/vn) and the
+// sum of the solved column Su = sum dz u**.
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(TPB) k_momentum(
+__global__ void __launch_bounds__(NT) k_momentum(
     KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
     const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
-    R* __restrict__ vn, R* __restrict__ Un, R* __restrict__ Vn, R* __restrict__ GU,
-    R* __restrict__ GV, R* __restrict__ Su, R* __restrict__ Sv) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
+    R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
+    R* __restrict__ Sv) {
+    __shared__ MomentumSmem<R> sm;
     const GeoD& g = p.g;
-    const int nz = g.nz, tid = threadIdx.x, nb = blockDim.x;
-    R* cpu = reinterpret_cast<R*>(smem_raw);
-    R* du = cpu + nz * nb;
-    R* cpv = du + nz * nb;
-    R* dv = cpv + nz * nb;
-    long c = (long)blockIdx.x * blockDim.x + tid;
-    if (c >= (long)g.nx * g.ny) return;
-    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    const long c2 = ix2(g, i, j), P = g.plane;
-    const int pitch = g.pitch;
-    const int ku = g.kbu[c2], kv = g.kbv[c2];
-    const int k0 = ku < kv ? ku : kv;
-    if (k0 >= nz) return;
-    const R rdxc = p.rdxc[j + OC_H], fu = p.fu[j + OC_H], fv = p.fv[j + OC_H];
-    R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
-    R cu = 0, dup = 0, cv = 0, dvp = 0;
-    for (int k = k0; k < nz; ++k) {
-        const long ck = k * P + c2;
-        const R rdz = p.rdz[k];
-        if (k >= ku) {   // ---------------- u at the west face of column (i, j)
-            const R u0 = u[ck];
-            const R vh = R(0.25) * (v[ck - 1] + v[ck] + v[ck - 1 + pitch] + v[ck + pitch]);
-            R q[5];
-            unsigned in = 0;
-#pragma unroll
-            for (int n = 0; n < 5; ++n) {
-                const int jj = vh >= R(0) ? j - 2 + n : j + 3 - n;
-                q[n] = zeta_at(p, u, v, i, jj, k);
-                in |= (k >= g.kbzin[ix2(g, i, jj)] ? 1u : 0u) << n;
-            }
-            const R zt = weno_adaptive(q, in, p.eps, p.linear);
-            const R dK = (kin_at(u, v, ck, pitch) - kin_at(u, v, ck - 1, pitch)) * rdxc;
-            const R dP = (pr[ck] - pr[ck - 1]) * rdxc;
-            R up = R(0), dn = R(0);
-            if (k + 1 < nz)
-                up = R(0.5) * (w[ck + P - 1] + w[ck + P]) * (u[ck + P] - u0) * p.rdzf[k + 1];
-            if (k - 1 >= ku)
-                dn = R(0.5) * (w[ck - 1] + w[ck]) * (u0 - u[ck - P]) * p.rdzf[k];
-            const R wind = k == nz - 1 ? taux_s[c2] : R(0);
-            const R G = (zt + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
-            if (!STEP) {
-                un[ck] = G;
-            } else {
-                const R gh = p.ca * G - p.cb * Gup[ck];
-                Gup[ck] = G;
-                sUn += p.dz[k] * u0;
-                sGU += p.dz[k] * gh;
-                const R us = u0 + p.dt * gh;
-                const R lo = k > ku ? p.dt * R(0.5) * (nu[ck - 1] + nu[ck]) * rdz * p.rdzf[k] : R(0);
-                const R hi = k < nz - 1
-                    ? p.dt * R(0.5) * (nu[ck + P - 1] + nu[ck + P]) * rdz * p.rdzf[k + 1] : R(0);
-                const R inv = R(1) / ((R(1) + lo + hi) + lo * cu);
-                cu = -hi * inv;
-                dup = (us + lo * dup) * inv;
-                cpu[k * nb + tid] = cu;
-                du[k * nb + tid] = dup;
-            }
-        }
-        if (k >= kv) {   // ---------------- v at the south face of column (i, j)
-            const R v0 = v[ck];
-            const R uh = R(0.25) * (u[ck - pitch] + u[ck + 1 - pitch] + u[ck] + u[ck + 1]);
-            R q[5];
-            unsigned in = 0;
-#pragma unroll
-            for (int n = 0; n < 5; ++n) {
-                const int ii = uh >= R(0) ? i - 2 + n : i + 3 - n;
-                q[n] = zeta_at(p, u, v, ii, j, k);
-                in |= (k >= g.kbzin[ix2(g, ii, j)] ? 1u : 0u) << n;
-            }
-            const R zt = weno_adaptive(q, in, p.eps, p.linear);
-            const R dK = (kin_at(u, v, ck, pitch) - kin_at(u, v, ck - pitch, pitch)) * p.rdy;
-            const R dP = (pr[ck] - pr[ck - pitch]) * p.rdy;
-            R up = R(0), dn = R(0);
-            if (k + 1 < nz)
-                up = R(0.5) * (w[ck + P - pitch] + w[ck + P]) * (v[ck + P] - v0) * p.rdzf[k + 1];
-            if (k - 1 >= kv)
-                dn = R(0.5) * (w[ck - pitch] + w[ck]) * (v0 - v[ck - P]) * p.rdzf[k];
-            const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
-            const R G = -(zt + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
-            if (!STEP) {
-                vn[ck] = G;
-            } else {
-                const R gh = p.ca * G - p.cb * Gvp[ck];
-                Gvp[ck] = G;
-                sVn += p.dz[k] * v0;
-                sGV += p.dz[k] * gh;
-                const R vs = v0 + p.dt * gh;
-                const R lo = k > kv
-                    ? p.dt * R(0.5) * (nu[ck - pitch] + nu[ck]) * rdz * p.rdzf[k] : R(0);
-                const R hi = k < nz - 1
-                    ? p.dt * R(0.5) * (nu[ck + P - pitch] + nu[ck + P]) * rdz * p.rdzf[k + 1] : R(0);
-                const R inv = R(1) / ((R(1) + lo + hi) + lo * cv);
-                cv = -hi * inv;
-                dvp = (vs + lo * dvp) * inv;
-                cpv[k * nb + tid] = cv;
-                dv[k * nb + tid] = dvp;
-            }
-        }
+    const int nz = g.nz;
+    const long P = g.plane;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool mine = i < g.nx && j < g.ny;
+    const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
+    if (tid == 0) sm.kmin = nz;
+    for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
+        const int a = q / (TX + 5), b = q % (TX + 5);
+        const long c = tix(g, i0 - 2 + b, j0 - 2 + a);
+        sm.kbz[a][b] = g.kbz[c];
+        sm.kbzin[a][b] = g.kbzin[c];
     }
-    if (!STEP) return;
+    const int ku = mine ? (int)g.kbu[c2] : nz, kv = mine ? (int)g.kbv[c2] : nz;
+    __syncthreads();
+    const int k0 = ku < kv ? ku : kv;
+    if (k0 < nz) atomicMin(&sm.kmin, k0);
+    __syncthreads();
+    const int kstart = sm.kmin;
+    if (kstart >= nz) return;
+    // w and nu on the bottom faces of level kstart
+    for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
+        const int a = q / (TX + 1), b = q % (TX + 1);
+        const long c = kstart * P + tix(g, i0 - 1 + b, j0 - 1 + a);
+        sm.w[0][a][b] = w[c];
+        sm.nu[0][a][b] = nu[c];
+    }
+    const int jr = (mine ? j : 0) + OC_H;
+    const R rdxc = p.rdxc[jr], fu = p.fu[jr], fv = p.fv[jr];
+    R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
+    R cuk = 0, duk = 0, cvk = 0, dvk = 0;
+    // own faces: u, v at k-1 (lower) and k+1 (upper); level k comes from the tile
+    R ulo = R(0), vlo = R(0);
+    if (mine && kstart >= 1) {
+        ulo = u[(kstart - 1) * P + c2];
+        vlo = v[(kstart - 1) * P + c2];
+    }
+    int cur = 0;
+    for (int k = kstart; k < nz; ++k) {
+        const long Pk = k * P;
+        const int nxt = 1 - cur;
+        // ---- stage level k: u, v (halo 3), pressure, and w, nu of level k+1
+        for (int q = tid; q < (TY + 6) * (TX + 5); q += NT) {
+            const int a = q / (TX + 5), b = q % (TX + 5);
+            sm.u[a][b] = u[Pk + tix(g, i0 - 2 + b, j0 - 3 + a)];
+        }
+        for (int q = tid; q < (TY + 5) * (TX + 6); q += NT) {
+            const int a = q / (TX + 6), b = q % (TX + 6);
+            sm.v[a][b] = v[Pk + tix(g, i0 - 3 + b, j0 - 2 + a)];
+        }
+        for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
+            const int a = q / (TX + 1), b = q % (TX + 1);
+            const long c = tix(g, i0 - 1 + b, j0 - 1 + a);
+            sm.p[a][b] = pr[Pk + c];
+            if (k + 1 < nz) {
+                sm.w[nxt][a][b] = w[Pk + P + c];
+                sm.nu[nxt][a][b] = nu[Pk + P + c];
+            }
+        }
+        R uhi = R(0), vhi = R(0);
+        if (mine && k + 1 < nz) {
+            uhi = u[Pk + P + c2];
+            vhi = v[Pk + P + c2];
+        }
+        __syncthreads();
+        // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
+        for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
+            const int a = q / (TX + 5), b = q % (TX + 5);
+            const int jc = j0 - 2 + a;
+            R zz = R(0);
+            if (k >= sm.kbz[a][b]) {
+                const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
+                // u(i, jc) = sm.u[a + 1][b], u(i, jc-1) = sm.u[a][b];
+                // v(i, jc) = sm.v[a][b + 1], v(i-1, jc) = sm.v[a][b]
+                const R circ = p.dy * (sm.v[a][b + 1] - sm.v[a][b])
+                             - (p.dxc[jrc] * sm.u[a + 1][b] - p.dxc[jrc - 1] * sm.u[a][b]);
+                zz = circ * p.rAz[jrc];
+            }
+            sm.z[a][b] = zz;
+        }
+        for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
+            const int a = q / (TX + 1), b = q % (TX + 1);
+            // centre (i0-1+b, j0-1+a): u at b+1, b+2 of row a+2; v at col b+2 rows a+1, a+2
+            const R ua = sm.u[a + 2][b + 1], ub = sm.u[a + 2][b + 2];
+            const R va = sm.v[a + 1][b + 2], vb = sm.v[a + 2][b + 2];
+            sm.K[a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
+        }
+        __syncthreads();
+        if (mine) {
+            const R rdz = p.rdz[k];
+            if (k >= ku) {   // ---------------- u at the west face of column (i, j)
+                const R u0 = sm.u[ty + 3][tx + 2];
+                const R vh = R(0.25) * (sm.v[ty + 2][tx + 2] + sm.v[ty + 2][tx + 3]
+                                      + sm.v[ty + 3][tx + 2] + sm.v[ty + 3][tx + 3]);
+                R q[5];
+                unsigned in = 0;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int a = vh >= R(0) ? ty + n : ty + 5 - n;   // corner row j-2+..
+                    q[n] = sm.z[a][tx + 2];
+                    in |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
+                }
+                const R zt = weno_adaptive(q, in, p.eps, p.linear);
+                const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty + 1][tx]) * rdxc;
+                const R dP = (sm.p[ty + 1][tx + 1] - sm.p[ty + 1][tx]) * rdxc;
+                R up = R(0), dn = R(0);
+                if (k + 1 < nz)
+                    up = R(0.5) * (sm.w[nxt][ty + 1][tx] + sm.w[nxt][ty + 1][tx + 1]) * (uhi - u0) * p.rdzf[k + 1];
+                if (k - 1 >= ku)
+                    dn = R(0.5) * (sm.w[cur][ty + 1][tx] + sm.w[cur][ty + 1][tx + 1]) * (u0 - ulo) * p.rdzf[k];
+                const R wind = k == nz - 1 ? taux_s[c2] : R(0);
+                const R G = (zt + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
+                const long ck = Pk + c2;
+                if (!STEP) {
+                    un[ck] = G;
+                } else {
+                    const R gh = p.ca * G - p.cb * Gup[ck];
+                    Gup[ck] = G;
+                    sUn += p.dz[k] * u0;
+                    sGU += p.dz[k] * gh;
+                    const R us = u0 + p.dt * gh;
+                    const R lo = k > ku
+                        ? p.dt * R(0.5) * (sm.nu[cur][ty + 1][tx] + sm.nu[cur][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                    const R hi = k < nz - 1
+                        ? p.dt * R(0.5) * (sm.nu[nxt][ty + 1][tx] + sm.nu[nxt][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                    const R inv = R(1) / ((R(1) + lo + hi) + lo * cuk);
+                    cuk = -hi * inv;
+                    duk = (us + lo * duk) * inv;
+                    cu[ck] = cuk;
+                    un[ck] = duk;
+                }
+            }
+            if (k >= kv) {   // ---------------- v at the south face of column (i, j)
+                const R v0 = sm.v[ty + 2][tx + 3];
+                const R uh = R(0.25) * (sm.u[ty + 2][tx + 2] + sm.u[ty + 2][tx + 3]
+                                      + sm.u[ty + 3][tx + 2] + sm.u[ty + 3][tx + 3]);
+                R q[5];
+                unsigned in = 0;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int b = uh >= R(0) ? tx + n : tx + 5 - n;   // corner col i-2+..
+                    q[n] = sm.z[ty + 2][b];
+                    in |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
+                }
+                const R zt = weno_adaptive(q, in, p.eps, p.linear);
+                const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty][tx + 1]) * p.rdy;
+                const R dP = (sm.p[ty + 1][tx + 1] - sm.p[ty][tx + 1]) * p.rdy;
+                R up = R(0), dn = R(0);
+                if (k + 1 < nz)
+                    up = R(0.5) * (sm.w[nxt][ty][tx + 1] + sm.w[nxt][ty + 1][tx + 1]) * (vhi - v0) * p.rdzf[k + 1];
+                if (k - 1 >= kv)
+                    dn = R(0.5) * (sm.w[cur][ty][tx + 1] + sm.w[cur][ty + 1][tx + 1]) * (v0 - vlo) * p.rdzf[k];
+                const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
+                const R G = -(zt + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
+                const long ck = Pk + c2;
+                if (!STEP) {
+                    vn[ck] = G;
+                } else {
+                    const R gh = p.ca * G - p.cb * Gvp[ck];
+                    Gvp[ck] = G;
+                    sVn += p.dz[k] * v0;
+                    sGV += p.dz[k] * gh;
+                    const R vs = v0 + p.dt * gh;
+                    const R lo = k > kv
+                        ? p.dt * R(0.5) * (sm.nu[cur][ty][tx + 1] + sm.nu[cur][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                    const R hi = k < nz - 1
+                        ? p.dt * R(0.5) * (sm.nu[nxt][ty][tx + 1] + sm.nu[nxt][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                    const R inv = R(1) / ((R(1) + lo + hi) + lo * cvk);
+                    cvk = -hi * inv;
+                    dvk = (vs + lo * dvk) * inv;
+                    cv[ck] = cvk;
+                    vn[ck] = dvk;
+                }
+            }
+            ulo = sm.u[ty + 3][tx + 2];
+            vlo = sm.v[ty + 2][tx + 3];
+        }
+        cur = nxt;
+        __syncthreads();
+    }
+    if (!STEP || !mine) return;
     if (ku < nz) {
-        R x = du[(nz - 1) * nb + tid];
-        un[(nz - 1) * P + c2] = x;
+        R x = duk;   // level nz-1
         R s = p.dz[nz - 1] * x;
         for (int k = nz - 2; k >= ku; --k) {
-            x = du[k * nb + tid] - cpu[k * nb + tid] * x;
-            un[k * P + c2] = x;
+            const long ck = k * P + c2;
+            x = un[ck] - cu[ck] * x;
+            un[ck] = x;
             s += p.dz[k] * x;
         }
         Un[c2] = sUn;
@@ -405,12 +561,12 @@ __global__ void __launch_bounds__(TPB) k_momentum(
         Su[c2] = s;
     }
     if (kv < nz) {
-        R x = dv[(nz - 1) * nb + tid];
-        vn[(nz - 1) * P + c2] = x;
+        R x = dvk;
         R s = p.dz[nz - 1] * x;
         for (int k = nz - 2; k >= kv; --k) {
-            x = dv[k * nb + tid] - cpv[k * nb + tid] * x;
-            vn[k * P + c2] = x;
+            const long ck = k * P + c2;
+            x = vn[ck] - cv[ck] * x;
+            vn[ck] = x;
             s += p.dz[k] * x;
         }
         Vn[c2] = sVn;
@@ -542,34 +698,10 @@ __global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
 
 // ------------------------------------------------------------------ launchers
 
-// Column kernels keep the Thomas coefficients of every level in shared memory:
-// per thread 3 (tracers) or 4 (momentum) values per level.  The block shrinks (in whole
-// warps) so that the block's share stays within 200 KB.
-static int column_tpb(int nz, int vals, size_t esz) {
-    const size_t per = (size_t)vals * nz * esz;
-    int t = (int)((200u * 1024u) / per) / 32 * 32;
-    return t > TPB ? TPB : (t < 32 ? 32 : t);
-}
-template <typename R>
-static size_t tracer_smem(int nz) { return (size_t)3 * nz * column_tpb(nz, 3, sizeof(R)) * sizeof(R); }
-template <typename R>
-static size_t momentum_smem(int nz) { return (size_t)4 * nz * column_tpb(nz, 4, sizeof(R)) * sizeof(R); }
-
 template <typename R>
 int setup_kernel_attributes(int nz) {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_tracer<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tracer_smem<R>(nz));
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_tracer<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tracer_smem<R>(nz));
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_momentum<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)momentum_smem<R>(nz));
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_momentum<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)momentum_smem<R>(nz));
-    return (int)e;
+    (void)nz;
+    return (int)cudaSuccess;
 }
 
 template <typename R>
@@ -580,30 +712,26 @@ void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
 
 template <typename R>
 void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
-    const long n = (long)p.g.nx * p.g.ny;
-    const size_t sm = tracer_smem<R>(p.g.nz);
-    const int tpb = column_tpb(p.g.nz, 3, sizeof(R));
+    const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
     if (step)
-        k_tracer<R, true><<<nblocks(n, tpb), tpb, sm, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap,
-                                                          b.GT, b.GS, b.Tn, b.Sn);
+        k_tracer<R, true><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
+                                                 b.Tn, b.Sn);
     else
-        k_tracer<R, false><<<nblocks(n, tpb), tpb, sm, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap,
-                                                           b.GT, b.GS, b.Tn, b.Sn);
+        k_tracer<R, false><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
+                                                  b.Tn, b.Sn);
 }
 
 template <typename R>
 void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
-    const long n = (long)p.g.nx * p.g.ny;
-    const size_t sm = momentum_smem<R>(p.g.nz);
-    const int tpb = column_tpb(p.g.nz, 4, sizeof(R));
+    const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
     if (step)
-        k_momentum<R, true><<<nblocks(n, tpb), tpb, sm, s>>>(
-            p, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.Un, b.Vn,
-            b.GU, b.GV, b.Su, b.Sv);
+        k_momentum<R, true><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
+                                                   b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
+                                                   b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
     else
-        k_momentum<R, false><<<nblocks(n, tpb), tpb, sm, s>>>(
-            p, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.Un, b.Vn,
-            b.GU, b.GV, b.Su, b.Sv);
+        k_momentum<R, false><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
+                                                    b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
+                                                    b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
 }
 
 // flush the FP32 partial sums into the FP64 accumulators every this many substeps
