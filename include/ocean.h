@@ -217,6 +217,24 @@ int ocean_weno_faces(const void* d_q, const void* d_vel, const unsigned char* d_
 int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, const void* d_d,
                           void* d_x, int n, int nsys, int precision, void* stream);
 
+/* The batched tridiagonal solve above, for callers that cannot allocate device memory:
+ * code that runs while a CUDA graph is being captured (allocation cannot be captured),
+ * code embedded in a framework that owns every allocation on the device, or a runtime
+ * with a fixed memory budget.  It allocates nothing: the Thomas coefficients go to one
+ * static device array of OCEAN_TRIDIAG_STATIC_WORDS 8-byte words (16 MiB) that every GPU
+ * loading the library holds until the process exits.  Same arguments, layout and result
+ * as ocean_tridiag_batched, with n >= 1 and n * nsys at most OCEAN_TRIDIAG_STATIC_WORDS
+ * (OCEAN_FP64) or twice that (OCEAN_MIXED); larger requests return OCEAN_ERR_ARG with a
+ * message and launch nothing.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) while that device is current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's
+ * contents (nothing needs clearing: every value read is first written by the same
+ * call); calls that overlap on the GPU race on it.  The paper has no counterpart. */
+#define OCEAN_TRIDIAG_STATIC_WORDS (1 << 21)
+int ocean_tridiag_batched_static(const void* d_a, const void* d_b, const void* d_c,
+                                 const void* d_d, void* d_x, int n, int nsys, int precision,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

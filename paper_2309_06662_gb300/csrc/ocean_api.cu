@@ -691,6 +691,9 @@ void ocean_destroy(ocean_t h) {
     delete h;
 }
 
+// message for ocean_last_error(NULL) from entry points that have no handle
+void oc_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 const char* ocean_last_error(ocean_t h) {
     return h ? h->err.c_str() : g_last_error.c_str();
 }

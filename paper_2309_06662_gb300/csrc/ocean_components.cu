@@ -1,6 +1,8 @@
 // ocean_components.cu -- standalone kernels over caller-owned device buffers: the
 // adaptive-order WENO-Z face reconstruction and the batched Thomas solve, the same
 // device functions the step kernels use, exposed for component-level checks.
+#include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "ocean.h"
@@ -90,3 +92,128 @@ int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, con
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batched tridiagonal solve without any allocation.
+//
+// For callers that must not allocate device memory: code running while a CUDA graph
+// is being captured (an allocation is not a capturable operation), code embedded in
+// another framework that owns every allocation on the device, or a runtime with a fixed
+// memory budget.  The solve above keeps the Thomas coefficients c' in a per-thread
+// local-memory frame that the driver sets aside at launch; this variant keeps them,
+// level-major, in one file-scope device array instead, so the call needs no memory
+// beyond the caller's inputs and outputs and this module's static storage.
+//
+// The array holds OCEAN_TRIDIAG_STATIC_WORDS 8-byte words (16 MiB) on every GPU that
+// loads the library, until the process exits: n * nsys may not exceed that many
+// doubles, or twice that many floats.  Every call uses the same array and leaves its
+// coefficients there; nothing needs clearing, because each call writes every element
+// it reads before reading it.  Calls whose execution overlaps on the GPU (different
+// streams, or different host threads) race on the array and must be serialised.
+
+static __device__ __align__(256) double g_tridiag_cp[OCEAN_TRIDIAG_STATIC_WORDS];
+
+namespace {
+
+// c'(k, s) lives at cp[k * nsys + s]: the threads of a warp touch consecutive words
+template <typename R>
+__global__ void k_tridiag_static(const R* __restrict__ a, const R* __restrict__ b,
+                                 const R* __restrict__ c, const R* __restrict__ d,
+                                 R* __restrict__ x, R* __restrict__ cp, int n, int nsys) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    R inv = R(1) / b[s];
+    R cprev = c[s] * inv;
+    cp[s] = cprev;
+    x[s] = d[s] * inv;
+    for (int k = 1; k < n; ++k) {
+        const long e = (long)k * nsys + s;
+        const R ak = a[e];
+        inv = R(1) / (b[e] - ak * cprev);
+        cprev = c[e] * inv;
+        cp[e] = cprev;
+        x[e] = (d[e] - ak * x[e - nsys]) * inv;
+    }
+    for (int k = n - 2; k >= 0; --k) {
+        const long e = (long)k * nsys + s;
+        x[e] = x[e] - cp[e] * x[e + nsys];
+    }
+}
+
+// device address of the static array on the current device, looked up once per device
+std::mutex g_static_mu;
+void* g_static_ptr[128];
+
+int static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        oc_set_last_error(cudaGetErrorString(e));
+        return OCEAN_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 128) {
+        oc_set_last_error("device index out of range for the static scratch table");
+        return OCEAN_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_tridiag_cp);
+        if (e != cudaSuccess || !p) {
+            oc_set_last_error(e != cudaSuccess ? cudaGetErrorString(e)
+                                               : "cudaGetSymbolAddress returned null");
+            return OCEAN_ERR_CUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return OCEAN_OK;
+}
+
+}  // namespace
+
+extern "C" int ocean_tridiag_batched_static(const void* d_a, const void* d_b, const void* d_c,
+                                            const void* d_d, void* d_x, int n, int nsys,
+                                            int precision, void* stream) {
+    if (!d_a || !d_b || !d_c || !d_d || !d_x) {
+        oc_set_last_error("ocean_tridiag_batched_static: null array");
+        return OCEAN_ERR_ARG;
+    }
+    if (n < 1 || nsys < 1) {
+        oc_set_last_error("ocean_tridiag_batched_static: n and nsys must be >= 1");
+        return OCEAN_ERR_ARG;
+    }
+    if (precision != OCEAN_FP64 && precision != OCEAN_MIXED) {
+        oc_set_last_error("ocean_tridiag_batched_static: unknown precision");
+        return OCEAN_ERR_ARG;
+    }
+    const size_t esz = precision == OCEAN_FP64 ? sizeof(double) : sizeof(float);
+    const size_t cap = sizeof(g_tridiag_cp) / esz;
+    if ((size_t)n * (size_t)nsys > cap) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "ocean_tridiag_batched_static: n * nsys = %zu exceeds the static scratch of %zu "
+                 "elements (%zu bytes)", (size_t)n * (size_t)nsys, cap, sizeof(g_tridiag_cp));
+        oc_set_last_error(msg);
+        return OCEAN_ERR_ARG;
+    }
+    void* cp = nullptr;
+    int rc = static_scratch(&cp);
+    if (rc != OCEAN_OK) return rc;
+    const int tpb = 128, nb = (nsys + tpb - 1) / tpb;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == OCEAN_FP64)
+        k_tridiag_static<double><<<nb, tpb, 0, s>>>((const double*)d_a, (const double*)d_b,
+                                                    (const double*)d_c, (const double*)d_d,
+                                                    (double*)d_x, (double*)cp, n, nsys);
+    else
+        k_tridiag_static<float><<<nb, tpb, 0, s>>>((const float*)d_a, (const float*)d_b,
+                                                   (const float*)d_c, (const float*)d_d,
+                                                   (float*)d_x, (float*)cp, n, nsys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        oc_set_last_error(cudaGetErrorString(e));
+        return OCEAN_ERR_CUDA;
+    }
+    return OCEAN_OK;
+}

@@ -110,6 +110,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_kernel_launches": (c_long, [pv]),
             "ocean_weno_faces": (c_int, [pv, pv, pv, c_int, pv, c_int, c_double, c_int, pv]),
             "ocean_tridiag_batched": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
+            "ocean_tridiag_batched_static": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
