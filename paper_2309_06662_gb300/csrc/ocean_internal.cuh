@@ -112,6 +112,72 @@ __device__ __forceinline__ R weno_adaptive(const R* q, unsigned in, R eps, int l
     return q[2];
 }
 
+// ----------------------------------------------------------------------- paired WENO
+// Two reconstructions that share one stencil and one mask (T and S on the same face, or
+// the two vorticity reconstructions of a thread): in FP32 they run as one stream of
+// Blackwell's packed two-lane FP32 instructions (fma/mul/add .f32x2), with the weights'
+// divisions as fast reciprocals; in FP64 as two scalar calls.
+
+template <typename R> struct WenoPair {
+    static __device__ __forceinline__ void run(const R* qa, const R* qb, unsigned ina,
+                                               unsigned inb, R eps, int linear, R& oa, R& ob) {
+        oa = weno_adaptive(qa, ina, eps, linear);
+        ob = weno_adaptive(qb, inb, eps, linear);
+    }
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// fifth-order WENO-Z of two stencils at once (same definition as weno5)
+__device__ __forceinline__ float2 weno5z_x2(float2 q0, float2 q1, float2 q2, float2 q3,
+                                            float2 q4, float eps) {
+    const float2 s6 = f2(1.0f / 6.0f), c13 = f2(13.0f / 12.0f), qr = f2(0.25f);
+    const float2 p0 = f2mul(f2fma(q0, f2(2.f), f2fma(q1, f2(-7.f), f2mul(q2, f2(11.f)))), s6);
+    const float2 p1 = f2mul(f2fma(q1, f2(-1.f), f2fma(q2, f2(5.f), f2mul(q3, f2(2.f)))), s6);
+    const float2 p2 = f2mul(f2fma(q2, f2(2.f), f2fma(q3, f2(5.f), f2mul(q4, f2(-1.f)))), s6);
+    float2 a = f2add(f2fma(q1, f2(-2.f), q0), q2), b = f2fma(q2, f2(3.f), f2fma(q1, f2(-4.f), q0));
+    const float2 b0 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
+    a = f2add(f2fma(q2, f2(-2.f), q1), q3);
+    b = f2add(q1, f2mul(q3, f2(-1.f)));
+    const float2 b1 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
+    a = f2add(f2fma(q3, f2(-2.f), q2), q4);
+    b = f2fma(q3, f2(-4.f), f2fma(q2, f2(3.f), q4));
+    const float2 b2 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
+    const float2 tau = make_float2(fabsf(b0.x - b2.x), fabsf(b0.y - b2.y));
+    const float2 r0 = make_float2(fminf(__fdividef(tau.x, b0.x + eps), 1e18f),
+                                  fminf(__fdividef(tau.y, b0.y + eps), 1e18f));
+    const float2 r1 = make_float2(fminf(__fdividef(tau.x, b1.x + eps), 1e18f),
+                                  fminf(__fdividef(tau.y, b1.y + eps), 1e18f));
+    const float2 r2 = make_float2(fminf(__fdividef(tau.x, b2.x + eps), 1e18f),
+                                  fminf(__fdividef(tau.y, b2.y + eps), 1e18f));
+    const float2 a0 = f2mul(f2(0.1f), f2fma(r0, r0, f2(1.f)));
+    const float2 a1 = f2mul(f2(0.6f), f2fma(r1, r1, f2(1.f)));
+    const float2 a2 = f2mul(f2(0.3f), f2fma(r2, r2, f2(1.f)));
+    const float2 num = f2fma(a0, p0, f2fma(a1, p1, f2mul(a2, p2)));
+    const float2 den = f2add(f2add(a0, a1), a2);
+    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
+template <> struct WenoPair<float> {
+    static __device__ __forceinline__ void run(const float* qa, const float* qb, unsigned ina,
+                                               unsigned inb, float eps, int linear, float& oa,
+                                               float& ob) {
+        if (ina == 31u && inb == 31u && !linear) {
+            const float2 o = weno5z_x2(make_float2(qa[0], qb[0]), make_float2(qa[1], qb[1]),
+                                       make_float2(qa[2], qb[2]), make_float2(qa[3], qb[3]),
+                                       make_float2(qa[4], qb[4]), eps);
+            oa = o.x;
+            ob = o.y;
+            return;
+        }
+        oa = weno_adaptive(qa, ina, eps, linear);
+        ob = weno_adaptive(qb, inb, eps, linear);
+    }
+};
+
 // ----------------------------------------------------------------------- launchers
 // Implemented in ocean_kernels.cu, instantiated for double and float.
 

@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
 // the same thread, so they stay in L2), which keeps shared memory small and occupancy
 // bounded by registers only.
 constexpr int TX = 32, TY = 8, NT = TX * TY;
+// resident blocks per SM the register budget is sized for (FP64 needs more registers)
+template <typename R> struct TileOcc { static constexpr int value = 3; };
+template <> struct TileOcc<double> { static constexpr int value = 1; };
 
 // padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
 // the domain stage a few columns beyond it, whose values only feed threads that are
@@ -126,11 +129,25 @@ __device__ __forceinline__ long tix(const GeoD& g, int i, int j) {
     return ix2(g, i, j);
 }
 
+// asynchronous global -> shared copies of one element (cp.async, completion tracked per
+// thread by commit/wait groups), so the next level's tile streams in while this level
+// is computed
+__device__ __forceinline__ void cp_async_el(float* dst, const float* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ tracers
 
 template <typename R>
 struct TracerSmem {
-    R T[TY + 6][TX + 6], S[TY + 6][TX + 6];           // anomalies of level k, halo 3
+    R T[2][TY + 6][TX + 6], S[2][TY + 6][TX + 6];     // anomalies of levels k, k+1, halo 3
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
     R fxU[TY][TX + 1], fxT[TY][TX + 1], fxS[TY][TX + 1];   // x-face transport and fluxes
@@ -147,7 +164,7 @@ struct TracerSmem {
 // (WENO is translation-equivariant, so adding U Tref(k) gives the flux of T itself);
 // vertical ones reconstruct full values, since the reference varies along the column.
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const R* __restrict__ u,
                                                const R* __restrict__ v, const R* __restrict__ w,
                                                const R* __restrict__ T, const R* __restrict__ S,
                                                R* __restrict__ kap, R* __restrict__ GTp,
@@ -185,6 +202,19 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
     const int kstart = sm.kmin;
     if (kstart >= nz) return;   // the whole patch is land
 
+    // ---- the staged tile (halo 3) streams in one level ahead, double buffered
+    constexpr int TT = (TY + 6) * (TX + 6);
+    auto stage = [&](int k, int buf) {
+        for (int q = tid; q < TT; q += NT) {
+            const int a = q / (TX + 6), b = q % (TX + 6);
+            const long c = k * P + tix(g, i0 - 3 + b, j0 - 3 + a);
+            cp_async_el(&sm.T[buf][a][b], &T[c]);
+            cp_async_el(&sm.S[buf][a][b], &S[c]);
+        }
+        cp_async_commit();
+    };
+    stage(kstart, 0);
+
     const R rac = p.rAc[(mine ? j : 0) + OC_H];
     // register window of full values at levels k-2 .. k+3 (0 outside the column)
     R wT[6], wS[6];
@@ -199,14 +229,29 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
 
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        // ---- stage the anomalies of level k (halo 3)
-        for (int q = tid; q < (TY + 6) * (TX + 6); q += NT) {
-            const int a = q / (TX + 6), b = q % (TX + 6);
-            const long c = Pk + tix(g, i0 - 3 + b, j0 - 3 + a);
-            sm.T[a][b] = T[c];
-            sm.S[a][b] = S[c];
-        }
+        const int cb = (k - kstart) & 1;
+        // ---- level k has landed; start level k+1 into the other buffer (its previous
+        // readers finished before this barrier)
+        cp_async_wait_all();
         __syncthreads();
+        if (k + 1 < nz) stage(k + 1, 1 - cb);
+        // own-cell operands of level k, issued before the face work
+        const bool live = mine && k >= kb;
+        const long ck = Pk + c2;
+        R wt = R(0), k0 = R(0), k1 = R(0), gT0 = R(0), gS0 = R(0), T0 = R(0), S0 = R(0);
+        if (live) {
+            if (k + 1 < nz) {
+                wt = w[ck + P];
+                if (STEP) k1 = kap[ck + P];
+            }
+            if (STEP) {
+                k0 = kap[ck];
+                gT0 = GTp[ck];
+                gS0 = GSp[ck];
+                T0 = T[ck];
+                S0 = S[ck];
+            }
+        }
         const R dzk = p.dz[k];
         // ---- x-face fluxes, each face once
         for (int q = tid; q < TY * (TX + 1); q += NT) {
@@ -219,13 +264,15 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
 #pragma unroll
                 for (int n = 0; n < 5; ++n) {
                     const int col = ut >= R(0) ? b + n : b + 5 - n;
-                    qT[n] = sm.T[a + 3][col];
-                    qS[n] = sm.S[a + 3][col];
+                    qT[n] = sm.T[cb][a + 3][col];
+                    qS[n] = sm.S[cb][a + 3][col];
                     in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
                 }
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
                 fU = ut * p.dy * dzk;
-                fT = fU * weno_adaptive(qT, in, p.eps, p.linear);
-                fS = fU * weno_adaptive(qS, in, p.eps, p.linear);
+                fT = fU * rT;
+                fS = fU * rS;
             }
             sm.fxU[a][b] = fU;
             sm.fxT[a][b] = fT;
@@ -243,13 +290,15 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
 #pragma unroll
                 for (int n = 0; n < 5; ++n) {
                     const int row = vt >= R(0) ? a + n : a + 5 - n;
-                    qT[n] = sm.T[row][b + 3];
-                    qS[n] = sm.S[row][b + 3];
+                    qT[n] = sm.T[cb][row][b + 3];
+                    qS[n] = sm.S[cb][row][b + 3];
                     in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
                 }
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
                 fV = vt * p.dxv[fj + OC_H] * dzk;
-                fT = fV * weno_adaptive(qT, in, p.eps, p.linear);
-                fS = fV * weno_adaptive(qS, in, p.eps, p.linear);
+                fT = fV * rT;
+                fS = fV * rS;
             }
             sm.fyV[a][b] = fV;
             sm.fyT[a][b] = fT;
@@ -257,11 +306,9 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
         }
         __syncthreads();
         // ---- own cell
-        if (mine && k >= kb) {
-            const long ck = Pk + c2;
+        if (live) {
             R ftT = R(0), ftS = R(0);
             if (k + 1 < nz) {   // flux through the top face (bottom face of cell k+1)
-                const R wt = w[ck + P];
                 const bool pos = wt >= R(0);
                 R qT[5], qS[5];
                 unsigned in = 0;
@@ -274,8 +321,10 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
                     const int kk = pos ? k - 2 + n : k + 3 - n;
                     in |= (kk >= kb && kk < nz ? 1u : 0u) << n;
                 }
-                ftT = wt * weno_adaptive(qT, in, p.eps, p.linear);
-                ftS = wt * weno_adaptive(qS, in, p.eps, p.linear);
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                ftT = wt * rT;
+                ftS = wt * rS;
             }
             const R rdz = p.rdz[k];
             const R divU = sm.fxU[ty][tx + 1] - sm.fxU[ty][tx] + sm.fyV[ty + 1][tx] - sm.fyV[ty][tx];
@@ -289,17 +338,17 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
                 Tn[ck] = GT;
                 Sn[ck] = GS;
             } else {
-                const R gT = p.ca * GT - p.cb * GTp[ck];
-                const R gS = p.ca * GS - p.cb * GSp[ck];
+                const R gT = p.ca * GT - p.cb * gT0;
+                const R gS = p.ca * GS - p.cb * gS0;
                 GTp[ck] = GT;
                 GSp[ck] = GS;
-                const R lo = k > kb ? p.dt * kap[ck] * rdz * p.rdzf[k] : R(0);
-                const R hi = k < nz - 1 ? p.dt * kap[ck + P] * rdz * p.rdzf[k + 1] : R(0);
+                const R lo = k > kb ? p.dt * k0 * rdz * p.rdzf[k] : R(0);
+                const R hi = k < nz - 1 ? p.dt * k1 * rdz * p.rdzf[k + 1] : R(0);
                 // the diffusion of the reference profile moves to the right-hand side:
                 // (I - dt D) T'^{n+1} = T'* + dt D Tref
-                const R Ts = T[ck] + p.dt * gT
+                const R Ts = T0 + p.dt * gT
                            + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
-                const R Ss = S[ck] + p.dt * gS
+                const R Ss = S0 + p.dt * gS
                            + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
                 const R inv = R(1) / ((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
                 cprev = -hi * inv;
@@ -322,7 +371,6 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
             wT[5] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
             wS[5] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
         }
-        __syncthreads();   // the staged level and fluxes are reused by the next level
     }
     if (!STEP || !mine || kb >= nz) return;
     R xT = dTprev, xS = dSprev;   // level nz-1: x = d'
@@ -340,13 +388,13 @@ __global__ void __launch_bounds__(NT) k_tracer(KP<R> p, const R* __restrict__ u,
 
 template <typename R>
 struct MomentumSmem {
-    R u[TY + 6][TX + 5];      // u(k) at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3)
-    R v[TY + 5][TX + 6];      // v(k) at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
+    R u[2][TY + 6][TX + 5];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3); levels k, k+1
+    R v[2][TY + 5][TX + 6];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
+    R p[2][TY + 1][TX + 1];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
+    R w[3][TY + 1][TX + 1];   // w on the bottom faces of levels k, k+1, k+2 (ring), same centres
+    R nu[3][TY + 1][TX + 1];  // nu on those faces
     R z[TY + 5][TX + 5];      // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3)
-    R K[TY + 1][TX + 1];      // kinetic energy at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
-    R p[TY + 1][TX + 1];      // pressure anomaly, same centres
-    R w[2][TY + 1][TX + 1];   // w on the bottom faces of levels k and k+1, same centres
-    R nu[2][TY + 1][TX + 1];  // nu on those faces
+    R K[TY + 1][TX + 1];      // kinetic energy at the centres
     short kbz[TY + 5][TX + 5], kbzin[TY + 5][TX + 5];
     int kmin;
 };
@@ -356,7 +404,7 @@ struct MomentumSmem {
 // backward-Euler vertical viscosity (Thomas: c' in cu/cv scratch, d' in un/vn) and the
 // sum of the solved column Su = sum dz u**.
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT) k_momentum(
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
     KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
     const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
@@ -386,51 +434,67 @@ __global__ void __launch_bounds__(NT) k_momentum(
     __syncthreads();
     const int kstart = sm.kmin;
     if (kstart >= nz) return;
-    // w and nu on the bottom faces of level kstart
-    for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
-        const int a = q / (TX + 1), b = q % (TX + 1);
-        const long c = kstart * P + tix(g, i0 - 1 + b, j0 - 1 + a);
-        sm.w[0][a][b] = w[c];
-        sm.nu[0][a][b] = nu[c];
-    }
+
+    // ---- asynchronous staging: u, v, p of a level into buffer b; w, nu of a level into
+    // ring slot r
+    constexpr int TU = (TY + 6) * (TX + 5), TV = (TY + 5) * (TX + 6), TC = (TY + 1) * (TX + 1);
+    auto stage_uvp = [&](int k, int b) {
+        const long Pk = k * P;
+        for (int q = tid; q < TU; q += NT) {
+            const int a = q / (TX + 5), c = q % (TX + 5);
+            cp_async_el(&sm.u[b][a][c], &u[Pk + tix(g, i0 - 2 + c, j0 - 3 + a)]);
+        }
+        for (int q = tid; q < TV; q += NT) {
+            const int a = q / (TX + 6), c = q % (TX + 6);
+            cp_async_el(&sm.v[b][a][c], &v[Pk + tix(g, i0 - 3 + c, j0 - 2 + a)]);
+        }
+        for (int q = tid; q < TC; q += NT) {
+            const int a = q / (TX + 1), c = q % (TX + 1);
+            cp_async_el(&sm.p[b][a][c], &pr[Pk + tix(g, i0 - 1 + c, j0 - 1 + a)]);
+        }
+    };
+    auto stage_wnu = [&](int k, int r) {
+        const long Pk = k * P;
+        for (int q = tid; q < TC; q += NT) {
+            const int a = q / (TX + 1), c = q % (TX + 1);
+            const long o = Pk + tix(g, i0 - 1 + c, j0 - 1 + a);
+            cp_async_el(&sm.w[r][a][c], &w[o]);
+            cp_async_el(&sm.nu[r][a][c], &nu[o]);
+        }
+    };
+    stage_uvp(kstart, 0);
+    stage_wnu(kstart, 0);
+    if (kstart + 1 < nz) stage_wnu(kstart + 1, 1);
+    cp_async_commit();
+
     const int jr = (mine ? j : 0) + OC_H;
     const R rdxc = p.rdxc[jr], fu = p.fu[jr], fv = p.fv[jr];
     R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
-    // own faces: u, v at k-1 (lower) and k+1 (upper); level k comes from the tile
+    // own faces: u, v at k-1 (lower); level k comes from the tile, k+1 from global
     R ulo = R(0), vlo = R(0);
     if (mine && kstart >= 1) {
         ulo = u[(kstart - 1) * P + c2];
         vlo = v[(kstart - 1) * P + c2];
     }
-    int cur = 0;
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        const int nxt = 1 - cur;
-        // ---- stage level k: u, v (halo 3), pressure, and w, nu of level k+1
-        for (int q = tid; q < (TY + 6) * (TX + 5); q += NT) {
-            const int a = q / (TX + 5), b = q % (TX + 5);
-            sm.u[a][b] = u[Pk + tix(g, i0 - 2 + b, j0 - 3 + a)];
-        }
-        for (int q = tid; q < (TY + 5) * (TX + 6); q += NT) {
-            const int a = q / (TX + 6), b = q % (TX + 6);
-            sm.v[a][b] = v[Pk + tix(g, i0 - 3 + b, j0 - 2 + a)];
-        }
-        for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
-            const int a = q / (TX + 1), b = q % (TX + 1);
-            const long c = tix(g, i0 - 1 + b, j0 - 1 + a);
-            sm.p[a][b] = pr[Pk + c];
-            if (k + 1 < nz) {
-                sm.w[nxt][a][b] = w[Pk + P + c];
-                sm.nu[nxt][a][b] = nu[Pk + P + c];
-            }
-        }
-        R uhi = R(0), vhi = R(0);
+        const int cb = (k - kstart) & 1;
+        const int rc = (k - kstart) % 3, rn = (rc + 1) % 3, rnn = (rc + 2) % 3;
+        cp_async_wait_all();
+        __syncthreads();   // level k is in; buffers of the previous level are free
+        if (k + 1 < nz) stage_uvp(k + 1, 1 - cb);
+        if (k + 2 < nz) stage_wnu(k + 2, rnn);
+        cp_async_commit();
+        R uhi = R(0), vhi = R(0), gu0 = R(0), gv0 = R(0);
         if (mine && k + 1 < nz) {
             uhi = u[Pk + P + c2];
             vhi = v[Pk + P + c2];
         }
-        __syncthreads();
+        if (STEP && mine) {
+            if (k >= ku) gu0 = Gup[Pk + c2];
+            if (k >= kv) gv0 = Gvp[Pk + c2];
+        }
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
         for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
             const int a = q / (TX + 5), b = q % (TX + 5);
@@ -438,59 +502,68 @@ __global__ void __launch_bounds__(NT) k_momentum(
             R zz = R(0);
             if (k >= sm.kbz[a][b]) {
                 const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
-                // u(i, jc) = sm.u[a + 1][b], u(i, jc-1) = sm.u[a][b];
-                // v(i, jc) = sm.v[a][b + 1], v(i-1, jc) = sm.v[a][b]
-                const R circ = p.dy * (sm.v[a][b + 1] - sm.v[a][b])
-                             - (p.dxc[jrc] * sm.u[a + 1][b] - p.dxc[jrc - 1] * sm.u[a][b]);
+                // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
+                // v(i-1, jc) = v[a][b]
+                const R circ = p.dy * (sm.v[cb][a][b + 1] - sm.v[cb][a][b])
+                             - (p.dxc[jrc] * sm.u[cb][a + 1][b] - p.dxc[jrc - 1] * sm.u[cb][a][b]);
                 zz = circ * p.rAz[jrc];
             }
             sm.z[a][b] = zz;
         }
-        for (int q = tid; q < (TY + 1) * (TX + 1); q += NT) {
+        for (int q = tid; q < TC; q += NT) {
             const int a = q / (TX + 1), b = q % (TX + 1);
-            // centre (i0-1+b, j0-1+a): u at b+1, b+2 of row a+2; v at col b+2 rows a+1, a+2
-            const R ua = sm.u[a + 2][b + 1], ub = sm.u[a + 2][b + 2];
-            const R va = sm.v[a + 1][b + 2], vb = sm.v[a + 2][b + 2];
+            // centre (i0-1+b, j0-1+a): u at cols b+1, b+2 of row a+2; v at col b+2, rows a+1, a+2
+            const R ua = sm.u[cb][a + 2][b + 1], ub = sm.u[cb][a + 2][b + 2];
+            const R va = sm.v[cb][a + 1][b + 2], vb = sm.v[cb][a + 2][b + 2];
             sm.K[a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
         }
         __syncthreads();
         if (mine) {
             const R rdz = p.rdz[k];
-            if (k >= ku) {   // ---------------- u at the west face of column (i, j)
-                const R u0 = sm.u[ty + 3][tx + 2];
-                const R vh = R(0.25) * (sm.v[ty + 2][tx + 2] + sm.v[ty + 2][tx + 3]
-                                      + sm.v[ty + 3][tx + 2] + sm.v[ty + 3][tx + 3]);
-                R q[5];
-                unsigned in = 0;
+            const bool du_ = k >= ku, dv_ = k >= kv;
+            // ---- the two vorticity reconstructions of this thread
+            const R u0 = sm.u[cb][ty + 3][tx + 2];
+            const R v0 = sm.v[cb][ty + 2][tx + 3];
+            const R vh = R(0.25) * (sm.v[cb][ty + 2][tx + 2] + sm.v[cb][ty + 2][tx + 3]
+                                  + sm.v[cb][ty + 3][tx + 2] + sm.v[cb][ty + 3][tx + 3]);
+            const R uh = R(0.25) * (sm.u[cb][ty + 2][tx + 2] + sm.u[cb][ty + 2][tx + 3]
+                                  + sm.u[cb][ty + 3][tx + 2] + sm.u[cb][ty + 3][tx + 3]);
+            R qa[5], qb[5];
+            unsigned ina = 0, inb = 0;
 #pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int a = vh >= R(0) ? ty + n : ty + 5 - n;   // corner row j-2+..
-                    q[n] = sm.z[a][tx + 2];
-                    in |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
-                }
-                const R zt = weno_adaptive(q, in, p.eps, p.linear);
+            for (int n = 0; n < 5; ++n) {
+                const int a = vh >= R(0) ? ty + n : ty + 5 - n;   // corner rows j-2.. (u-face)
+                qa[n] = sm.z[a][tx + 2];
+                ina |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
+                const int b = uh >= R(0) ? tx + n : tx + 5 - n;   // corner cols i-2.. (v-face)
+                qb[n] = sm.z[ty + 2][b];
+                inb |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
+            }
+            R ztu, ztv;
+            WenoPair<R>::run(qa, qb, ina, inb, p.eps, p.linear, ztu, ztv);
+            if (du_) {   // ---------------- u at the west face of column (i, j)
                 const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty + 1][tx]) * rdxc;
-                const R dP = (sm.p[ty + 1][tx + 1] - sm.p[ty + 1][tx]) * rdxc;
+                const R dP = (sm.p[cb][ty + 1][tx + 1] - sm.p[cb][ty + 1][tx]) * rdxc;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[nxt][ty + 1][tx] + sm.w[nxt][ty + 1][tx + 1]) * (uhi - u0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[rn][ty + 1][tx] + sm.w[rn][ty + 1][tx + 1]) * (uhi - u0) * p.rdzf[k + 1];
                 if (k - 1 >= ku)
-                    dn = R(0.5) * (sm.w[cur][ty + 1][tx] + sm.w[cur][ty + 1][tx + 1]) * (u0 - ulo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[rc][ty + 1][tx] + sm.w[rc][ty + 1][tx + 1]) * (u0 - ulo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? taux_s[c2] : R(0);
-                const R G = (zt + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
+                const R G = (ztu + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
                     un[ck] = G;
                 } else {
-                    const R gh = p.ca * G - p.cb * Gup[ck];
+                    const R gh = p.ca * G - p.cb * gu0;
                     Gup[ck] = G;
                     sUn += p.dz[k] * u0;
                     sGU += p.dz[k] * gh;
                     const R us = u0 + p.dt * gh;
                     const R lo = k > ku
-                        ? p.dt * R(0.5) * (sm.nu[cur][ty + 1][tx] + sm.nu[cur][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rc][ty + 1][tx] + sm.nu[rc][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[nxt][ty + 1][tx] + sm.nu[nxt][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rn][ty + 1][tx] + sm.nu[rn][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
@@ -498,41 +571,29 @@ __global__ void __launch_bounds__(NT) k_momentum(
                     un[ck] = duk;
                 }
             }
-            if (k >= kv) {   // ---------------- v at the south face of column (i, j)
-                const R v0 = sm.v[ty + 2][tx + 3];
-                const R uh = R(0.25) * (sm.u[ty + 2][tx + 2] + sm.u[ty + 2][tx + 3]
-                                      + sm.u[ty + 3][tx + 2] + sm.u[ty + 3][tx + 3]);
-                R q[5];
-                unsigned in = 0;
-#pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int b = uh >= R(0) ? tx + n : tx + 5 - n;   // corner col i-2+..
-                    q[n] = sm.z[ty + 2][b];
-                    in |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
-                }
-                const R zt = weno_adaptive(q, in, p.eps, p.linear);
+            if (dv_) {   // ---------------- v at the south face of column (i, j)
                 const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty][tx + 1]) * p.rdy;
-                const R dP = (sm.p[ty + 1][tx + 1] - sm.p[ty][tx + 1]) * p.rdy;
+                const R dP = (sm.p[cb][ty + 1][tx + 1] - sm.p[cb][ty][tx + 1]) * p.rdy;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[nxt][ty][tx + 1] + sm.w[nxt][ty + 1][tx + 1]) * (vhi - v0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[rn][ty][tx + 1] + sm.w[rn][ty + 1][tx + 1]) * (vhi - v0) * p.rdzf[k + 1];
                 if (k - 1 >= kv)
-                    dn = R(0.5) * (sm.w[cur][ty][tx + 1] + sm.w[cur][ty + 1][tx + 1]) * (v0 - vlo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[rc][ty][tx + 1] + sm.w[rc][ty + 1][tx + 1]) * (v0 - vlo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
-                const R G = -(zt + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
+                const R G = -(ztv + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
                     vn[ck] = G;
                 } else {
-                    const R gh = p.ca * G - p.cb * Gvp[ck];
+                    const R gh = p.ca * G - p.cb * gv0;
                     Gvp[ck] = G;
                     sVn += p.dz[k] * v0;
                     sGV += p.dz[k] * gh;
                     const R vs = v0 + p.dt * gh;
                     const R lo = k > kv
-                        ? p.dt * R(0.5) * (sm.nu[cur][ty][tx + 1] + sm.nu[cur][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rc][ty][tx + 1] + sm.nu[rc][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[nxt][ty][tx + 1] + sm.nu[nxt][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rn][ty][tx + 1] + sm.nu[rn][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
@@ -540,12 +601,11 @@ __global__ void __launch_bounds__(NT) k_momentum(
                     vn[ck] = dvk;
                 }
             }
-            ulo = sm.u[ty + 3][tx + 2];
-            vlo = sm.v[ty + 2][tx + 3];
+            ulo = u0;
+            vlo = v0;
         }
-        cur = nxt;
-        __syncthreads();
     }
+    cp_async_wait_all();
     if (!STEP || !mine) return;
     if (ku < nz) {
         R x = duk;   // level nz-1
