@@ -298,7 +298,7 @@ def main():
     bb = roofline.barotropic_bytes_per_column(esz, int(p["n_substeps"])) * wet_cols
     phase_frac["barotropic"] = {"ms": round(tb, 4), "GBs": round(bb / (tb / 1e3) / 1e9, 1),
                                 "frac": round(bb / (tb / 1e3) / 1e9 / peak, 3),
-                                "kernels": 2 * int(p["n_substeps"]) + 2}
+                                "kernels": -(-int(p["n_substeps"]) // 6) + 2}
 
     # ---------------------------------------------------------------- end to end, host buffers
     taux = torch.from_numpy(np.ascontiguousarray(case.taux)).pin_memory().numpy()

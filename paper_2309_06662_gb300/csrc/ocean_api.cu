@@ -59,7 +59,7 @@ struct ocean_s {
          *GV = nullptr, *Su = nullptr, *Sv = nullptr, *Ub = nullptr, *Vb = nullptr,
          *dE = nullptr, *paccE = nullptr, *paccU = nullptr, *paccV = nullptr, *gxe = nullptr,
          *gye = nullptr, *corrU = nullptr, *corrV = nullptr, *Hu = nullptr, *Hv = nullptr,
-         *rHu = nullptr, *rHv = nullptr;
+         *rHu = nullptr, *rHv = nullptr, *Ub2 = nullptr, *Vb2 = nullptr, *dE2 = nullptr;
     double *eta = nullptr, *accE = nullptr, *accU = nullptr, *accV = nullptr;
     short *kb = nullptr, *kbu = nullptr, *kbv = nullptr, *kbz = nullptr, *kbzin = nullptr;
     void* rowm = nullptr;   // 7 row arrays of (ny + 2H) elements
@@ -165,7 +165,8 @@ size_t layout(ocean_t m, char* base) {
     m->w = f3(); m->p = f3(); m->kap = f3(); m->nu = f3(); m->wk = f3();
     void** two[] = {&m->taux_s, &m->tauy_s, &m->Un, &m->Vn, &m->GU, &m->GV, &m->Su, &m->Sv,
                     &m->Ub, &m->Vb, &m->dE, &m->paccE, &m->paccU, &m->paccV, &m->gxe, &m->gye,
-                    &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv};
+                    &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv, &m->Ub2, &m->Vb2,
+                    &m->dE2};
     for (void** q : two) *q = f2();
     m->eta = c.take<double>(n2); m->accE = c.take<double>(n2);
     m->accU = c.take<double>(n2); m->accV = c.take<double>(n2);
@@ -443,6 +444,7 @@ StepBuffers<R> make_bufs(const ocean_t m) {
     b.Ub = P(m->Ub); b.Vb = P(m->Vb); b.dE = P(m->dE); b.paccE = P(m->paccE);
     b.paccU = P(m->paccU); b.paccV = P(m->paccV); b.gxe = P(m->gxe); b.gye = P(m->gye);
     b.corrU = P(m->corrU); b.corrV = P(m->corrV);
+    b.Ub2 = P(m->Ub2); b.Vb2 = P(m->Vb2); b.dE2 = P(m->dE2);
     b.Hu = P(m->Hu); b.Hv = P(m->Hv); b.rHu = P(m->rHu); b.rHv = P(m->rHv);
     b.eta = m->eta; b.accE = m->accE; b.accU = m->accU; b.accV = m->accV;
     return b;
@@ -452,7 +454,7 @@ StepBuffers<R> make_bufs(const ocean_t m) {
 long launches_per_step(const ocean_t m) {
     const long hk = (m->px ? 1 : 0) + (m->py ? 1 : 0);
     const long ns = m->prm.n_substeps;
-    return 3 + (hk + 1 + ns * (2 + 3 * hk) + 1) + 1 + hk;
+    return 3 + (hk + 1 + baro_passes((int)ns) + 1) + 1 + hk;
 }
 
 template <typename R>

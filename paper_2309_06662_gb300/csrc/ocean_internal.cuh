@@ -191,6 +191,7 @@ template <typename R> struct StepBuffers {
     const R *taux_s, *tauy_s;  // wind stress / (rho0 dz_top)
     R *Un, *Vn, *GU, *GV, *Su, *Sv;         // column sums (2-D)
     R *Ub, *Vb, *dE, *paccE, *paccU, *paccV, *gxe, *gye, *corrU, *corrV;
+    R *Ub2, *Vb2, *dE2;        // second buffers of the barotropic state (passes ping-pong)
     const R *Hu, *Hv, *rHu, *rHv;
     double *eta, *accE, *accU, *accV;
 };
@@ -206,6 +207,8 @@ void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double d
                        cudaStream_t s);
 template <typename R>
 void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s);
+// kernel launches of one barotropic sub-cycle of ns substeps, halos excluded
+int baro_passes(int ns);
 template <typename R>
 void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s);
 template <typename R>

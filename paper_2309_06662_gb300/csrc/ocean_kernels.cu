@@ -13,7 +13,8 @@
 //               kinetic-energy and pressure gradients, vertical advection, wind),
 //               quasi-AB2, vertical viscosity solve, column sums for the barotropic mode;
 //               2.5-D tiled
-//   k_baro_*    split-explicit barotropic sub-cycle with equal-weight averaging
+//   k_baro_*    split-explicit barotropic sub-cycle with equal-weight averaging, BS
+//               substeps per pass on shared-memory regions (temporal blocking)
 //   k_correct   barotropic correction of u and v
 //   k_halo*     periodic halo copies
 // One thread owns one water column; threads of a warp hold neighbouring columns of a
@@ -662,61 +663,120 @@ __global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restr
     gye[c2] = Hv[c2] > R(0) ? R(eta[c2] - eta[c2 - g.pitch]) : R(0);
 }
 
-// deta^m = deta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]^{m-1}
-template <typename R>
-__global__ void k_baro_eta(KP<R> p, const R* __restrict__ Ub, const R* __restrict__ Vb, R* dE,
-                           R* paccE, R dtau) {
-    const GeoD& g = p.g;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (long)g.nx * g.ny) return;
-    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    const long c2 = ix2(g, i, j);
-    if (g.kb[c2] >= g.nz) return;
-    const R div = p.dy * (Ub[c2 + 1] - Ub[c2])
-                + p.dxv[j + 1 + OC_H] * Vb[c2 + g.pitch] - p.dxv[j + OC_H] * Vb[c2];
-    const R e = dE[c2] - dtau * p.rAc[j + OC_H] * div;
-    dE[c2] = e;
-    paccE[c2] += e;
+// Temporal blocking of the sub-cycle (the one-GPU form of the paper's barotropic halo as
+// wide as the number of substeps): a block owns a BRX x BRY region of columns in shared
+// memory, an interior plus a BS-wide halo, and advances it BS substeps per pass; each
+// substep's forward-backward pair shrinks the valid region by one column on each side,
+// so after BS substeps the interior is exact.  One pass reads the state once and writes
+// it once instead of once per substep.  The state ping-pongs between two global buffers
+// across passes (neighbouring blocks read their halos from the previous pass).
+constexpr int BRX = 64, BRY = 32, BS = 6, BNT = 512, BC = BRX * BRY / BNT;
+
+// padded index of (i, j) with periodic wrap; -1 beyond a wall
+__device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
+    if (g.px) { i %= g.nx; if (i < 0) i += g.nx; }
+    else if (i < 0 || i >= g.nx) return -1;
+    if (g.py) { j %= g.ny; if (j < 0) j += g.ny; }
+    else if (j < 0 || j >= g.ny) return -1;
+    jw = j;
+    return ix2(g, i, j);
 }
 
-// U^m = U^{m-1} + dtau [-g H_u (eta^m_i - eta^m_{i-1})/dx_c + G_U] (and V); partial sums
-// of deta, U - U^n, V - V^n are flushed into the FP64 accumulators when `flush`
 template <typename R>
-__global__ void k_baro_uv(KP<R> p, const R* __restrict__ dE, const R* __restrict__ gxe,
-                          const R* __restrict__ gye, const R* __restrict__ Hu,
-                          const R* __restrict__ Hv, const R* __restrict__ GU,
-                          const R* __restrict__ GV, const R* __restrict__ Un,
-                          const R* __restrict__ Vn, R* Ub, R* Vb, R* paccE, R* paccU, R* paccV,
-                          double* accE, double* accU, double* accV, R dtau, R grav, int flush) {
+__global__ void __launch_bounds__(BNT) k_baro_pass(
+    KP<R> p, const R* __restrict__ Ea, const R* __restrict__ Ua, const R* __restrict__ Va,
+    R* __restrict__ Eb, R* __restrict__ Ub, R* __restrict__ Vb, const R* __restrict__ gxe,
+    const R* __restrict__ gye, const R* __restrict__ Hu, const R* __restrict__ Hv,
+    const R* __restrict__ GU, const R* __restrict__ GV, const R* __restrict__ Un,
+    const R* __restrict__ Vn, double* __restrict__ accE, double* __restrict__ accU,
+    double* __restrict__ accV, int nsub, R dtau, R grav) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    R* sE = reinterpret_cast<R*>(bsm);
+    R* sU = sE + BRX * BRY;
+    R* sV = sU + BRX * BRY;
     const GeoD& g = p.g;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (long)g.nx * g.ny) return;
-    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    const long c2 = ix2(g, i, j);
-    const R hu = Hu[c2], hv = Hv[c2];
-    R pu = paccU[c2], pv = paccV[c2];
-    if (hu > R(0)) {
-        const R Unew = Ub[c2] + dtau * (-grav * hu * (gxe[c2] + (dE[c2] - dE[c2 - 1])) * p.rdxc[j + OC_H]
-                                        + GU[c2]);
-        Ub[c2] = Unew;
-        pu += Unew - Un[c2];
+    const int tid = threadIdx.x;
+    const int IX = BRX - 2 * BS, IY = BRY - 2 * BS;
+    const int i0 = blockIdx.x * IX - BS, j0 = blockIdx.y * IY - BS;   // region origin
+    long gc[BC];
+    R Au[BC], Bu[BC], Av[BC], Bv[BC], ce[BC], dN[BC], dS[BC], u0[BC], v0[BC];
+    R pE[BC], pU[BC], pV[BC];
+    bool own[BC];
+#pragma unroll
+    for (int r = 0; r < BC; ++r) {
+        const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
+        int jw = 0;
+        const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
+        gc[r] = c;
+        own[r] = rx >= BS && rx < BRX - BS && ry >= BS && ry < BRY - BS && i0 + rx < g.nx &&
+                 j0 + ry < g.ny;
+        pE[r] = pU[r] = pV[r] = R(0);
+        if (c >= 0) {
+            sE[q] = Ea[c];
+            sU[q] = Ua[c];
+            sV[q] = Va[c];
+            const R hu = Hu[c], hv = Hv[c];
+            // U += dtau [-g H_u (gxe + deta_i - deta_{i-1})/dx_c + G_U]
+            //    = U + Bu - Au (deta_i - deta_{i-1})
+            Au[r] = hu > R(0) ? dtau * grav * hu * p.rdxc[jw + OC_H] : R(0);
+            Bu[r] = hu > R(0) ? dtau * GU[c] - Au[r] * gxe[c] : R(0);
+            Av[r] = hv > R(0) ? dtau * grav * hv * p.rdy : R(0);
+            Bv[r] = hv > R(0) ? dtau * GV[c] - Av[r] * gye[c] : R(0);
+            const bool wet = g.kb[c] < g.nz;
+            ce[r] = wet ? dtau * p.rAc[jw + OC_H] : R(0);
+            dN[r] = p.dxv[jw + 1 + OC_H];
+            dS[r] = p.dxv[jw + OC_H];
+            u0[r] = own[r] ? Un[c] : R(0);
+            v0[r] = own[r] ? Vn[c] : R(0);
+        } else {
+            sE[q] = sU[q] = sV[q] = R(0);
+            Au[r] = Bu[r] = Av[r] = Bv[r] = ce[r] = dN[r] = dS[r] = u0[r] = v0[r] = R(0);
+        }
     }
-    if (hv > R(0)) {
-        const R Vnew = Vb[c2] + dtau * (-grav * hv * (gye[c2] + (dE[c2] - dE[c2 - g.pitch])) * p.rdy
-                                        + GV[c2]);
-        Vb[c2] = Vnew;
-        pv += Vnew - Vn[c2];
+    __syncthreads();
+    for (int m = 0; m < nsub; ++m) {
+        // deta^m = deta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]
+        // (each column reads only its own deta here, so it can be overwritten in place)
+#pragma unroll
+        for (int r = 0; r < BC; ++r) {
+            const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
+            if (rx + 1 < BRX && ry + 1 < BRY && ce[r] != R(0)) {
+                const R div = p.dy * (sU[q + 1] - sU[q]) + dN[r] * sV[q + BRX] - dS[r] * sV[q];
+                const R e = sE[q] - ce[r] * div;
+                sE[q] = e;
+                pE[r] += e;
+            }
+        }
+        __syncthreads();
+        // U^m, V^m from eta^m (each column reads only its own U, V here)
+#pragma unroll
+        for (int r = 0; r < BC; ++r) {
+            const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
+            if (rx >= 1 && Au[r] != R(0)) {
+                const R un = sU[q] + Bu[r] - Au[r] * (sE[q] - sE[q - 1]);
+                sU[q] = un;
+                pU[r] += un - u0[r];
+            }
+            if (ry >= 1 && Av[r] != R(0)) {
+                const R vn = sV[q] + Bv[r] - Av[r] * (sE[q] - sE[q - BRX]);
+                sV[q] = vn;
+                pV[r] += vn - v0[r];
+            }
+        }
+        __syncthreads();
     }
-    if (flush) {
-        accE[c2] += (double)paccE[c2];
-        accU[c2] += (double)pu;
-        accV[c2] += (double)pv;
-        paccE[c2] = R(0);
-        pu = R(0);
-        pv = R(0);
+#pragma unroll
+    for (int r = 0; r < BC; ++r) {
+        if (!own[r]) continue;
+        const int q = tid + r * BNT;
+        const long c = gc[r];
+        Eb[c] = sE[q];
+        Ub[c] = sU[q];
+        Vb[c] = sV[q];
+        accE[c] += (double)pE[r];
+        accU[c] += (double)pU[r];
+        accV[c] += (double)pV[r];
     }
-    paccU[c2] = pu;
-    paccV[c2] = pv;
 }
 
 // eta^{n+1} = eta^n + mean(deta) in FP64; correction of the depth-integrated velocity
@@ -794,9 +854,6 @@ void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStr
                                                     b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
 }
 
-// flush the FP32 partial sums into the FP64 accumulators every this many substeps
-#define OC_BARO_FLUSH 8
-
 template <typename R>
 void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double dt, R grav,
                        cudaStream_t s) {
@@ -808,21 +865,25 @@ void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double d
     k_baro_begin<R><<<nbk, TPB, 0, s>>>(p, b.Un, b.Vn, b.eta, b.Hu, b.Hv, b.Ub, b.Vb, b.dE,
                                        b.paccE, b.paccU, b.paccV, b.accE, b.accU, b.accV, b.gxe,
                                        b.gye);
-    for (int m = 1; m <= ns; ++m) {
-        if (g.px || g.py) {
-            launch_halo2<R>(g, b.Ub, s);
-            launch_halo2<R>(g, b.Vb, s);
-        }
-        k_baro_eta<R><<<nbk, TPB, 0, s>>>(p, b.Ub, b.Vb, b.dE, b.paccE, dtau);
-        if (g.px || g.py) launch_halo2<R>(g, b.dE, s);
-        const int flush = (m % OC_BARO_FLUSH == 0) || m == ns;
-        k_baro_uv<R><<<nbk, TPB, 0, s>>>(p, b.dE, b.gxe, b.gye, b.Hu, b.Hv, b.GU, b.GV, b.Un,
-                                        b.Vn, b.Ub, b.Vb, b.paccE, b.paccU, b.paccV, b.accE,
-                                        b.accU, b.accV, dtau, grav, flush);
+    const dim3 grid((g.nx + BRX - 2 * BS - 1) / (BRX - 2 * BS),
+                    (g.ny + BRY - 2 * BS - 1) / (BRY - 2 * BS));
+    const size_t smem = (size_t)3 * BRX * BRY * sizeof(R);
+    R *Ea = b.dE, *Ua = b.Ub, *Va = b.Vb, *Eb = b.dE2, *Ub = b.Ub2, *Vb = b.Vb2;
+    for (int m0 = 0; m0 < ns; m0 += BS) {
+        const int nsub = ns - m0 < BS ? ns - m0 : BS;
+        k_baro_pass<R><<<grid, BNT, smem, s>>>(p, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye, b.Hu,
+                                               b.Hv, b.GU, b.GV, b.Un, b.Vn, b.accE, b.accU,
+                                               b.accV, nsub, dtau, grav);
+        R* t;
+        t = Ea; Ea = Eb; Eb = t;
+        t = Ua; Ua = Ub; Ub = t;
+        t = Va; Va = Vb; Vb = t;
     }
     k_baro_end<R><<<nbk, TPB, 0, s>>>(p, b.eta, b.accE, b.accU, b.accV, b.Un, b.Vn, b.Su, b.Sv,
                                      b.rHu, b.rHv, b.corrU, b.corrV, 1.0 / ns);
 }
+
+int baro_passes(int ns) { return (ns + BS - 1) / BS; }
 
 template <typename R>
 void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {

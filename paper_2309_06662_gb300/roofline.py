@@ -32,17 +32,17 @@ KERNEL_WORDS = {
 }
 
 
-def barotropic_bytes_per_column(esz: int, n_substeps: int, flush_every: int = 8) -> float:
-    """Bytes the split-explicit sub-cycle moves per wet column and step, as written:
-    begin (U^n, V^n, H_u, H_v, eta^n in; U, V, deta, partial sums, gradients and the
-    FP64 accumulators out), per substep the deta kernel (U, V, deta, partial in; deta,
-    partial out) and the U/V kernel (14 words in, 4 out), a flush of the partial sums
-    into the FP64 accumulators every `flush_every` substeps, and the end kernel."""
+def barotropic_bytes_per_column(esz: int, n_substeps: int, per_pass: int = 6) -> float:
+    """Bytes the split-explicit sub-cycle moves per wet column and step, as written: the
+    begin kernel (U^n, V^n, H_u, H_v and FP64 eta^n in; U, V, deta, partial sums and the
+    eta gradients out, FP64 accumulators cleared), one temporally blocked pass per
+    `per_pass` substeps (state deta, U, V, the six read-only terms and U^n, V^n in; the
+    state out and the three FP64 accumulators read and written), and the end kernel."""
+    passes = -(-n_substeps // per_pass)
     begin = 12 * esz + 8 + 24
-    sub = 24 * esz
-    flushes = -(-n_substeps // flush_every)
+    one_pass = 14 * esz + 48
     end = 8 * esz + 40
-    return begin + n_substeps * sub + flushes * (48 + esz) + end
+    return begin + passes * one_pass + end
 
 
 def wet_cells(depth: np.ndarray, z_faces: np.ndarray, min_depth: float) -> int:
