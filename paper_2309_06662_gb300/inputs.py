@@ -321,3 +321,20 @@ def latlon_window(case_nx: int, case_ny: int, lat: float, i0: int, j0: int, wx: 
     dlon = 360.0 / case_nx
     dlat = 2.0 * lat / case_ny
     return (i0 * dlon, (i0 + wx) * dlon, -lat + j0 * dlat, -lat + (j0 + wy) * dlat)
+
+
+# ----------------------------------------------------------------------------- closure weights
+
+def mlp_seeded_params(seed: int, dims, gain: float = 1.0):
+    """Seeded initial weights of a column MLP with layer widths `dims`: W [in, out] and b
+    [out] per layer, drawn N(0, gain^2/in) and stored as integers |n| <= 255 times a power
+    of two, so every value is exactly representable in bfloat16 (and float32)."""
+    params = []
+    for li, (a, b) in enumerate(zip(dims[:-1], dims[1:])):
+        sigma = gain / math.sqrt(a)
+        q = 6 - int(math.floor(math.log2(sigma)))          # sigma * 2^q in [64, 128)
+        n = np.clip(np.round(random_normal(seed, 100 + li, a * b) * sigma * 2.0 ** q), -255, 255)
+        W = (n * 2.0 ** -q).reshape(a, b)
+        nb = np.clip(np.round(random_normal(seed, 200 + li, b) * 0.1 * sigma * 2.0 ** q), -255, 255)
+        params.append((W, nb * 2.0 ** -q))
+    return params
