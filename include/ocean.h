@@ -217,6 +217,53 @@ int ocean_weno_faces(const void* d_q, const void* d_vel, const unsigned char* d_
 int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, const void* d_d,
                           void* d_x, int n, int nsys, int precision, void* stream);
 
+/* ---- learned column closure (the network, its loss and its training) ----
+ *
+ * A column MLP standing in for the subgrid tracer fluxes (the paper's own runs use the
+ * Richardson-number closure, Sec. "How performance was measured"; this network is an
+ * extension trained on coarse-grained fine runs of this same solver).  Layers:
+ * x (6 nz) -> H -> H -> H -> y (3 nz), SiLU after each hidden layer, BF16 tensor-core
+ * GEMMs with FP32 accumulation and FP32 master weights.  Inputs per column: T, S,
+ * centre-averaged u, v at the nz levels, N^2 and shear^2 on the nz bottom faces, each
+ * z-scored, 0 on dry levels.  Outputs: kappa_k = kappa softplus(y_k) (vertical
+ * diffusivity on face k), dG_T = gT y_{nz+k}, dG_S = gS y_{2nz+k} (tracer tendency
+ * corrections).  Flat parameter layout: for each layer W [in][out] row-major, then b
+ * [out]. */
+typedef struct ocean_mlp_s* ocean_mlp_t;
+
+/* Device pointers of one training batch of M columns: X [M][6nz] normalised features
+ * (fp32); per face or level [M][nz]: dzT, dzS (coarse vertical gradients on faces), FT,
+ * FS (subgrid vertical fluxes on faces), GT, GS (lateral residual tendencies on levels);
+ * face, wet (1 = the entry counts). */
+typedef struct {
+    const float *X, *dzT, *dzS, *FT, *FS, *GT, *GS;
+    const unsigned char *face, *wet;
+} ocean_batch;
+
+/* Output scales and loss normalisations:
+ * L = mean_face[((-kappa_k dzT - FT)/sFT)^2 + ((-kappa_k dzS - FS)/sFS)^2]
+ *   + mean_wet[((dG_T - GT)/sGT)^2 + ((dG_S - GS)/sGS)^2]. */
+typedef struct {
+    float kappa, gT, gS, sFT, sFS, sGT, sGS;
+} ocean_closure_scales;
+
+size_t ocean_mlp_param_count(int nz, int hidden);
+/* Allocates the weights, Adam state and activations for batches of up to max_batch
+ * columns (a multiple of 8) on `stream`; params may be NULL (zeros). */
+int ocean_mlp_create(int nz, int hidden, int max_batch, const float* params, void* stream,
+                     ocean_mlp_t* out);
+void ocean_mlp_destroy(ocean_mlp_t h);
+int ocean_mlp_set_params(ocean_mlp_t h, const float* host, size_t count);  /* resets Adam */
+int ocean_mlp_get_params(ocean_mlp_t h, float* host, size_t count);
+/* y = MLP(x) for M <= max_batch rows: d_X fp32 [M][6nz], d_Y fp32 [M][3nz] */
+int ocean_mlp_forward(ocean_mlp_t h, const float* d_X, int M, float* d_Y);
+/* Loss of a batch and the gradients (to host_grads in the flat layout, if not NULL). */
+int ocean_mlp_loss_grad(ocean_mlp_t h, const ocean_batch* batch, int M,
+                        const ocean_closure_scales* scales, float* loss, float* host_grads);
+/* One Adam step (lr; beta = 0.9, 0.999; eps = 1e-8) on a batch; the loss before it. */
+int ocean_mlp_train_step(ocean_mlp_t h, const ocean_batch* batch, int M,
+                         const ocean_closure_scales* scales, float lr, float* loss);
+
 /* The batched tridiagonal solve above, for callers that cannot allocate device memory:
  * code that runs while a CUDA graph is being captured (allocation cannot be captured),
  * code embedded in a framework that owns every allocation on the device, or a runtime

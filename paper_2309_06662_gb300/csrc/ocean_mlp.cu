@@ -1,0 +1,614 @@
+// ocean_mlp.cu -- the learned column closure's network on the tensor cores: BF16 GEMMs
+// with FP32 accumulation and fused epilogues (bias, SiLU, SiLU backward, transposed
+// copies for the weight gradients), the closure loss and its gradient, Adam on FP32
+// master weights, and the trainer handle of the C ABI.
+//
+// Network (see include/ocean.h): x (6 nz) -> H -> H -> H -> y (3 nz), SiLU after each
+// hidden layer.  Layer weights W [in][out]; the GEMMs read W^T [out][in] in the forward
+// pass and W [in][out] in the backward pass, both kept as BF16 copies of the FP32 master.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ocean.h"
+#include "ocean_internal.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+// ------------------------------------------------------------------ GEMM (tensor cores)
+
+constexpr int GM = 128, GN = 128, GK = 32, GLD = GK + 8, GTH = 256;
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool pred) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = pred ? 16 : 0;   // src-size 0: the 16 bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                        const void* p) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(s));
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad_f(float z) {
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+enum EpiMode { EPI_F32 = 0, EPI_SILU = 1, EPI_SILU_BWD = 2 };
+
+struct Epi {
+    int mode;
+    const float* bias;   // [N] (forward modes)
+    float* outF;         // fp32 [M][ldF]: C (+bias), or the pre-activation z
+    int ldF;
+    bf16* outB;          // bf16 [M][ldB]: silu(z), or dz
+    int ldB;
+    bf16* outT;          // bf16 [N][ldT]: transposed copy of outB (nullable)
+    int ldT;
+    const float* Zin;    // fp32 [M][ldZ] pre-activation (SiLU backward)
+    int ldZ;
+};
+
+__device__ __forceinline__ void epi_store(const Epi& e, int m, int n, float acc) {
+    if (e.mode == EPI_F32) {
+        e.outF[(long)m * e.ldF + n] = acc + (e.bias ? e.bias[n] : 0.f);
+    } else if (e.mode == EPI_SILU) {
+        const float z = acc + e.bias[n];
+        if (e.outF) e.outF[(long)m * e.ldF + n] = z;
+        const bf16 h = __float2bfloat16_rn(silu_f(z));
+        e.outB[(long)m * e.ldB + n] = h;
+        if (e.outT) e.outT[(long)n * e.ldT + m] = h;
+    } else {
+        const bf16 d = __float2bfloat16_rn(acc * silu_grad_f(e.Zin[(long)m * e.ldZ + n]));
+        e.outB[(long)m * e.ldB + n] = d;
+        if (e.outT) e.outT[(long)n * e.ldT + m] = d;
+    }
+}
+
+// C[m][n] = sum_k A[m][k] B[n][k]; A [M][lda], B [N][ldb] row-major BF16 (lda, ldb and K
+// multiples of 8); 128 x 128 block tiles, 8 warps of 64 x 32, m16n8k16 BF16 MMAs with
+// FP32 accumulators, cp.async double-buffered K tiles of 32.
+__global__ void __launch_bounds__(GTH) k_gemm_nt(const bf16* __restrict__ A, int lda,
+                                                 const bf16* __restrict__ B, int ldb, int M,
+                                                 int N, int K, Epi e) {
+    __shared__ __align__(128) bf16 sA[2][GM][GLD];
+    __shared__ __align__(128) bf16 sB[2][GN][GLD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    const int wm = warp >> 2, wn = warp & 3;
+    float acc[4][4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    auto load = [&](int kt, int buf) {
+        const int k0 = kt * GK;
+        for (int c = tid; c < GM * GK / 8; c += GTH) {
+            const int r = c >> 2, kc = (c & 3) * 8;
+            const int gm = m0 + r, gk = k0 + kc;
+            const bool p = gm < M && gk < K;
+            cp16(&sA[buf][r][kc], p ? (const void*)(A + (long)gm * lda + gk) : (const void*)A, p);
+            const int gn = n0 + r;
+            const bool q = gn < N && gk < K;
+            cp16(&sB[buf][r][kc], q ? (const void*)(B + (long)gn * ldb + gk) : (const void*)B, q);
+        }
+        cp_commit();
+    };
+    const int nk = (K + GK - 1) / GK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load(kt + 1, (kt + 1) & 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const int buf = kt & 1;
+#pragma unroll
+        for (int kk = 0; kk < GK; kk += 16) {
+            unsigned af[4][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+                ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3],
+                        &sA[buf][wm * 64 + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj) {
+                unsigned r0, r1, r2, r3;
+                ldsm_x4(r0, r1, r2, r3,
+                        &sB[buf][wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3)]
+                           [kk + ((lane >> 3) & 1) * 8]);
+                bfr[2 * nj][0] = r0;
+                bfr[2 * nj][1] = r1;
+                bfr[2 * nj + 1][0] = r2;
+                bfr[2 * nj + 1][1] = r3;
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const int mr = m0 + wm * 64 + mi * 16 + g;
+            const int nc = n0 + wn * 32 + ni * 8 + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = mr + 8 * h;
+                if (m >= M) continue;
+                if (nc < N) epi_store(e, m, nc, acc[mi][ni][2 * h]);
+                if (nc + 1 < N) epi_store(e, m, nc + 1, acc[mi][ni][2 * h + 1]);
+            }
+        }
+}
+
+void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& e,
+             cudaStream_t s) {
+    const dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
+    k_gemm_nt<<<grid, GTH, 0, s>>>(A, lda, B, ldb, M, N, K, e);
+}
+
+// ------------------------------------------------------------------ elementwise kernels
+
+// fp32 [M][C] -> bf16 [M][ldo] (and, if T, bf16 transpose [C][ldt])
+__global__ void k_to_bf16(const float* __restrict__ x, int M, int C, bf16* __restrict__ o,
+                          int ldo, bf16* __restrict__ t, int ldt) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long)M * C) return;
+    const int m = (int)(q / C), c = (int)(q % C);
+    const bf16 b = __float2bfloat16_rn(x[q]);
+    o[(long)m * ldo + c] = b;
+    if (t) t[(long)c * ldt + m] = b;
+}
+
+// sum over m of dz^T rows: db[o] = sum_m dzT[o][m]
+__global__ void k_rowsum(const bf16* __restrict__ dzT, int ld, int M, int N, float* __restrict__ out) {
+    const int o = blockIdx.x;
+    if (o >= N) return;
+    float s = 0.f;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) s += __bfloat162float(dzT[(long)o * ld + m]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[o] = red[0];
+}
+
+// counts of the face and wet masks of a batch (2 ints)
+__global__ void k_count_masks(const unsigned char* __restrict__ face,
+                              const unsigned char* __restrict__ wet, long n, int* out) {
+    int a = 0, b = 0;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        a += face[q] != 0;
+        b += wet[q] != 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], a);
+        atomicAdd(&out[1], b);
+    }
+}
+
+__device__ __forceinline__ float softplus_f(float z) { return z > 20.f ? z : log1pf(__expf(z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return 1.f / (1.f + __expf(-z)); }
+
+// Closure loss: per column m and level k, with kap = kappa softplus(y_k),
+//   rT = (-kap dzT - FT)/sFT, rS likewise on faces; qT = (gT y_{nz+k} - GT)/sGT, qS on
+//   wet levels; L = (sum rT^2 + rS^2)/n_face + (sum qT^2 + qS^2)/n_wet.
+// Writes dL/dy as bf16 [M][3nz] and its transpose, and per-block partial losses.
+__global__ void k_closure_loss(const float* __restrict__ Y, int M, int nz, ocean_closure_scales sc,
+                               const float* __restrict__ dzT, const float* __restrict__ dzS,
+                               const float* __restrict__ FT, const float* __restrict__ FS,
+                               const float* __restrict__ GT, const float* __restrict__ GS,
+                               const unsigned char* __restrict__ face,
+                               const unsigned char* __restrict__ wet, const int* __restrict__ counts,
+                               bf16* __restrict__ dY, bf16* __restrict__ dYt, int ldt,
+                               double* __restrict__ partial) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const float nf = fmaxf(1.f, (float)counts[0]), nw = fmaxf(1.f, (float)counts[1]);
+    double l = 0.0;
+    if (q < (long)M * nz) {
+        const int m = (int)(q / nz), k = (int)(q % nz);
+        const float* y = Y + (long)m * 3 * nz;
+        const float yk = y[k], ykap = sc.kappa * softplus_f(yk);
+        float dk = 0.f, dgt = 0.f, dgs = 0.f;
+        if (face[q]) {
+            const float rT = (-ykap * dzT[q] - FT[q]) / sc.sFT;
+            const float rS = (-ykap * dzS[q] - FS[q]) / sc.sFS;
+            l += (double)rT * rT + (double)rS * rS;
+            l /= nf;
+            dk = (2.f * rT * (-dzT[q]) / sc.sFT + 2.f * rS * (-dzS[q]) / sc.sFS) / nf;
+            dk *= sc.kappa * sigmoid_f(yk);
+        }
+        if (wet[q]) {
+            const float qT = (sc.gT * y[nz + k] - GT[q]) / sc.sGT;
+            const float qS = (sc.gS * y[2 * nz + k] - GS[q]) / sc.sGS;
+            l += ((double)qT * qT + (double)qS * qS) / nw;
+            dgt = 2.f * qT / sc.sGT * sc.gT / nw;
+            dgs = 2.f * qS / sc.sGS * sc.gS / nw;
+        }
+        const long base = (long)m * 3 * nz;
+        const bf16 b0 = __float2bfloat16_rn(dk), b1 = __float2bfloat16_rn(dgt), b2 = __float2bfloat16_rn(dgs);
+        dY[base + k] = b0;
+        dY[base + nz + k] = b1;
+        dY[base + 2 * nz + k] = b2;
+        dYt[(long)k * ldt + m] = b0;
+        dYt[(long)(nz + k) * ldt + m] = b1;
+        dYt[(long)(2 * nz + k) * ldt + m] = b2;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ p, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += p[b];
+        out[0] = s;
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights of one layer, then the two BF16
+// copies: W [in][out] and W^T [out][in]
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long n, int out, float lr, float b1, float b2,
+                       float eps, float c1, float c2, bf16* __restrict__ wb, bf16* __restrict__ wt,
+                       int in) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float gq = g[q];
+    const float mq = b1 * m[q] + (1.f - b1) * gq;
+    const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    const float wq = w[q] - lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    w[q] = wq;
+    if (wb) {
+        const bf16 b = __float2bfloat16_rn(wq);
+        wb[q] = b;
+        const int i = (int)(q / out), o = (int)(q % out);
+        wt[(long)o * in + i] = b;
+    }
+}
+
+__global__ void k_weight_copies(const float* __restrict__ w, long n, int out, int in,
+                                bf16* __restrict__ wb, bf16* __restrict__ wt) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const bf16 b = __float2bfloat16_rn(w[q]);
+    wb[q] = b;
+    const int i = (int)(q / out), o = (int)(q % out);
+    wt[(long)o * in + i] = b;
+}
+
+inline int nb(long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ trainer handle
+
+struct ocean_mlp_s {
+    int nz = 0, hidden = 0, max_batch = 0;
+    int dims[5] = {};
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+    // per layer
+    float *W[4] = {}, *b[4] = {}, *gW[4] = {}, *gb[4] = {}, *mW[4] = {}, *vW[4] = {}, *mb[4] = {},
+          *vb[4] = {};
+    bf16 *Wb[4] = {}, *Wt[4] = {};
+    // activations of one batch
+    bf16 *X = nullptr, *Xt = nullptr, *H[3] = {}, *Ht[3] = {}, *dYb = nullptr, *dYt = nullptr,
+         *dZ[2] = {}, *dZt[2] = {};
+    float *Z[3] = {}, *Y = nullptr;
+    double *partial = nullptr, *lossd = nullptr;
+    int* counts = nullptr;
+    long step = 0;
+    std::string err;
+};
+
+namespace {
+
+int mfail(ocean_mlp_t h, int code, const char* msg) {
+    if (h) h->err = msg;
+    oc_set_last_error(msg);
+    return code;
+}
+
+template <typename T>
+T* dalloc(ocean_mlp_t h, size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+    h->allocs.push_back(p);
+    cudaMemsetAsync(p, 0, n * sizeof(T), h->stream);
+    return reinterpret_cast<T*>(p);
+}
+
+// forward pass of M rows of bf16 features already in h->X; keeps Z, H (and their
+// transposes when train) for the backward pass; output fp32 Y [M][out]
+void forward(ocean_mlp_t h, int M, bool train, float* Yout) {
+    cudaStream_t s = h->stream;
+    const bf16* a = h->X;
+    int lda = h->dims[0];
+    for (int l = 0; l < 4; ++l) {
+        const int in = h->dims[l], out = h->dims[l + 1];
+        Epi e{};
+        if (l < 3) {
+            e.mode = EPI_SILU;
+            e.bias = h->b[l];
+            e.outF = train ? h->Z[l] : nullptr;
+            e.ldF = out;
+            e.outB = h->H[l];
+            e.ldB = out;
+            e.outT = train ? h->Ht[l] : nullptr;
+            e.ldT = h->max_batch;
+        } else {
+            e.mode = EPI_F32;
+            e.bias = h->b[l];
+            e.outF = Yout;
+            e.ldF = out;
+        }
+        gemm_nt(a, lda, h->Wt[l], in, M, out, in, e, s);
+        if (l < 3) {
+            a = h->H[l];
+            lda = out;
+        }
+    }
+}
+
+// gradients of the closure loss for a batch (forward included); loss to host
+int loss_and_grads(ocean_mlp_t h, const ocean_batch* bt, int M, const ocean_closure_scales* sc,
+                   float* loss) {
+    cudaStream_t s = h->stream;
+    const int nz = h->nz, in0 = h->dims[0], out = h->dims[4], MB = h->max_batch;
+    k_to_bf16<<<nb((long)M * in0, 256), 256, 0, s>>>(bt->X, M, in0, h->X, in0, h->Xt, MB);
+    forward(h, M, true, h->Y);
+    cudaMemsetAsync(h->counts, 0, 2 * sizeof(int), s);
+    k_count_masks<<<64, 256, 0, s>>>(bt->face, bt->wet, (long)M * nz, h->counts);
+    const int lb = nb((long)M * nz, 256);
+    k_closure_loss<<<lb, 256, 0, s>>>(h->Y, M, nz, *sc, bt->dzT, bt->dzS, bt->FT, bt->FS, bt->GT,
+                                      bt->GS, bt->face, bt->wet, h->counts, h->dYb, h->dYt, MB,
+                                      h->partial);
+    k_sum_partials<<<1, 32, 0, s>>>(h->partial, lb, h->lossd);
+    // backward: layer 4 (linear), then 3, 2, 1 (SiLU)
+    const bf16* dz = h->dYb;
+    const bf16* dzt = h->dYt;
+    for (int l = 3; l >= 0; --l) {
+        const int li = h->dims[l], lo = h->dims[l + 1];
+        const bf16* actT = l > 0 ? h->Ht[l - 1] : h->Xt;   // [li][MB]
+        Epi ew{};
+        ew.mode = EPI_F32;
+        ew.outF = h->gW[l];
+        ew.ldF = lo;
+        gemm_nt(actT, MB, dzt, MB, li, lo, M, ew, s);       // dW[i][o] = sum_m a[m][i] dz[m][o]
+        k_rowsum<<<lo, 256, 0, s>>>(dzt, MB, M, lo, h->gb[l]);
+        if (l > 0) {
+            const int nxt = l & 1;
+            Epi ed{};
+            ed.mode = EPI_SILU_BWD;
+            ed.outB = h->dZ[nxt];
+            ed.ldB = li;
+            ed.outT = h->dZt[nxt];
+            ed.ldT = MB;
+            ed.Zin = h->Z[l - 1];
+            ed.ldZ = li;
+            gemm_nt(dz, lo, h->Wb[l], lo, M, li, lo, ed, s);   // dh[m][i] = sum_o dz[m][o] W[i][o]
+            dz = h->dZ[nxt];
+            dzt = h->dZt[nxt];
+        }
+    }
+    (void)out;
+    if (loss) {
+        double L = 0.0;
+        if (cudaMemcpyAsync(&L, h->lossd, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return mfail(h, OCEAN_ERR_CUDA, "loss copy failed");
+        *loss = (float)L;
+    }
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : mfail(h, OCEAN_ERR_CUDA, "kernel launch failed");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+size_t ocean_mlp_param_count(int nz, int hidden) {
+    if (nz < 1 || hidden < 16) return 0;
+    const size_t d[5] = {(size_t)6 * nz, (size_t)hidden, (size_t)hidden, (size_t)hidden, (size_t)3 * nz};
+    size_t n = 0;
+    for (int l = 0; l < 4; ++l) n += d[l] * d[l + 1] + d[l + 1];
+    return n;
+}
+
+int ocean_mlp_create(int nz, int hidden, int max_batch, const float* params, void* stream,
+                     ocean_mlp_t* out) {
+    if (!out) return mfail(nullptr, OCEAN_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (nz < 1 || nz > OC_NZMAX || hidden < 16 || hidden % 16 || max_batch < 1 || max_batch % 8)
+        return mfail(nullptr, OCEAN_ERR_ARG,
+                     "ocean_mlp_create: need 1 <= nz <= 192, hidden a multiple of 16, max_batch a positive multiple of 8");
+    ocean_mlp_t h = new ocean_mlp_s();
+    h->nz = nz;
+    h->hidden = hidden;
+    h->max_batch = max_batch;
+    h->stream = (cudaStream_t)stream;
+    const int d[5] = {6 * nz, hidden, hidden, hidden, 3 * nz};
+    memcpy(h->dims, d, sizeof d);
+    bool ok = true;
+    for (int l = 0; l < 4 && ok; ++l) {
+        const size_t nw = (size_t)d[l] * d[l + 1], nbias = d[l + 1];
+        ok = (h->W[l] = dalloc<float>(h, nw)) && (h->b[l] = dalloc<float>(h, nbias)) &&
+             (h->gW[l] = dalloc<float>(h, nw)) && (h->gb[l] = dalloc<float>(h, nbias)) &&
+             (h->mW[l] = dalloc<float>(h, nw)) && (h->vW[l] = dalloc<float>(h, nw)) &&
+             (h->mb[l] = dalloc<float>(h, nbias)) && (h->vb[l] = dalloc<float>(h, nbias)) &&
+             (h->Wb[l] = dalloc<bf16>(h, nw)) && (h->Wt[l] = dalloc<bf16>(h, nw));
+    }
+    const size_t MB = max_batch;
+    ok = ok && (h->X = dalloc<bf16>(h, MB * d[0])) && (h->Xt = dalloc<bf16>(h, MB * d[0])) &&
+         (h->Y = dalloc<float>(h, MB * d[4])) && (h->dYb = dalloc<bf16>(h, MB * d[4])) &&
+         (h->dYt = dalloc<bf16>(h, MB * d[4])) && (h->partial = dalloc<double>(h, MB * nz / 256 + 2)) &&
+         (h->lossd = dalloc<double>(h, 1)) && (h->counts = dalloc<int>(h, 2));
+    for (int l = 0; l < 3 && ok; ++l)
+        ok = (h->H[l] = dalloc<bf16>(h, MB * hidden)) && (h->Ht[l] = dalloc<bf16>(h, MB * hidden)) &&
+             (h->Z[l] = dalloc<float>(h, MB * hidden));
+    for (int l = 0; l < 2 && ok; ++l)
+        ok = (h->dZ[l] = dalloc<bf16>(h, MB * (size_t)hidden)) && (h->dZt[l] = dalloc<bf16>(h, MB * (size_t)hidden));
+    if (!ok) {
+        ocean_mlp_destroy(h);
+        return mfail(nullptr, OCEAN_ERR_OOM, "ocean_mlp_create: device allocation failed");
+    }
+    if (params) {
+        int rc = ocean_mlp_set_params(h, params, ocean_mlp_param_count(nz, hidden));
+        if (rc) {
+            ocean_mlp_destroy(h);
+            return rc;
+        }
+    }
+    *out = h;
+    return OCEAN_OK;
+}
+
+void ocean_mlp_destroy(ocean_mlp_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+int ocean_mlp_set_params(ocean_mlp_t h, const float* host, size_t count) {
+    if (!h || !host) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (count != ocean_mlp_param_count(h->nz, h->hidden))
+        return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_set_params: wrong parameter count");
+    const float* p = host;
+    for (int l = 0; l < 4; ++l) {
+        const size_t nw = (size_t)h->dims[l] * h->dims[l + 1], nbias = h->dims[l + 1];
+        cudaMemcpyAsync(h->W[l], p, nw * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        p += nw;
+        cudaMemcpyAsync(h->b[l], p, nbias * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        p += nbias;
+        k_weight_copies<<<nb(nw, 256), 256, 0, h->stream>>>(h->W[l], nw, h->dims[l + 1], h->dims[l],
+                                                          h->Wb[l], h->Wt[l]);
+        cudaMemsetAsync(h->mW[l], 0, nw * sizeof(float), h->stream);
+        cudaMemsetAsync(h->vW[l], 0, nw * sizeof(float), h->stream);
+        cudaMemsetAsync(h->mb[l], 0, nbias * sizeof(float), h->stream);
+        cudaMemsetAsync(h->vb[l], 0, nbias * sizeof(float), h->stream);
+    }
+    h->step = 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return mfail(h, OCEAN_ERR_CUDA, "ocean_mlp_set_params: copy failed");
+    return OCEAN_OK;
+}
+
+int ocean_mlp_get_params(ocean_mlp_t h, float* host, size_t count) {
+    if (!h || !host) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (count != ocean_mlp_param_count(h->nz, h->hidden))
+        return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_get_params: wrong parameter count");
+    float* p = host;
+    for (int l = 0; l < 4; ++l) {
+        const size_t nw = (size_t)h->dims[l] * h->dims[l + 1], nbias = h->dims[l + 1];
+        cudaMemcpyAsync(p, h->W[l], nw * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+        p += nw;
+        cudaMemcpyAsync(p, h->b[l], nbias * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+        p += nbias;
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return mfail(h, OCEAN_ERR_CUDA, "ocean_mlp_get_params: copy failed");
+    return OCEAN_OK;
+}
+
+int ocean_mlp_forward(ocean_mlp_t h, const float* d_X, int M, float* d_Y) {
+    if (!h || !d_X || !d_Y) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (M < 1 || M > h->max_batch) return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_forward: 1 <= M <= max_batch");
+    const int in0 = h->dims[0];
+    k_to_bf16<<<nb((long)M * in0, 256), 256, 0, h->stream>>>(d_X, M, in0, h->X, in0, nullptr, 0);
+    forward(h, M, false, d_Y);
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : mfail(h, OCEAN_ERR_CUDA, "kernel launch failed");
+}
+
+int ocean_mlp_loss_grad(ocean_mlp_t h, const ocean_batch* batch, int M,
+                        const ocean_closure_scales* sc, float* loss, float* host_grads) {
+    if (!h || !batch || !sc) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (M < 1 || M > h->max_batch || M % 8)
+        return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_loss_grad: M must be a multiple of 8 in [8, max_batch]");
+    int rc = loss_and_grads(h, batch, M, sc, loss);
+    if (rc) return rc;
+    if (host_grads) {
+        float* p = host_grads;
+        for (int l = 0; l < 4; ++l) {
+            const size_t nw = (size_t)h->dims[l] * h->dims[l + 1], nbias = h->dims[l + 1];
+            cudaMemcpyAsync(p, h->gW[l], nw * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+            p += nw;
+            cudaMemcpyAsync(p, h->gb[l], nbias * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+            p += nbias;
+        }
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return mfail(h, OCEAN_ERR_CUDA, "gradient copy failed");
+    }
+    return OCEAN_OK;
+}
+
+int ocean_mlp_train_step(ocean_mlp_t h, const ocean_batch* batch, int M,
+                         const ocean_closure_scales* sc, float lr, float* loss) {
+    if (!h || !batch || !sc) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (M < 1 || M > h->max_batch || M % 8)
+        return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_train_step: M must be a multiple of 8 in [8, max_batch]");
+    int rc = loss_and_grads(h, batch, M, sc, loss);
+    if (rc) return rc;
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+    for (int l = 0; l < 4; ++l) {
+        const long nw = (long)h->dims[l] * h->dims[l + 1], nbias = h->dims[l + 1];
+        k_adam<<<nb(nw, 256), 256, 0, h->stream>>>(h->W[l], h->gW[l], h->mW[l], h->vW[l], nw,
+                                                   h->dims[l + 1], lr, b1, b2, eps, c1, c2,
+                                                   h->Wb[l], h->Wt[l], h->dims[l]);
+        k_adam<<<nb(nbias, 256), 256, 0, h->stream>>>(h->b[l], h->gb[l], h->mb[l], h->vb[l], nbias,
+                                                      1, lr, b1, b2, eps, c1, c2, nullptr, nullptr, 1);
+    }
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : mfail(h, OCEAN_ERR_CUDA, "kernel launch failed");
+}
+
+}  // extern "C"

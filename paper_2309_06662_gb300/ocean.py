@@ -52,6 +52,14 @@ class OceanParams(ctypes.Structure):
                 ("check_every", c_int), ("taux", POINTER(c_double)), ("tauy", POINTER(c_double))]
 
 
+class OceanBatch(ctypes.Structure):
+    _fields_ = [(n, c_void_p) for n in ("X", "dzT", "dzS", "FT", "FS", "GT", "GS", "face", "wet")]
+
+
+class ClosureScales(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("kappa", "gT", "gS", "sFT", "sFS", "sGT", "sGS")]
+
+
 class OceanDiag(ctypes.Structure):
     _fields_ = [("step", c_long), ("tracer_T", c_double), ("tracer_S", c_double),
                 ("volume_eta", c_double), ("ke", c_double), ("max_cfl", c_double),
@@ -111,6 +119,16 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_weno_faces": (c_int, [pv, pv, pv, c_int, pv, c_int, c_double, c_int, pv]),
             "ocean_tridiag_batched": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
             "ocean_tridiag_batched_static": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
+            "ocean_mlp_param_count": (c_size_t, [c_int, c_int]),
+            "ocean_mlp_create": (c_int, [c_int, c_int, c_int, POINTER(ctypes.c_float), pv, POINTER(pv)]),
+            "ocean_mlp_destroy": (None, [pv]),
+            "ocean_mlp_set_params": (c_int, [pv, POINTER(ctypes.c_float), c_size_t]),
+            "ocean_mlp_get_params": (c_int, [pv, POINTER(ctypes.c_float), c_size_t]),
+            "ocean_mlp_forward": (c_int, [pv, pv, c_int, pv]),
+            "ocean_mlp_loss_grad": (c_int, [pv, POINTER(OceanBatch), c_int, POINTER(ClosureScales),
+                                            POINTER(ctypes.c_float), POINTER(ctypes.c_float)]),
+            "ocean_mlp_train_step": (c_int, [pv, POINTER(OceanBatch), c_int, POINTER(ClosureScales),
+                                             ctypes.c_float, POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -351,3 +369,97 @@ def tridiag_batched(a, b, c, d, precision: int = OCEAN_FP64):
                                       c_void_p(x.data_ptr()), n, nsys, precision, c_void_p(s))
     _check(rc)
     return x
+
+
+# ----------------------------------------------------------------------------- closure network
+
+def flatten_params(params) -> np.ndarray:
+    """[(W [in, out], b [out])...] -> the flat float32 layout of the C ABI."""
+    return np.concatenate([np.concatenate([W.reshape(-1), b.reshape(-1)]) for W, b in params]
+                          ).astype(np.float32)
+
+
+def unflatten_params(flat: np.ndarray, dims):
+    out, o = [], 0
+    for a, b in zip(dims[:-1], dims[1:]):
+        W = flat[o:o + a * b].reshape(a, b)
+        o += a * b
+        out.append((W, flat[o:o + b]))
+        o += b
+    return out
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(ctypes.c_float))
+
+
+class MLP:
+    """The closure network's trainer handle (ocean_mlp_*) on torch's current stream."""
+
+    def __init__(self, nz: int, hidden: int, max_batch: int, params=None):
+        torch = _torch_cuda()
+        L = load()
+        self.nz, self.hidden, self.max_batch = nz, hidden, max_batch
+        self.dims = [6 * nz, hidden, hidden, hidden, 3 * nz]
+        self.count = L.ocean_mlp_param_count(nz, hidden)
+        flat = flatten_params(params) if params is not None else None
+        h = c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream
+        _check(L.ocean_mlp_create(nz, hidden, max_batch, _fp(flat) if flat is not None else None,
+                                  c_void_p(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ocean_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        flat = np.zeros(self.count, dtype=np.float32)
+        _check(load().ocean_mlp_get_params(self._h, _fp(flat), flat.size))
+        return unflatten_params(flat.astype(np.float64), self.dims)
+
+    def set_params(self, params) -> None:
+        flat = flatten_params(params)
+        _check(load().ocean_mlp_set_params(self._h, _fp(flat), flat.size))
+
+    def forward(self, X):
+        """X: torch CUDA float32 [M, 6nz] -> Y [M, 3nz]."""
+        torch = _torch_cuda()
+        X = X.to(device="cuda", dtype=torch.float32).contiguous()
+        Y = torch.empty((X.shape[0], self.dims[-1]), device="cuda", dtype=torch.float32)
+        _check(load().ocean_mlp_forward(self._h, c_void_p(X.data_ptr()), X.shape[0],
+                                        c_void_p(Y.data_ptr())))
+        return Y
+
+    @staticmethod
+    def batch(tensors):
+        """ocean_batch from a dict of torch CUDA tensors (float32 / uint8, contiguous)."""
+        b = OceanBatch()
+        for k in ("X", "dzT", "dzS", "FT", "FS", "GT", "GS", "face", "wet"):
+            setattr(b, k, tensors[k].data_ptr())
+        return b
+
+    def loss_grad(self, tensors, scales: dict, grads: bool = True):
+        b = self.batch(tensors)
+        sc = ClosureScales(**scales)
+        loss = ctypes.c_float()
+        g = np.zeros(self.count, dtype=np.float32) if grads else None
+        _check(load().ocean_mlp_loss_grad(self._h, ctypes.byref(b), tensors["X"].shape[0],
+                                          ctypes.byref(sc), ctypes.byref(loss),
+                                          _fp(g) if g is not None else None))
+        return loss.value, (unflatten_params(g.astype(np.float64), self.dims) if grads else None)
+
+    def train_step(self, tensors, scales: dict, lr: float) -> float:
+        b = self.batch(tensors)
+        sc = ClosureScales(**scales)
+        loss = ctypes.c_float()
+        _check(load().ocean_mlp_train_step(self._h, ctypes.byref(b), tensors["X"].shape[0],
+                                           ctypes.byref(sc), lr, ctypes.byref(loss)))
+        return loss.value
