@@ -108,6 +108,8 @@ typedef struct {
     int check_every;
     const double* taux;
     const double* tauy;
+    int closure_hidden;     /* hidden width of the learned closure to reserve memory for
+                               (0 = none; otherwise a multiple of 16) */
 } ocean_params;
 
 typedef struct {
@@ -263,6 +265,39 @@ int ocean_mlp_loss_grad(ocean_mlp_t h, const ocean_batch* batch, int M,
 /* One Adam step (lr; beta = 0.9, 0.999; eps = 1e-8) on a batch; the loss before it. */
 int ocean_mlp_train_step(ocean_mlp_t h, const ocean_batch* batch, int M,
                          const ocean_closure_scales* scales, float lr, float* loss);
+
+/* Load a trained closure into a model created with closure_hidden > 0: the flat network
+ * parameters (ocean_mlp_param_count(nz, closure_hidden) floats), the feature statistics
+ * mu, sigma (6 nz each, host) and the output scales.  From then on every step with
+ * params.closure == OCEAN_CLOSURE_LEARNED runs the network on all columns after the
+ * Richardson-number closure: its diffusivity replaces kappa on the interior wet faces and
+ * its corrections are added to the tracer tendencies; a column with any non-finite output
+ * keeps the Richardson-number kappa and gets no correction. */
+int ocean_set_closure(ocean_t h, const float* params, size_t count, const float* mu,
+                      const float* sigma, const ocean_closure_scales* scales);
+
+/* Network inputs of the model's current state for every column c = j nx + i (device
+ * outputs, each may be NULL): d_X [nx ny][6nz] z-scored with mu, sigma (host, 6nz each;
+ * required with d_X), d_face / d_wet [nx ny][nz] masks (interior wet faces, wet levels),
+ * d_dzT / d_dzS [nx ny][nz] vertical gradients of T and S on the faces. */
+int ocean_closure_features(ocean_t h, const float* mu, const float* sigma, float* d_X,
+                           unsigned char* d_face, unsigned char* d_wet, float* d_dzT,
+                           float* d_dzS);
+
+/* Coarse-grain the fine model's state onto the coarse one (same levels, same reference
+ * profiles, nx and ny r times smaller): tracers and the fine tendencies of the last
+ * ocean_tendencies call as volume means over wet fine cells, u and v as means over the
+ * wet fine faces on each coarse face, eta as an area mean.  The coarse state is replaced
+ * (its step count is left alone).  Device outputs [ncoarse][nz]: d_FT, d_FS the subgrid
+ * vertical fluxes <w T_f> - <w><T_f> on coarse faces, d_GTm, d_GSm the mean fine
+ * tendencies. */
+int ocean_coarse_grain(ocean_t fine, ocean_t coarse, int r, float* d_FT, float* d_FS,
+                       float* d_GTm, float* d_GSm);
+
+/* Lateral residual targets on the coarse model (after ocean_tendencies on it):
+ * d_GTt = d_GTm - G_T(coarse) + (F_{k+1} - F_k)/dz_k, and likewise for S. */
+int ocean_closure_targets(ocean_t coarse, const float* d_GTm, const float* d_GSm,
+                          const float* d_FT, const float* d_FS, float* d_GTt, float* d_GSt);
 
 /* The batched tridiagonal solve above, for callers that cannot allocate device memory:
  * code that runs while a CUDA graph is being captured (allocation cannot be captured),

@@ -69,6 +69,7 @@ def lib():
             L.ora_recon.argtypes = [P(d), P(i), d, i]
             L.ora_thomas.argtypes = [i, P(d), P(d), P(d), P(d), P(d)]
             L.ora_barotropic.argtypes = [ctypes.c_void_p, P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
+            L.ora_set_closure_fields.argtypes = [ctypes.c_void_p, P(d), P(d), P(d)]
             L.ora_kbot.restype = i
             L.ora_kbot.argtypes = [ctypes.c_void_p, i, i]
             _lib = L
@@ -178,6 +179,17 @@ class OracleModel:
         lib().ora_diagnostics(self._h, _dp(out))
         return dict(tracer_T=out[0], tracer_S=out[1], volume_eta=out[2], ke=out[3],
                     max_cfl=out[4], nonfinite=bool(out[5]), wet_volume=out[6], step=int(out[7]))
+
+    def kb_array(self):
+        return np.array([[self.kbot(i, j) for i in range(self.nx)] for j in range(self.ny)])
+
+    def set_closure_fields(self, kappa, dGT, dGS) -> None:
+        """Learned diffusivity and tracer corrections for the next steps (None: remove)."""
+        if kappa is None:
+            lib().ora_set_closure_fields(self._h, None, None, None)
+            return
+        k, a, b = (_f64(x) for x in (kappa, dGT, dGS))
+        lib().ora_set_closure_fields(self._h, _dp(k), _dp(a), _dp(b))
 
     def barotropic(self, eta, U, V, GU, GV):
         """Run the sub-cycle alone; returns (eta_bar, U_bar, V_bar)."""

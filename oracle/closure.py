@@ -201,3 +201,90 @@ def subgrid_vertical_flux(w, T, kb, area, r: int):
     F = wT - wm * Tm
     F[0] = 0.0
     return F
+
+
+# ----------------------------------------------------------------------------- in the model
+
+def learned_fields(model, params, mu, sigma, scales, bf16: bool = True):
+    """The learned closure's diffusivity (on interior wet faces) and tracer corrections
+    (on wet cells) for an oracle model's current state, [nz, ny, nx] each; a column with
+    any non-finite output keeps nan diffusivity (meaning: the Richardson value) and gets
+    no correction."""
+    c = model.case
+    p = model.params
+    kb = model.kb_array()
+    raw, msk = column_features(model.get("T"), model.get("S"), model.get("u"), model.get("v"),
+                               kb, np.asarray(c.z_faces), p["g"], p["alpha"], p["beta_s"],
+                               bool(c.periodic_x), bool(c.periodic_y))
+    X = normalise(raw, msk, np.asarray(mu, float), np.asarray(sigma, float))
+    Y, _ = mlp_forward(params, X, bf16=bf16)
+    nz, ny, nx = model.nz, model.ny, model.nx
+    kap, dgt, dgs = closure_outputs(Y, nz, scales)
+    ok = np.all(np.isfinite(Y), axis=1)[:, None]
+    k = np.arange(nz)[None, :]
+    kbf = kb.reshape(-1)[:, None]
+    face = (k >= kbf + 1) & ok
+    wet = (k >= kbf) & ok
+    K = np.where(face, kap, np.nan)
+    A = np.where(wet, dgt, 0.0)
+    B = np.where(wet, dgs, 0.0)
+    shape = lambda Z: Z.T.reshape(nz, ny, nx)
+    return shape(K), shape(A), shape(B)
+
+
+def step_learned(model, nsteps, params, mu, sigma, scales, bf16: bool = True):
+    """Advance an oracle model with the learned closure: before each step the network is
+    evaluated on the current state and its fields handed to the FP64 step."""
+    for _ in range(nsteps):
+        kap, dgt, dgs = learned_fields(model, params, mu, sigma, scales, bf16)
+        # nan marks faces that keep the Richardson-number kappa: fill them from it
+        model.tendencies()
+        kri = model.get("kappa")
+        kap = np.where(np.isnan(kap), kri, kap)
+        model.set_closure_fields(kap, dgt, dgs)
+        model.step(1)
+        model.set_closure_fields(None, None, None)
+
+
+def coarse_grain_state(fine: dict, kbf, kbc, area_rows, r: int):
+    """4-way coarse-graining of a fine state (the same operator as the CUDA path):
+    fine = dict(u, v, T, S, w, GT, GS [nz, ny, nx], eta [ny, nx]); kbf / kbc the lowest
+    wet levels of fine / coarse columns (kbu, kbv derived, periodic in x); area_rows the
+    fine cell area per row.  Returns the coarse (u, v, T, S, eta) and FT, FS, GTm, GSm."""
+    T = fine["T"]
+    nz, ny, nx = T.shape
+    Ny, Nx = ny // r, nx // r
+    k = np.arange(nz)[:, None, None]
+    area = np.broadcast_to(area_rows[:, None], (ny, nx))
+    wetf = (k >= kbf[None]).astype(float) * area[None]
+    out = {}
+    for name in ("T", "S", "GT", "GS"):
+        mean, _ = coarse_grain_mean(fine[name], wetf, r)
+        out[name] = mean
+    wetc = k >= kbc[None]
+    for name in ("T", "S"):
+        out[name] = np.where(wetc, out[name], 0.0)
+    GTm = np.where(wetc, out.pop("GT"), 0.0)
+    GSm = np.where(wetc, out.pop("GS"), 0.0)
+    FT = subgrid_vertical_flux(fine["w"], fine["T"], kbf, area, r)
+    FS = subgrid_vertical_flux(fine["w"], fine["S"], kbf, area, r)
+    facec = k >= kbc[None] + 1
+    FT = np.where(facec, FT, 0.0)
+    FS = np.where(facec, FS, 0.0)
+    # u on the coarse west faces: fine faces (r I, r J + b); v on south faces (r I + a, r J)
+    kbuf = np.maximum(kbf, np.roll(kbf, 1, axis=1))
+    kbvf = np.maximum(kbf, np.vstack([np.full((1, nx), nz), kbf[:-1]]))
+    kbuc = np.maximum(kbc, np.roll(kbc, 1, axis=1))
+    kbvc = np.maximum(kbc, np.vstack([np.full((1, Nx), nz), kbc[:-1]]))
+    uw = (k >= kbuf[None]).astype(float)
+    us = (fine["u"] * uw)[:, :, ::r].reshape(nz, Ny, r, Nx).sum(axis=2)
+    un = uw[:, :, ::r].reshape(nz, Ny, r, Nx).sum(axis=2)
+    out["u"] = np.where((k >= kbuc[None]) & (un > 0), us / np.maximum(un, 1), 0.0)
+    vw = (k >= kbvf[None]).astype(float)
+    vs = (fine["v"] * vw)[:, ::r, :].reshape(nz, Ny, Nx, r).sum(axis=3)
+    vn = vw[:, ::r, :].reshape(nz, Ny, Nx, r).sum(axis=3)
+    out["v"] = np.where((k >= kbvc[None]) & (vn > 0), vs / np.maximum(vn, 1), 0.0)
+    colw = (kbf < nz).astype(float) * area
+    eta, W = coarse_grain_mean(fine["eta"], colw, r)
+    out["eta"] = np.where((kbc < nz) & (W > 0), eta, 0.0)
+    return out, FT, FS, GTm, GSm

@@ -53,6 +53,9 @@ typedef struct {
     double *b, *p, *w, *kap, *nu;
     double *Gu, *Gv, *GT, *GS;
     double *GU, *GV, *U, *V, *Hu, *Hv;
+    /* learned closure: diffusivity on interior wet faces and tracer tendency corrections
+     * supplied for the next steps (NULL = Richardson-number closure only) */
+    double *ext_kap, *ext_dGT, *ext_dGS;
 } ora_t;
 
 #define PI 3.14159265358979323846
@@ -272,6 +275,9 @@ static void diagnose(ora_t* m) {
                 m->kap[at3(m, i, j, k)] = kap;
                 m->nu[at3(m, i, j, k)] = nu;
             }
+            /* a learned diffusivity replaces kappa on the interior wet faces */
+            if (m->ext_kap)
+                for (int k = kb + 1; k < nz; k++) m->kap[at3(m, i, j, k)] = m->ext_kap[at3(m, i, j, k)];
         }
     }
 }
@@ -416,7 +422,35 @@ void ora_tendencies(ora_t* m) {
     diagnose(m);
     tracer_tendency(m, m->T, m->GT);
     tracer_tendency(m, m->S, m->GS);
+    if (m->ext_dGT) {   /* learned tracer tendency corrections on wet cells */
+        long n3 = (long)m->nx * m->ny * m->nz;
+        for (long c = 0; c < n3; c++) {
+            m->GT[c] += m->ext_dGT[c];
+            m->GS[c] += m->ext_dGS[c];
+        }
+    }
     momentum_tendency(m);
+}
+
+/* Supply (or, with NULL, remove) the learned closure's fields for the following steps:
+ * kappa on bottom faces and dG_T, dG_S on cells, [nz][ny][nx]; copied.  Values outside
+ * interior wet faces (kappa) or wet cells (dG) are ignored. */
+void ora_set_closure_fields(ora_t* m, const double* kap, const double* dgt, const double* dgs) {
+    long n3 = (long)m->nx * m->ny * m->nz;
+    free(m->ext_kap); free(m->ext_dGT); free(m->ext_dGS);
+    m->ext_kap = m->ext_dGT = m->ext_dGS = 0;
+    if (!kap) return;
+    m->ext_kap = malloc(n3 * sizeof(double));
+    m->ext_dGT = malloc(n3 * sizeof(double));
+    m->ext_dGS = malloc(n3 * sizeof(double));
+    memcpy(m->ext_kap, kap, n3 * sizeof(double));
+    for (long c = 0; c < n3; c++) {
+        int k = (int)(c / ((long)m->nx * m->ny));
+        long c2 = c % ((long)m->nx * m->ny);
+        int w = k >= m->kb[c2];
+        m->ext_dGT[c] = w ? dgt[c] : 0.0;
+        m->ext_dGS[c] = w ? dgs[c] : 0.0;
+    }
 }
 
 /* ------------------------------------------------------------------ implicit solve */
@@ -756,6 +790,7 @@ void ora_destroy(ora_t* m) {
                       m->Gu, m->Gv, m->GT, m->GS, m->GU, m->GV, m->U, m->V, m->Hu, m->Hv};
     for (unsigned a = 0; a < sizeof(arrs) / sizeof(arrs[0]); a++) free(arrs[a]);
     free(m->kb);
+    free(m->ext_kap); free(m->ext_dGT); free(m->ext_dGS);
     free(m);
 }
 

@@ -77,6 +77,15 @@ struct ocean_s {
     double phase_ms[OCEAN_NPHASE] = {};
     long prof_steps = 0;
     long launches = 0;         // kernels enqueued by this handle
+    // learned closure: network (bf16 W^T per layer, fp32 biases), feature statistics,
+    // activations of all columns and the tracer corrections
+    int cl_hidden = 0;
+    bool cl_ready = false;
+    ocean_closure_scales cl_sc{};
+    int cl_dims[5] = {};
+    void *cl_X = nullptr, *cl_H0 = nullptr, *cl_H1 = nullptr, *cl_Wt[4] = {}, *cl_dGT = nullptr,
+         *cl_dGS = nullptr;
+    float *cl_Y = nullptr, *cl_b[4] = {}, *cl_stage = nullptr, *cl_mu = nullptr, *cl_sigma = nullptr;
     double dy = 0;
     int cur = 0;
     long nstep = 0;
@@ -128,6 +137,8 @@ int validate(const ocean_grid* g, const ocean_params* p) {
     if (p->closure != OCEAN_CLOSURE_RI && p->closure != OCEAN_CLOSURE_LEARNED)
         return fail(nullptr, OCEAN_ERR_ARG, "unknown closure");
     if (p->check_every < 0) return fail(nullptr, OCEAN_ERR_ARG, "check_every must be >= 0");
+    if (p->closure_hidden < 0 || p->closure_hidden % 16)
+        return fail(nullptr, OCEAN_ERR_ARG, "closure_hidden must be 0 or a positive multiple of 16");
     return OCEAN_OK;
 }
 
@@ -179,6 +190,28 @@ size_t layout(ocean_t m, char* base) {
     m->dlev = c.take<double>(3 * (size_t)m->nz);
     m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes()));
     m->diag_out = c.take<double>(8);
+    m->cl_mu = c.take<float>(6 * (size_t)m->nz);
+    m->cl_sigma = c.take<float>(6 * (size_t)m->nz);
+    m->cl_hidden = m->prm.closure_hidden;
+    if (m->cl_hidden > 0) {
+        const int H = m->cl_hidden, nz = m->nz;
+        const int d[5] = {6 * nz, H, H, H, 3 * nz};
+        for (int q = 0; q < 5; ++q) m->cl_dims[q] = d[q];
+        const size_t M = (size_t)m->nx * m->ny;
+        m->cl_X = c.take<char>(M * d[0] * 2);
+        m->cl_H0 = c.take<char>(M * H * 2);
+        m->cl_H1 = c.take<char>(M * H * 2);
+        m->cl_Y = c.take<float>(M * d[4]);
+        size_t big = 0;
+        for (int l = 0; l < 4; ++l) {
+            m->cl_Wt[l] = c.take<char>((size_t)d[l] * d[l + 1] * 2);
+            m->cl_b[l] = c.take<float>(d[l + 1]);
+            big = std::max(big, (size_t)d[l] * d[l + 1]);
+        }
+        m->cl_stage = c.take<float>(big);
+        m->cl_dGT = f3();
+        m->cl_dGS = f3();
+    }
     return c.off + 256;
 }
 
@@ -457,11 +490,29 @@ long launches_per_step(const ocean_t m) {
     return 3 + (hk + 1 + baro_passes((int)ns) + 1) + 1 + hk;
 }
 
+// the learned closure after the Richardson-number closure: network on every column, then
+// its diffusivity into kap and its tracer corrections into b.dGT, b.dGS
+template <typename R>
+bool enqueue_closure(ocean_t m, const KP<R>& k, StepBuffers<R>& b) {
+    if (!(m->cl_ready && m->prm.closure == OCEAN_CLOSURE_LEARNED)) return false;
+    cudaStream_t s = m->stream;
+    launch_closure_features<R>(k, b.u, b.v, b.T, b.S, m->cl_mu, m->cl_sigma, nullptr, m->cl_X,
+                               nullptr, nullptr, nullptr, nullptr, s);
+    closure_forward(m->cl_X, m->nx * m->ny, m->cl_Wt, m->cl_b, m->cl_dims, m->cl_H0, m->cl_H1,
+                    m->cl_Y, s);
+    launch_closure_apply<R>(k, m->cl_Y, m->cl_sc.kappa, m->cl_sc.gT, m->cl_sc.gS, b.kap,
+                            reinterpret_cast<R*>(m->cl_dGT), reinterpret_cast<R*>(m->cl_dGS), s);
+    b.dGT = reinterpret_cast<const R*>(m->cl_dGT);
+    b.dGS = reinterpret_cast<const R*>(m->cl_dGS);
+    m->launches += 6;
+    return true;
+}
+
 template <typename R>
 void enqueue_step(ocean_t m) {
     const bool first = m->nstep == 0;
     const KP<R> k = make_kp<R>(m, first);
-    const StepBuffers<R> b = make_bufs<R>(m);
+    StepBuffers<R> b = make_bufs<R>(m);
     cudaStream_t s = m->stream;
     std::vector<cudaEvent_t> ev;
     auto mark = [&]() {
@@ -473,6 +524,7 @@ void enqueue_step(ocean_t m) {
     };
     mark();
     launch_diag<R>(k, b, s);
+    enqueue_closure<R>(m, k, b);
     mark();
     launch_tracer<R>(k, b, true, s);
     mark();
@@ -496,8 +548,9 @@ void enqueue_step(ocean_t m) {
 template <typename R>
 void enqueue_tendencies(ocean_t m) {
     const KP<R> k = make_kp<R>(m, m->nstep == 0);
-    const StepBuffers<R> b = make_bufs<R>(m);
+    StepBuffers<R> b = make_bufs<R>(m);
     launch_diag<R>(k, b, m->stream);
+    enqueue_closure<R>(m, k, b);
     launch_tracer<R>(k, b, false, m->stream);
     launch_momentum<R>(k, b, false, m->stream);
     m->tend_valid = true;
@@ -853,6 +906,128 @@ int ocean_diagnostics(ocean_t h, ocean_diag* out) {
     out->max_cfl = d[4];
     out->nonfinite = d[5] != 0.0;
     out->wet_volume = d[6];
+    return OCEAN_OK;
+}
+
+int ocean_set_closure(ocean_t h, const float* params, size_t count, const float* mu,
+                      const float* sigma, const ocean_closure_scales* sc) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!params || !mu || !sigma || !sc) return fail(h, OCEAN_ERR_ARG, "null argument");
+    if (h->cl_hidden <= 0)
+        return fail(h, OCEAN_ERR_STATE, "the model was created with closure_hidden = 0");
+    if (count != ocean_mlp_param_count(h->nz, h->cl_hidden))
+        return fail(h, OCEAN_ERR_ARG, "closure parameter count %zu, expected %zu", count,
+                    ocean_mlp_param_count(h->nz, h->cl_hidden));
+    const float* p = params;
+    for (int l = 0; l < 4; ++l) {
+        const int in = h->cl_dims[l], out = h->cl_dims[l + 1];
+        upload_bytes(h, h->cl_stage, p, (size_t)in * out * sizeof(float));
+        closure_weight_transpose(h->cl_stage, in, out, h->cl_Wt[l], h->stream);
+        p += (size_t)in * out;
+        upload_bytes(h, h->cl_b[l], p, (size_t)out * sizeof(float));
+        p += out;
+    }
+    upload_bytes(h, h->cl_mu, mu, 6 * (size_t)h->nz * sizeof(float));
+    upload_bytes(h, h->cl_sigma, sigma, 6 * (size_t)h->nz * sizeof(float));
+    OC_CUDA(h, cudaGetLastError());
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->cl_sc = *sc;
+    h->cl_ready = true;
+    h->tend_valid = false;
+    return OCEAN_OK;
+}
+
+int ocean_closure_features(ocean_t h, const float* mu, const float* sigma, float* d_X,
+                           unsigned char* d_face, unsigned char* d_wet, float* d_dzT,
+                           float* d_dzS) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (d_X && (!mu || !sigma)) return fail(h, OCEAN_ERR_ARG, "features need mu and sigma");
+    if (d_X) {
+        upload_bytes(h, h->cl_mu, mu, 6 * (size_t)h->nz * sizeof(float));
+        upload_bytes(h, h->cl_sigma, sigma, 6 * (size_t)h->nz * sizeof(float));
+    }
+    if (h->prec == OCEAN_FP64) {
+        const KP<double> k = make_kp<double>(h, false);
+        const StepBuffers<double> b = make_bufs<double>(h);
+        launch_closure_features<double>(k, b.u, b.v, b.T, b.S, h->cl_mu, h->cl_sigma, d_X, nullptr,
+                                        d_face, d_wet, d_dzT, d_dzS, h->stream);
+    } else {
+        const KP<float> k = make_kp<float>(h, false);
+        const StepBuffers<float> b = make_bufs<float>(h);
+        launch_closure_features<float>(k, b.u, b.v, b.T, b.S, h->cl_mu, h->cl_sigma, d_X, nullptr,
+                                       d_face, d_wet, d_dzT, d_dzS, h->stream);
+    }
+    h->launches += 1;
+    OC_CUDA(h, cudaGetLastError());
+    OC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return OCEAN_OK;
+}
+
+int ocean_coarse_grain(ocean_t f, ocean_t c, int r, float* d_FT, float* d_FS, float* d_GTm,
+                       float* d_GSm) {
+    if (!f || !c) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!d_FT || !d_FS || !d_GTm || !d_GSm) return fail(f, OCEAN_ERR_ARG, "null output");
+    if (r < 1 || c->nx * r != f->nx || c->ny * r != f->ny || c->nz != f->nz || c->prec != f->prec ||
+        c->px != f->px || c->py != f->py)
+        return fail(f, OCEAN_ERR_ARG, "coarse grid must be the fine grid with nx, ny divided by r");
+    for (int k = 0; k <= f->nz; ++k)
+        if (f->zf[k] != c->zf[k]) return fail(f, OCEAN_ERR_ARG, "fine and coarse levels differ");
+    if (f->Tref != c->Tref || f->Sref != c->Sref)
+        return fail(f, OCEAN_ERR_ARG, "fine and coarse reference profiles differ (ocean_set_reference)");
+    if (!f->tend_valid) return fail(f, OCEAN_ERR_STATE, "call ocean_tendencies on the fine model first");
+    OC_CUDA(f, cudaStreamSynchronize(c->stream));
+    const int fc = f->cur, fn = 1 - f->cur, cc = c->cur;
+    if (f->prec == OCEAN_FP64) {
+        using R = double;
+        auto P = [](void* q) { return reinterpret_cast<R*>(q); };
+        const KP<R> kf = make_kp<R>(f, false), kc = make_kp<R>(c, false);
+        launch_coarse_grain<R>(kf, kc, r, P(f->u[fc]), P(f->v[fc]), P(f->T[fc]), P(f->S[fc]), P(f->w),
+                               P(f->T[fn]), P(f->S[fn]), f->eta, P(c->u[cc]), P(c->v[cc]),
+                               P(c->T[cc]), P(c->S[cc]), c->eta, d_FT, d_FS, d_GTm, d_GSm, f->stream);
+        if (c->px || c->py) {
+            R* q[4] = {P(c->u[cc]), P(c->v[cc]), P(c->T[cc]), P(c->S[cc])};
+            launch_halo3<R>(kc.g, q, 4, f->stream);
+        }
+    } else {
+        using R = float;
+        auto P = [](void* q) { return reinterpret_cast<R*>(q); };
+        const KP<R> kf = make_kp<R>(f, false), kc = make_kp<R>(c, false);
+        launch_coarse_grain<R>(kf, kc, r, P(f->u[fc]), P(f->v[fc]), P(f->T[fc]), P(f->S[fc]), P(f->w),
+                               P(f->T[fn]), P(f->S[fn]), f->eta, P(c->u[cc]), P(c->v[cc]),
+                               P(c->T[cc]), P(c->S[cc]), c->eta, d_FT, d_FS, d_GTm, d_GSm, f->stream);
+        if (c->px || c->py) {
+            R* q[4] = {P(c->u[cc]), P(c->v[cc]), P(c->T[cc]), P(c->S[cc])};
+            launch_halo3<R>(kc.g, q, 4, f->stream);
+        }
+    }
+    f->launches += 2;
+    OC_CUDA(f, cudaGetLastError());
+    OC_CUDA(f, cudaStreamSynchronize(f->stream));
+    c->tend_valid = false;
+    return OCEAN_OK;
+}
+
+int ocean_closure_targets(ocean_t c, const float* d_GTm, const float* d_GSm, const float* d_FT,
+                          const float* d_FS, float* d_GTt, float* d_GSt) {
+    if (!c) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    if (!d_GTm || !d_GSm || !d_FT || !d_FS || !d_GTt || !d_GSt)
+        return fail(c, OCEAN_ERR_ARG, "null device array");
+    if (!c->tend_valid) return fail(c, OCEAN_ERR_STATE, "call ocean_tendencies on the coarse model first");
+    const int n = 1 - c->cur;
+    if (c->prec == OCEAN_FP64) {
+        const KP<double> k = make_kp<double>(c, false);
+        launch_closure_targets<double>(k, reinterpret_cast<double*>(c->T[n]),
+                                       reinterpret_cast<double*>(c->S[n]), d_GTm, d_GSm, d_FT,
+                                       d_FS, d_GTt, d_GSt, c->stream);
+    } else {
+        const KP<float> k = make_kp<float>(c, false);
+        launch_closure_targets<float>(k, reinterpret_cast<float*>(c->T[n]),
+                                      reinterpret_cast<float*>(c->S[n]), d_GTm, d_GSm, d_FT, d_FS,
+                                      d_GTt, d_GSt, c->stream);
+    }
+    c->launches += 1;
+    OC_CUDA(c, cudaGetLastError());
+    OC_CUDA(c, cudaStreamSynchronize(c->stream));
     return OCEAN_OK;
 }
 

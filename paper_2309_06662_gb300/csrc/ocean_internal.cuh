@@ -188,6 +188,7 @@ template <typename R> struct StepBuffers {
     R *Gu, *Gv, *GT, *GS;      // G^{n-1} in, G^n out
     R *w, *p, *kap, *nu;       // diagnostics (kap also holds the tracers' Thomas c')
     R *wk;                     // 3-D scratch (the v-viscosity Thomas c')
+    const R *dGT, *dGS;        // learned-closure tracer tendency corrections (or null)
     const R *taux_s, *tauy_s;  // wind stress / (rho0 dz_top)
     R *Un, *Vn, *GU, *GV, *Su, *Sv;         // column sums (2-D)
     R *Ub, *Vb, *dE, *paccE, *paccU, *paccV, *gxe, *gye, *corrU, *corrV;
@@ -235,3 +236,25 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
 
 // Sets the message ocean_last_error(NULL) returns (entry points without a handle).
 extern "C" void oc_set_last_error(const char* msg);
+
+// ---- learned closure (ocean_closure.cu, ocean_mlp.cu)
+template <typename R>
+void launch_closure_features(const KP<R>& p, const R* u, const R* v, const R* T, const R* S,
+                             const float* mu, const float* sigma, float* Xf, void* Xb,
+                             unsigned char* face, unsigned char* wet, float* dzT, float* dzS,
+                             cudaStream_t s);
+template <typename R>
+void launch_closure_apply(const KP<R>& p, const float* Y, float ks, float gt, float gs, R* kap,
+                          R* dGT, R* dGS, cudaStream_t s);
+template <typename R>
+void launch_coarse_grain(const KP<R>& pf, const KP<R>& pc, int r, const R* uf, const R* vf,
+                         const R* Tf, const R* Sf, const R* wf, const R* GTf, const R* GSf,
+                         const double* etaf, R* uc, R* vc, R* Tc, R* Sc, double* etac, float* FT,
+                         float* FS, float* GTm, float* GSm, cudaStream_t s);
+template <typename R>
+void launch_closure_targets(const KP<R>& p, const R* GcT, const R* GcS, const float* GTm,
+                            const float* GSm, const float* FT, const float* FS, float* GTt,
+                            float* GSt, cudaStream_t s);
+void closure_forward(const void* Xb, int M, const void* const* Wt, const float* const* b,
+                     const int* dims, void* H0, void* H1, float* Y, cudaStream_t s);
+void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s);

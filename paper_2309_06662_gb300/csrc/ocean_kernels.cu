@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const
                                                const R* __restrict__ T, const R* __restrict__ S,
                                                R* __restrict__ kap, R* __restrict__ GTp,
                                                R* __restrict__ GSp, R* __restrict__ Tn,
-                                               R* __restrict__ Sn) {
+                                               R* __restrict__ Sn, const R* __restrict__ dGT,
+                                               const R* __restrict__ dGS) {
     __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
@@ -331,8 +332,12 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const
             const R divU = sm.fxU[ty][tx + 1] - sm.fxU[ty][tx] + sm.fyV[ty + 1][tx] - sm.fyV[ty][tx];
             const R hT = sm.fxT[ty][tx + 1] - sm.fxT[ty][tx] + sm.fyT[ty + 1][tx] - sm.fyT[ty][tx];
             const R hS = sm.fxS[ty][tx + 1] - sm.fxS[ty][tx] + sm.fyS[ty + 1][tx] - sm.fyS[ty][tx];
-            const R GT = -((p.Tref[k] * divU + hT) * rac + (ftT - fzT)) * rdz;
-            const R GS = -((p.Sref[k] * divU + hS) * rac + (ftS - fzS)) * rdz;
+            R GT = -((p.Tref[k] * divU + hT) * rac + (ftT - fzT)) * rdz;
+            R GS = -((p.Sref[k] * divU + hS) * rac + (ftS - fzS)) * rdz;
+            if (dGT) {   // learned-closure corrections, part of G^n
+                GT += dGT[ck];
+                GS += dGS[ck];
+            }
             fzT = ftT;
             fzS = ftS;
             if (!STEP) {
@@ -835,10 +840,10 @@ void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStrea
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
     if (step)
         k_tracer<R, true><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
-                                                 b.Tn, b.Sn);
+                                                 b.Tn, b.Sn, b.dGT, b.dGS);
     else
         k_tracer<R, false><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
-                                                  b.Tn, b.Sn);
+                                                  b.Tn, b.Sn, b.dGT, b.dGS);
 }
 
 template <typename R>

@@ -327,6 +327,51 @@ inline int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
+// ------------------------------------------------------------------ inference inside the step
+
+// y = MLP(x) for M columns of bf16 features Xb [M][dims0], weights W^T (bf16 [out][in])
+// and biases per layer, hidden activations ping-ponging through H0/H1 (bf16 [M][H])
+void closure_forward(const void* Xb, int M, const void* const* Wt, const float* const* b,
+                     const int* dims, void* H0, void* H1, float* Y, cudaStream_t s) {
+    const bf16* a = reinterpret_cast<const bf16*>(Xb);
+    int lda = dims[0];
+    bf16* H[2] = {reinterpret_cast<bf16*>(H0), reinterpret_cast<bf16*>(H1)};
+    for (int l = 0; l < 4; ++l) {
+        Epi e{};
+        e.bias = b[l];
+        if (l < 3) {
+            e.mode = EPI_SILU;
+            e.outB = H[l & 1];
+            e.ldB = dims[l + 1];
+        } else {
+            e.mode = EPI_F32;
+            e.outF = Y;
+            e.ldF = dims[l + 1];
+        }
+        gemm_nt(a, lda, reinterpret_cast<const bf16*>(Wt[l]), dims[l], M, dims[l + 1], dims[l], e, s);
+        if (l < 3) {
+            a = H[l & 1];
+            lda = dims[l + 1];
+        }
+    }
+}
+
+namespace {
+__global__ void k_transpose_bf16(const float* __restrict__ w, long n, int out, int in,
+                                 bf16* __restrict__ wt) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = (int)(q / out), o = (int)(q % out);
+    wt[(long)o * in + i] = __float2bfloat16_rn(w[q]);
+}
+}  // namespace
+
+// W^T [out][in] in bf16 from fp32 W [in][out] on the device (the forward pass's operand)
+void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s) {
+    const long n = (long)in * out;
+    k_transpose_bf16<<<nb(n, 256), 256, 0, s>>>(W, n, out, in, reinterpret_cast<bf16*>(Wt));
+}
+
 // ------------------------------------------------------------------ trainer handle
 
 struct ocean_mlp_s {

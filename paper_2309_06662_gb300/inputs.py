@@ -338,3 +338,43 @@ def mlp_seeded_params(seed: int, dims, gain: float = 1.0):
         nb = np.clip(np.round(random_normal(seed, 200 + li, b) * 0.1 * sigma * 2.0 ** q), -255, 255)
         params.append((W, nb * 2.0 ** -q))
     return params
+
+
+def restrict_depth(depth: np.ndarray, r: int, row_area: np.ndarray,
+                   min_depth: float = 50.0) -> np.ndarray:
+    """Coarse bathymetry of r x r blocks: area-weighted mean depth (land counting as 0),
+    columns shallower than min_depth become land."""
+    ny, nx = depth.shape
+    a = np.broadcast_to(row_area[:, None], (ny, nx))
+    d = (depth * a).reshape(ny // r, r, nx // r, r).sum(axis=(1, 3))
+    d /= a.reshape(ny // r, r, nx // r, r).sum(axis=(1, 3))
+    d[d < min_depth] = 0.0
+    return d
+
+
+def latlon_row_area(ny: int, lat: float, nx: int, radius: float = 6.371e6) -> np.ndarray:
+    """Cell area per row of a global lat-lon grid from -lat to lat (the product form
+    R cos(phi) dlambda R dphi)."""
+    dphi = math.radians(2.0 * lat / ny)
+    phi = np.radians(-lat + (np.arange(ny) + 0.5) * (2.0 * lat / ny))
+    return radius * np.cos(phi) * math.radians(360.0 / nx) * radius * dphi
+
+
+def latlon_pair(nxc: int, nyc: int, nz: int, lat: float, r: int, seed: int, dt_coarse: float,
+                ns_coarse: int, ns_fine: int, corr_deg: float = 10.0, noise: float = 0.05):
+    """A fine lat-lon case (r times finer, dt/r) and its coarse counterpart whose
+    bathymetry is the fine one restricted to r x r blocks; the coarse T, S start as block
+    means of the fine ones."""
+    fine = latlon_case(r * nxc, r * nyc, nz, lat, seed, dt_coarse / r, ns_fine, 1, "fine",
+                       noise=noise, corr_deg=corr_deg)
+    area = latlon_row_area(r * nyc, lat, r * nxc)
+    dc = restrict_depth(fine.depth, r, area)
+    dc[0, :] = 0.0
+    dc[-1, :] = 0.0
+    blk = lambda F: F.reshape(nz, nyc, r, nxc, r).mean(axis=(2, 4))
+    coarse = Case("coarse", 1, nxc, nyc, nz, True, False, 0.0, 360.0, -lat, lat, fine.z_faces, dc,
+                  fine.taux.reshape(nyc, r, nxc, r).mean(axis=(1, 3)),
+                  np.zeros((nyc, nxc)), blk(fine.T), blk(fine.S), dict(fine.params), steps=1)
+    coarse.params["dt"] = dt_coarse
+    coarse.params["n_substeps"] = ns_coarse
+    return fine, coarse

@@ -49,7 +49,8 @@ class OceanParams(ctypes.Structure):
                 ("ri_a", c_double), ("nu_b", c_double), ("kappa_b", c_double),
                 ("kappa_conv", c_double), ("weno_eps", c_double), ("weno_linear", c_int),
                 ("min_depth", c_double), ("precision", c_int), ("closure", c_int),
-                ("check_every", c_int), ("taux", POINTER(c_double)), ("tauy", POINTER(c_double))]
+                ("check_every", c_int), ("taux", POINTER(c_double)), ("tauy", POINTER(c_double)),
+                ("closure_hidden", c_int)]
 
 
 class OceanBatch(ctypes.Structure):
@@ -120,6 +121,12 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_tridiag_batched": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
             "ocean_tridiag_batched_static": (c_int, [pv, pv, pv, pv, pv, c_int, c_int, c_int, pv]),
             "ocean_mlp_param_count": (c_size_t, [c_int, c_int]),
+            "ocean_set_closure": (c_int, [pv, POINTER(ctypes.c_float), c_size_t, POINTER(ctypes.c_float),
+                                          POINTER(ctypes.c_float), POINTER(ClosureScales)]),
+            "ocean_closure_features": (c_int, [pv, POINTER(ctypes.c_float), POINTER(ctypes.c_float),
+                                               pv, pv, pv, pv, pv]),
+            "ocean_coarse_grain": (c_int, [pv, pv, c_int, pv, pv, pv, pv]),
+            "ocean_closure_targets": (c_int, [pv, pv, pv, pv, pv, pv, pv]),
             "ocean_mlp_create": (c_int, [c_int, c_int, c_int, POINTER(ctypes.c_float), pv, POINTER(pv)]),
             "ocean_mlp_destroy": (None, [pv]),
             "ocean_mlp_set_params": (c_int, [pv, POINTER(ctypes.c_float), c_size_t]),
@@ -170,7 +177,7 @@ def make_grid(case):
 
 
 def make_params(p: Dict[str, float], precision: int, taux=None, tauy=None, closure: int = 0,
-                check_every: int = 0):
+                check_every: int = 0, closure_hidden: int = 0):
     keep = []
     tx = ty = None
     if taux is not None:
@@ -184,7 +191,8 @@ def make_params(p: Dict[str, float], precision: int, taux=None, tauy=None, closu
         p["T0"], p["S0"], p["f0"], p["beta_plane"], p["omega"], p["radius"], p["nu0"], p["ri_a"],
         p["nu_b"], p["kappa_b"], p["kappa_conv"], p["weno_eps"], int(p["weno_linear"]),
         p["min_depth"], precision, closure, check_every,
-        _dp(tx) if tx is not None else None, _dp(ty) if ty is not None else None)
+        _dp(tx) if tx is not None else None, _dp(ty) if ty is not None else None,
+        closure_hidden)
     return prm, keep
 
 
@@ -192,7 +200,8 @@ class Ocean:
     """One model handle on the current CUDA device, in a torch-allocated arena."""
 
     def __init__(self, case, precision: int = OCEAN_FP64, params: Optional[dict] = None,
-                 check_every: int = 0, own_memory: bool = False):
+                 check_every: int = 0, own_memory: bool = False, closure: int = OCEAN_CLOSURE_RI,
+                 closure_hidden: int = 0):
         torch = _torch_cuda()
         L = load()
         p = dict(case.params)
@@ -202,8 +211,8 @@ class Ocean:
         self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
         self.precision = precision
         grid, self._zf = make_grid(case)
-        prm, self._keep = make_params(p, precision, case.taux, case.tauy,
-                                      check_every=check_every)
+        prm, self._keep = make_params(p, precision, case.taux, case.tauy, closure=closure,
+                                      check_every=check_every, closure_hidden=closure_hidden)
         depth = np.ascontiguousarray(case.depth, dtype=np.float64)
         h = c_void_p()
         self._arena = None
@@ -296,6 +305,58 @@ class Ocean:
         for f in CHECKPOINT_FIELDS:
             self.set(f, d[f])
         self.nstep = int(d["step"])
+
+    # ---- learned closure
+    def set_closure(self, params, mu, sigma, scales: dict) -> None:
+        flat = flatten_params(params)
+        m = np.ascontiguousarray(mu, dtype=np.float32)
+        sg = np.ascontiguousarray(sigma, dtype=np.float32)
+        sc = ClosureScales(**scales)
+        _check(load().ocean_set_closure(self._h, _fp(flat), flat.size, _fp(m), _fp(sg),
+                                        ctypes.byref(sc)), self._h)
+
+    def closure_features(self, mu=None, sigma=None):
+        """Device (torch) features X [ncol, 6nz] (with mu, sigma), masks and gradients."""
+        torch = _torch_cuda()
+        nc, nz = self.nx * self.ny, self.nz
+        out = dict(face=torch.empty((nc, nz), dtype=torch.uint8, device="cuda"),
+                   wet=torch.empty((nc, nz), dtype=torch.uint8, device="cuda"),
+                   dzT=torch.empty((nc, nz), dtype=torch.float32, device="cuda"),
+                   dzS=torch.empty((nc, nz), dtype=torch.float32, device="cuda"))
+        Xp = None
+        m = sg = None
+        if mu is not None:
+            out["X"] = torch.empty((nc, 6 * nz), dtype=torch.float32, device="cuda")
+            Xp = c_void_p(out["X"].data_ptr())
+            m = np.ascontiguousarray(mu, dtype=np.float32)
+            sg = np.ascontiguousarray(sigma, dtype=np.float32)
+        _check(load().ocean_closure_features(
+            self._h, _fp(m) if m is not None else None, _fp(sg) if sg is not None else None, Xp,
+            c_void_p(out["face"].data_ptr()), c_void_p(out["wet"].data_ptr()),
+            c_void_p(out["dzT"].data_ptr()), c_void_p(out["dzS"].data_ptr())), self._h)
+        return out
+
+    def coarse_grain_to(self, coarse, r: int):
+        """Coarse-grain this (fine) model onto `coarse`; returns the device targets."""
+        torch = _torch_cuda()
+        nc, nz = coarse.nx * coarse.ny, coarse.nz
+        t = {k: torch.empty((nc, nz), dtype=torch.float32, device="cuda")
+             for k in ("FT", "FS", "GTm", "GSm")}
+        _check(load().ocean_coarse_grain(self._h, coarse._h, r,
+                                         *(c_void_p(t[k].data_ptr()) for k in ("FT", "FS", "GTm", "GSm"))),
+               self._h)
+        return t
+
+    def closure_targets(self, t):
+        """Lateral residual targets (after tendencies()) into t["GT"], t["GS"]."""
+        torch = _torch_cuda()
+        nc, nz = self.nx * self.ny, self.nz
+        t["GT"] = torch.empty((nc, nz), dtype=torch.float32, device="cuda")
+        t["GS"] = torch.empty((nc, nz), dtype=torch.float32, device="cuda")
+        _check(load().ocean_closure_targets(
+            self._h, *(c_void_p(t[k].data_ptr()) for k in ("GTm", "GSm", "FT", "FS", "GT", "GS"))),
+            self._h)
+        return t
 
     def set_wind_stress(self, taux, tauy) -> None:
         tx = np.ascontiguousarray(taux, dtype=np.float64)

