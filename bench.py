@@ -2,8 +2,10 @@
 """Benchmark of one baroclinic time step of the hydrostatic free-surface ocean on GB300.
 
 Workload (default): the 1/12-degree lat-lon configuration, 4320 x 1680 x 48 cells
-(70S-70N), dt = 300 s, 60 barotropic substeps, in the mixed-precision form (FP32 fields
-and stencils; FP64 free surface, barotropic averages and conservation sums).  Inputs are
+(70S-70N), dt = 180 s, 60 barotropic substeps, in the mixed-precision form (FP32 fields
+and stencils; FP64 free surface, barotropic averages and conservation sums).
+`--workload ensemble96` times the batched ensemble instead: 96 closed basins of seeded
+uneven sizes (32-512 x 32-512 x 8-48), stepped together.  Inputs are
 seeded and synthetic: random-field bathymetry and stratified T/S with noise stand in for
 the ECCO2-forced realistic domain of the paper (Sec. "How performance was measured").
 
@@ -39,6 +41,7 @@ WORKLOADS = {
     "latlon_quarter": (inputs.latlon_quarter_case, "latlon_1/4deg_1440x560x48"),
     "latlon_1deg": (inputs.latlon_1deg_case, "latlon_1deg_360x160x32"),
     "box": (inputs.box_case, "box_32x32x8"),
+    "ensemble96": (lambda: inputs.ensemble_cases(96, seed=5), "ensemble_96_basins"),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -189,7 +192,11 @@ def reference_arm(args, rank: int):
     import oracle
     make, wname = WORKLOADS[args.workload]
     case = make()
+    member = ""
+    if isinstance(case, list):          # an ensemble: its first member stands in
+        case, member = case[0], " (member 0 of the ensemble)"
     sample, desc = oracle_sample(case)
+    desc += member
     m = oracle.OracleModel(sample)
     m.step(max(1, args.warmup))
     t0 = time.perf_counter()
@@ -221,6 +228,121 @@ def config_block(case, wname, precision):
             "l2": "inputs larger than L2 (every 3-D field > 1 GB)"}
 
 
+def ensemble_main(args, cases, wname, rank, world, local, dist):
+    """The batched ensemble: all members advanced by one graph launch per step, against
+    the same members stepped one after another with ocean_step."""
+    import torch
+    from paper_2309_06662_gb300 import ocean
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cells = sum(c.nx * c.ny * c.nz for c in cases)
+    wet = sum(roofline.wet_cells(c.depth, c.z_faces, c.params["min_depth"]) for c in cases)
+    wet_cols = sum(roofline.wet_columns(c.depth, c.params["min_depth"], c.z_faces) for c in cases)
+    E = ocean.Ensemble(cases)
+    stream = torch.cuda.ExternalStream(E.stream)
+    tuned = E.autotune(reps=2)           # real steps: part of the warm-up
+    E.step(max(1, args.warmup))
+    barrier()
+    launches0 = E.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        E.step_async(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = E.launches - launches0
+    # the same members stepped one by one (single-model kernels, launches per member)
+    ev0.record(stream)
+    for m in E.members:
+        m.step_async(1)
+    ev1.record(stream)
+    barrier()
+    ms_seq = ev0.elapsed_time(ev1)
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = cells / (ms_all / 1e3) * world
+    kinds = E.kind_times()
+    esz = 4
+    words = {"diag": roofline.KERNEL_WORDS["diag"], "tracer": roofline.KERNEL_WORDS["tracer"],
+             "momentum": roofline.KERNEL_WORDS["momentum"],
+             "correct": roofline.KERNEL_WORDS["correct"]}
+    top = max(words, key=lambda k: kinds[k])
+    peak, peak_src = measured_peaks()
+    algo = words[top] * esz * wet
+    achieved = algo / (kinds[top] / 1e3) / 1e9
+    step_bytes = roofline.STEP_WORDS_PER_CELL * esz * wet + \
+        roofline.barotropic_bytes_per_column(esz, 30) * wet_cols
+    # end to end: per step every member's wind stress from pinned host memory, the
+    # ensemble step, and every member's diagnostics read back
+    winds = [(torch.from_numpy(np.ascontiguousarray(c.taux)).pin_memory().numpy(),
+              torch.from_numpy(np.ascontiguousarray(c.tauy)).pin_memory().numpy()) for c in cases]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for m, (tx, ty) in zip(E.members, winds):
+            m.set_wind_stress(tx, ty)
+        E.step_async(1)
+        diags = [m.diagnostics() for m in E.members]
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    healthy = all(not d["nonfinite"] and d["max_cfl"] < 1.0 for d in diags)
+    shapes = E.launch_shapes()
+    E.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_sample(cases[0], args.cpu_seconds)
+        cpu.pop("s_per_step", None)
+        cpu["sample"] += " (member 0 of the ensemble)"
+    if rank == 0:
+        nz = sorted({c.nz for c in cases})
+        line = {
+            "metric": "cell_updates_per_s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded closed beta-plane basins: random-field bathymetry, "
+                    "stratified T/S with noise, zonal wind 0.05-0.2 N/m^2)",
+            "config": {"workload": wname, "members": len(cases), "cells": cells,
+                       "nx_range": [min(c.nx for c in cases), max(c.nx for c in cases)],
+                       "ny_range": [min(c.ny for c in cases), max(c.ny for c in cases)],
+                       "nz": nz, "dt_s": 600.0, "n_substeps": 30,
+                       "precision": "mixed", "parallelism": "replicas (one ensemble per GPU)",
+                       "l2": "inputs larger than L2 (the ensemble's state is ~10 GB)"},
+            "wet_cells": wet,
+            "one_by_one": {"ms_per_step": ms_seq, "value": cells / (ms_seq / 1e3),
+                           "ensemble_speedup": ms_seq / ms},
+            "autotune": {"steps": tuned, "shapes": shapes,
+                         "kind_ms": {k: round(v, 4) for k, v in kinds.items()}},
+            "step_hbm": {"algorithmic_bytes": step_bytes,
+                         "GBs": step_bytes / (ms_all / 1e3) / 1e9,
+                         "frac": step_bytes / (ms_all / 1e3) / 1e9 / peak, "of": peak_src},
+            "roofline": {"bound": "hbm", "kernel": "k_ens_" + top, "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": algo, "ms_per_launch": kinds[top],
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "e2e": {"value": cells / e2e_s, "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": int(sum(a.nbytes + b.nbytes for a, b in winds)),
+                    "d2h_bytes_per_step": 64 * len(cases), "healthy": healthy,
+                    "what": "per step: every member's wind stress host->device, one ensemble "
+                            "step, every member's diagnostics device->host"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -240,6 +362,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     make, wname = WORKLOADS[args.workload]
+    if args.workload == "ensemble96":
+        ensemble_main(args, make(), wname, rank, world, local, dist)
+        return
     case = make()
     p = case.params
     wet = roofline.wet_cells(case.depth, case.z_faces, p["min_depth"])

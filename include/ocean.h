@@ -228,7 +228,7 @@ int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, con
  * GEMMs with FP32 accumulation and FP32 master weights.  Inputs per column: T, S,
  * centre-averaged u, v at the nz levels, N^2 and shear^2 on the nz bottom faces, each
  * z-scored, 0 on dry levels.  Outputs: kappa_k = kappa softplus(y_k) (vertical
- * diffusivity on face k), dG_T = gT y_{nz+k}, dG_S = gS y_{2nz+k} (tracer tendency
+ * diffusivity on face k, added to the Richardson-number one), dG_T = gT y_{nz+k}, dG_S = gS y_{2nz+k} (tracer tendency
  * corrections).  Flat parameter layout: for each layer W [in][out] row-major, then b
  * [out]. */
 typedef struct ocean_mlp_s* ocean_mlp_t;
@@ -270,9 +270,9 @@ int ocean_mlp_train_step(ocean_mlp_t h, const ocean_batch* batch, int M,
  * parameters (ocean_mlp_param_count(nz, closure_hidden) floats), the feature statistics
  * mu, sigma (6 nz each, host) and the output scales.  From then on every step with
  * params.closure == OCEAN_CLOSURE_LEARNED runs the network on all columns after the
- * Richardson-number closure: its diffusivity replaces kappa on the interior wet faces and
- * its corrections are added to the tracer tendencies; a column with any non-finite output
- * keeps the Richardson-number kappa and gets no correction. */
+ * Richardson-number closure: its diffusivity is added to kappa on the interior wet faces
+ * and its corrections to the tracer tendencies; a column with any non-finite output keeps
+ * the Richardson-number kappa alone and gets no correction. */
 int ocean_set_closure(ocean_t h, const float* params, size_t count, const float* mu,
                       const float* sigma, const ocean_closure_scales* scales);
 
@@ -316,6 +316,52 @@ int ocean_closure_targets(ocean_t coarse, const float* d_GTm, const float* d_GSm
 int ocean_tridiag_batched_static(const void* d_a, const void* d_b, const void* d_c,
                                  const void* d_d, void* d_x, int n, int nsys, int precision,
                                  void* stream);
+
+/* ---- batched ensemble ----
+ *
+ * Many independent models (members) of different sizes advanced together: one step of
+ * the ensemble is one step of every member, run as one sequence of persistent kernels
+ * whose blocks take work items (member, column chunk / tile / barotropic region) from a
+ * list sorted by decreasing cost, so that one launch per phase covers all members (the
+ * paper motivates ensembles in its introduction but runs none; this is this library's
+ * design).  After the first step each step is one CUDA graph launch.  Each member
+ * computes exactly what ocean_step computes for it alone.
+ *
+ * Members are created from per-member grids, depths and parameters (arrays of length
+ * `members`) in one device allocation on one stream owned by the ensemble; they must
+ * share precision, dt and n_substeps, be closed (no periodic direction) and use the
+ * Richardson-number closure.  ocean_ensemble_member returns a member's handle (owned by
+ * the ensemble; do not destroy it): ocean_set_field, ocean_get_field, ocean_diagnostics
+ * and the other per-model calls work on it.  Stepping a member on its own with
+ * ocean_step puts it out of step with the others; ocean_ensemble_step then returns
+ * OCEAN_ERR_STATE until all members have taken the same number of steps again. */
+typedef struct ocean_ensemble_s* ocean_ensemble_t;
+int ocean_ensemble_create(int members, const ocean_grid* grids, const double* const* depths,
+                          const ocean_params* params, ocean_ensemble_t* out);
+void ocean_ensemble_destroy(ocean_ensemble_t e);
+int ocean_ensemble_size(ocean_ensemble_t e);
+ocean_t ocean_ensemble_member(ocean_ensemble_t e, int i);     /* NULL if out of range */
+void* ocean_ensemble_stream(ocean_ensemble_t e);              /* cudaStream_t */
+/* n steps of every member; _async returns once they are enqueued */
+int ocean_ensemble_step(ocean_ensemble_t e, int n);
+int ocean_ensemble_step_async(ocean_ensemble_t e, int n);
+/* Autotuner of the launch shapes: runs reps x (largest candidate count) real steps (they
+ * advance the ensemble; every candidate computes the same result), timing each kernel
+ * kind under each candidate grid size (one item per block, or persistent with 1, 2 or
+ * the occupancy limit of blocks per SM) and schedule (static or atomic counter), then
+ * keeps the fastest per kind and rebuilds the step graphs.  *steps_taken receives the
+ * number of steps run (may be NULL). */
+int ocean_ensemble_autotune(ocean_ensemble_t e, int reps, int* steps_taken);
+/* Launch shape of each kernel kind (OCEAN_ENS_NKIND entries each): blocks per launch,
+ * 1 if the atomic-counter schedule is used, and the number of work items. */
+#define OCEAN_ENS_NKIND 7   /* diag, tracer, momentum, baro begin, baro pass, baro end, correct */
+int ocean_ensemble_launch_shapes(ocean_ensemble_t e, int* grid, int* dynamic, int* items);
+/* kernels enqueued by the ensemble's own steps */
+long ocean_ensemble_kernel_launches(ocean_ensemble_t e);
+/* Device time (ms, CUDA events on the ensemble's stream) of each kernel kind's launches
+ * in one step under its chosen shape, the best over the autotuner's steps (all passes
+ * together for the barotropic pass); 0 before ocean_ensemble_autotune. */
+int ocean_ensemble_kind_times(ocean_ensemble_t e, double* ms);
 
 #ifdef __cplusplus
 }

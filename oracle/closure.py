@@ -10,7 +10,10 @@ be checked against it:
              (shear squared) on the nz bottom faces (0 on the sea-floor face), z-scored
              with per-feature statistics; 0 on dry levels;
   network    6 nz -> H -> H -> H -> 3 nz, SiLU after each hidden layer;
-  outputs    kappa_k = kappa_scale softplus(y_k) on interior wet faces, and tracer
+  outputs    kappa_k = kappa_scale softplus(y_k) on interior wet faces, added to the
+             Richardson-number diffusivity (the network supplies the resolved-eddy
+             flux that the coarse grid misses; convective and background mixing stay
+             with the Richardson-number closure, as in the fine run), and tracer
              tendency corrections dG_T = gT_scale y_{nz+k}, dG_S = gS_scale y_{2nz+k};
   loss       mean squared error of the parameterised vertical flux -kappa dz<T> (and
              S) against the coarse-grained subgrid flux <wT> - <w><T>, plus that of dG
@@ -206,10 +209,9 @@ def subgrid_vertical_flux(w, T, kb, area, r: int):
 # ----------------------------------------------------------------------------- in the model
 
 def learned_fields(model, params, mu, sigma, scales, bf16: bool = True):
-    """The learned closure's diffusivity (on interior wet faces) and tracer corrections
-    (on wet cells) for an oracle model's current state, [nz, ny, nx] each; a column with
-    any non-finite output keeps nan diffusivity (meaning: the Richardson value) and gets
-    no correction."""
+    """The learned closure's extra diffusivity (on interior wet faces) and tracer
+    corrections (on wet cells) for an oracle model's current state, [nz, ny, nx] each; a
+    column with any non-finite output gets neither (0)."""
     c = model.case
     p = model.params
     kb = model.kb_array()
@@ -225,7 +227,7 @@ def learned_fields(model, params, mu, sigma, scales, bf16: bool = True):
     kbf = kb.reshape(-1)[:, None]
     face = (k >= kbf + 1) & ok
     wet = (k >= kbf) & ok
-    K = np.where(face, kap, np.nan)
+    K = np.where(face, kap, 0.0)
     A = np.where(wet, dgt, 0.0)
     B = np.where(wet, dgs, 0.0)
     shape = lambda Z: Z.T.reshape(nz, ny, nx)
@@ -234,14 +236,13 @@ def learned_fields(model, params, mu, sigma, scales, bf16: bool = True):
 
 def step_learned(model, nsteps, params, mu, sigma, scales, bf16: bool = True):
     """Advance an oracle model with the learned closure: before each step the network is
-    evaluated on the current state and its fields handed to the FP64 step."""
+    evaluated on the current state and its diffusivity, added to the Richardson-number
+    one of that state, and its corrections handed to the FP64 step."""
     for _ in range(nsteps):
         kap, dgt, dgs = learned_fields(model, params, mu, sigma, scales, bf16)
-        # nan marks faces that keep the Richardson-number kappa: fill them from it
         model.tendencies()
         kri = model.get("kappa")
-        kap = np.where(np.isnan(kap), kri, kap)
-        model.set_closure_fields(kap, dgt, dgs)
+        model.set_closure_fields(kri + kap, dgt, dgs)
         model.step(1)
         model.set_closure_fields(None, None, None)
 

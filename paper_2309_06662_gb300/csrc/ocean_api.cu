@@ -463,10 +463,11 @@ KP<R> make_kp(const ocean_t m, bool first) {
     return k;
 }
 
+// buffers of a step from state buffer `cur` (default: the current one)
 template <typename R>
-StepBuffers<R> make_bufs(const ocean_t m) {
+StepBuffers<R> make_bufs(const ocean_t m, int cur = -1) {
     StepBuffers<R> b{};
-    const int c = m->cur, n = 1 - m->cur;
+    const int c = cur < 0 ? m->cur : cur, n = 1 - c;
     auto P = [](void* q) { return reinterpret_cast<R*>(q); };
     b.u = P(m->u[c]); b.v = P(m->v[c]); b.T = P(m->T[c]); b.S = P(m->S[c]);
     b.un = P(m->u[n]); b.vn = P(m->v[n]); b.Tn = P(m->T[n]); b.Sn = P(m->S[n]);
@@ -491,7 +492,7 @@ long launches_per_step(const ocean_t m) {
 }
 
 // the learned closure after the Richardson-number closure: network on every column, then
-// its diffusivity into kap and its tracer corrections into b.dGT, b.dGS
+// its diffusivity added to kap and its tracer corrections into b.dGT, b.dGS
 template <typename R>
 bool enqueue_closure(ocean_t m, const KP<R>& k, StepBuffers<R>& b) {
     if (!(m->cl_ready && m->prm.closure == OCEAN_CLOSURE_LEARNED)) return false;
@@ -711,6 +712,46 @@ int get_field_t(ocean_t m, const FieldRef& r, int id, double* host) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Model internals the batched ensemble (ocean_ensemble.cu) builds on.
+
+int oc_member_create(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                     void* arena, size_t arena_bytes, void* stream, ocean_t* out) {
+    return create_common(grid, depth, params, arena, arena_bytes, stream, false, out);
+}
+
+OcMemberInfo oc_member_info(const ocean_s* m) {
+    OcMemberInfo r{};
+    r.nx = m->nx; r.ny = m->ny; r.nz = m->nz; r.px = m->px; r.py = m->py;
+    r.prec = m->prec; r.ns = m->prm.n_substeps; r.dt = m->prm.dt; r.g = m->prm.g;
+    r.learned = m->prm.closure == OCEAN_CLOSURE_LEARNED || m->cl_hidden > 0;
+    r.cur = m->cur; r.nstep = m->nstep;
+    return r;
+}
+
+int oc_member_kb(const ocean_s* m, int i, int j) {
+    return m->h_kb[hix2(const_cast<ocean_t>(m), i, j)];
+}
+
+template <typename R>
+EnsMember<R> oc_member_entry(const ocean_s* m, bool first, int cur) {
+    EnsMember<R> e{};
+    e.k = make_kp<R>(const_cast<ocean_t>(m), first);
+    e.b = make_bufs<R>(const_cast<ocean_t>(m), cur);
+    const int ns = m->prm.n_substeps;
+    e.dtau = (R)(2.0 * m->prm.dt / (ns + 1.0));   // as in the single-model sub-cycle
+    e.rns = 1.0 / ns;
+    return e;
+}
+template EnsMember<double> oc_member_entry<double>(const ocean_s*, bool, int);
+template EnsMember<float> oc_member_entry<float>(const ocean_s*, bool, int);
+
+void oc_member_advance(ocean_s* m) {
+    m->cur = 1 - m->cur;
+    m->nstep += 1;
+    m->tend_valid = false;
+}
 
 // =========================================================================== C ABI
 

@@ -1,7 +1,7 @@
 // ocean_closure.cu -- model-side kernels of the learned column closure: network inputs
-// from a model state, the network outputs applied inside the step (diffusivity and
-// tracer-tendency corrections, with the Richardson-number values kept for any column
-// whose outputs are not finite), and the training targets obtained by coarse-graining
+// from a model state, the network outputs applied inside the step (a diffusivity added
+// to the Richardson-number one and tracer-tendency corrections, neither applied to a
+// column whose outputs are not finite), and the training targets obtained by coarse-graining
 // a fine model onto a coarse one (r x r blocks of columns, same levels).
 #include <cuda_bf16.h>
 
@@ -67,7 +67,8 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
     }
 }
 
-// network outputs -> diffusivity on the interior wet faces and tracer corrections
+// network outputs -> extra diffusivity on the interior wet faces (added to the
+// Richardson-number value already in kap) and tracer corrections
 template <typename R>
 __global__ void k_closure_apply(KP<R> p, const float* __restrict__ Y, float ks, float gt,
                                 float gs, R* __restrict__ kap, R* __restrict__ dGT,
@@ -83,7 +84,7 @@ __global__ void k_closure_apply(KP<R> p, const float* __restrict__ Y, float ks, 
     for (int q = 0; q < 3 * nz; ++q) ok = ok && isfinite(y[q]);
     for (int k = 0; k < nz; ++k) {
         const long ck = k * P + c2;
-        if (ok && k >= kb + 1) kap[ck] = (R)(ks * softplus_c(y[k]));
+        if (ok && k >= kb + 1) kap[ck] = kap[ck] + (R)(ks * softplus_c(y[k]));
         dGT[ck] = (ok && k >= kb) ? (R)(gt * y[nz + k]) : R(0);
         dGS[ck] = (ok && k >= kb) ? (R)(gs * y[2 * nz + k]) : R(0);
     }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ocean.h"
+
 // Horizontal halo width of every padded field: five-point WENO stencils reach three
 // cells beyond a face, staggered averages one more.
 #define OC_H 4
@@ -258,3 +260,48 @@ void launch_closure_targets(const KP<R>& p, const R* GcT, const R* GcS, const fl
 void closure_forward(const void* Xb, int M, const void* const* Wt, const float* const* b,
                      const int* dims, void* H0, void* H1, float* Y, cudaStream_t s);
 void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s);
+
+// ---- batched ensemble (kernels in ocean_kernels.cu, host side in ocean_ensemble.cu)
+// One member's step parameters and buffers, read by the persistent ensemble kernels from
+// a device table (one table per (first step, buffer parity) combination).
+template <typename R> struct EnsMember {
+    KP<R> k;
+    StepBuffers<R> b;
+    R dtau;       // barotropic substep 2 dt / (n_substeps + 1)
+    double rns;   // 1 / n_substeps
+};
+// Work item: member m and the position of its unit of work: a column chunk (a), a
+// tracer/momentum tile (a, b) or a barotropic region (a, b).
+struct EnsItem { int m, a, b, cost; };
+enum {
+    ENS_DIAG = 0, ENS_TRACER, ENS_MOMENTUM, ENS_BARO_BEGIN, ENS_BARO_PASS, ENS_BARO_END,
+    ENS_CORRECT, ENS_NKIND
+};
+// Units of work: columns per chunk of the column kernels, tile and region interiors.
+struct EnsShape { int chunk, tile_x, tile_y, region_x, region_y, pass_substeps; };
+EnsShape ens_shape();
+// Resident blocks per SM of each ensemble kernel (occupancy calculator).
+template <typename R> int ens_blocks_per_sm(int kind);
+// One persistent launch of kind `kind` over work[0..nwork): `grid` blocks; items taken in
+// order from an atomic counter if `counter` (zeroed beforehand), else blockIdx.x +
+// n gridDim.x.  For ENS_BARO_PASS: `odd` selects the ping-pong direction, `nsub` the
+// substeps of this pass.
+template <typename R>
+void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwork, int grid,
+                int* counter, int odd, int nsub, cudaStream_t s);
+
+// Model internals the ensemble builds on (ocean_api.cu): a model in a caller-provided
+// arena on a caller's stream; its sizes and step state; the lowest wet level of column
+// (i, j); its table entry for a step from buffer `cur` (first: the Euler start); and
+// the bookkeeping after the ensemble has stepped it.
+struct OcMemberInfo {
+    int nx, ny, nz, px, py, prec, ns, learned, cur;
+    long nstep;
+    double dt, g;
+};
+int oc_member_create(const ocean_grid* grid, const double* depth, const ocean_params* params,
+                     void* arena, size_t arena_bytes, void* stream, ocean_t* out);
+OcMemberInfo oc_member_info(const ocean_s* m);
+int oc_member_kb(const ocean_s* m, int i, int j);
+template <typename R> EnsMember<R> oc_member_entry(const ocean_s* m, bool first, int cur);
+void oc_member_advance(ocean_s* m);

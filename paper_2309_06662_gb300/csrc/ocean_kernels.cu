@@ -46,15 +46,20 @@ __device__ __forceinline__ R buoy_anom(const KP<R>& p, R Ta, R Sa) {
 
 // ------------------------------------------------------------------ diagnostics
 
+// Each kernel body below is a device function of the model's parameters and of the
+// position of its work item (a column counter, a tile or a region), called by the
+// kernel of one model (position from blockIdx) and by the ensemble's persistent kernels
+// (position from a work list), so both run the same code.
+
+// column c of the (nx + 2) x (ny + 2) ring-extended horizontal grid
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
-                                              const R* __restrict__ v, const R* __restrict__ T,
-                                              const R* __restrict__ S, R* __restrict__ w,
-                                              R* __restrict__ pr, R* __restrict__ kap,
-                                              R* __restrict__ nu) {
+__device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* __restrict__ u,
+                                         const R* __restrict__ v, const R* __restrict__ T,
+                                         const R* __restrict__ S, R* __restrict__ w,
+                                         R* __restrict__ pr, R* __restrict__ kap,
+                                         R* __restrict__ nu) {
     const GeoD& g = p.g;
     const int W = g.nx + 2;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)W * (g.ny + 2)) return;
     const int i = (int)(c % W) - 1, j = (int)(c / W) - 1;
     const long c2 = ix2(g, i, j);
@@ -72,38 +77,54 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
         pr[k * P + c2] = pk;
         bup = bk;
     }
-    // vertical velocity on bottom faces, integrated upward from the sea floor
+    // one upward sweep: w on the bottom faces, integrated from the sea floor, and the
+    // Richardson-number closure on the interior faces, from the levels k-1 (kept in
+    // registers) and k
     const R dy = p.dy, dxvS = p.dxv[j + OC_H], dxvN = p.dxv[j + 1 + OC_H], rac = p.rAc[j + OC_H];
     R wk = R(0);
     w[kb * P + c2] = wk;
-    for (int k = kb; k < nz - 1; ++k) {
+    R Tm = R(0), Sm = R(0), ub = R(0), vb = R(0);
+    for (int k = kb; k < nz; ++k) {
         const long ck = k * P + c2;
-        R div = dy * p.dz[k] * (u[ck + 1] - u[ck])
-              + p.dz[k] * (dxvN * v[ck + g.pitch] - dxvS * v[ck]);
-        wk = wk - div * rac;
-        w[ck + P] = wk;
-    }
-    // Richardson-number closure on the interior w-faces
-    for (int k = kb + 1; k < nz; ++k) {
-        const long ck = k * P + c2, cm = ck - P;
-        R rz = p.rdzf[k];
-        R n2 = p.grav * (p.alpha * ((T[ck] - T[cm]) + p.dTref[k])
-                         - p.beta_s * ((S[ck] - S[cm]) + p.dSref[k])) * rz;
-        R ua = R(0.5) * (u[ck] + u[ck + 1]), ub = R(0.5) * (u[cm] + u[cm + 1]);
-        R va = R(0.5) * (v[ck] + v[ck + g.pitch]), vb = R(0.5) * (v[cm] + v[cm + g.pitch]);
-        R s2 = ((ua - ub) * (ua - ub) + (va - vb) * (va - vb)) * rz * rz;
-        R kk, nn;
-        if (n2 < R(0)) {
-            kk = p.kappa_conv; nn = p.kappa_conv;
-        } else {
-            R ri = n2 / (s2 > R(1e-14) ? s2 : R(1e-14));
-            R q = R(1) + p.ri_a * ri;
-            nn = p.nu0 / (q * q) + p.nu_b;
-            kk = nn / q + p.kappa_b;
+        const R Tk = T[ck], Sk = S[ck];
+        const R u0 = u[ck], u1 = u[ck + 1], v0 = v[ck], v1 = v[ck + g.pitch];
+        if (k < nz - 1) {
+            R div = dy * p.dz[k] * (u1 - u0) + p.dz[k] * (dxvN * v1 - dxvS * v0);
+            wk = wk - div * rac;
+            w[ck + P] = wk;
         }
-        kap[ck] = kk;
-        nu[ck] = nn;
+        const R ua = R(0.5) * (u0 + u1), va = R(0.5) * (v0 + v1);
+        if (k > kb) {
+            R rz = p.rdzf[k];
+            R n2 = p.grav * (p.alpha * ((Tk - Tm) + p.dTref[k])
+                             - p.beta_s * ((Sk - Sm) + p.dSref[k])) * rz;
+            R s2 = ((ua - ub) * (ua - ub) + (va - vb) * (va - vb)) * rz * rz;
+            R kk, nn;
+            if (n2 < R(0)) {
+                kk = p.kappa_conv; nn = p.kappa_conv;
+            } else {
+                R ri = n2 / (s2 > R(1e-14) ? s2 : R(1e-14));
+                R q = R(1) + p.ri_a * ri;
+                nn = p.nu0 / (q * q) + p.nu_b;
+                kk = nn / q + p.kappa_b;
+            }
+            kap[ck] = kk;
+            nu[ck] = nn;
+        }
+        Tm = Tk;
+        Sm = Sk;
+        ub = ua;
+        vb = va;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
+                                              const R* __restrict__ v, const R* __restrict__ T,
+                                              const R* __restrict__ S, R* __restrict__ w,
+                                              R* __restrict__ pr, R* __restrict__ kap,
+                                              R* __restrict__ nu) {
+    diag_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, u, v, T, S, w, pr, kap, nu);
 }
 
 // ------------------------------------------------------------------ tile layout
@@ -164,20 +185,21 @@ struct TracerSmem {
 // goes to Tn, Sn), back substitution down.  Horizontal fluxes reconstruct the anomalies
 // (WENO is translation-equivariant, so adding U Tref(k) gives the flux of T itself);
 // vertical ones reconstruct full values, since the reference varies along the column.
+// tile (bx, by): columns [bx TX, bx TX + TX) x [by TY, by TY + TY)
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const R* __restrict__ u,
-                                               const R* __restrict__ v, const R* __restrict__ w,
-                                               const R* __restrict__ T, const R* __restrict__ S,
-                                               R* __restrict__ kap, R* __restrict__ GTp,
-                                               R* __restrict__ GSp, R* __restrict__ Tn,
-                                               R* __restrict__ Sn, const R* __restrict__ dGT,
-                                               const R* __restrict__ dGS) {
+__device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const int by,
+                                            const R* __restrict__ u, const R* __restrict__ v,
+                                            const R* __restrict__ w, const R* __restrict__ T,
+                                            const R* __restrict__ S, R* __restrict__ kap,
+                                            R* __restrict__ GTp, R* __restrict__ GSp,
+                                            R* __restrict__ Tn, R* __restrict__ Sn,
+                                            const R* __restrict__ dGT, const R* __restrict__ dGS) {
     __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
     const long P = g.plane;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool mine = i < g.nx && j < g.ny;
     const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
@@ -390,6 +412,18 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const
     }
 }
 
+template <typename R, bool STEP>
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const R* __restrict__ u,
+                                               const R* __restrict__ v, const R* __restrict__ w,
+                                               const R* __restrict__ T, const R* __restrict__ S,
+                                               R* __restrict__ kap, R* __restrict__ GTp,
+                                               R* __restrict__ GSp, R* __restrict__ Tn,
+                                               R* __restrict__ Sn, const R* __restrict__ dGT,
+                                               const R* __restrict__ dGS) {
+    tracer_tile<R, STEP>(p, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn, Sn, dGT,
+                         dGS);
+}
+
 // ------------------------------------------------------------------ momentum
 
 template <typename R>
@@ -410,19 +444,19 @@ struct MomentumSmem {
 // backward-Euler vertical viscosity (Thomas: c' in cu/cv scratch, d' in un/vn) and the
 // sum of the solved column Su = sum dz u**.
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
-    KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
-    const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
-    const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
-    R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
-    R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
-    R* __restrict__ Sv) {
+__device__ __forceinline__ void momentum_tile(
+    const KP<R>& p, const int bx, const int by, const R* __restrict__ u,
+    const R* __restrict__ v, const R* __restrict__ w, const R* __restrict__ pr,
+    const R* __restrict__ nu, const R* __restrict__ taux_s, const R* __restrict__ tauy_s,
+    R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un, R* __restrict__ vn,
+    R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un, R* __restrict__ Vn,
+    R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su, R* __restrict__ Sv) {
     __shared__ MomentumSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
     const long P = g.plane;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool mine = i < g.nx && j < g.ny;
     const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
@@ -641,17 +675,31 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
     }
 }
 
+template <typename R, bool STEP>
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
+    KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
+    const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
+    const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
+    R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
+    R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
+    R* __restrict__ Sv) {
+    momentum_tile<R, STEP>(p, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s, Gup, Gvp,
+                           un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
+}
+
 // ------------------------------------------------------------------ barotropic mode
 
 // start of the sub-cycle: U^0 = U^n, deta^0 = 0, accumulators cleared, the gradient of
 // the FP64 free surface eta^n formed once (in R)
 template <typename R>
-__global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restrict__ Vn,
-                             const double* __restrict__ eta, const R* __restrict__ Hu,
-                             const R* __restrict__ Hv, R* Ub, R* Vb, R* dE, R* paccE, R* paccU,
-                             R* paccV, double* accE, double* accU, double* accV, R* gxe, R* gye) {
+__device__ __forceinline__ void baro_begin_col(const KP<R>& p, const long c,
+                                               const R* __restrict__ Un, const R* __restrict__ Vn,
+                                               const double* __restrict__ eta,
+                                               const R* __restrict__ Hu, const R* __restrict__ Hv,
+                                               R* Ub, R* Vb, R* dE, R* paccE, R* paccU, R* paccV,
+                                               double* accE, double* accU, double* accV, R* gxe,
+                                               R* gye) {
     const GeoD& g = p.g;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j);
@@ -668,6 +716,15 @@ __global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restr
     gye[c2] = Hv[c2] > R(0) ? R(eta[c2] - eta[c2 - g.pitch]) : R(0);
 }
 
+template <typename R>
+__global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restrict__ Vn,
+                             const double* __restrict__ eta, const R* __restrict__ Hu,
+                             const R* __restrict__ Hv, R* Ub, R* Vb, R* dE, R* paccE, R* paccU,
+                             R* paccV, double* accE, double* accU, double* accV, R* gxe, R* gye) {
+    baro_begin_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, Un, Vn, eta, Hu, Hv, Ub,
+                      Vb, dE, paccE, paccU, paccV, accE, accU, accV, gxe, gye);
+}
+
 // Temporal blocking of the sub-cycle (the one-GPU form of the paper's barotropic halo as
 // wide as the number of substeps): a block owns a BRX x BRY region of columns in shared
 // memory, an interior plus a BS-wide halo, and advances it BS substeps per pass; each
@@ -676,6 +733,12 @@ __global__ void k_baro_begin(KP<R> p, const R* __restrict__ Un, const R* __restr
 // it once instead of once per substep.  The state ping-pongs between two global buffers
 // across passes (neighbouring blocks read their halos from the previous pass).
 constexpr int BRX = 64, BRY = 32, BS = 6, BNT = 512, BC = BRX * BRY / BNT;
+// dynamic shared memory of a region: eta, U, V planes and three per-row arrays
+template <typename R> constexpr size_t baro_smem() { return (3 * BRX * BRY + 3 * BRY) * sizeof(R); }
+// resident blocks per SM: in FP32 two (registers <= 64), so that one block's loads
+// overlap another's substeps; the FP64 form needs more registers than that allows
+template <typename R> struct BaroOcc { static constexpr int value = 2; };
+template <> struct BaroOcc<double> { static constexpr int value = 1; };
 
 // padded index of (i, j) with periodic wrap; -1 beyond a wall
 __device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
@@ -687,34 +750,49 @@ __device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
     return ix2(g, i, j);
 }
 
+// region (bx, by): the interior [bx IX, bx IX + IX) x [by IY, by IY + IY) and its halo
 template <typename R>
-__global__ void __launch_bounds__(BNT) k_baro_pass(
-    KP<R> p, const R* __restrict__ Ea, const R* __restrict__ Ua, const R* __restrict__ Va,
-    R* __restrict__ Eb, R* __restrict__ Ub, R* __restrict__ Vb, const R* __restrict__ gxe,
-    const R* __restrict__ gye, const R* __restrict__ Hu, const R* __restrict__ Hv,
-    const R* __restrict__ GU, const R* __restrict__ GV, const R* __restrict__ Un,
-    const R* __restrict__ Vn, double* __restrict__ accE, double* __restrict__ accU,
-    double* __restrict__ accV, int nsub, R dtau, R grav) {
+__device__ __forceinline__ void baro_region(
+    const KP<R>& p, const int bx, const int by, const R* __restrict__ Ea,
+    const R* __restrict__ Ua, const R* __restrict__ Va, R* __restrict__ Eb, R* __restrict__ Ub,
+    R* __restrict__ Vb, const R* __restrict__ gxe, const R* __restrict__ gye,
+    const R* __restrict__ Hu, const R* __restrict__ Hv, const R* __restrict__ GU,
+    const R* __restrict__ GV, const R* __restrict__ Un, const R* __restrict__ Vn,
+    double* __restrict__ accE, double* __restrict__ accU, double* __restrict__ accV, int nsub,
+    R dtau, R grav) {
     extern __shared__ __align__(16) unsigned char bsm[];
     R* sE = reinterpret_cast<R*>(bsm);
     R* sU = sE + BRX * BRY;
     R* sV = sU + BRX * BRY;
+    R* sDN = sV + BRX * BRY;   // per region row: dxv of the north and south faces and
+    R* sDS = sDN + BRY;        // dtau / A_c (0 for rows outside the domain)
+    R* sCe = sDS + BRY;
     const GeoD& g = p.g;
     const int tid = threadIdx.x;
     const int IX = BRX - 2 * BS, IY = BRY - 2 * BS;
-    const int i0 = blockIdx.x * IX - BS, j0 = blockIdx.y * IY - BS;   // region origin
-    long gc[BC];
-    R Au[BC], Bu[BC], Av[BC], Bv[BC], ce[BC], dN[BC], dS[BC], u0[BC], v0[BC];
+    const int i0 = bx * IX - BS, j0 = by * IY - BS;   // region origin
+    // a thread owns the cells (rx, ry0 + r BNT/BRX), r < BC, of one region column
+    const int rx = tid % BRX, ry0 = tid / BRX;
+    constexpr int RS = BNT / BRX;
+    if (tid < BRY) {
+        int j = j0 + tid;
+        if (g.py) { j %= g.ny; if (j < 0) j += g.ny; }
+        const bool in = j >= 0 && j < g.ny;
+        sDS[tid] = in ? p.dxv[j + OC_H] : R(0);
+        sDN[tid] = in ? p.dxv[j + 1 + OC_H] : R(0);
+        sCe[tid] = in ? dtau * p.rAc[j + OC_H] : R(0);
+    }
+    R Au[BC], Bu[BC], Av[BC], Bv[BC], u0[BC], v0[BC];
     R pE[BC], pU[BC], pV[BC];
-    bool own[BC];
+    unsigned wetm = 0, ownm = 0;
 #pragma unroll
     for (int r = 0; r < BC; ++r) {
-        const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
+        const int ry = ry0 + r * RS, q = ry * BRX + rx;
         int jw = 0;
         const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
-        gc[r] = c;
-        own[r] = rx >= BS && rx < BRX - BS && ry >= BS && ry < BRY - BS && i0 + rx < g.nx &&
-                 j0 + ry < g.ny;
+        const bool own = rx >= BS && rx < BRX - BS && ry >= BS && ry < BRY - BS &&
+                         i0 + rx < g.nx && j0 + ry < g.ny;
+        ownm |= (own ? 1u : 0u) << r;
         pE[r] = pU[r] = pV[r] = R(0);
         if (c >= 0) {
             sE[q] = Ea[c];
@@ -727,15 +805,12 @@ __global__ void __launch_bounds__(BNT) k_baro_pass(
             Bu[r] = hu > R(0) ? dtau * GU[c] - Au[r] * gxe[c] : R(0);
             Av[r] = hv > R(0) ? dtau * grav * hv * p.rdy : R(0);
             Bv[r] = hv > R(0) ? dtau * GV[c] - Av[r] * gye[c] : R(0);
-            const bool wet = g.kb[c] < g.nz;
-            ce[r] = wet ? dtau * p.rAc[jw + OC_H] : R(0);
-            dN[r] = p.dxv[jw + 1 + OC_H];
-            dS[r] = p.dxv[jw + OC_H];
-            u0[r] = own[r] ? Un[c] : R(0);
-            v0[r] = own[r] ? Vn[c] : R(0);
+            wetm |= (g.kb[c] < g.nz ? 1u : 0u) << r;
+            u0[r] = own ? Un[c] : R(0);
+            v0[r] = own ? Vn[c] : R(0);
         } else {
             sE[q] = sU[q] = sV[q] = R(0);
-            Au[r] = Bu[r] = Av[r] = Bv[r] = ce[r] = dN[r] = dS[r] = u0[r] = v0[r] = R(0);
+            Au[r] = Bu[r] = Av[r] = Bv[r] = u0[r] = v0[r] = R(0);
         }
     }
     __syncthreads();
@@ -744,10 +819,10 @@ __global__ void __launch_bounds__(BNT) k_baro_pass(
         // (each column reads only its own deta here, so it can be overwritten in place)
 #pragma unroll
         for (int r = 0; r < BC; ++r) {
-            const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
-            if (rx + 1 < BRX && ry + 1 < BRY && ce[r] != R(0)) {
-                const R div = p.dy * (sU[q + 1] - sU[q]) + dN[r] * sV[q + BRX] - dS[r] * sV[q];
-                const R e = sE[q] - ce[r] * div;
+            const int ry = ry0 + r * RS, q = ry * BRX + rx;
+            if (rx + 1 < BRX && ry + 1 < BRY && ((wetm >> r) & 1u)) {
+                const R div = p.dy * (sU[q + 1] - sU[q]) + sDN[ry] * sV[q + BRX] - sDS[ry] * sV[q];
+                const R e = sE[q] - sCe[ry] * div;
                 sE[q] = e;
                 pE[r] += e;
             }
@@ -756,7 +831,7 @@ __global__ void __launch_bounds__(BNT) k_baro_pass(
         // U^m, V^m from eta^m (each column reads only its own U, V here)
 #pragma unroll
         for (int r = 0; r < BC; ++r) {
-            const int q = tid + r * BNT, rx = q % BRX, ry = q / BRX;
+            const int ry = ry0 + r * RS, q = ry * BRX + rx;
             if (rx >= 1 && Au[r] != R(0)) {
                 const R un = sU[q] + Bu[r] - Au[r] * (sE[q] - sE[q - 1]);
                 sU[q] = un;
@@ -772,9 +847,10 @@ __global__ void __launch_bounds__(BNT) k_baro_pass(
     }
 #pragma unroll
     for (int r = 0; r < BC; ++r) {
-        if (!own[r]) continue;
-        const int q = tid + r * BNT;
-        const long c = gc[r];
+        if (!((ownm >> r) & 1u)) continue;
+        const int ry = ry0 + r * RS, q = ry * BRX + rx;
+        int jw = 0;
+        const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
         Eb[c] = sE[q];
         Ub[c] = sU[q];
         Vb[c] = sV[q];
@@ -784,17 +860,30 @@ __global__ void __launch_bounds__(BNT) k_baro_pass(
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_baro_pass(
+    KP<R> p, const R* __restrict__ Ea, const R* __restrict__ Ua, const R* __restrict__ Va,
+    R* __restrict__ Eb, R* __restrict__ Ub, R* __restrict__ Vb, const R* __restrict__ gxe,
+    const R* __restrict__ gye, const R* __restrict__ Hu, const R* __restrict__ Hv,
+    const R* __restrict__ GU, const R* __restrict__ GV, const R* __restrict__ Un,
+    const R* __restrict__ Vn, double* __restrict__ accE, double* __restrict__ accU,
+    double* __restrict__ accV, int nsub, R dtau, R grav) {
+    baro_region<R>(p, blockIdx.x, blockIdx.y, Ea, Ua, Va, Eb, Ub, Vb, gxe, gye, Hu, Hv, GU, GV,
+                   Un, Vn, accE, accU, accV, nsub, dtau, grav);
+}
+
 // eta^{n+1} = eta^n + mean(deta) in FP64; correction of the depth-integrated velocity
 // (Ubar - sum dz u**)/H_u with Ubar = U^n + mean(U - U^n)
 template <typename R>
-__global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE,
-                           const double* __restrict__ accU, const double* __restrict__ accV,
-                           const R* __restrict__ Un, const R* __restrict__ Vn,
-                           const R* __restrict__ Su, const R* __restrict__ Sv,
-                           const R* __restrict__ rHu, const R* __restrict__ rHv, R* corrU,
-                           R* corrV, double rns) {
+__device__ __forceinline__ void baro_end_col(const KP<R>& p, const long c, double* eta,
+                                             const double* __restrict__ accE,
+                                             const double* __restrict__ accU,
+                                             const double* __restrict__ accV,
+                                             const R* __restrict__ Un, const R* __restrict__ Vn,
+                                             const R* __restrict__ Su, const R* __restrict__ Sv,
+                                             const R* __restrict__ rHu, const R* __restrict__ rHv,
+                                             R* corrU, R* corrV, double rns) {
     const GeoD& g = p.g;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j);
@@ -804,10 +893,21 @@ __global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE
 }
 
 template <typename R>
-__global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
-                          const R* __restrict__ corrU, const R* __restrict__ corrV) {
+__global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE,
+                           const double* __restrict__ accU, const double* __restrict__ accV,
+                           const R* __restrict__ Un, const R* __restrict__ Vn,
+                           const R* __restrict__ Su, const R* __restrict__ Sv,
+                           const R* __restrict__ rHu, const R* __restrict__ rHv, R* corrU,
+                           R* corrV, double rns) {
+    baro_end_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, eta, accE, accU, accV, Un,
+                    Vn, Su, Sv, rHu, rHv, corrU, corrV, rns);
+}
+
+template <typename R>
+__device__ __forceinline__ void correct_col(const KP<R>& p, const long c, R* __restrict__ un,
+                                            R* __restrict__ vn, const R* __restrict__ corrU,
+                                            const R* __restrict__ corrV) {
     const GeoD& g = p.g;
-    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j), P = g.plane;
@@ -817,17 +917,18 @@ __global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
     for (int k = kv; k < g.nz; ++k) vn[k * P + c2] += cv;
 }
 
+template <typename R>
+__global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
+                          const R* __restrict__ corrU, const R* __restrict__ corrV) {
+    correct_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, un, vn, corrU, corrV);
+}
+
 // ------------------------------------------------------------------ halos
 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
 
-template <typename R>
-int setup_kernel_attributes(int nz) {
-    (void)nz;
-    return (int)cudaSuccess;
-}
 
 template <typename R>
 void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
@@ -872,7 +973,7 @@ void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double d
                                        b.gye);
     const dim3 grid((g.nx + BRX - 2 * BS - 1) / (BRX - 2 * BS),
                     (g.ny + BRY - 2 * BS - 1) / (BRY - 2 * BS));
-    const size_t smem = (size_t)3 * BRX * BRY * sizeof(R);
+    const size_t smem = baro_smem<R>();
     R *Ea = b.dE, *Ua = b.Ub, *Va = b.Vb, *Eb = b.dE2, *Ub = b.Ub2, *Vb = b.Vb2;
     for (int m0 = 0; m0 < ns; m0 += BS) {
         const int nsub = ns - m0 < BS ? ns - m0 : BS;
@@ -1076,6 +1177,192 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
     k_diag_final<<<1, 32, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
 }
 
+// ------------------------------------------------------------------ batched ensemble
+// Persistent kernels over a work list of (member, position) items.  A block takes items
+// blockIdx.x, blockIdx.x + gridDim.x, ... (static schedule) or the next item of an
+// atomic counter (dynamic schedule); the host sorts the list by decreasing cost, so
+// either schedule hands out the long items first.  Each item runs the same body as the
+// single-model kernel, with the member's parameters and buffers from a device table.
+
+namespace {
+
+__device__ __forceinline__ int ens_first(int* counter, int* s_next) {
+    if (!counter) return blockIdx.x;
+    if (threadIdx.x == 0 && threadIdx.y == 0) *s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_next;
+}
+
+// the barrier frees the item's shared memory (and *s_next) for the next item
+__device__ __forceinline__ int ens_next(int* counter, int* s_next, int it) {
+    __syncthreads();
+    if (!counter) return it + gridDim.x;
+    if (threadIdx.x == 0 && threadIdx.y == 0) *s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_next;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_ens_diag(const EnsMember<R>* __restrict__ mem,
+                                                  const EnsItem* __restrict__ work, int nwork,
+                                                  int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        diag_col<R>(p, (long)e.a * TPB + threadIdx.x, b.u, b.v, b.T, b.S, b.w, b.p, b.kap, b.nu);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_tracer(
+    const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
+    int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        tracer_tile<R, true>(p, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS, b.Tn, b.Sn,
+                             b.dGT, b.dGS);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_momentum(
+    const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
+    int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        momentum_tile<R, true>(p, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
+                               b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_ens_baro_begin(const EnsMember<R>* __restrict__ mem,
+                                                        const EnsItem* __restrict__ work,
+                                                        int nwork, int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        baro_begin_col<R>(p, (long)e.a * TPB + threadIdx.x, b.Un, b.Vn, b.eta, b.Hu, b.Hv, b.Ub,
+                          b.Vb, b.dE, b.paccE, b.paccU, b.paccV, b.accE, b.accU, b.accV, b.gxe,
+                          b.gye);
+    }
+}
+
+// odd passes run from the second buffers back into the first, as in the single model
+template <typename R>
+__global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_ens_baro_pass(const EnsMember<R>* __restrict__ mem,
+                                                       const EnsItem* __restrict__ work,
+                                                       int nwork, int* counter, int odd,
+                                                       int nsub) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        const R dtau = mem[e.m].dtau;
+        R *Ea = b.dE, *Ua = b.Ub, *Va = b.Vb, *Eb = b.dE2, *Ub = b.Ub2, *Vb = b.Vb2;
+        if (odd) {
+            Ea = b.dE2; Ua = b.Ub2; Va = b.Vb2;
+            Eb = b.dE; Ub = b.Ub; Vb = b.Vb;
+        }
+        baro_region<R>(p, e.a, e.b, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye, b.Hu, b.Hv, b.GU, b.GV,
+                       b.Un, b.Vn, b.accE, b.accU, b.accV, nsub, dtau, p.grav);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_ens_baro_end(const EnsMember<R>* __restrict__ mem,
+                                                      const EnsItem* __restrict__ work,
+                                                      int nwork, int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        baro_end_col<R>(p, (long)e.a * TPB + threadIdx.x, b.eta, b.accE, b.accU, b.accV, b.Un,
+                        b.Vn, b.Su, b.Sv, b.rHu, b.rHv, b.corrU, b.corrV, mem[e.m].rns);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_ens_correct(const EnsMember<R>* __restrict__ mem,
+                                                     const EnsItem* __restrict__ work,
+                                                     int nwork, int* counter) {
+    __shared__ int s_next;
+    for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
+        const EnsItem e = work[it];
+        const KP<R>& p = mem[e.m].k;
+        const StepBuffers<R>& b = mem[e.m].b;
+        correct_col<R>(p, (long)e.a * TPB + threadIdx.x, b.un, b.vn, b.corrU, b.corrV);
+    }
+}
+
+}  // namespace
+
+EnsShape ens_shape() { return EnsShape{TPB, TX, TY, BRX - 2 * BS, BRY - 2 * BS, BS}; }
+
+template <typename R>
+int ens_blocks_per_sm(int kind) {
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    switch (kind) {
+        case ENS_DIAG: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_diag<R>, TPB, 0); break;
+        case ENS_TRACER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_tracer<R>, NT, 0); break;
+        case ENS_MOMENTUM: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_momentum<R>, NT, 0); break;
+        case ENS_BARO_BEGIN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_baro_begin<R>, TPB, 0); break;
+        case ENS_BARO_PASS:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_baro_pass<R>, BNT,
+                                                              baro_smem<R>());
+            break;
+        case ENS_BARO_END: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_baro_end<R>, TPB, 0); break;
+        case ENS_CORRECT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_correct<R>, TPB, 0); break;
+        default: return 0;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+template <typename R>
+void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwork, int grid,
+                int* counter, int odd, int nsub, cudaStream_t s) {
+    if (nwork <= 0 || grid <= 0) return;
+    const dim3 tile(TX, TY);
+    switch (kind) {
+        case ENS_DIAG: k_ens_diag<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_TRACER: k_ens_tracer<R><<<grid, tile, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_MOMENTUM: k_ens_momentum<R><<<grid, tile, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_BARO_BEGIN: k_ens_baro_begin<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_BARO_PASS:
+            k_ens_baro_pass<R><<<grid, BNT, baro_smem<R>(), s>>>(
+                mem, work, nwork, counter, odd, nsub);
+            break;
+        case ENS_BARO_END: k_ens_baro_end<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_CORRECT: k_ens_correct<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
+        default: break;
+    }
+}
+
+// the FP64 region (three planes and the row arrays) is just above the 48 KB of dynamic
+// shared memory a kernel gets without opting in
+template <typename R>
+int setup_kernel_attributes(int nz) {
+    (void)nz;
+    const int bytes = (int)baro_smem<R>();
+    cudaError_t e = cudaFuncSetAttribute(k_baro_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ens_baro_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return (int)e;
+}
+
 // ------------------------------------------------------------------ instantiations
 
 #define OC_INST(R)                                                                          \
@@ -1091,7 +1378,10 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
     template void launch_halo2<R>(const GeoD&, R*, cudaStream_t);                           \
     template void launch_diagnostics<R>(const GeoD&, const DiagMetrics&, const R*, const R*, \
                                         const R*, const R*, const R*, const double*,        \
-                                        double*, double*, cudaStream_t);
+                                        double*, double*, cudaStream_t);                \
+    template int ens_blocks_per_sm<R>(int);                                                 \
+    template void launch_ens<R>(int, const EnsMember<R>*, const EnsItem*, int, int, int*,   \
+                                int, int, cudaStream_t);
 
 OC_INST(double)
 OC_INST(float)

@@ -378,3 +378,40 @@ def latlon_pair(nxc: int, nyc: int, nz: int, lat: float, r: int, seed: int, dt_c
     coarse.params["dt"] = dt_coarse
     coarse.params["n_substeps"] = ns_coarse
     return fine, coarse
+
+
+# ----------------------------------------------------------------------------- ensemble
+
+def ensemble_member_case(seed: int, nx: int, ny: int, nz: int, wind: float, dT: float,
+                         dx: float = 20e3) -> Case:
+    """One closed beta-plane basin of the ensemble: dx = dy = 20 km, uniform levels to
+    5500 m, random-field bathymetry (correlation 10 cells, land where shallower than
+    50 m and on the first and last rows), zonal wind `wind` cos(pi y / Ly), T linear
+    from 2 + dT (top) to 2 C and S from 34.5 to 35 with 0.05 noise, dt 600 s, 30
+    substeps."""
+    zf = uniform_z_faces(nz, 5500.0)
+    depth = random_field_depth(nx, ny, 1.0, 1.0, seed, corr_deg=10.0, periodic_x=False)
+    Ly = ny * dx
+    yc = (np.arange(ny) + 0.5) * dx
+    taux = np.repeat((wind * np.cos(math.pi * yc / Ly))[:, None], nx, axis=1)
+    tauy = np.zeros((ny, nx))
+    T, S = _stratified(zf, ny, nx, seed, 2.0 + dT, 2.0, 34.5, 35.0, 0.05)
+    p = default_params()
+    p.update(dt=600.0, n_substeps=30)
+    return Case(f"member_{seed}", 0, nx, ny, nz, False, False, 0.0, nx * dx, 0.0, Ly, zf,
+                depth, taux, tauy, T, S, p, steps=1)
+
+
+def ensemble_cases(count: int = 96, seed: int = 5, n_lo: int = 32, n_hi: int = 512,
+                   levels=(8, 16, 32, 48)):
+    """`count` uneven members: member m draws (seed + m) nx, ny ~ U[n_lo, n_hi], nz from
+    `levels`, wind ~ U[0.05, 0.2] N/m^2 and dT ~ U[10, 20] C."""
+    out = []
+    for m in range(count):
+        s = seed + m
+        u = random_uniform(s, 50, 5)
+        nx = n_lo + int(u[0] * (n_hi - n_lo + 1))
+        ny = n_lo + int(u[1] * (n_hi - n_lo + 1))
+        nz = int(levels[int(u[2] * len(levels))])
+        out.append(ensemble_member_case(s, nx, ny, nz, 0.05 + 0.15 * u[3], 10.0 + 10.0 * u[4]))
+    return out

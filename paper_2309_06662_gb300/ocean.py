@@ -136,6 +136,18 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
                                             POINTER(ctypes.c_float), POINTER(ctypes.c_float)]),
             "ocean_mlp_train_step": (c_int, [pv, POINTER(OceanBatch), c_int, POINTER(ClosureScales),
                                              ctypes.c_float, POINTER(ctypes.c_float)]),
+            "ocean_ensemble_create": (c_int, [c_int, POINTER(OceanGrid), POINTER(pd),
+                                              POINTER(OceanParams), POINTER(pv)]),
+            "ocean_ensemble_destroy": (None, [pv]),
+            "ocean_ensemble_size": (c_int, [pv]),
+            "ocean_ensemble_member": (pv, [pv, c_int]),
+            "ocean_ensemble_stream": (pv, [pv]),
+            "ocean_ensemble_step": (c_int, [pv, c_int]),
+            "ocean_ensemble_step_async": (c_int, [pv, c_int]),
+            "ocean_ensemble_autotune": (c_int, [pv, c_int, POINTER(c_int)]),
+            "ocean_ensemble_launch_shapes": (c_int, [pv, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+            "ocean_ensemble_kernel_launches": (c_long, [pv]),
+            "ocean_ensemble_kind_times": (c_int, [pv, pd]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -238,11 +250,31 @@ class Ocean:
         if case.eta is not None:
             self.set("eta", case.eta)
 
+    @classmethod
+    def _member(cls, handle, case, precision: int, params: dict):
+        """A handle owned by an Ensemble (never destroyed here), set to the case's state."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.nx, self.ny, self.nz = case.nx, case.ny, case.nz
+        self.precision = precision
+        self._arena = None
+        self._borrowed = True
+        self._h = c_void_p(handle)
+        self.set("T", case.T)
+        self.set("S", case.S)
+        if case.u is not None:
+            self.set("u", case.u)
+        if case.v is not None:
+            self.set("v", case.v)
+        if case.eta is not None:
+            self.set("eta", case.eta)
+        return self
+
     def close(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value:
+        if h is not None and h.value and not getattr(self, "_borrowed", False):
             load().ocean_destroy(h)
-            self._h = None
+        self._h = None
         self._arena = None
 
     def __del__(self):
@@ -524,3 +556,92 @@ class MLP:
         _check(load().ocean_mlp_train_step(self._h, ctypes.byref(b), tensors["X"].shape[0],
                                            ctypes.byref(sc), lr, ctypes.byref(loss)))
         return loss.value
+
+
+# ----------------------------------------------------------------------------- ensemble
+
+ENS_KINDS = ["diag", "tracer", "momentum", "baro_begin", "baro_pass", "baro_end", "correct"]
+
+
+class Ensemble:
+    """ocean_ensemble_*: many closed-basin models stepped together by persistent kernels
+    over a (member, tile) work list, one CUDA graph per step."""
+
+    def __init__(self, cases, precision: int = OCEAN_MIXED, params: Optional[dict] = None):
+        _torch_cuda()
+        L = load()
+        M = len(cases)
+        grids = (OceanGrid * M)()
+        prms = (OceanParams * M)()
+        depths = (POINTER(c_double) * M)()
+        self._keep = []
+        plist = []
+        for i, c in enumerate(cases):
+            p = dict(c.params)
+            if params:
+                p.update(params)
+            plist.append(p)
+            g, zf = make_grid(c)
+            pr, keep = make_params(p, precision, c.taux, c.tauy)
+            d = np.ascontiguousarray(c.depth, dtype=np.float64)
+            self._keep += [zf, keep, d]
+            grids[i] = g
+            prms[i] = pr
+            depths[i] = _dp(d)
+        h = c_void_p()
+        _check(L.ocean_ensemble_create(M, grids, depths, prms, ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.members = [Ocean._member(L.ocean_ensemble_member(h, i), c, precision, plist[i])
+                        for i, c in enumerate(cases)]
+        self.cells = int(sum(c.nx * c.ny * c.nz for c in cases))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            for m in self.members:
+                m._h = None
+            load().ocean_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, n: int = 1) -> None:
+        _check(load().ocean_ensemble_step(self._h, int(n)))
+
+    def step_async(self, n: int = 1) -> None:
+        _check(load().ocean_ensemble_step_async(self._h, int(n)))
+
+    def sync(self) -> None:
+        self.members[0].sync()
+
+    def autotune(self, reps: int = 1) -> int:
+        """Tune the launch shapes on real steps; returns the number of steps taken."""
+        n = c_int()
+        _check(load().ocean_ensemble_autotune(self._h, int(reps), ctypes.byref(n)))
+        return n.value
+
+    def launch_shapes(self):
+        g, d, w = ((c_int * len(ENS_KINDS))() for _ in range(3))
+        _check(load().ocean_ensemble_launch_shapes(self._h, g, d, w))
+        return {k: dict(grid=g[i], dynamic=bool(d[i]), items=w[i]) for i, k in enumerate(ENS_KINDS)}
+
+    def kind_times(self):
+        """Device ms per step of each kernel kind under its tuned shape (after autotune)."""
+        ms = np.zeros(len(ENS_KINDS))
+        _check(load().ocean_ensemble_kind_times(self._h, _dp(ms)))
+        return dict(zip(ENS_KINDS, ms.tolist()))
+
+    @property
+    def launches(self) -> int:
+        return load().ocean_ensemble_kernel_launches(self._h)
+
+    @property
+    def stream(self) -> int:
+        return load().ocean_ensemble_stream(self._h) or 0

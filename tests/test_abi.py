@@ -57,3 +57,53 @@ def test_arena_size_and_argument_errors_without_gpu():
     assert L.ocean_create(ctypes.byref(g), None, ctypes.byref(prm), ctypes.byref(h)) == -1
     assert L.ocean_step(None, 1) == -1
     assert L.ocean_get_step(None) == -1
+
+
+def test_ensemble_argument_errors_without_gpu():
+    # ocean_ensemble_create checks its members on the host before any device call
+    from paper_2309_06662_gb300 import inputs
+    cases = inputs.ensemble_cases(2, seed=60, n_lo=8, n_hi=12, levels=(4,))
+    L = ocean.load()
+    M = len(cases)
+    grids = (ocean.OceanGrid * M)()
+    prms = (ocean.OceanParams * M)()
+    depths = (ctypes.POINTER(ctypes.c_double) * M)()
+    keep = []
+    for i, c in enumerate(cases):
+        g, zf = ocean.make_grid(c)
+        p, k = ocean.make_params(c.params, ocean.OCEAN_MIXED, c.taux, c.tauy)
+        import numpy as np
+        d = np.ascontiguousarray(c.depth)
+        keep += [zf, k, d]
+        grids[i], prms[i] = g, p
+        depths[i] = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    grids[1].periodic_x = 1
+    assert L.ocean_ensemble_create(M, grids, depths, prms, ctypes.byref(h)) == -1
+    assert b"closed basins" in L.ocean_last_error(None)
+    grids[1].periodic_x = 0
+    prms[1].dt = 300.0
+    assert L.ocean_ensemble_create(M, grids, depths, prms, ctypes.byref(h)) == -1
+    assert b"share precision" in L.ocean_last_error(None)
+    prms[1].dt = prms[0].dt
+    prms[0].closure = ocean.OCEAN_CLOSURE_LEARNED
+    assert L.ocean_ensemble_create(M, grids, depths, prms, ctypes.byref(h)) == -1
+    prms[0].closure = ocean.OCEAN_CLOSURE_RI
+    assert L.ocean_ensemble_create(0, grids, depths, prms, ctypes.byref(h)) == -1
+    assert L.ocean_ensemble_step(None, 1) == -1
+    assert L.ocean_ensemble_member(None, 0) is None
+    assert L.ocean_ensemble_kernel_launches(None) == -1
+
+
+def test_ensemble_recipe():
+    from paper_2309_06662_gb300 import inputs
+    cs = inputs.ensemble_cases(12, seed=5)
+    for c in cs:
+        assert 32 <= c.nx <= 512 and 32 <= c.ny <= 512 and c.nz in (8, 16, 32, 48)
+        assert not c.periodic_x and not c.periodic_y and c.kind == 0
+        assert c.depth.max() <= 5500.0 and (c.depth[0] == 0).all() and (c.depth[-1] == 0).all()
+        assert 0.05 <= c.taux.max() <= 0.2 + 1e-12
+        assert c.params["dt"] == 600.0 and c.params["n_substeps"] == 30
+    assert len({(c.nx, c.ny, c.nz) for c in cs}) == len(cs)     # uneven members
+    again = inputs.ensemble_cases(12, seed=5)
+    assert all((a.depth == b.depth).all() and (a.T == b.T).all() for a, b in zip(cs, again))

@@ -1,6 +1,7 @@
-"""Pins of the oracle's learned-closure step (CPU): a network that reproduces the
-Richardson-number diffusivity leaves the step unchanged, and a constant tendency
-correction adds exactly dt * c * (wet volume) of tracer."""
+"""Pins of the oracle's learned-closure step (CPU): a network whose diffusivity is a
+constant K2 on top of a Richardson-number closure that gives K1 everywhere is the plain
+step with K1 + K2, and a constant tendency correction adds exactly dt * c * (wet volume)
+of tracer."""
 import math
 
 import numpy as np
@@ -8,7 +9,6 @@ import numpy as np
 import oracle
 from oracle import closure as C
 from paper_2309_06662_gb300 import inputs
-from tests.oracle_cases import seeded_velocity
 
 SCALES = dict(kappa=1e-2, gT=1e-6, gS=1e-7, sFT=1, sFS=1, sGT=1, sGS=1)
 
@@ -21,27 +21,32 @@ def _net(nz, hidden, last_bias):
 
 
 def _case(K):
+    """kappa = K on every interior face: nu0 = nu_b = 0, and a start from rest with
+    uniform salinity, so no face turns convective in five steps (convective faces would
+    also set nu = kappa_conv, which the network does not touch)."""
     c = inputs.latlon_small_case(seed=12)
-    c.u, c.v = seeded_velocity(c, 4, 0.03)
-    # kappa = kappa_b everywhere: nu0 = nu_b = 0, convective value equal to it
+    c.S = np.where(c.S != 0.0, 35.0, 0.0)
     return c.with_params(nu0=0.0, nu_b=0.0, kappa_b=K, kappa_conv=K)
 
 
-def test_learned_closure_reproducing_ri_kappa_is_the_plain_step():
-    K = 3e-3
-    c = _case(K)
-    nz = c.nz
+def test_learned_diffusivity_adds_to_the_richardson_kappa():
+    K1, K2 = 1e-3, 2e-3
+    nz = _case(K1).nz
     b = np.zeros(3 * nz)
-    b[:nz] = math.log(math.expm1(K / SCALES["kappa"]))     # softplus^{-1}(K / kappa_scale)
+    b[:nz] = math.log(math.expm1(K2 / SCALES["kappa"]))    # softplus^{-1}(K2 / kappa_scale)
     params = _net(nz, 16, b)
     mu, sigma = np.zeros(6 * nz), np.ones(6 * nz)
-    a = oracle.OracleModel(c)
+    a = oracle.OracleModel(_case(K1 + K2))
     a.step(5)
-    m = oracle.OracleModel(c)
+    m = oracle.OracleModel(_case(K1))
     C.step_learned(m, 5, params, mu, sigma, SCALES, bf16=False)
     for f in ("u", "v", "T", "S", "eta"):
         x, y = m.get(f), a.get(f)
         assert np.max(np.abs(x - y)) <= 1e-13 * max(1.0, np.max(np.abs(y))), f
+    # and the diffusivity really matters at this size
+    c = oracle.OracleModel(_case(K1))
+    c.step(5)
+    assert np.max(np.abs(c.get("T") - a.get("T"))) > 1e-9
 
 
 def test_constant_tendency_correction_adds_dt_c_volume():

@@ -1,0 +1,114 @@
+"""The batched ensemble (GPU): every member of an ensemble step computes bit for bit what
+ocean_step computes for it alone, whatever launch shapes the autotuner picks, and the
+members follow the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2309_06662_gb300 import inputs, ocean
+from tests.parity import max_rel
+
+FIELDS = ("u", "v", "T_anom", "S_anom", "eta", "Gu_prev", "GT_prev")
+
+
+def _cases(count=7, seed=40):
+    # uneven sizes, including a member narrower than one tile and one region
+    return inputs.ensemble_cases(count, seed=seed, n_lo=20, n_hi=90, levels=(4, 8, 12))
+
+
+def _alone(cases, precision, steps):
+    """The same members stepped one by one with ocean_step (own handles)."""
+    out = []
+    for c in cases:
+        m = ocean.Ocean(c, precision=precision)
+        m.step(steps)
+        out.append({f: m.get(f) for f in FIELDS})
+        m.close()
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [ocean.OCEAN_MIXED, ocean.OCEAN_FP64])
+def test_ensemble_step_is_each_member_alone(precision):
+    cases = _cases()
+    E = ocean.Ensemble(cases, precision=precision)
+    E.step(6)                     # Euler start, then both graph parities
+    ref = _alone(cases, precision, 6)
+    for i, m in enumerate(E.members):
+        assert m.nstep == 6
+        for f in FIELDS:
+            assert np.array_equal(m.get(f), ref[i][f]), (i, f)
+    assert E.launches == 6 * (6 + 5)
+    E.close()
+
+
+@pytest.mark.gpu
+def test_autotuned_shapes_keep_results():
+    cases = _cases(seed=41)
+    E = ocean.Ensemble(cases)
+    n = E.autotune(reps=1)
+    assert n >= 7
+    shapes = E.launch_shapes()
+    for k, s in shapes.items():
+        assert 1 <= s["grid"] <= max(1, s["items"]), (k, s)
+    E.step(3)
+    ref = _alone(cases, ocean.OCEAN_MIXED, n + 3)
+    for i, m in enumerate(E.members):
+        for f in FIELDS:
+            assert np.array_equal(m.get(f), ref[i][f]), (i, f)
+    E.close()
+
+
+@pytest.mark.gpu
+def test_members_follow_the_oracle():
+    oracle = pytest.importorskip("oracle")
+    cases = _cases(count=3, seed=42)
+    E = ocean.Ensemble(cases, precision=ocean.OCEAN_FP64)
+    E.step(10)
+    for i, c in enumerate(cases):
+        o = oracle.OracleModel(c)
+        o.step(10)
+        for f in ("u", "v", "T", "S", "eta"):
+            assert max_rel(E.members[i].get(f), o.get(f)) <= 1e-10, (i, f)
+    E.close()
+
+
+@pytest.mark.gpu
+def test_a_member_stepped_alone_puts_the_ensemble_out_of_step():
+    cases = _cases(count=3, seed=43)
+    E = ocean.Ensemble(cases)
+    E.step(2)
+    E.members[1].step(1)
+    with pytest.raises(ocean.OceanError) as err:
+        E.step(1)
+    assert err.value.code == -6
+    E.members[0].step(1)
+    E.members[2].step(1)
+    E.step(1)
+    assert all(m.nstep == 4 for m in E.members)
+    E.close()
+
+
+@pytest.mark.gpu
+def test_member_diagnostics_and_checkpoint():
+    cases = _cases(count=3, seed=44)
+    E = ocean.Ensemble(cases)
+    d0 = [m.diagnostics() for m in E.members]
+    E.step(4)
+    for m, d in zip(E.members, d0):
+        d1 = m.diagnostics()
+        assert not d1["nonfinite"]
+        # closed basins: tracer and volume conserved to roundoff of the FP32 state
+        assert abs(d1["tracer_T"] - d["tracer_T"]) <= 1e-6 * abs(d["tracer_T"])
+    # restart every member of a fresh ensemble from checkpoints: the continuation is
+    # the same bit for bit
+    cks = [m.checkpoint() for m in E.members]
+    E.step(2)
+    E2 = ocean.Ensemble(cases)
+    for m, ck in zip(E2.members, cks):
+        m.restore(ck)
+    E2.step(2)
+    for a, b in zip(E.members, E2.members):
+        for f in FIELDS:
+            assert np.array_equal(a.get(f), b.get(f)), f
+    E.close()
+    E2.close()
