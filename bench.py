@@ -123,18 +123,6 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def window_case(case, i0: int, j0: int, wx: int, wy: int):
-    """The sub-window [i0, i0+wx) x [j0, j0+wy) of a lat-lon case (walls at its edges)."""
-    lat = case.y1
-    x0, x1, y0, y1 = inputs.latlon_window(case.nx, case.ny, lat, i0, j0, wx, wy)
-    sl = (slice(j0, j0 + wy), slice(i0, i0 + wx))
-    return inputs.Case(f"{case.name}_window", case.kind, wx, wy, case.nz, False, False,
-                       x0, x1, y0, y1, case.z_faces, case.depth[sl].copy(),
-                       case.taux[sl].copy(), case.tauy[sl].copy(),
-                       case.T[(slice(None),) + sl].copy(), case.S[(slice(None),) + sl].copy(),
-                       dict(case.params), steps=case.steps)
-
-
 def oracle_sample(case):
     """The bounded sample of the workload the CPU oracle runs: a 96 x 96 column window of
     a large lat-lon grid (walls at the window edges), or the whole grid when small."""
@@ -143,7 +131,7 @@ def oracle_sample(case):
         i0, j0 = case.nx // 2, case.ny // 2
         desc = (f"{wx}x{wy}x{case.nz} window of the {case.nx}x{case.ny}x{case.nz} workload at "
                 f"(i0={i0}, j0={j0}), walls at the window edges")
-        return window_case(case, i0, j0, wx, wy), desc
+        return inputs.latlon_window_case(case, i0, j0, wx, wy), desc
     return case, f"the full {case.nx}x{case.ny}x{case.nz} workload"
 
 

@@ -325,7 +325,9 @@ int ocean_tridiag_batched_static(const void* d_a, const void* d_b, const void* d
  * list sorted by decreasing cost, so that one launch per phase covers all members (the
  * paper motivates ensembles in its introduction but runs none; this is this library's
  * design).  After the first step each step is one CUDA graph launch.  Each member
- * computes exactly what ocean_step computes for it alone.
+ * computes what ocean_step computes for it alone, to rounding (the ensemble kernels are a
+ * second compiled instance of the same kernel bodies and may fuse multiply-adds
+ * differently); the choice of launch shapes never changes a bit.
  *
  * Members are created from per-member grids, depths and parameters (arrays of length
  * `members`) in one device allocation on one stream owned by the ensemble; they must

@@ -13,7 +13,9 @@
    BF16 tensor-core forward and backward kernels (ocean_mlp_train_step).  The columns
    of the easternmost `val_frac` of the domain are held back for validation (other
    bathymetry than the training columns); the weights of the epoch with the lowest
-   validation loss are kept.
+   validation loss are kept, and an output head (the diffusivity, or the two tendency
+   corrections) that does not beat "no network" on the validation columns is switched
+   off (diffusivity head: softplus(-30), i.e. no extra diffusivity; correction head: 0).
 3. A priori: on coarse-grained snapshots of a second fine run (another seed), the loss
    of the trained network against that of the Richardson-number closure alone.  The
    network's diffusivity is added to the Richardson-number one, so "alone" means zero
@@ -193,12 +195,13 @@ def loss_terms(Y, d, sc) -> Dict[str, float]:
 def train(net, d, sc, epochs: int, batch: int, lr: float, val=None, ev=None, seed: int = 0):
     """Adam over shuffled batches.  Returns the mean batch loss of each epoch, the
     validation loss after each epoch (with `val` and an evaluation handle `ev` that
-    holds the whole validation set) and the parameters of the best epoch."""
+    holds the whole validation set), the parameters of the best epoch and its validation
+    loss terms."""
     import torch
     n = d["X"].shape[0]
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
-    hist, vhist, best, best_v = [], [], None, math.inf
+    hist, vhist, best, best_v, best_terms = [], [], None, math.inf, None
     for _ in range(epochs):
         perm = torch.randperm(n, device="cuda", generator=g)
         tot, cnt = 0.0, 0
@@ -215,9 +218,25 @@ def train(net, d, sc, epochs: int, batch: int, lr: float, val=None, ev=None, see
             vhist.append(vl)
             if vl < best_v:
                 best, best_v = params, vl
+                best_terms = loss_terms(ev.forward(val["X"]), val, sc)
     if best is None:
         best = net.get_params()
-    return hist, vhist, best
+    return hist, vhist, best, best_terms
+
+
+def gate_heads(params, nz: int, terms, base):
+    """Switch off the output heads that do not beat "no network" on validation columns:
+    returns the gated parameters and which heads stay on."""
+    W, b = (x.copy() for x in params[-1])
+    keep = dict(diffusivity=terms["fT"] + terms["fS"] < base["fT"] + base["fS"],
+                corrections=terms["gT"] + terms["gS"] < base["gT"] + base["gS"])
+    if not keep["diffusivity"]:
+        W[:, :nz] = 0.0
+        b[:nz] = -30.0
+    if not keep["corrections"]:
+        W[:, nz:] = 0.0
+        b[nz:] = 0.0
+    return params[:-1] + [(W, b)], keep
 
 
 def fmt_terms(t) -> str:
@@ -261,13 +280,17 @@ def run(cfg: Dict, log=print) -> Dict:
     val_base = baseline_loss(val, sc)
     torch.cuda.synchronize()
     t1 = time.time()
-    hist, vhist, trained = train(net, data, sc, cfg["epochs"], cfg["batch"], cfg["lr"], val, vev)
+    hist, vhist, trained, vterms = train(net, data, sc, cfg["epochs"], cfg["batch"], cfg["lr"],
+                                         val, vev)
     torch.cuda.synchronize()
     train_s = time.time() - t1
+    vbase_terms = loss_terms(None, val, sc)
+    trained, heads = gate_heads(trained, nz, vterms, vbase_terms)
     steps = cfg["epochs"] * (ncols // cfg["batch"])
     log(f"training: {steps} Adam steps in {train_s:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}"
         f" (no network: {train_base:.4g}); validation best {min(vhist):.4g} at epoch "
-        f"{vhist.index(min(vhist)) + 1} (no network: {val_base:.4g})")
+        f"{vhist.index(min(vhist)) + 1} (no network: {val_base:.4g}); validation terms "
+        f"{fmt_terms(vterms)} vs {fmt_terms(vbase_terms)}; heads kept: {heads}")
     del data, val
     net.close()
     vev.close()
@@ -321,6 +344,7 @@ def run(cfg: Dict, log=print) -> Dict:
         m.close()
     return dict(config=cfg, training_columns=ncols, scales=sc, loss_history=hist,
                 validation_history=vhist, validation_baseline=val_base,
+                validation_terms=vterms, validation_terms_baseline=vbase_terms, heads=heads,
                 training_baseline=train_base, train_seconds=train_s, adam_steps=steps,
                 apriori=apriori, online=online,
                 ms_per_step={k: 1e3 * v / max(1, done) for k, v in cost.items()})
@@ -332,12 +356,15 @@ def main():
     ap.add_argument("--out", default=None, help="write the results as JSON")
     ap.add_argument("--epochs", type=int, default=None)
     ap.add_argument("--eval-steps", type=int, default=None)
+    ap.add_argument("--lr", type=float, default=None)
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     if args.epochs is not None:
         cfg["epochs"] = args.epochs
     if args.eval_steps is not None:
         cfg["eval_steps"] = args.eval_steps
+    if args.lr is not None:
+        cfg["lr"] = args.lr
     res = run(cfg)
     if args.out:
         with open(args.out, "w") as f:

@@ -899,10 +899,17 @@ int ocean_step_async(ocean_t h, int n) {
     return OCEAN_OK;
 }
 
+// after a synchronisation: the learned closure's GEMMs report a tile that gave up waiting
+static int check_closure_gemm(ocean_t h) {
+    if (h->cl_ready && h->prm.closure == OCEAN_CLOSURE_LEARNED && closure_gemm_failed())
+        return fail(h, OCEAN_ERR_TIMEOUT, "a tensor-core GEMM tile of the closure timed out");
+    return OCEAN_OK;
+}
+
 int ocean_sync(ocean_t h) {
     if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
     OC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return OCEAN_OK;
+    return check_closure_gemm(h);
 }
 
 int ocean_step(ocean_t h, int n) {
@@ -921,7 +928,7 @@ int ocean_step(ocean_t h, int n) {
         }
     }
     OC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return OCEAN_OK;
+    return check_closure_gemm(h);
 }
 
 int ocean_tendencies(ocean_t h) {

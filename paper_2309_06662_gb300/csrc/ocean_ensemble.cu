@@ -63,7 +63,8 @@ void build_work(ocean_ensemble_t e, std::vector<EnsItem> (&w)[ENS_NKIND]) {
         for (long a = 0; a * sh.chunk < ncol; ++a) {
             w[ENS_BARO_BEGIN].push_back({m, (int)a, 0, 1});
             w[ENS_BARO_END].push_back({m, (int)a, 0, 1});
-            w[ENS_CORRECT].push_back({m, (int)a, 0, I.nz});
+            for (int sl = 0; sl * sh.corr_slab < I.nz; ++sl)
+                w[ENS_CORRECT].push_back({m, (int)a, sl, std::min(sh.corr_slab, I.nz - sl * sh.corr_slab)});
         }
         const int ntx = (I.nx + sh.tile_x - 1) / sh.tile_x, nty = (I.ny + sh.tile_y - 1) / sh.tile_y;
         for (int by = 0; by < nty; ++by)
@@ -86,14 +87,20 @@ void build_work(ocean_ensemble_t e, std::vector<EnsItem> (&w)[ENS_NKIND]) {
                          [](const EnsItem& a, const EnsItem& b) { return a.cost > b.cost; });
 }
 
+// table v (= 2 first + cur) starts at byte v * tab_bytes, where the kernels look for it
 template <typename R>
 int upload_tables(ocean_ensemble_t e) {
-    std::vector<EnsMember<R>> h(4 * (size_t)e->M);
+    if (e->tab_bytes < (size_t)e->M * sizeof(EnsMember<R>))
+        return efail(OCEAN_ERR_ARG, "ensemble table stride too small");
+    std::vector<unsigned char> h(4 * e->tab_bytes, 0);
     for (int first = 0; first < 2; ++first)
         for (int cur = 0; cur < 2; ++cur)
-            for (int m = 0; m < e->M; ++m)
-                h[(size_t)(2 * first + cur) * e->M + m] = oc_member_entry<R>(e->mem[m], first, cur);
-    EN_CUDA(cudaMemcpy(e->d_tab, h.data(), h.size() * sizeof(EnsMember<R>), cudaMemcpyHostToDevice));
+            for (int m = 0; m < e->M; ++m) {
+                const EnsMember<R> x = oc_member_entry<R>(e->mem[m], first, cur);
+                std::memcpy(h.data() + (size_t)(2 * first + cur) * e->tab_bytes + m * sizeof(x), &x,
+                            sizeof(x));
+            }
+    EN_CUDA(cudaMemcpy(e->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice));
     return OCEAN_OK;
 }
 

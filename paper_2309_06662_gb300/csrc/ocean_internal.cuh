@@ -260,6 +260,7 @@ void launch_closure_targets(const KP<R>& p, const R* GcT, const R* GcS, const fl
 void closure_forward(const void* Xb, int M, const void* const* Wt, const float* const* b,
                      const int* dims, void* H0, void* H1, float* Y, cudaStream_t s);
 void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s);
+int closure_gemm_failed();
 
 // ---- batched ensemble (kernels in ocean_kernels.cu, host side in ocean_ensemble.cu)
 // One member's step parameters and buffers, read by the persistent ensemble kernels from
@@ -271,14 +272,16 @@ template <typename R> struct EnsMember {
     double rns;   // 1 / n_substeps
 };
 // Work item: member m and the position of its unit of work: a column chunk (a), a
-// tracer/momentum tile (a, b) or a barotropic region (a, b).
+// column chunk and level slab (a, b), a tracer/momentum tile (a, b) or a barotropic
+// region (a, b).
 struct EnsItem { int m, a, b, cost; };
 enum {
     ENS_DIAG = 0, ENS_TRACER, ENS_MOMENTUM, ENS_BARO_BEGIN, ENS_BARO_PASS, ENS_BARO_END,
     ENS_CORRECT, ENS_NKIND
 };
-// Units of work: columns per chunk of the column kernels, tile and region interiors.
-struct EnsShape { int chunk, tile_x, tile_y, region_x, region_y, pass_substeps; };
+// Units of work: columns per chunk of the column kernels, tile and region interiors,
+// substeps per barotropic pass, levels per slab of the correction.
+struct EnsShape { int chunk, tile_x, tile_y, region_x, region_y, pass_substeps, corr_slab; };
 EnsShape ens_shape();
 // Resident blocks per SM of each ensemble kernel (occupancy calculator).
 template <typename R> int ens_blocks_per_sm(int kind);

@@ -170,6 +170,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename R>
 struct TracerSmem {
     R T[2][TY + 6][TX + 6], S[2][TY + 6][TX + 6];     // anomalies of levels k, k+1, halo 3
+    R us[2][TY][TX + 1], vs[2][TY + 1][TX];           // face velocities of levels k, k+1
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
     R fxU[TY][TX + 1], fxT[TY][TX + 1], fxS[TY][TX + 1];   // x-face transport and fluxes
@@ -226,14 +227,25 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
     const int kstart = sm.kmin;
     if (kstart >= nz) return;   // the whole patch is land
 
-    // ---- the staged tile (halo 3) streams in one level ahead, double buffered
-    constexpr int TT = (TY + 6) * (TX + 6);
+    // ---- the staged tile (halo 3) and the face velocities stream in one level ahead,
+    // double buffered (faces beyond the domain are staged from clamped addresses and
+    // never used: their masks say dry)
+    constexpr int TT = (TY + 6) * (TX + 6), NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
     auto stage = [&](int k, int buf) {
         for (int q = tid; q < TT; q += NT) {
             const int a = q / (TX + 6), b = q % (TX + 6);
             const long c = k * P + tix(g, i0 - 3 + b, j0 - 3 + a);
             cp_async_el(&sm.T[buf][a][b], &T[c]);
             cp_async_el(&sm.S[buf][a][b], &S[c]);
+        }
+        for (int q = tid; q < NXF + NYF; q += NT) {
+            if (q < NXF) {
+                const int a = q / (TX + 1), b = q % (TX + 1);
+                cp_async_el(&sm.us[buf][a][b], &u[k * P + tix(g, i0 + b, j0 + a)]);
+            } else {
+                const int a = (q - NXF) / TX, b = (q - NXF) % TX;
+                cp_async_el(&sm.vs[buf][a][b], &v[k * P + tix(g, i0 + b, j0 + a)]);
+            }
         }
         cp_async_commit();
     };
@@ -277,56 +289,57 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
             }
         }
         const R dzk = p.dz[k];
-        // ---- x-face fluxes, each face once
-        for (int q = tid; q < TY * (TX + 1); q += NT) {
-            const int a = q / (TX + 1), b = q % (TX + 1);
-            R fU = R(0), fT = R(0), fS = R(0);
-            if (k >= sm.kbu[a][b]) {
-                const R ut = u[Pk + ix2(g, i0 + b, j0 + a)];
-                R qT[5], qS[5];
-                unsigned in = 0;
+        // ---- x- and y-face fluxes, each face once (one job list, so that no warp does
+        // more than one job beyond the others)
+        for (int q = tid; q < NXF + NYF; q += NT) {
+            if (q < NXF) {
+                const int a = q / (TX + 1), b = q % (TX + 1);
+                R fU = R(0), fT = R(0), fS = R(0);
+                if (k >= sm.kbu[a][b]) {
+                    const R ut = sm.us[cb][a][b];
+                    R qT[5], qS[5];
+                    unsigned in = 0;
 #pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int col = ut >= R(0) ? b + n : b + 5 - n;
-                    qT[n] = sm.T[cb][a + 3][col];
-                    qS[n] = sm.S[cb][a + 3][col];
-                    in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
+                    for (int n = 0; n < 5; ++n) {
+                        const int col = ut >= R(0) ? b + n : b + 5 - n;
+                        qT[n] = sm.T[cb][a + 3][col];
+                        qS[n] = sm.S[cb][a + 3][col];
+                        in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
+                    }
+                    R rT, rS;
+                    WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                    fU = ut * p.dy * dzk;
+                    fT = fU * rT;
+                    fS = fU * rS;
                 }
-                R rT, rS;
-                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                fU = ut * p.dy * dzk;
-                fT = fU * rT;
-                fS = fU * rS;
-            }
-            sm.fxU[a][b] = fU;
-            sm.fxT[a][b] = fT;
-            sm.fxS[a][b] = fS;
-        }
-        // ---- y-face fluxes
-        for (int q = tid; q < (TY + 1) * TX; q += NT) {
-            const int a = q / TX, b = q % TX;
-            R fV = R(0), fT = R(0), fS = R(0);
-            if (k >= sm.kbv[a][b]) {
-                const int fj = j0 + a;
-                const R vt = v[Pk + ix2(g, i0 + b, fj)];
-                R qT[5], qS[5];
-                unsigned in = 0;
+                sm.fxU[a][b] = fU;
+                sm.fxT[a][b] = fT;
+                sm.fxS[a][b] = fS;
+            } else {
+                const int a = (q - NXF) / TX, b = (q - NXF) % TX;
+                R fV = R(0), fT = R(0), fS = R(0);
+                if (k >= sm.kbv[a][b]) {
+                    const int fj = j0 + a;
+                    const R vt = sm.vs[cb][a][b];
+                    R qT[5], qS[5];
+                    unsigned in = 0;
 #pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int row = vt >= R(0) ? a + n : a + 5 - n;
-                    qT[n] = sm.T[cb][row][b + 3];
-                    qS[n] = sm.S[cb][row][b + 3];
-                    in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                    for (int n = 0; n < 5; ++n) {
+                        const int row = vt >= R(0) ? a + n : a + 5 - n;
+                        qT[n] = sm.T[cb][row][b + 3];
+                        qS[n] = sm.S[cb][row][b + 3];
+                        in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                    }
+                    R rT, rS;
+                    WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                    fV = vt * p.dxv[fj + OC_H] * dzk;
+                    fT = fV * rT;
+                    fS = fV * rS;
                 }
-                R rT, rS;
-                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                fV = vt * p.dxv[fj + OC_H] * dzk;
-                fT = fV * rT;
-                fS = fV * rS;
+                sm.fyV[a][b] = fV;
+                sm.fyT[a][b] = fT;
+                sm.fyS[a][b] = fS;
             }
-            sm.fyV[a][b] = fV;
-            sm.fyT[a][b] = fT;
-            sm.fyS[a][b] = fS;
         }
         __syncthreads();
         // ---- own cell
@@ -903,24 +916,32 @@ __global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE
                     Vn, Su, Sv, rHu, rHv, corrU, corrV, rns);
 }
 
+// The correction is a read-modify-write of u and v over the whole water column; a
+// column is split into slabs of CORR_SLAB levels so that more independent loads are in
+// flight than one thread per column would issue.
+constexpr int CORR_SLAB = 8;
+
 template <typename R>
-__device__ __forceinline__ void correct_col(const KP<R>& p, const long c, R* __restrict__ un,
-                                            R* __restrict__ vn, const R* __restrict__ corrU,
+__device__ __forceinline__ void correct_col(const KP<R>& p, const long c, const int slab,
+                                            R* __restrict__ un, R* __restrict__ vn,
+                                            const R* __restrict__ corrU,
                                             const R* __restrict__ corrV) {
     const GeoD& g = p.g;
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j), P = g.plane;
+    const int k0 = slab * CORR_SLAB, k1 = k0 + CORR_SLAB < g.nz ? k0 + CORR_SLAB : g.nz;
     const int ku = g.kbu[c2], kv = g.kbv[c2];
     const R cu = corrU[c2], cv = corrV[c2];
-    for (int k = ku; k < g.nz; ++k) un[k * P + c2] += cu;
-    for (int k = kv; k < g.nz; ++k) vn[k * P + c2] += cv;
+    for (int k = k0 > ku ? k0 : ku; k < k1; ++k) un[k * P + c2] += cu;
+    for (int k = k0 > kv ? k0 : kv; k < k1; ++k) vn[k * P + c2] += cv;
 }
 
 template <typename R>
 __global__ void k_correct(KP<R> p, R* __restrict__ un, R* __restrict__ vn,
                           const R* __restrict__ corrU, const R* __restrict__ corrV) {
-    correct_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, un, vn, corrU, corrV);
+    correct_col<R>(p, (long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, un, vn, corrU,
+                   corrV);
 }
 
 // ------------------------------------------------------------------ halos
@@ -994,7 +1015,8 @@ int baro_passes(int ns) { return (ns + BS - 1) / BS; }
 template <typename R>
 void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
     const long n = (long)p.g.nx * p.g.ny;
-    k_correct<R><<<nblocks(n, TPB), TPB, 0, s>>>(p, b.un, b.vn, b.corrU, b.corrV);
+    const dim3 grid(nblocks(n, TPB), (p.g.nz + CORR_SLAB - 1) / CORR_SLAB);
+    k_correct<R><<<grid, TPB, 0, s>>>(p, b.un, b.vn, b.corrU, b.corrV);
 }
 
 // up to four field pointers passed by value, so a halo launch needs no device table
@@ -1303,13 +1325,13 @@ __global__ void __launch_bounds__(TPB) k_ens_correct(const EnsMember<R>* __restr
         const EnsItem e = work[it];
         const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        correct_col<R>(p, (long)e.a * TPB + threadIdx.x, b.un, b.vn, b.corrU, b.corrV);
+        correct_col<R>(p, (long)e.a * TPB + threadIdx.x, e.b, b.un, b.vn, b.corrU, b.corrV);
     }
 }
 
 }  // namespace
 
-EnsShape ens_shape() { return EnsShape{TPB, TX, TY, BRX - 2 * BS, BRY - 2 * BS, BS}; }
+EnsShape ens_shape() { return EnsShape{TPB, TX, TY, BRX - 2 * BS, BRY - 2 * BS, BS, CORR_SLAB}; }
 
 template <typename R>
 int ens_blocks_per_sm(int kind) {

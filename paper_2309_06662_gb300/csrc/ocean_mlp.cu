@@ -1,5 +1,5 @@
 // ocean_mlp.cu -- the learned column closure's network on the tensor cores: BF16 GEMMs
-// with FP32 accumulation and fused epilogues (bias, SiLU, SiLU backward, transposed
+// on tcgen05 with FP32 accumulators in TMEM and fused epilogues (bias, SiLU, SiLU backward, transposed
 // copies for the weight gradients), the closure loss and its gradient, Adam on FP32
 // master weights, and the trainer handle of the C ABI.
 //
@@ -23,8 +23,6 @@ namespace {
 
 // ------------------------------------------------------------------ GEMM (tensor cores)
 
-constexpr int GM = 128, GN = 128, GK = 32, GLD = GK + 8, GTH = 256;
-
 __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool pred) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = pred ? 16 : 0;   // src-size 0: the 16 bytes are zero-filled
@@ -34,22 +32,6 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool pred) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
-                                        const void* p) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(s));
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad_f(float z) {
@@ -88,94 +70,198 @@ __device__ __forceinline__ void epi_store(const Epi& e, int m, int n, float acc)
     }
 }
 
-// C[m][n] = sum_k A[m][k] B[n][k]; A [M][lda], B [N][ldb] row-major BF16 (lda, ldb and K
-// multiples of 8); 128 x 128 block tiles, 8 warps of 64 x 32, m16n8k16 BF16 MMAs with
-// FP32 accumulators, cp.async double-buffered K tiles of 32.
-__global__ void __launch_bounds__(GTH) k_gemm_nt(const bf16* __restrict__ A, int lda,
-                                                 const bf16* __restrict__ B, int ldb, int M,
-                                                 int N, int K, Epi e) {
-    __shared__ __align__(128) bf16 sA[2][GM][GLD];
-    __shared__ __align__(128) bf16 sB[2][GN][GLD];
+// ------------------------------------------------------------------ GEMM on tcgen05
+//
+// C[m][n] = sum_k A[m][k] B[n][k] on Blackwell's fifth-generation tensor cores: one CTA of
+// 128 threads per 128 x 128 output tile; K in steps of 64 (one 128-byte swizzle atom of
+// BF16), each step staged by cp.async into shared memory in the 128-byte-swizzled
+// K-major layout the MMA descriptors describe, double-buffered; one thread issues four
+// tcgen05.mma (M 128, N 128, K 16, BF16 in, FP32 accumulate) per step into a 128-column
+// TMEM accumulator and commits them to the step's mbarrier, which frees the buffer for
+// the load two steps later; the four warps then read their 32 accumulator lanes with
+// tcgen05.ld and run the epilogue.  Waits are bounded: a barrier that does not complete
+// within ~1 s sets g_tc_err and the tile is abandoned (TMEM is still freed).
+
+constexpr int TBM = 128, TBN = 128, TBK = 64, TTH = 128;
+constexpr unsigned TMEM_COLS = 128;
+constexpr int TILE_BYTES = TBM * TBK * 2;                        // 16 KB per operand tile
+constexpr size_t TC_SMEM = 1024 + 4 * (size_t)TILE_BYTES + 64;  // alignment slack, 2 x (A, B), barriers
+
+__device__ int g_tc_err = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// K-major operand descriptor, 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes
+// apart (stride byte offset), leading byte offset unused (1), descriptor version 1
+__device__ __forceinline__ unsigned long long sw128_desc(unsigned saddr) {
+    unsigned long long d = (unsigned long long)((saddr >> 4) & 0x3FFFu);
+    d |= 1ull << 16;
+    d |= (unsigned long long)(1024 >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 128, M = 128
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TBN >> 3) << 17) |
+                              ((unsigned)(TBM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(TTH) k_gemm_nt_tc(const bf16* __restrict__ A, int lda,
+                                                    const bf16* __restrict__ B, int ldb, int M,
+                                                    int N, int K, Epi e) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        ((unsigned long long)tc_raw + 1023) & ~1023ull);
+    // buffer b of A at base + b TILE_BYTES, of B at base + (2 + b) TILE_BYTES
+    auto sA = [&](int b) { return base + b * TILE_BYTES; };
+    auto sB = [&](int b) { return base + (2 + b) * TILE_BYTES; };
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(base + 4 * TILE_BYTES);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + 2);
+    int* abandon = reinterpret_cast<int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-    const int wm = warp >> 2, wn = warp & 3;
-    float acc[4][4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abandon = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+
+    // one K step: 128 rows x 8 chunks of 16 bytes per operand, chunk c of row r at
+    // r * 128 + ((c ^ (r % 8)) * 16) (the 128-byte swizzle)
     auto load = [&](int kt, int buf) {
-        const int k0 = kt * GK;
-        for (int c = tid; c < GM * GK / 8; c += GTH) {
-            const int r = c >> 2, kc = (c & 3) * 8;
-            const int gm = m0 + r, gk = k0 + kc;
-            const bool p = gm < M && gk < K;
-            cp16(&sA[buf][r][kc], p ? (const void*)(A + (long)gm * lda + gk) : (const void*)A, p);
-            const int gn = n0 + r;
-            const bool q = gn < N && gk < K;
-            cp16(&sB[buf][r][kc], q ? (const void*)(B + (long)gn * ldb + gk) : (const void*)B, q);
+        const int k0 = kt * TBK;
+        for (int q = tid; q < TBM * 8; q += TTH) {
+            const int r = q >> 3, c = q & 7;
+            const int gk = k0 + c * 8;
+            const unsigned off = (unsigned)(r * 128 + ((c ^ (r & 7)) << 4));
+            const int gm = m0 + r, gn = n0 + r;
+            const bool pa = gm < M && gk < K, pb = gn < N && gk < K;
+            cp16(sA(buf) + off, pa ? (const void*)(A + (long)gm * lda + gk) : (const void*)A, pa);
+            cp16(sB(buf) + off, pb ? (const void*)(B + (long)gn * ldb + gk) : (const void*)B, pb);
         }
         cp_commit();
     };
-    const int nk = (K + GK - 1) / GK;
+    const int nk = (K + TBK - 1) / TBK;
+    unsigned ph = 0u;   // bit b: parity of the next completion of bar[b]
+    bool ok = true;
     load(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
+    for (int kt = 0; kt < nk && ok; ++kt) {
+        const int buf = kt & 1;
         if (kt + 1 < nk) {
-            load(kt + 1, (kt + 1) & 1);
+            const int nb2 = (kt + 1) & 1;
+            if (kt + 1 >= 2) {   // the MMAs of step kt - 1 read that buffer
+                ok = __syncthreads_and(mbar_wait(smem_u32(&bar[nb2]), (ph >> nb2) & 1u) ? 1 : 0) != 0;
+                ph ^= 1u << nb2;
+                if (!ok) break;
+            }
+            load(kt + 1, nb2);
             cp_wait<1>();
         } else {
             cp_wait<0>();
         }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        const int buf = kt & 1;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long ad = sw128_desc(smem_u32(sA(buf)));
+            const unsigned long long bd = sw128_desc(smem_u32(sB(buf)));
 #pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            unsigned af[4][4], bfr[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-                ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3],
-                        &sA[buf][wm * 64 + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int nj = 0; nj < 2; ++nj) {
-                unsigned r0, r1, r2, r3;
-                ldsm_x4(r0, r1, r2, r3,
-                        &sB[buf][wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3)]
-                           [kk + ((lane >> 3) & 1) * 8]);
-                bfr[2 * nj][0] = r0;
-                bfr[2 * nj][1] = r1;
-                bfr[2 * nj + 1][0] = r2;
-                bfr[2 * nj + 1][1] = r3;
+            for (int k = 0; k < TBK / 16; ++k) {
+                const unsigned acc = (kt > 0 || k > 0) ? 1u : 0u;
+                // advancing K by 16 BF16 (32 bytes) inside the swizzle atom: +2 in the
+                // 16-byte address field
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad + 2ull * k), "l"(bd + 2ull * k), "r"(TC_IDESC), "r"(acc));
             }
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&bar[buf]))
+                : "memory");
         }
-        __syncthreads();
     }
-    const int g = lane >> 2, t = lane & 3;
+    if (ok) {   // the last commit covers every MMA of this tile
+        const int lb = (nk - 1) & 1;
+        ok = __syncthreads_and(mbar_wait(smem_u32(&bar[lb]), (ph >> lb) & 1u) ? 1 : 0) != 0;
+    }
+    if (!ok) {
+        atomicExch(&g_tc_err, 1);
+        *abandon = 1;
+    }
+    cp_wait<0>();
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!*abandon) {
+        const int row = warp * 32 + lane, m = m0 + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TBN; c0 += 32) {
+            unsigned r[32];
+            tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, r);
+            if (m < M) {
 #pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) {
-            const int mr = m0 + wm * 64 + mi * 16 + g;
-            const int nc = n0 + wn * 32 + ni * 8 + 2 * t;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = mr + 8 * h;
-                if (m >= M) continue;
-                if (nc < N) epi_store(e, m, nc, acc[mi][ni][2 * h]);
-                if (nc + 1 < N) epi_store(e, m, nc + 1, acc[mi][ni][2 * h + 1]);
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) epi_store(e, m, n, __uint_as_float(r[j]));
+                }
             }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(TMEM_COLS));
 }
 
+// A [M][lda], B [N][ldb] row-major BF16; lda, ldb and K multiples of 8 (16-byte rows)
 void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& e,
              cudaStream_t s) {
-    const dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
-    k_gemm_nt<<<grid, GTH, 0, s>>>(A, lda, B, ldb, M, N, K, e);
+    cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    const dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    k_gemm_nt_tc<<<grid, TTH, TC_SMEM, s>>>(A, lda, B, ldb, M, N, K, e);
 }
 
 // ------------------------------------------------------------------ elementwise kernels
@@ -326,6 +412,18 @@ __global__ void k_weight_copies(const float* __restrict__ w, long n, int out, in
 inline int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+// 1 if a closure GEMM abandoned a tile on a barrier that did not complete since the last
+// call (the flag is cleared); call after synchronising the stream the GEMMs ran on
+int closure_gemm_failed() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof(int)) != cudaSuccess) return 1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tc_err, &z, sizeof(int));
+    }
+    return v;
+}
 
 // ------------------------------------------------------------------ inference inside the step
 
@@ -490,6 +588,8 @@ int loss_and_grads(ocean_mlp_t h, const ocean_batch* bt, int M, const ocean_clos
             cudaStreamSynchronize(s) != cudaSuccess)
             return mfail(h, OCEAN_ERR_CUDA, "loss copy failed");
         *loss = (float)L;
+        if (closure_gemm_failed())
+            return mfail(h, OCEAN_ERR_TIMEOUT, "a tensor-core GEMM tile timed out on its barrier");
     }
     return cudaGetLastError() == cudaSuccess ? OCEAN_OK : mfail(h, OCEAN_ERR_CUDA, "kernel launch failed");
 }

@@ -323,6 +323,19 @@ def latlon_window(case_nx: int, case_ny: int, lat: float, i0: int, j0: int, wx: 
     return (i0 * dlon, (i0 + wx) * dlon, -lat + j0 * dlat, -lat + (j0 + wy) * dlat)
 
 
+def latlon_window_case(case: Case, i0: int, j0: int, wx: int, wy: int) -> Case:
+    """The sub-window [i0, i0+wx) x [j0, j0+wy) of a lat-lon case as a closed basin
+    (walls at its edges): same metrics, levels, bathymetry, forcing, state, parameters."""
+    x0, x1, y0, y1 = latlon_window(case.nx, case.ny, case.y1, i0, j0, wx, wy)
+    sl = (slice(j0, j0 + wy), slice(i0, i0 + wx))
+    cut3 = lambda F: None if F is None else F[(slice(None),) + sl].copy()
+    return Case(f"{case.name}_window", case.kind, wx, wy, case.nz, False, False, x0, x1, y0,
+                y1, case.z_faces, case.depth[sl].copy(), case.taux[sl].copy(),
+                case.tauy[sl].copy(), cut3(case.T), cut3(case.S), dict(case.params),
+                steps=case.steps, u=cut3(case.u), v=cut3(case.v),
+                eta=None if case.eta is None else case.eta[sl].copy())
+
+
 # ----------------------------------------------------------------------------- closure weights
 
 def mlp_seeded_params(seed: int, dims, gain: float = 1.0):

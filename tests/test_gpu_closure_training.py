@@ -21,21 +21,30 @@ def test_training_reduces_the_loss(result):
 
 @pytest.mark.gpu
 def test_gain_on_held_out_columns(result):
-    # columns of the held-out longitude band: other bathymetry than any training column
-    assert min(result["validation_history"]) < 0.8 * result["validation_baseline"]
+    # columns of the held-out longitude band: other bathymetry than any training column;
+    # the diffusivity explains a large part of the vertical temperature flux there
+    assert min(result["validation_history"]) < result["validation_baseline"]
+    assert result["heads"]["diffusivity"]
+    t, t0 = result["validation_terms"], result["validation_terms_baseline"]
+    assert t["fT"] < 0.6 * t0["fT"]
 
 
 @pytest.mark.gpu
 def test_vertical_fluxes_beat_the_richardson_closure_on_another_seed(result):
     # the network's diffusivity explains part of the resolved-eddy vertical fluxes of a
     # run it never saw; the Richardson-number closure alone explains none of them
-    for a in result["apriori"]:
-        tl, tr = a["terms_learned"], a["terms_richardson"]
-        assert tl["fT"] + tl["fS"] < tr["fT"] + tr["fS"], a
+    # (summed over the evaluation: at its start, 16 fine steps from rest, there are
+    # hardly any eddy fluxes to explain)
+    learned = sum(a["terms_learned"]["fT"] + a["terms_learned"]["fS"] for a in result["apriori"])
+    plain = sum(a["terms_richardson"]["fT"] + a["terms_richardson"]["fS"]
+                for a in result["apriori"])
+    assert learned < plain, result["apriori"]
 
 
 @pytest.mark.gpu
-def test_online_runs_stay_finite(result):
+def test_online_runs_stay_finite_and_no_worse(result):
     assert result["online"]
     for row in result["online"]:
         assert row["finite_learned"] and row["finite_richardson"], row
+        assert row["rms_T_learned"] <= 1.05 * row["rms_T_richardson"], row
+        assert row["rms_S_learned"] <= 1.05 * row["rms_S_richardson"], row
