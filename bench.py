@@ -5,7 +5,9 @@ Workload (default): the 1/12-degree lat-lon configuration, 4320 x 1680 x 48 cell
 (70S-70N), dt = 180 s, 60 barotropic substeps, in the mixed-precision form (FP32 fields
 and stencils; FP64 free surface, barotropic averages and conservation sums).
 `--workload ensemble96` times the batched ensemble instead: 96 closed basins of seeded
-uneven sizes (32-512 x 32-512 x 8-48), stepped together.  Inputs are
+uneven sizes (32-512 x 32-512 x 8-48), stepped together.  `--workload learned_half` times
+the 1/2-degree step with the learned column closure (network 288-256-256-256-144 on every
+column, seeded weights) and the closure's BF16 tensor-core GEMM chain.  Inputs are
 seeded and synthetic: random-field bathymetry and stratified T/S with noise stand in for
 the ECCO2-forced realistic domain of the paper (Sec. "How performance was measured").
 
@@ -42,6 +44,7 @@ WORKLOADS = {
     "latlon_1deg": (inputs.latlon_1deg_case, "latlon_1deg_360x160x32"),
     "box": (inputs.box_case, "box_32x32x8"),
     "ensemble96": (lambda: inputs.ensemble_cases(96, seed=5), "ensemble_96_basins"),
+    "learned_half": (inputs.latlon_half_case, "latlon_1/2deg_720x320x48_learned_closure"),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -53,6 +56,17 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_tensor_peak():
+    """Dense BF16 tensor peak (TFLOP/s): the measured burst figure, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured bf16_tflops (burst)"
+    return 1900.0, "fallback 1.9 PFLOP/s bf16"
 
 
 def source_digest() -> str:
@@ -216,6 +230,106 @@ def config_block(case, wname, precision):
             "l2": "inputs larger than L2 (every 3-D field > 1 GB)"}
 
 
+def learned_main(args, case, wname, rank, world, local, dist):
+    """The 1/2-degree step with the learned closure in the loop (seeded network, feature
+    statistics of the initial state), against the same step with the Richardson-number
+    closure alone; the closure network's GEMM chain timed on all columns."""
+    import torch
+    from paper_2309_06662_gb300 import ocean
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    nz, H = case.nz, 256
+    dims = [6 * nz, H, H, H, 3 * nz]
+    params = inputs.mlp_seeded_params(11, dims, gain=0.5)
+    sc = dict(kappa=1e-4, gT=1e-10, gS=1e-11, sFT=1.0, sFS=1.0, sGT=1.0, sGS=1.0)
+    cells = case.nx * case.ny * case.nz
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, closure in (("learned", ocean.OCEAN_CLOSURE_LEARNED), ("richardson", ocean.OCEAN_CLOSURE_RI)):
+        m = ocean.Ocean(case, precision=ocean.OCEAN_MIXED, closure=closure,
+                        closure_hidden=H if closure == ocean.OCEAN_CLOSURE_LEARNED else 0)
+        if closure == ocean.OCEAN_CLOSURE_LEARNED:
+            raw = m.closure_features(np.zeros(6 * nz), np.ones(6 * nz))
+            X = raw["X"].double()
+            mu = X.mean(0).cpu().numpy()
+            sd = X.std(0).clamp(min=1e-30).cpu().numpy()
+            m.set_closure(params, mu, sd, sc)
+        m.step_async(args.warmup)
+        m.sync()
+        barrier()
+        l0 = m.launches
+        with ClockSampler(local) as clk:
+            barrier()
+            ev0.record()
+            m.step_async(args.steps)
+            ev1.record()
+            barrier()
+        res[name] = dict(ms=ev0.elapsed_time(ev1) / args.steps, launches=m.launches - l0,
+                         clocks=clk.summary(), healthy=not m.diagnostics()["nonfinite"])
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    # the network's GEMM chain over all columns: 4 tcgen05 GEMMs (+ the BF16 conversion)
+    M = case.nx * case.ny
+    net = ocean.MLP(nz, H, M + (-M) % 8, params)
+    Xc = torch.randn(M, 6 * nz, device="cuda")
+    for _ in range(3):
+        net.forward(Xc)
+    barrier()
+    reps = 20
+    ev0.record()
+    for _ in range(reps):
+        net.forward(Xc)
+    ev1.record()
+    barrier()
+    ms_net = ev0.elapsed_time(ev1) / reps
+    net.close()
+    flops = 2.0 * M * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    peak, src = measured_tensor_peak()
+    achieved = flops / (ms_net / 1e3) / 1e12
+    ms = res["learned"]["ms"]
+    p = case.params
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_sample(case, args.cpu_seconds)
+        cpu.pop("s_per_step", None)
+        cpu["sample"] += " (Richardson-number closure: the oracle of the learned step is numpy, see oracle/closure.py)"
+    if rank == 0:
+        line = {
+            "metric": "cell_updates_per_s", "value": cells / (ms / 1e3) * world,
+            "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic (seeded random-field bathymetry, stratified T/S; seeded network weights)",
+            "config": {"workload": wname, "nx": case.nx, "ny": case.ny, "nz": case.nz,
+                       "cells": cells, "dt_s": p["dt"], "n_substeps": int(p["n_substeps"]),
+                       "precision": "mixed + BF16 closure network", "network": dims,
+                       "parallelism": "replicas (one full model per GPU)",
+                       "l2": "inputs larger than L2"},
+            "sypd": metrics.sypd(p["dt"], ms / 1e3),
+            "richardson_only": {"ms_per_step": res["richardson"]["ms"],
+                                "closure_overhead_ms": ms - res["richardson"]["ms"]},
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_nt_tc (4-GEMM chain)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "algorithmic_flops_per_chain": flops, "ms_per_chain": ms_net,
+                         "peak_source": src},
+            "e2e": None,
+            "gpu_launches": res["learned"]["launches"],
+            "clocks": res["learned"]["clocks"],
+            "healthy": res["learned"]["healthy"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def ensemble_main(args, cases, wname, rank, world, local, dist):
     """The batched ensemble: all members advanced by one graph launch per step, against
     the same members stepped one after another with ocean_step."""
@@ -344,6 +458,9 @@ def main():
     from paper_2309_06662_gb300 import ocean
 
     torch.cuda.set_device(local)
+    # a stream of our own: the library captures each step as a CUDA graph, which the
+    # legacy default stream does not allow
+    torch.cuda.set_stream(torch.cuda.Stream())
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -352,6 +469,9 @@ def main():
     make, wname = WORKLOADS[args.workload]
     if args.workload == "ensemble96":
         ensemble_main(args, make(), wname, rank, world, local, dist)
+        return
+    if args.workload == "learned_half":
+        learned_main(args, make(), wname, rank, world, local, dist)
         return
     case = make()
     p = case.params
@@ -371,16 +491,20 @@ def main():
     launches0 = m.launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        m.profile(True)
         barrier()
         ev0.record()
         m.step_async(args.steps)
         ev1.record()
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
+    launches = m.launches - launches0
+    # per-phase device times from the library's own events, on extra steps launched
+    # without the step graph (the events sit between the phases)
+    m.profile(True)
+    m.step_async(min(args.steps, 5))
+    m.sync()
     phases, nprof = m.phase_times()
     m.profile(False)
-    launches = m.launches - launches0
     ms_all = ms
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)

@@ -90,6 +90,10 @@ struct ocean_s {
     int cur = 0;
     long nstep = 0;
     bool tend_valid = false;
+    // the step as a CUDA graph, per buffer parity and with / without the learned closure
+    // (captured on first use; dropped when a launch argument changes)
+    cudaGraphExec_t graph[2][2] = {};
+    bool graphs_off = false;   // the stream cannot be captured (the legacy default stream)
     std::string err;
 };
 
@@ -505,23 +509,35 @@ bool enqueue_closure(ocean_t m, const KP<R>& k, StepBuffers<R>& b) {
                             reinterpret_cast<R*>(m->cl_dGT), reinterpret_cast<R*>(m->cl_dGS), s);
     b.dGT = reinterpret_cast<const R*>(m->cl_dGT);
     b.dGS = reinterpret_cast<const R*>(m->cl_dGS);
-    m->launches += 6;
     return true;
 }
 
+bool closure_on(const ocean_t m) { return m->cl_ready && m->prm.closure == OCEAN_CLOSURE_LEARNED; }
+
+// kernels one step enqueues, the learned closure's six included
+long step_launches(const ocean_t m) { return launches_per_step(m) + (closure_on(m) ? 6 : 0); }
+
+void drop_graphs(ocean_t m) {
+    for (auto& row : m->graph)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
+// the kernels of one step from buffer m->cur (with profiling events when `ev`)
 template <typename R>
-void enqueue_step(ocean_t m) {
-    const bool first = m->nstep == 0;
+void launch_step(ocean_t m, bool first, std::vector<cudaEvent_t>* ev) {
     const KP<R> k = make_kp<R>(m, first);
     StepBuffers<R> b = make_bufs<R>(m);
     cudaStream_t s = m->stream;
-    std::vector<cudaEvent_t> ev;
     auto mark = [&]() {
-        if (!m->prof) return;
+        if (!ev) return;
         cudaEvent_t e;
         cudaEventCreate(&e);
         cudaEventRecord(e, s);
-        ev.push_back(e);
+        ev->push_back(e);
     };
     mark();
     launch_diag<R>(k, b, s);
@@ -539,11 +555,47 @@ void enqueue_step(ocean_t m) {
         launch_halo3<R>(k.g, f, 4, s);
     }
     mark();
-    if (m->prof) m->prof_pending.push_back(ev);
-    m->launches += launches_per_step(m);
+}
+
+// One step: direct launches for the first (Euler) step and while profiling, else the
+// step's CUDA graph for this buffer parity (captured on first use).
+template <typename R>
+int enqueue_step(ocean_t m) {
+    const bool first = m->nstep == 0;
+    if (first || m->prof || m->graphs_off) {
+        std::vector<cudaEvent_t> ev;
+        launch_step<R>(m, first, m->prof ? &ev : nullptr);
+        if (m->prof) m->prof_pending.push_back(ev);
+    } else {
+        cudaGraphExec_t& g = m->graph[m->cur][closure_on(m) ? 1 : 0];
+        if (!g) {
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                (void)cudaGetLastError();   // not capturable: launch directly from now on
+                m->graphs_off = true;
+                launch_step<R>(m, false, nullptr);
+            } else {
+                launch_step<R>(m, false, nullptr);
+                cudaError_t e = cudaStreamEndCapture(m->stream, &gr);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&g, gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+                if (e != cudaSuccess) {
+                    g = nullptr;
+                    return fail(m, OCEAN_ERR_CUDA, "step graph capture failed: %s", cudaGetErrorString(e));
+                }
+            }
+        }
+        if (g) {
+            cudaError_t e = cudaGraphLaunch(g, m->stream);
+            if (e != cudaSuccess)
+                return fail(m, OCEAN_ERR_CUDA, "cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+        }
+    }
+    m->launches += step_launches(m);
     m->cur = 1 - m->cur;
     m->nstep += 1;
     m->tend_valid = false;
+    return OCEAN_OK;
 }
 
 template <typename R>
@@ -551,7 +603,7 @@ void enqueue_tendencies(ocean_t m) {
     const KP<R> k = make_kp<R>(m, m->nstep == 0);
     StepBuffers<R> b = make_bufs<R>(m);
     launch_diag<R>(k, b, m->stream);
-    enqueue_closure<R>(m, k, b);
+    if (enqueue_closure<R>(m, k, b)) m->launches += 6;
     launch_tracer<R>(k, b, false, m->stream);
     launch_momentum<R>(k, b, false, m->stream);
     m->tend_valid = true;
@@ -780,6 +832,7 @@ int ocean_create_in(const ocean_grid* grid, const double* depth, const ocean_par
 void ocean_destroy(ocean_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     for (auto& ev : h->prof_pending)
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (h->own_arena && h->arena) cudaFree(h->arena);
@@ -892,8 +945,8 @@ int ocean_step_async(ocean_t h, int n) {
     if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
     if (n < 0) return fail(h, OCEAN_ERR_ARG, "n must be >= 0");
     for (int q = 0; q < n; ++q) {
-        if (h->prec == OCEAN_FP64) enqueue_step<double>(h);
-        else enqueue_step<float>(h);
+        const int rc = h->prec == OCEAN_FP64 ? enqueue_step<double>(h) : enqueue_step<float>(h);
+        if (rc) return rc;
     }
     OC_CUDA(h, cudaGetLastError());
     return OCEAN_OK;
@@ -966,6 +1019,8 @@ int ocean_set_closure(ocean_t h, const float* params, size_t count, const float*
     if (count != ocean_mlp_param_count(h->nz, h->cl_hidden))
         return fail(h, OCEAN_ERR_ARG, "closure parameter count %zu, expected %zu", count,
                     ocean_mlp_param_count(h->nz, h->cl_hidden));
+    if (closure_gemm_setup() != (int)cudaSuccess)
+        return fail(h, OCEAN_ERR_CUDA, "GEMM shared-memory attribute could not be set");
     const float* p = params;
     for (int l = 0; l < 4; ++l) {
         const int in = h->cl_dims[l], out = h->cl_dims[l + 1];
@@ -981,6 +1036,7 @@ int ocean_set_closure(ocean_t h, const float* params, size_t count, const float*
     OC_CUDA(h, cudaStreamSynchronize(h->stream));
     h->cl_sc = *sc;
     h->cl_ready = true;
+    drop_graphs(h);   // the closure's scales are launch arguments
     h->tend_valid = false;
     return OCEAN_OK;
 }

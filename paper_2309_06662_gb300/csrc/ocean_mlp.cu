@@ -136,6 +136,64 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// Epilogue of 32 consecutive columns n0 .. n0+31 of row m held by one thread: the row-major
+// outputs go out as 16-byte vectors when the whole run is inside the matrix (the leading
+// dimensions are multiples of 8, so the vectors are aligned); the transposed copy is
+// written element by element (the lanes of a warp hold consecutive rows, so those
+// stores coalesce across the warp).
+__device__ __forceinline__ void epi_run32(const Epi& e, int m, int n0, int N, const unsigned* r) {
+    if (n0 + 32 > N) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (n0 + j < N) epi_store(e, m, n0 + j, __uint_as_float(r[j]));
+        return;
+    }
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    if (e.mode == EPI_SILU_BWD) {
+        const float4* z4 = reinterpret_cast<const float4*>(e.Zin + (long)m * e.ldZ + n0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 z = z4[q];
+            v[4 * q] *= silu_grad_f(z.x);
+            v[4 * q + 1] *= silu_grad_f(z.y);
+            v[4 * q + 2] *= silu_grad_f(z.z);
+            v[4 * q + 3] *= silu_grad_f(z.w);
+        }
+    } else if (e.bias) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += e.bias[n0 + j];
+    }
+    if (e.mode == EPI_F32 || (e.mode == EPI_SILU && e.outF)) {
+        float4* o4 = reinterpret_cast<float4*>(e.outF + (long)m * e.ldF + n0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    if (e.mode == EPI_F32) return;
+    if (e.mode == EPI_SILU) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+    }
+    unsigned pk[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+    }
+    uint4* b4 = reinterpret_cast<uint4*>(e.outB + (long)m * e.ldB + n0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    if (e.outT) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const unsigned w = pk[j >> 1];
+            const unsigned short h = (j & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xFFFFu);
+            reinterpret_cast<unsigned short*>(e.outT)[(long)(n0 + j) * e.ldT + m] = h;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TTH) k_gemm_nt_tc(const bf16* __restrict__ A, int lda,
                                                     const bf16* __restrict__ B, int ldb, int M,
                                                     int N, int K, Epi e) {
@@ -240,13 +298,7 @@ __global__ void __launch_bounds__(TTH) k_gemm_nt_tc(const bf16* __restrict__ A, 
         for (int c0 = 0; c0 < TBN; c0 += 32) {
             unsigned r[32];
             tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, r);
-            if (m < M) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n < N) epi_store(e, m, n, __uint_as_float(r[j]));
-                }
-            }
+            if (m < M) epi_run32(e, m, n0 + c0, N, r);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -259,7 +311,6 @@ __global__ void __launch_bounds__(TTH) k_gemm_nt_tc(const bf16* __restrict__ A, 
 // A [M][lda], B [N][ldb] row-major BF16; lda, ldb and K multiples of 8 (16-byte rows)
 void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& e,
              cudaStream_t s) {
-    cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     const dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
     k_gemm_nt_tc<<<grid, TTH, TC_SMEM, s>>>(A, lda, B, ldb, M, N, K, e);
 }
@@ -412,6 +463,13 @@ __global__ void k_weight_copies(const float* __restrict__ w, long n, int out, in
 inline int nb(long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+// the GEMM's shared memory (above the default 48 KB); called before the first launch on a
+// device and outside stream capture
+int closure_gemm_setup() {
+    return (int)cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TC_SMEM);
+}
 
 // 1 if a closure GEMM abandoned a tile on a barrier that did not complete since the last
 // call (the flag is cleared); call after synchronising the stream the GEMMs ran on
@@ -620,6 +678,10 @@ int ocean_mlp_create(int nz, int hidden, int max_batch, const float* params, voi
     h->hidden = hidden;
     h->max_batch = max_batch;
     h->stream = (cudaStream_t)stream;
+    if (closure_gemm_setup() != (int)cudaSuccess) {
+        delete h;
+        return mfail(nullptr, OCEAN_ERR_CUDA, "GEMM shared-memory attribute could not be set");
+    }
     const int d[5] = {6 * nz, hidden, hidden, hidden, 3 * nz};
     memcpy(h->dims, d, sizeof d);
     bool ok = true;

@@ -304,8 +304,9 @@ def latlon_quarter_case(seed: int = 6) -> Case:
 
 
 def latlon_half_case(seed: int = 4, lat: float = 80.0) -> Case:
-    """1/2-degree, 720 x 320 x 48, 80S-80N, dt = 900 s, 60 substeps."""
-    return latlon_case(720, 320, 48, lat, seed, 900.0, 60, 2000, "latlon_half")
+    """1/2-degree, 720 x 320 x 48, 80S-80N, dt = 480 s (the step of the coarse model of the
+    closure experiments), 60 substeps, 2000 steps."""
+    return latlon_case(720, 320, 48, lat, seed, 480.0, 60, 2000, "latlon_half")
 
 
 def latlon_small_case(nx: int = 72, ny: int = 40, nz: int = 12, seed: int = 7,

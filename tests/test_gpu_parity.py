@@ -201,3 +201,21 @@ def test_latlon_1deg_fp64_10_steps():
     g, o = run_pair(c, ocean.OCEAN_FP64, 10)
     errs = state_errors(g, o)
     assert all(e <= FP64_TOL for e in errs.values()), errs
+
+
+@pytest.mark.gpu
+def test_graph_replayed_step_is_bitwise_the_direct_step():
+    # on a side stream the step after the Euler start is a CUDA graph per buffer parity;
+    # on the legacy default stream (not capturable) every kernel is launched directly
+    import torch
+    c = _moving_state(inputs.latlon_small_case(seed=21))
+    a = ocean.Ocean(c, precision=ocean.OCEAN_MIXED)
+    a.step(7)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        b = ocean.Ocean(c, precision=ocean.OCEAN_MIXED)
+        b.step(7)
+        launches = b.launches
+    assert launches == a.launches
+    for f in ("u", "v", "T_anom", "S_anom", "eta", "Gu_prev", "GT_prev"):
+        assert np.array_equal(a.get(f), b.get(f)), f
