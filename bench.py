@@ -58,6 +58,18 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest value of x over the ranks of the process group (x itself without one);
+    the tensor lives where the group's backend communicates (CUDA for NCCL, host for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_tensor_peak():
     """Dense BF16 tensor peak (TFLOP/s): the measured burst figure, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -291,7 +303,7 @@ def learned_main(args, case, wname, rank, world, local, dist):
     flops = 2.0 * M * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
     peak, src = measured_tensor_peak()
     achieved = flops / (ms_net / 1e3) / 1e12
-    ms = res["learned"]["ms"]
+    ms = max_over_ranks(res["learned"]["ms"], dist)
     p = case.params
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -366,11 +378,7 @@ def ensemble_main(args, cases, wname, rank, world, local, dist):
     ev1.record(stream)
     barrier()
     ms_seq = ev0.elapsed_time(ev1)
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = max_over_ranks(ms, dist)
     value = cells / (ms_all / 1e3) * world
     kinds = E.kind_times()
     esz = 4
@@ -505,11 +513,7 @@ def main():
     m.sync()
     phases, nprof = m.phase_times()
     m.profile(False)
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = max_over_ranks(ms, dist)
     value = metrics.cell_updates_per_s(case.nx, case.ny, case.nz, ms_all / 1e3, replicas=world)
 
     # ---------------------------------------------------------------- roofline of the top kernel
@@ -547,11 +551,7 @@ def main():
         m.step_async(1)
         d = m.diagnostics()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist)
     e2e_value = metrics.cell_updates_per_s(case.nx, case.ny, case.nz, e2e_s, replicas=world)
     healthy = not d["nonfinite"] and d["max_cfl"] < 1.0
     m.close()

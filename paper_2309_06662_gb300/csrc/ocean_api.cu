@@ -191,7 +191,7 @@ size_t layout(ocean_t m, char* base) {
     m->rowm = c.take<char>(7 * nr * e);
     m->levm = c.take<char>(8 * (size_t)m->nz * e);
     m->drow = c.take<double>(3 * nr);
-    m->dlev = c.take<double>(3 * (size_t)m->nz);
+    m->dlev = c.take<double>(4 * (size_t)m->nz + 3 * ((size_t)m->nz + 1));
     m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes()));
     m->diag_out = c.take<double>(8);
     m->cl_mu = c.take<float>(6 * (size_t)m->nz);
@@ -252,7 +252,7 @@ void upload_real(ocean_t m, const std::vector<double>& src, void* dst) {
 
 void upload_levels(ocean_t m) {
     const int nz = m->nz;
-    std::vector<double> lv(8 * (size_t)nz, 0.0), dl(3 * (size_t)nz);
+    std::vector<double> lv(8 * (size_t)nz, 0.0), dl(4 * (size_t)nz + 3 * ((size_t)nz + 1), 0.0);
     for (int k = 0; k < nz; ++k) {
         lv[k] = m->dz[k];
         lv[nz + k] = 1.0 / m->dz[k];
@@ -265,6 +265,17 @@ void upload_levels(ocean_t m) {
         dl[k] = m->dz[k];
         dl[nz + k] = m->Tref[k];
         dl[2 * nz + k] = m->Sref[k];
+        dl[3 * nz + k] = m->prm.dt / m->dz[k];
+    }
+    // sums from level kb to the top, kb = 0 .. nz: of Tref dz, Sref dz and dz (the
+    // reference part of a column's tracer content and its volume per unit area)
+    double* cT = dl.data() + 4 * nz;
+    double* cS = cT + nz + 1;
+    double* cV = cS + nz + 1;
+    for (int k = nz - 1; k >= 0; --k) {
+        cT[k] = cT[k + 1] + m->Tref[k] * m->dz[k];
+        cS[k] = cS[k + 1] + m->Sref[k] * m->dz[k];
+        cV[k] = cV[k + 1] + m->dz[k];
     }
     upload_real(m, lv, m->levm);
     upload_bytes(m, m->dlev, dl.data(), dl.size() * sizeof(double));
@@ -615,8 +626,11 @@ void enqueue_diagnostics(ocean_t m) {
     const StepBuffers<R> b = make_bufs<R>(m);
     launch_diag<R>(k, b, m->stream);   // w of the current state for the CFL number
     const size_t nr = (size_t)m->ny + 2 * OC_H;
-    DiagMetrics dm{m->drow, m->drow + nr, m->drow + 2 * nr, m->dlev, m->dlev + m->nz,
-                   m->dlev + 2 * m->nz, m->dy, 1.0 / m->dy, m->prm.dt};
+    const int nz = m->nz;
+    const double* cols = m->dlev + 4 * nz;
+    DiagMetrics dm{m->drow, m->drow + nr, m->drow + 2 * nr, m->dlev, m->dlev + nz,
+                   m->dlev + 2 * nz, m->dlev + 3 * nz, cols, cols + nz + 1, cols + 2 * (nz + 1),
+                   m->dy, 1.0 / m->dy, m->prm.dt};
     launch_diagnostics<R>(k.g, dm, b.u, b.v, b.T, b.S, b.w, m->eta, m->diag_part, m->diag_out,
                           m->stream);
 }

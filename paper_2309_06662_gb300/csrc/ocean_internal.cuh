@@ -219,9 +219,11 @@ void launch_halo2(const GeoD& g, R* f, cudaStream_t s);
 template <typename R>
 int setup_kernel_attributes(int nz);
 
-// FP64 metrics of the conservation reductions (row arrays indexed j + OC_H).
+// FP64 metrics of the conservation reductions (row arrays indexed j + OC_H; per level
+// dz, Tref, Sref, dt/dz; per lowest wet level kb = 0..nz the sums from kb to the top of
+// Tref dz, Sref dz and dz).
 struct DiagMetrics {
-    const double *Ac, *dxv, *rdxc, *dz, *Tref, *Sref;
+    const double *Ac, *dxv, *rdxc, *dz, *Tref, *Sref, *dtdz, *colT, *colS, *colV;
     double dy, rdy, dt;
 };
 

@@ -1101,47 +1101,58 @@ __device__ __forceinline__ void cs_merge(CSum& a, const CSum& b) {
     a.c += b.c;
 }
 
+// Per column: T' dz, S' dz summed in FP64 (one fused multiply-add per cell, exact
+// products), plus the reference part and the volume from the per-kb sums; kinetic energy
+// and the CFL number in the state's own precision; then Neumaier-compensated FP64 sums
+// over the columns.
 template <typename R>
 __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     GeoD g, DiagMetrics m, const R* __restrict__ u, const R* __restrict__ v,
     const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ w,
     const double* __restrict__ eta, double* __restrict__ partials) {
     CSum sT{0, 0}, sS{0, 0}, sE{0, 0}, sK{0, 0}, sV{0, 0};
-    double cfl = 0.0;
-    int bad = 0;
+    R cflr = R(0);
+    bool bad = false;
     const long ncol = (long)g.nx * g.ny;
+    const R dtr = (R)m.dt, rdyr = (R)m.rdy;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncol;
          c += (long)gridDim.x * blockDim.x) {
         const int i = (int)(c % g.nx), j = (int)(c / g.nx);
         const long c2 = ix2(g, i, j);
         const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
         const double ac = m.Ac[j + OC_H], av = m.dxv[j + OC_H] * m.dy;
-        const double rdx = m.rdxc[j + OC_H];
+        const R rdx = (R)m.rdxc[j + OC_H];
+        double tcol = 0.0, scol = 0.0;
+        R ku2 = R(0), kv2 = R(0);
         for (int k = 0; k < g.nz; ++k) {
             const long ck = k * g.plane + c2;
-            const double dz = m.dz[k];
-            const double tv = (double)T[ck] + m.Tref[k], sv = (double)S[ck] + m.Sref[k];
-            const double uv = (double)u[ck], vv = (double)v[ck];
-            if (!isfinite(tv) || !isfinite(sv) || !isfinite(uv) || !isfinite(vv)) bad = 1;
+            const R tq = T[ck], sq = S[ck], uq = u[ck], vq = v[ck];
+            bad = bad || !isfinite(tq) || !isfinite(sq) || !isfinite(uq) || !isfinite(vq);
+            const R dzr = (R)m.dz[k];
             if (k >= kb) {
-                const double vol = ac * dz;
-                cs_add(sT, tv * vol);
-                cs_add(sS, sv * vol);
-                cs_add(sV, vol);
-                cfl = fmax(cfl, fabs((double)w[ck]) * m.dt / dz);
+                tcol = fma((double)tq, m.dz[k], tcol);
+                scol = fma((double)sq, m.dz[k], scol);
+                cflr = fmax(cflr, fabs(w[ck]) * (R)m.dtdz[k]);
             }
             if (k >= ku) {
-                cs_add(sK, 0.5 * uv * uv * ac * dz);
-                cfl = fmax(cfl, fabs(uv) * m.dt * rdx);
+                ku2 += uq * uq * dzr;
+                cflr = fmax(cflr, fabs(uq) * dtr * rdx);
             }
             if (k >= kv) {
-                cs_add(sK, 0.5 * vv * vv * av * dz);
-                cfl = fmax(cfl, fabs(vv) * m.dt * m.rdy);
+                kv2 += vq * vq * dzr;
+                cflr = fmax(cflr, fabs(vq) * dtr * rdyr);
             }
         }
-        if (kb < g.nz) cs_add(sE, eta[c2] * ac);
-        if (!isfinite(eta[c2])) bad = 1;
+        if (kb < g.nz) {
+            cs_add(sT, (tcol + m.colT[kb]) * ac);
+            cs_add(sS, (scol + m.colS[kb]) * ac);
+            cs_add(sV, m.colV[kb] * ac);
+            cs_add(sE, eta[c2] * ac);
+        }
+        cs_add(sK, 0.5 * ((double)ku2 * ac + (double)kv2 * av));
+        bad = bad || !isfinite(eta[c2]);
     }
+    const double cfl = (double)cflr;
     // block reduction in a fixed order
     __shared__ CSum red[5][OC_DIAG_THREADS];
     __shared__ double rc[OC_DIAG_THREADS];
@@ -1149,7 +1160,7 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     const int t = threadIdx.x;
     red[0][t] = sT; red[1][t] = sS; red[2][t] = sE; red[3][t] = sK; red[4][t] = sV;
     rc[t] = cfl;
-    rb[t] = bad;
+    rb[t] = bad ? 1 : 0;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if (t < h) {

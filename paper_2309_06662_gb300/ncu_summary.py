@@ -39,21 +39,22 @@ def summarize(path):
 
 
 KEY_METRICS = [
-    "gpu__time_duration.sum", "dram__bytes_read.sum", "dram__bytes_write.sum",
+    "gpu__time_duration.sum", "launch__grid_size", "launch__block_size",
+    "launch__registers_per_thread", "launch__occupancy_limit_registers",
+    "launch__occupancy_limit_shared_mem", "dram__bytes_read.sum", "dram__bytes_write.sum",
     "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed",
     "sm__throughput.avg.pct_of_peak_sustained_elapsed",
-    "smsp__issue_active.avg.pct_of_peak_sustained_active",
-    "sm__warps_active.avg.per_cycle_active", "launch__registers_per_thread",
-    "launch__occupancy_limit_shared_mem", "launch__occupancy_limit_registers",
+    "sm__issue_active.avg.pct_of_peak_sustained_elapsed",
+    "sm__warps_active.avg.pct_of_peak_sustained_active",
+    "sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active",
     "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active",
-    "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active",
+    "sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active",
     "sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active",
-    "smsp__inst_executed.sum", "l1tex__t_sector_hit_rate.pct", "lts__t_sector_hit_rate.pct",
-    "smsp__pcsamp_warps_issue_stalled_long_scoreboard",
-    "smsp__pcsamp_warps_issue_stalled_barrier", "smsp__pcsamp_warps_issue_stalled_mio_throttle",
-    "smsp__pcsamp_warps_issue_stalled_short_scoreboard",
-    "smsp__pcsamp_warps_issue_stalled_math_pipe_throttle",
+    "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active",
+    "l1tex__data_bank_conflicts_pipe_lsu_mem_shared.sum",
+    "lts__t_sector_hit_rate.pct",
 ]
+STALL_PREFIX = "smsp__average_warps_issue_stalled_"
 
 
 def raw_metrics(csv_text: str):
@@ -69,6 +70,14 @@ def raw_metrics(csv_text: str):
             if k in hdr:
                 i = hdr.index(k)
                 lines.append(f"  {k:64s} {r[i]:>16s} {units[i]}")
+        lines.append("  warp stalls per issued instruction (>= 0.1):")
+        for i, k in enumerate(hdr):
+            if k.startswith(STALL_PREFIX) and k.endswith("_per_issue_active.ratio"):
+                try:
+                    if float(r[i]) >= 0.1:
+                        lines.append(f"    {k[len(STALL_PREFIX):-len('_per_issue_active.ratio')]:30s} {float(r[i]):6.2f}")
+                except ValueError:
+                    pass
         out.append("\n".join(lines))
     return "\n\n".join(out)
 
