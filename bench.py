@@ -265,10 +265,10 @@ def learned_main(args, case, wname, rank, world, local, dist):
         m = ocean.Ocean(case, precision=ocean.OCEAN_MIXED, closure=closure,
                         closure_hidden=H if closure == ocean.OCEAN_CLOSURE_LEARNED else 0)
         if closure == ocean.OCEAN_CLOSURE_LEARNED:
-            raw = m.closure_features(np.zeros(6 * nz), np.ones(6 * nz))
-            X = raw["X"].double()
-            mu = X.mean(0).cpu().numpy()
-            sd = X.std(0).clamp(min=1e-30).cpu().numpy()
+            # feature statistics of the initial state over the entries that count (a
+            # flat feature gets sigma 1), as the training pipeline computes them
+            from paper_2309_06662_gb300 import closure_train
+            mu, sd = closure_train.feature_stats(m.closure_features(np.zeros(6 * nz), np.ones(6 * nz)))
             m.set_closure(params, mu, sd, sc)
         m.step_async(args.warmup)
         m.sync()
@@ -285,17 +285,18 @@ def learned_main(args, case, wname, rank, world, local, dist):
         m.close()
         del m
         torch.cuda.empty_cache()
-    # the network's GEMM chain over all columns: 4 tcgen05 GEMMs (+ the BF16 conversion)
+    # the network's GEMM chain over all columns from BF16 features, as in the step:
+    # 4 tcgen05 GEMMs with their fused epilogues
     M = case.nx * case.ny
     net = ocean.MLP(nz, H, M + (-M) % 8, params)
-    Xc = torch.randn(M, 6 * nz, device="cuda")
+    Xc = torch.randn(M, 6 * nz, device="cuda").to(torch.bfloat16)
     for _ in range(3):
-        net.forward(Xc)
+        net.forward_bf16(Xc)
     barrier()
     reps = 20
     ev0.record()
     for _ in range(reps):
-        net.forward(Xc)
+        net.forward_bf16(Xc)
     ev1.record()
     barrier()
     ms_net = ev0.elapsed_time(ev1) / reps

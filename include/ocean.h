@@ -259,12 +259,22 @@ int ocean_mlp_set_params(ocean_mlp_t h, const float* host, size_t count);  /* re
 int ocean_mlp_get_params(ocean_mlp_t h, float* host, size_t count);
 /* y = MLP(x) for M <= max_batch rows: d_X fp32 [M][6nz], d_Y fp32 [M][3nz] */
 int ocean_mlp_forward(ocean_mlp_t h, const float* d_X, int M, float* d_Y);
+/* The same from BF16 inputs d_Xb [M][6nz] (16-byte aligned), as the model's step feeds the
+ * network: no conversion, only the four GEMMs and their epilogues. */
+int ocean_mlp_forward_bf16(ocean_mlp_t h, const void* d_Xb, int M, float* d_Y);
 /* Loss of a batch and the gradients (to host_grads in the flat layout, if not NULL). */
 int ocean_mlp_loss_grad(ocean_mlp_t h, const ocean_batch* batch, int M,
                         const ocean_closure_scales* scales, float* loss, float* host_grads);
 /* One Adam step (lr; beta = 0.9, 0.999; eps = 1e-8) on a batch; the loss before it. */
 int ocean_mlp_train_step(ocean_mlp_t h, const ocean_batch* batch, int M,
                          const ocean_closure_scales* scales, float lr, float* loss);
+
+/* Self-test of the bounded device waits the tensor-core GEMMs use (a wait on an mbarrier
+ * that gives up after ~1 s and reports OCEAN_ERR_TIMEOUT instead of hanging the GPU): one
+ * kernel on `stream` waits on a barrier that nothing completes, with a limit of `cycles`
+ * SM clock cycles.  Returns OCEAN_ERR_TIMEOUT when the wait gave up (the expected
+ * outcome; the CUDA context stays usable), OCEAN_OK if the barrier completed. */
+int ocean_selftest_bounded_wait(long long cycles, void* stream);
 
 /* Load a trained closure into a model created with closure_hidden > 0: the flat network
  * parameters (ocean_mlp_param_count(nz, closure_hidden) floats), the feature statistics

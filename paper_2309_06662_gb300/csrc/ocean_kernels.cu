@@ -1178,24 +1178,44 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     }
 }
 
-__global__ void k_diag_final(const double* __restrict__ partials, int nblk, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// the per-block partial sums merged in a fixed tree: each of 256 threads merges
+// nblk / 256 consecutive partials, then pairs of threads halve the set
+constexpr int FIN_TH = 256;
+__global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict__ partials,
+                                                       int nblk, double* out) {
+    __shared__ CSum red[5][FIN_TH];
+    __shared__ double rc[FIN_TH], rb[FIN_TH];
+    const int t = threadIdx.x;
     CSum a[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
     double cfl = 0.0, bad = 0.0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = t; b < nblk; b += FIN_TH) {
         const double* o = partials + (long)b * 12;
         for (int q = 0; q < 5; ++q) cs_merge(a[q], CSum{o[2 * q], o[2 * q + 1]});
         cfl = fmax(cfl, o[10]);
         bad = fmax(bad, o[11]);
     }
-    out[0] = a[0].s + a[0].c;
-    out[1] = a[1].s + a[1].c;
-    out[2] = a[2].s + a[2].c;
-    out[3] = a[3].s + a[3].c;
-    out[4] = cfl;
-    out[5] = bad;
-    out[6] = a[4].s + a[4].c;
-    out[7] = 0.0;
+    for (int q = 0; q < 5; ++q) red[q][t] = a[q];
+    rc[t] = cfl;
+    rb[t] = bad;
+    __syncthreads();
+    for (int h = FIN_TH / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int q = 0; q < 5; ++q) cs_merge(red[q][t], red[q][t + h]);
+            rc[t] = fmax(rc[t], rc[t + h]);
+            rb[t] = fmax(rb[t], rb[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = red[0][0].s + red[0][0].c;
+        out[1] = red[1][0].s + red[1][0].c;
+        out[2] = red[2][0].s + red[2][0].c;
+        out[3] = red[3][0].s + red[3][0].c;
+        out[4] = rc[0];
+        out[5] = rb[0];
+        out[6] = red[4][0].s + red[4][0].c;
+        out[7] = 0.0;
+    }
 }
 
 }  // namespace
@@ -1207,7 +1227,7 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
                         const R* S, const R* w, const double* eta, double* partials,
                         double* out, cudaStream_t s) {
     k_diag_sums<R><<<OC_DIAG_BLOCKS, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, w, eta, partials);
-    k_diag_final<<<1, 32, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
+    k_diag_final<<<1, FIN_TH, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
 }
 
 // ------------------------------------------------------------------ batched ensemble

@@ -6,9 +6,12 @@
 // Network (see include/ocean.h): x (6 nz) -> H -> H -> H -> y (3 nz), SiLU after each
 // hidden layer.  Layer weights W [in][out]; the GEMMs read W^T [out][in] in the forward
 // pass and W [in][out] in the backward pass, both kept as BF16 copies of the FP32 master.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -108,7 +111,10 @@ __device__ __forceinline__ unsigned long long sw128_desc(unsigned saddr) {
 constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TBN >> 3) << 17) |
                               ((unsigned)(TBM >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// spin on the barrier's phase `parity` for at most `limit` SM clock cycles (~1 s by
+// default); false if it did not complete
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          long long limit = 2000000000LL) {
     const long long t0 = clock64();
     while (true) {
         unsigned ok;
@@ -119,7 +125,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -162,8 +168,15 @@ __device__ __forceinline__ void epi_run32(const Epi& e, int m, int n0, int N, co
             v[4 * q + 3] *= silu_grad_f(z.w);
         }
     } else if (e.bias) {
+        const float4* b4 = reinterpret_cast<const float4*>(e.bias + n0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += e.bias[n0 + j];
+        for (int q = 0; q < 8; ++q) {
+            const float4 bq = b4[q];
+            v[4 * q] += bq.x;
+            v[4 * q + 1] += bq.y;
+            v[4 * q + 2] += bq.z;
+            v[4 * q + 3] += bq.w;
+        }
     }
     if (e.mode == EPI_F32 || (e.mode == EPI_SILU && e.outF)) {
         float4* o4 = reinterpret_cast<float4*>(e.outF + (long)m * e.ldF + n0);
@@ -308,11 +321,193 @@ __global__ void __launch_bounds__(TTH) k_gemm_nt_tc(const bf16* __restrict__ A, 
                      "r"(TMEM_COLS));
 }
 
-// A [M][lda], B [N][ldb] row-major BF16; lda, ldb and K multiples of 8 (16-byte rows)
+// ------------------------------------------------------------------ GEMM: TMA-fed tcgen05
+//
+// The same 128 x 128 tile and MMA sequence as k_gemm_nt_tc, with the operands brought in
+// by the tensor memory accelerator: one thread issues, per K step of 64, a 2-D bulk tensor
+// copy of the A tile (128 rows) and of the B tile (128 rows), 128-byte swizzled, into a
+// ring of GS stages; a second thread issues the MMAs of a stage once its full barrier
+// has counted the copied bytes and commits them to the stage's empty barrier, which the
+// copying thread waits for before reusing the stage; the last commit signals the
+// epilogue.  Rows and K beyond the matrix arrive as zeros (the copies' out-of-bounds
+// fill).  Needs the rows of A and B 16-byte aligned (leading dimensions multiples of 8).
+// Eight warps read the accumulator: warp w the lanes 32 (w % 4).. and the column half
+// w / 4, so the epilogue runs on twice the warps of the loading scheme.
+
+constexpr int GS = 2, TMA_TH = 256;
+constexpr size_t TMA_SMEM = 1024 + 2 * GS * (size_t)TILE_BYTES + 128;
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(TMA_TH) k_gemm_nt_tma(const __grid_constant__ CUtensorMap tA,
+                                                     const __grid_constant__ CUtensorMap tB,
+                                                     int M, int N, int K, Epi e) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        ((unsigned long long)tc_raw + 1023) & ~1023ull);
+    auto sA = [&](int st) { return base + st * TILE_BYTES; };
+    auto sB = [&](int st) { return base + (GS + st) * TILE_BYTES; };
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(base + 2 * GS * TILE_BYTES);
+    unsigned long long* empty = full + GS;
+    unsigned long long* done = empty + GS;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(done + 1);
+    int* abandon = reinterpret_cast<int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    const int nk = (K + TBK - 1) / TBK;
+
+    if (tid == 0) {
+        for (int st = 0; st < GS; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(done)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abandon = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- copies: stage kt % GS, after the MMAs of step kt - GS released it
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % GS, use = kt / GS;
+            if (kt >= GS && !mbar_wait(smem_u32(&empty[st]), (unsigned)(use - 1) & 1u)) {
+                atomicExch(&g_tc_err, 1);
+                *abandon = 1;
+                break;
+            }
+            mbar_expect(smem_u32(&full[st]), 2u * TILE_BYTES);
+            tma_load_2d(smem_u32(sA(st)), &tA, kt * TBK, m0, smem_u32(&full[st]));
+            tma_load_2d(smem_u32(sB(st)), &tB, kt * TBK, n0, smem_u32(&full[st]));
+            ++issued;
+        }
+        // on an abandoned tile, wait (bounded) for the copies still in flight
+        if (*abandon)
+            for (int kt = (issued > GS ? issued - GS : 0); kt < issued; ++kt)
+                mbar_wait(smem_u32(&full[kt % GS]), (unsigned)(kt / GS) & 1u);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMAs: four K-16 steps per stage into the TMEM accumulator
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % GS, use = kt / GS;
+            if (!mbar_wait(smem_u32(&full[st]), (unsigned)use & 1u)) {
+                atomicExch(&g_tc_err, 1);
+                *abandon = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long ad = sw128_desc(smem_u32(sA(st)));
+            const unsigned long long bd = sw128_desc(smem_u32(sB(st)));
+#pragma unroll
+            for (int k = 0; k < TBK / 16; ++k) {
+                const unsigned acc = (kt > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad + 2ull * k), "l"(bd + 2ull * k), "r"(TC_IDESC), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&empty[st]))
+                : "memory");
+        }
+        // arrives once every MMA issued above has completed
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(done))
+            : "memory");
+    }
+    const bool ok = __syncthreads_and(mbar_wait(smem_u32(done), 0u) ? 1 : 0) != 0;
+    if (!ok) {
+        atomicExch(&g_tc_err, 1);
+        *abandon = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!*abandon) {
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane, m = m0 + row;
+#pragma unroll 1
+        for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
+            unsigned r[32];
+            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
+            if (m < M) epi_run32(e, m, n0 + c0, N, r);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+}
+
+// tensor map of a row-major BF16 matrix [rows][ld] read K columns wide, boxes of 64
+// columns x TBM rows, 128-byte swizzle; false if the driver refuses it
+bool gemm_tensor_map(CUtensorMap* map, const bf16* ptr, int rows, int K, int ld) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
+    const cuuint32_t es[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Self-test of the bounded wait: a barrier that nothing completes; the wait gives up
+// after `limit` cycles and the kernel reports it instead of hanging
+__global__ void k_wait_selftest(long long limit, int* timed_out) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(smem_u32(&bar), 0u, limit);
+    if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+}
+
+// A [M][lda], B [N][ldb] row-major BF16 (lda, ldb and K multiples of 8, 16-byte aligned
+// rows): TMA-fed when the driver encodes both tensor maps, else staged by cp.async
 void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& e,
              cudaStream_t s) {
     const dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
-    k_gemm_nt_tc<<<grid, TTH, TC_SMEM, s>>>(A, lda, B, ldb, M, N, K, e);
+    CUtensorMap ta, tb;
+    if (gemm_tensor_map(&ta, A, M, K, lda) && gemm_tensor_map(&tb, B, N, K, ldb))
+        k_gemm_nt_tma<<<grid, TMA_TH, TMA_SMEM, s>>>(ta, tb, M, N, K, e);
+    else
+        k_gemm_nt_tc<<<grid, TTH, TC_SMEM, s>>>(A, lda, B, ldb, M, N, K, e);
 }
 
 // ------------------------------------------------------------------ elementwise kernels
@@ -467,8 +662,26 @@ inline int nb(long n, int t) { return (int)((n + t - 1) / t); }
 // the GEMM's shared memory (above the default 48 KB); called before the first launch on a
 // device and outside stream capture
 int closure_gemm_setup() {
-    return (int)cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TC_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_nt_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TMA_SMEM);
+    return (int)e;
+}
+
+// runs k_wait_selftest on `s`; 1 if the wait gave up (the expected outcome), 0 if it
+// completed, -1 on a CUDA error
+int closure_wait_selftest(long long limit, cudaStream_t s) {
+    int* d = nullptr;
+    int h = -1;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return -1;
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, d);
+    if (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        h = -1;
+    cudaFree(d);
+    return h;
 }
 
 // 1 if a closure GEMM abandoned a tile on a barrier that did not complete since the last
@@ -764,6 +977,24 @@ int ocean_mlp_get_params(ocean_mlp_t h, float* host, size_t count) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)
         return mfail(h, OCEAN_ERR_CUDA, "ocean_mlp_get_params: copy failed");
     return OCEAN_OK;
+}
+
+int ocean_selftest_bounded_wait(long long cycles, void* stream) {
+    if (cycles < 1) return mfail(nullptr, OCEAN_ERR_ARG, "cycles must be >= 1");
+    const int r = closure_wait_selftest(cycles, (cudaStream_t)stream);
+    if (r < 0) return mfail(nullptr, OCEAN_ERR_CUDA, "self-test kernel failed");
+    if (r == 1) return mfail(nullptr, OCEAN_ERR_TIMEOUT, "bounded wait gave up (self-test: expected)");
+    return OCEAN_OK;
+}
+
+int ocean_mlp_forward_bf16(ocean_mlp_t h, const void* d_Xb, int M, float* d_Y) {
+    if (!h || !d_Xb || !d_Y) return mfail(h, OCEAN_ERR_ARG, "null argument");
+    if (M < 1 || M > h->max_batch) return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_forward_bf16: 1 <= M <= max_batch");
+    if (((uintptr_t)d_Xb & 15) != 0) return mfail(h, OCEAN_ERR_ARG, "ocean_mlp_forward_bf16: d_Xb must be 16-byte aligned");
+    const void* Wt[4] = {h->Wt[0], h->Wt[1], h->Wt[2], h->Wt[3]};
+    const float* b[4] = {h->b[0], h->b[1], h->b[2], h->b[3]};
+    closure_forward(d_Xb, M, Wt, b, h->dims, h->H[0], h->H[1], d_Y, h->stream);
+    return cudaGetLastError() == cudaSuccess ? OCEAN_OK : mfail(h, OCEAN_ERR_CUDA, "kernel launch failed");
 }
 
 int ocean_mlp_forward(ocean_mlp_t h, const float* d_X, int M, float* d_Y) {

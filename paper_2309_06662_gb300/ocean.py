@@ -132,6 +132,8 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_mlp_set_params": (c_int, [pv, POINTER(ctypes.c_float), c_size_t]),
             "ocean_mlp_get_params": (c_int, [pv, POINTER(ctypes.c_float), c_size_t]),
             "ocean_mlp_forward": (c_int, [pv, pv, c_int, pv]),
+            "ocean_mlp_forward_bf16": (c_int, [pv, pv, c_int, pv]),
+            "ocean_selftest_bounded_wait": (c_int, [ctypes.c_longlong, pv]),
             "ocean_mlp_loss_grad": (c_int, [pv, POINTER(OceanBatch), c_int, POINTER(ClosureScales),
                                             POINTER(ctypes.c_float), POINTER(ctypes.c_float)]),
             "ocean_mlp_train_step": (c_int, [pv, POINTER(OceanBatch), c_int, POINTER(ClosureScales),
@@ -529,6 +531,15 @@ class MLP:
         Y = torch.empty((X.shape[0], self.dims[-1]), device="cuda", dtype=torch.float32)
         _check(load().ocean_mlp_forward(self._h, c_void_p(X.data_ptr()), X.shape[0],
                                         c_void_p(Y.data_ptr())))
+        return Y
+
+    def forward_bf16(self, Xb):
+        """Xb: torch CUDA bfloat16 [M, 6nz] -> Y [M, 3nz] (no input conversion)."""
+        torch = _torch_cuda()
+        Xb = Xb.to(device="cuda", dtype=torch.bfloat16).contiguous()
+        Y = torch.empty((Xb.shape[0], self.dims[-1]), device="cuda", dtype=torch.float32)
+        _check(load().ocean_mlp_forward_bf16(self._h, c_void_p(Xb.data_ptr()), Xb.shape[0],
+                                             c_void_p(Y.data_ptr())))
         return Y
 
     @staticmethod

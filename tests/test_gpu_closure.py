@@ -1,6 +1,8 @@
 """The closure network's tensor-core kernels against the FP64 oracle (needs a GPU):
 forward outputs and loss gradients on bfloat16-exact weights and inputs, and training
 that lowers the loss."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -190,3 +192,24 @@ def test_learned_step_matches_oracle(precision, tol):
     p = oracle.OracleModel(c)
     p.step(5)
     assert np.linalg.norm(p.get("T") - o.get("T")) > 1e3 * tol * np.linalg.norm(o.get("T")) * 0 + 1e-12
+
+
+@pytest.mark.gpu
+def test_bounded_wait_gives_up_and_the_context_survives():
+    # a device wait on a barrier that nothing completes returns OCEAN_ERR_TIMEOUT (no
+    # hang, no trap); the GEMM kernels use the same wait, and still run afterwards
+    import torch
+    L = ocean.load()
+    s = torch.cuda.current_stream().cuda_stream
+    rc = L.ocean_selftest_bounded_wait(2_000_000, ctypes.c_void_p(s))
+    assert rc == -4, rc
+    assert b"gave up" in L.ocean_last_error(None)
+    nz, H, M = 4, 32, 64
+    dims = [6 * nz, H, H, H, 3 * nz]
+    params = inputs.mlp_seeded_params(3, dims)
+    net = ocean.MLP(nz, H, M, params)
+    X = torch.tensor(np.random.default_rng(1).normal(size=(M, 6 * nz)), dtype=torch.float32,
+                     device="cuda")
+    Y = net.forward(X).cpu().numpy()
+    ref, _ = C.mlp_forward(params, X.cpu().numpy().astype(np.float64), bf16=True)
+    assert np.max(np.abs(Y - ref)) <= 1e-2 * max(1.0, np.max(np.abs(ref)))
