@@ -1033,8 +1033,9 @@ int ocean_set_closure(ocean_t h, const float* params, size_t count, const float*
     if (count != ocean_mlp_param_count(h->nz, h->cl_hidden))
         return fail(h, OCEAN_ERR_ARG, "closure parameter count %zu, expected %zu", count,
                     ocean_mlp_param_count(h->nz, h->cl_hidden));
-    if (closure_gemm_setup() != (int)cudaSuccess)
-        return fail(h, OCEAN_ERR_CUDA, "GEMM shared-memory attribute could not be set");
+    if (closure_gemm_setup() != (int)cudaSuccess ||
+        (h->prec == OCEAN_FP64 ? closure_tiles_setup<double>() : closure_tiles_setup<float>()) != (int)cudaSuccess)
+        return fail(h, OCEAN_ERR_CUDA, "closure kernels' shared-memory attributes could not be set");
     const float* p = params;
     for (int l = 0; l < 4; ++l) {
         const int in = h->cl_dims[l], out = h->cl_dims[l + 1];

@@ -16,17 +16,15 @@ __device__ __forceinline__ float softplus_c(float z) { return z > 20.f ? z : log
 
 // Per interior column c = j nx + i: raw features (T, S, centre u, v on levels; N^2 and
 // shear^2 on bottom faces), z-scored with mu/sigma where the entry counts (wet level or
-// interior face), else 0; optional fp32 and bf16 copies; masks and vertical gradients.
-template <typename R>
-__global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __restrict__ v,
-                                   const R* __restrict__ T, const R* __restrict__ S,
-                                   const float* __restrict__ mu, const float* __restrict__ sigma,
-                                   float* __restrict__ Xf, __nv_bfloat16* __restrict__ Xb,
-                                   unsigned char* __restrict__ face, unsigned char* __restrict__ wet,
-                                   float* __restrict__ dzT, float* __restrict__ dzS) {
+// interior face), else 0.  emit(fi, x, k, w, f, gT, gS) receives feature fi = q nz + k,
+// its value, and for q = 0 the level's masks and vertical gradients.
+template <typename R, typename Emit>
+__device__ __forceinline__ void column_features(const KP<R>& p, long c, const R* __restrict__ u,
+                                                const R* __restrict__ v, const R* __restrict__ T,
+                                                const R* __restrict__ S,
+                                                const float* __restrict__ mu,
+                                                const float* __restrict__ sigma, Emit emit) {
     const GeoD& g = p.g;
-    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx), nz = g.nz;
     const long c2 = ix2(g, i, j), P = g.plane;
     const int kb = g.kb[c2];
@@ -56,32 +54,105 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const int fi = q * nz + k;
-            const float x = use[q] ? raw[q] / sigma[fi] : 0.f;
-            if (Xf) Xf[c * 6 * nz + fi] = x;
-            if (Xb) Xb[c * 6 * nz + fi] = __float2bfloat16_rn(x);
+            emit(fi, use[q] ? raw[q] / sigma[fi] : 0.f, k, w, f, gT, gS);
         }
-        if (face) face[c * nz + k] = f;
-        if (wet) wet[c * nz + k] = w;
-        if (dzT) dzT[c * nz + k] = gT;
-        if (dzS) dzS[c * nz + k] = gS;
+    }
+}
+
+// features, masks and gradients of every column, one thread per column (the training
+// pipeline's extraction)
+template <typename R>
+__global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __restrict__ v,
+                                   const R* __restrict__ T, const R* __restrict__ S,
+                                   const float* __restrict__ mu, const float* __restrict__ sigma,
+                                   float* __restrict__ Xf, __nv_bfloat16* __restrict__ Xb,
+                                   unsigned char* __restrict__ face, unsigned char* __restrict__ wet,
+                                   float* __restrict__ dzT, float* __restrict__ dzS) {
+    const GeoD& g = p.g;
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const int nz = g.nz;
+    column_features<R>(p, c, u, v, T, S, mu, sigma,
+                       [&](int fi, float x, int k, bool w, bool f, float gT, float gS) {
+                           if (Xf) Xf[c * 6 * nz + fi] = x;
+                           if (Xb) Xb[c * 6 * nz + fi] = __float2bfloat16_rn(x);
+                           if (fi == k) {
+                               if (face) face[c * nz + k] = f;
+                               if (wet) wet[c * nz + k] = w;
+                               if (dzT) dzT[c * nz + k] = gT;
+                               if (dzS) dzS[c * nz + k] = gS;
+                           }
+                       });
+}
+
+// Rows of feature matrices and network outputs pass through shared memory, so the
+// row-major [column][feature] arrays are written and read with coalesced accesses
+// (one thread per column would touch one 2- or 4-byte element per row per access): a
+// block of fcols(nz) columns, rows padded by one 4-byte word (no bank conflicts).
+__host__ __device__ inline int fcols(int nz) { return nz <= 48 ? 128 : 32; }
+
+// BF16 features of the step's network pass (no masks or gradients)
+template <typename R>
+__global__ void __launch_bounds__(128) k_closure_xb(KP<R> p, const R* __restrict__ u,
+                                                    const R* __restrict__ v,
+                                                    const R* __restrict__ T,
+                                                    const R* __restrict__ S,
+                                                    const float* __restrict__ mu,
+                                                    const float* __restrict__ sigma,
+                                                    __nv_bfloat16* __restrict__ Xb) {
+    extern __shared__ __align__(16) unsigned char fx_raw[];
+    __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(fx_raw);
+    const GeoD& g = p.g;
+    const int nz = g.nz, F = 6 * nz, ld = F + 2, FC = fcols(nz);
+    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * FC;
+    const int t = threadIdx.x;
+    if (t < FC && c0 + t < ncol) {
+        __nv_bfloat16* row = tile + (long)t * ld;
+        column_features<R>(p, c0 + t, u, v, T, S, mu, sigma,
+                           [&](int fi, float x, int, bool, bool, float, float) {
+                               row[fi] = __float2bfloat16_rn(x);
+                           });
+    }
+    __syncthreads();
+    // the block's rows are contiguous in Xb: copy them out as 4-byte pairs (F is even)
+    const long rows = ncol - c0 < FC ? ncol - c0 : FC;
+    const int pairs = F / 2;
+    unsigned* dst = reinterpret_cast<unsigned*>(Xb + c0 * F);
+    for (long q = t; q < rows * pairs; q += blockDim.x) {
+        const long r = q / pairs, e = q - r * pairs;
+        dst[q] = *reinterpret_cast<const unsigned*>(tile + r * ld + 2 * e);
     }
 }
 
 // network outputs -> extra diffusivity on the interior wet faces (added to the
-// Richardson-number value already in kap) and tracer corrections
+// Richardson-number value already in kap) and tracer corrections; the block's rows of Y
+// come in through shared memory (coalesced)
 template <typename R>
-__global__ void k_closure_apply(KP<R> p, const float* __restrict__ Y, float ks, float gt,
-                                float gs, R* __restrict__ kap, R* __restrict__ dGT,
-                                R* __restrict__ dGS) {
+__global__ void __launch_bounds__(128) k_closure_apply(KP<R> p, const float* __restrict__ Y,
+                                                       float ks, float gt, float gs,
+                                                       R* __restrict__ kap, R* __restrict__ dGT,
+                                                       R* __restrict__ dGS) {
+    extern __shared__ __align__(16) unsigned char fy_raw[];
+    float* tile = reinterpret_cast<float*>(fy_raw);
     const GeoD& g = p.g;
-    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (long)g.nx * g.ny) return;
-    const int i = (int)(c % g.nx), j = (int)(c / g.nx), nz = g.nz;
+    const int nz = g.nz, F = 3 * nz, ld = F + 1, FC = fcols(nz);
+    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * FC;
+    const int t = threadIdx.x;
+    const long rows = ncol - c0 < FC ? ncol - c0 : FC;
+    const float* src = Y + c0 * F;
+    for (long q = t; q < rows * F; q += blockDim.x) {
+        const long r = q / F;
+        tile[r * ld + (q - r * F)] = src[q];
+    }
+    __syncthreads();
+    if (t >= FC || c0 + t >= ncol) return;
+    const long c = c0 + t;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j), P = g.plane;
     const int kb = g.kb[c2];
-    const float* y = Y + c * 3 * nz;
+    const float* y = tile + (long)t * ld;
     bool ok = true;
-    for (int q = 0; q < 3 * nz; ++q) ok = ok && isfinite(y[q]);
+    for (int q = 0; q < F; ++q) ok = ok && isfinite(y[q]);
     for (int k = 0; k < nz; ++k) {
         const long ck = k * P + c2;
         if (ok && k >= kb + 1) kap[ck] = kap[ck] + (R)(ks * softplus_c(y[k]));
@@ -222,14 +293,38 @@ void launch_closure_features(const KP<R>& p, const R* u, const R* v, const R* T,
                              const float* mu, const float* sigma, float* Xf, void* Xb,
                              unsigned char* face, unsigned char* wet, float* dzT, float* dzS,
                              cudaStream_t s) {
-    k_closure_features<R><<<cblocks((long)p.g.nx * p.g.ny), CT, 0, s>>>(
+    const long ncol = (long)p.g.nx * p.g.ny;
+    if (Xb && !Xf && !face && !wet && !dzT && !dzS) {   // the step's BF16 features
+        const int FC = fcols(p.g.nz);
+        const size_t smem = (size_t)FC * (6 * p.g.nz + 2) * sizeof(__nv_bfloat16);
+        k_closure_xb<R><<<(int)((ncol + FC - 1) / FC), 128, smem, s>>>(
+            p, u, v, T, S, mu, sigma, reinterpret_cast<__nv_bfloat16*>(Xb));
+        return;
+    }
+    k_closure_features<R><<<cblocks(ncol), CT, 0, s>>>(
         p, u, v, T, S, mu, sigma, Xf, reinterpret_cast<__nv_bfloat16*>(Xb), face, wet, dzT, dzS);
 }
 
 template <typename R>
 void launch_closure_apply(const KP<R>& p, const float* Y, float ks, float gt, float gs, R* kap,
                           R* dGT, R* dGS, cudaStream_t s) {
-    k_closure_apply<R><<<cblocks((long)p.g.nx * p.g.ny), CT, 0, s>>>(p, Y, ks, gt, gs, kap, dGT, dGS);
+    const long ncol = (long)p.g.nx * p.g.ny;
+    const int FC = fcols(p.g.nz);
+    const size_t smem = (size_t)FC * (3 * p.g.nz + 1) * sizeof(float);
+    k_closure_apply<R><<<(int)((ncol + FC - 1) / FC), 128, smem, s>>>(p, Y, ks, gt, gs, kap, dGT,
+                                                                       dGS);
+}
+
+// the tiled kernels' shared memory (up to ~75 KB, above the default 48 KB); set before
+// the first launch and outside stream capture
+template <typename R>
+int closure_tiles_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_closure_xb<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         100 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_closure_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 100 * 1024);
+    return (int)e;
 }
 
 template <typename R>
@@ -254,6 +349,7 @@ void launch_closure_targets(const KP<R>& p, const R* GcT, const R* GcS, const fl
                                              const R*, const float*, const float*, float*,     \
                                              void*, unsigned char*, unsigned char*, float*,    \
                                              float*, cudaStream_t);                            \
+    template int closure_tiles_setup<R>();                                                     \
     template void launch_closure_apply<R>(const KP<R>&, const float*, float, float, float, R*, \
                                           R*, R*, cudaStream_t);                               \
     template void launch_coarse_grain<R>(const KP<R>&, const KP<R>&, int, const R*, const R*,  \

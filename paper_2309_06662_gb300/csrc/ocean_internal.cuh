@@ -263,6 +263,7 @@ void closure_forward(const void* Xb, int M, const void* const* Wt, const float* 
                      const int* dims, void* H0, void* H1, float* Y, cudaStream_t s);
 void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s);
 int closure_gemm_failed();
+template <typename R> int closure_tiles_setup();
 int closure_gemm_setup();
 
 // ---- batched ensemble (kernels in ocean_kernels.cu, host side in ocean_ensemble.cu)
