@@ -1,8 +1,11 @@
 // ocean_api.cu -- host side of libocean's C ABI: validation, metrics and masks, the
 // device arena, field transfer and the per-step launch sequence.  All arithmetic of the
 // step itself runs in the kernels of ocean_kernels.cu.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -93,6 +96,7 @@ struct ocean_s {
     // the step as a CUDA graph, per buffer parity and with / without the learned closure
     // (captured on first use; dropped when a launch argument changes)
     cudaGraphExec_t graph[2][2] = {};
+    TileMaps tmaps[2];         // tensor maps of the state, per buffer parity
     bool graphs_off = false;   // the stream cannot be captured (the legacy default stream)
     std::string err;
 };
@@ -496,7 +500,29 @@ StepBuffers<R> make_bufs(const ocean_t m, int cur = -1) {
     b.Ub2 = P(m->Ub2); b.Vb2 = P(m->Vb2); b.dE2 = P(m->dE2);
     b.Hu = P(m->Hu); b.Hv = P(m->Hv); b.rHu = P(m->rHu); b.rHv = P(m->rHv);
     b.eta = m->eta; b.accE = m->accE; b.accU = m->accU; b.accV = m->accV;
+    b.tm = m->tmaps[c];
     return b;
+}
+
+// tensor maps of T, S, u, v of both buffer parities (3-D views of the padded fields)
+bool build_tile_maps(ocean_t m) {
+    const CUtensorMapDataType dt =
+        m->prec == OCEAN_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const unsigned long long dims[3] = {(unsigned long long)m->pitch,
+                                        (unsigned long long)(m->ny + 2 * OC_H),
+                                        (unsigned long long)m->nz};
+    const unsigned long long strides[2] = {(unsigned long long)m->pitch * m->esz,
+                                           (unsigned long long)m->plane * m->esz};
+    const unsigned boxTS[3] = {40, 14, 1}, boxU[3] = {36, 8, 1}, boxV[3] = {32, 9, 1};
+    for (int c = 0; c < 2; ++c) {
+        TileMaps& t = m->tmaps[c];
+        if (!oc_encode_tiled(&t.T, dt, 3, m->T[c], dims, strides, boxTS, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+            !oc_encode_tiled(&t.S, dt, 3, m->S[c], dims, strides, boxTS, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+            !oc_encode_tiled(&t.u, dt, 3, m->u[c], dims, strides, boxU, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+            !oc_encode_tiled(&t.v, dt, 3, m->v[c], dims, strides, boxV, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return false;
+    }
+    return true;
 }
 
 // kernels one step enqueues (each periodic direction adds one halo kernel per halo fill)
@@ -695,6 +721,10 @@ int create_common(const ocean_grid* grid, const double* depth, const ocean_param
         ocean_destroy(m);
         return r;
     }
+    if (!build_tile_maps(m)) {
+        ocean_destroy(m);
+        return fail(nullptr, OCEAN_ERR_CUDA, "the driver refused the tile kernels' tensor maps");
+    }
     rc = build_geometry(m, depth);
     if (rc == OCEAN_OK) rc = set_wind(m, params->taux, params->tauy);
     if (rc != OCEAN_OK) {
@@ -778,6 +808,37 @@ int get_field_t(ocean_t m, const FieldRef& r, int id, double* host) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Tensor maps through the driver's entry point (no link-time dependence on libcuda).
+
+bool oc_encode_tiled(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* ptr,
+                     const unsigned long long* dims, const unsigned long long* strides,
+                     const unsigned* box, CUtensorMapSwizzle swizzle) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return false;
+    cuuint64_t d[5];
+    cuuint64_t st[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i < rank - 1) st[i] = strides[i];
+    }
+    return encode(map, type, (cuuint32_t)rank, const_cast<void*>(ptr), d, st, bx, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // ---------------------------------------------------------------------------------------
 // Model internals the batched ensemble (ocean_ensemble.cu) builds on.
@@ -966,10 +1027,13 @@ int ocean_step_async(ocean_t h, int n) {
     return OCEAN_OK;
 }
 
-// after a synchronisation: the learned closure's GEMMs report a tile that gave up waiting
+// after a synchronisation: device waits that gave up (the learned closure's GEMM tiles,
+// the tile kernels' tensor copies) become OCEAN_ERR_TIMEOUT
 static int check_closure_gemm(ocean_t h) {
     if (h->cl_ready && h->prm.closure == OCEAN_CLOSURE_LEARNED && closure_gemm_failed())
         return fail(h, OCEAN_ERR_TIMEOUT, "a tensor-core GEMM tile of the closure timed out");
+    if (tile_wait_failed())
+        return fail(h, OCEAN_ERR_TIMEOUT, "a tile kernel's wait for its tensor copies timed out");
     return OCEAN_OK;
 }
 

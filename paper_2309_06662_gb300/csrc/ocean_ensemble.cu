@@ -317,6 +317,8 @@ int ocean_ensemble_step(ocean_ensemble_t e, int n) {
     int rc = ocean_ensemble_step_async(e, n);
     if (rc) return rc;
     EN_CUDA(cudaStreamSynchronize(e->stream));
+    if (tile_wait_failed())
+        return efail(OCEAN_ERR_TIMEOUT, "a tile kernel's wait for its tensor copies timed out");
     return OCEAN_OK;
 }
 

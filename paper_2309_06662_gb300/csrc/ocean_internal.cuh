@@ -3,6 +3,7 @@
 // of libocean only.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -183,6 +184,18 @@ template <> struct WenoPair<float> {
 // ----------------------------------------------------------------------- launchers
 // Implemented in ocean_kernels.cu, instantiated for double and float.
 
+// Tensor maps (TMA descriptors) of the fields the tracer tile stages, for one buffer
+// parity: 3-D [nz][ny + 2H][pitch] views of T, S, u, v (boxes: T and S 40 x 14 columns x
+// rows, u 36 x 8, v 32 x 9, one level).
+struct __align__(64) TileMaps {
+    CUtensorMap T, S, u, v;
+};
+
+// Encodes a tiled tensor map through the driver's entry point; false if refused.
+bool oc_encode_tiled(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* ptr,
+                     const unsigned long long* dims, const unsigned long long* strides,
+                     const unsigned* box, CUtensorMapSwizzle swizzle);
+
 template <typename R> struct StepBuffers {
     // state n (read) and n+1 (written)
     const R *u, *v, *T, *S;
@@ -197,6 +210,7 @@ template <typename R> struct StepBuffers {
     R *Ub2, *Vb2, *dE2;        // second buffers of the barotropic state (passes ping-pong)
     const R *Hu, *Hv, *rHu, *rHv;
     double *eta, *accE, *accU, *accV;
+    TileMaps tm;               // tensor maps of the state read by the tracer tile
 };
 
 template <typename R>
@@ -263,6 +277,7 @@ void closure_forward(const void* Xb, int M, const void* const* Wt, const float* 
                      const int* dims, void* H0, void* H1, float* Y, cudaStream_t s);
 void closure_weight_transpose(const float* W, int in, int out, void* Wt, cudaStream_t s);
 int closure_gemm_failed();
+int tile_wait_failed();
 template <typename R> int closure_tiles_setup();
 int closure_gemm_setup();
 

@@ -165,12 +165,62 @@ __device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---- tensor-memory-accelerator copies of tiles, completed on an mbarrier
+__device__ int g_tile_err = 0;   // set when a tile's bounded wait gave up
+
+__device__ __forceinline__ unsigned sm_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(unsigned long long* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm_u32(b)));
+}
+__device__ __forceinline__ void bar_inval(unsigned long long* b) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(sm_u32(b)));
+}
+__device__ __forceinline__ void bar_expect(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+// one level (z) of a 3-D box at (x, y); x times the element size is a multiple of 16
+__device__ __forceinline__ void tma_level(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(sm_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(sm_u32(b))
+        : "memory");
+}
+// waits (at most ~1 s of SM clock) for phase `parity` of the barrier; on giving up it
+// flags g_tile_err (the host reports OCEAN_ERR_TIMEOUT) and returns
+__device__ __forceinline__ void bar_wait(unsigned long long* b, unsigned parity) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(sm_u32(b)), "r"(parity)
+            : "memory");
+        if (ok) return;
+        if (clock64() - t0 > 2000000000LL) {
+            atomicExch(&g_tile_err, 1);
+            return;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ tracers
 
+// TMA destinations first, each buffer a multiple of 128 bytes: T, S tiles of 14 x 40
+// (rows j0-3 .., columns i0-4 ..; rows 14, 15 unused), u faces 8 x 36 (columns i0 ..,
+// 33 used), v faces 9 x 32
 template <typename R>
-struct TracerSmem {
-    R T[2][TY + 6][TX + 6], S[2][TY + 6][TX + 6];     // anomalies of levels k, k+1, halo 3
-    R us[2][TY][TX + 1], vs[2][TY + 1][TX];           // face velocities of levels k, k+1
+struct __align__(128) TracerSmem {
+    R T[2][TY + 8][TX + 8], S[2][TY + 8][TX + 8];     // anomalies of levels k, k+1
+    R us[2][TY][TX + 4], vs[2][TY + 1][TX];           // face velocities of levels k, k+1
+    unsigned long long bar[2];                        // buffer b's copies have landed
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
     R fxU[TY][TX + 1], fxT[TY][TX + 1], fxS[TY][TX + 1];   // x-face transport and fluxes
@@ -188,7 +238,8 @@ struct TracerSmem {
 // vertical ones reconstruct full values, since the reference varies along the column.
 // tile (bx, by): columns [bx TX, bx TX + TX) x [by TY, by TY + TY)
 template <typename R, bool STEP>
-__device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const int by,
+__device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, const int bx,
+                                            const int by,
                                             const R* __restrict__ u, const R* __restrict__ v,
                                             const R* __restrict__ w, const R* __restrict__ T,
                                             const R* __restrict__ S, R* __restrict__ kap,
@@ -228,26 +279,25 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
     if (kstart >= nz) return;   // the whole patch is land
 
     // ---- the staged tile (halo 3) and the face velocities stream in one level ahead,
-    // double buffered (faces beyond the domain are staged from clamped addresses and
-    // never used: their masks say dry)
-    constexpr int TT = (TY + 6) * (TX + 6), NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
+    // double buffered, as four tensor copies one thread issues per level (rows and
+    // columns beyond the arrays arrive as zeros and feed only threads outside the domain)
+    constexpr int NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
+    constexpr unsigned STAGE_BYTES =
+        (unsigned)sizeof(R) * (2u * 14u * 40u + (unsigned)TY * 36u + (unsigned)(TY + 1) * TX);
+    if (tid == 0) {
+        bar_init(&sm.bar[0]);
+        bar_init(&sm.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
     auto stage = [&](int k, int buf) {
-        for (int q = tid; q < TT; q += NT) {
-            const int a = q / (TX + 6), b = q % (TX + 6);
-            const long c = k * P + tix(g, i0 - 3 + b, j0 - 3 + a);
-            cp_async_el(&sm.T[buf][a][b], &T[c]);
-            cp_async_el(&sm.S[buf][a][b], &S[c]);
+        if (tid == 0) {
+            bar_expect(&sm.bar[buf], STAGE_BYTES);
+            tma_level(&sm.T[buf][0][0], &tm.T, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
+            tma_level(&sm.S[buf][0][0], &tm.S, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
+            tma_level(&sm.us[buf][0][0], &tm.u, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+            tma_level(&sm.vs[buf][0][0], &tm.v, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
         }
-        for (int q = tid; q < NXF + NYF; q += NT) {
-            if (q < NXF) {
-                const int a = q / (TX + 1), b = q % (TX + 1);
-                cp_async_el(&sm.us[buf][a][b], &u[k * P + tix(g, i0 + b, j0 + a)]);
-            } else {
-                const int a = (q - NXF) / TX, b = (q - NXF) % TX;
-                cp_async_el(&sm.vs[buf][a][b], &v[k * P + tix(g, i0 + b, j0 + a)]);
-            }
-        }
-        cp_async_commit();
     };
     stage(kstart, 0);
 
@@ -268,7 +318,10 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
         const int cb = (k - kstart) & 1;
         // ---- level k has landed; start level k+1 into the other buffer (its previous
         // readers finished before this barrier)
-        cp_async_wait_all();
+        bar_wait(&sm.bar[cb], (unsigned)((k - kstart) >> 1) & 1u);
+        // this thread's reads of the other buffer (the previous level) are ordered before
+        // the tensor copy that overwrites it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (k + 1 < nz) stage(k + 1, 1 - cb);
         // own-cell operands of level k, issued before the face work
@@ -302,8 +355,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
 #pragma unroll
                     for (int n = 0; n < 5; ++n) {
                         const int col = ut >= R(0) ? b + n : b + 5 - n;
-                        qT[n] = sm.T[cb][a + 3][col];
-                        qS[n] = sm.S[cb][a + 3][col];
+                        qT[n] = sm.T[cb][a + 3][col + 1];
+                        qS[n] = sm.S[cb][a + 3][col + 1];
                         in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
                     }
                     R rT, rS;
@@ -326,8 +379,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
 #pragma unroll
                     for (int n = 0; n < 5; ++n) {
                         const int row = vt >= R(0) ? a + n : a + 5 - n;
-                        qT[n] = sm.T[cb][row][b + 3];
-                        qS[n] = sm.S[cb][row][b + 3];
+                        qT[n] = sm.T[cb][row][b + 4];
+                        qS[n] = sm.S[cb][row][b + 4];
                         in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
                     }
                     R rT, rS;
@@ -413,6 +466,11 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
             wS[5] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
         }
     }
+    __syncthreads();   // every copy waited for: the barriers can be retired
+    if (tid == 0) {
+        bar_inval(&sm.bar[0]);
+        bar_inval(&sm.bar[1]);
+    }
     if (!STEP || !mine || kb >= nz) return;
     R xT = dTprev, xS = dSprev;   // level nz-1: x = d'
     for (int k = nz - 2; k >= kb; --k) {
@@ -426,15 +484,17 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const int bx, const 
 }
 
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p, const R* __restrict__ u,
+__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p,
+                                               const __grid_constant__ TileMaps tm,
+                                               const R* __restrict__ u,
                                                const R* __restrict__ v, const R* __restrict__ w,
                                                const R* __restrict__ T, const R* __restrict__ S,
                                                R* __restrict__ kap, R* __restrict__ GTp,
                                                R* __restrict__ GSp, R* __restrict__ Tn,
                                                R* __restrict__ Sn, const R* __restrict__ dGT,
                                                const R* __restrict__ dGS) {
-    tracer_tile<R, STEP>(p, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn, Sn, dGT,
-                         dGS);
+    tracer_tile<R, STEP>(p, tm, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn, Sn,
+                         dGT, dGS);
 }
 
 // ------------------------------------------------------------------ momentum
@@ -961,11 +1021,11 @@ template <typename R>
 void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
     if (step)
-        k_tracer<R, true><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
-                                                 b.Tn, b.Sn, b.dGT, b.dGS);
+        k_tracer<R, true><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
+                                                 b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
     else
-        k_tracer<R, false><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
-                                                  b.Tn, b.Sn, b.dGT, b.dGS);
+        k_tracer<R, false><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
+                                                  b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
 }
 
 template <typename R>
@@ -1277,8 +1337,8 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_tracer(
         const EnsItem e = work[it];
         const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        tracer_tile<R, true>(p, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS, b.Tn, b.Sn,
-                             b.dGT, b.dGS);
+        tracer_tile<R, true>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
+                             b.Tn, b.Sn, b.dGT, b.dGS);
     }
 }
 
@@ -1414,6 +1474,17 @@ int setup_kernel_attributes(int nz) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ens_baro_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return (int)e;
+}
+
+// 1 if a tile kernel's bounded wait gave up since the last call (the flag is cleared)
+int tile_wait_failed() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tile_err, sizeof(int)) != cudaSuccess) return 1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tile_err, &z, sizeof(int));
+    }
+    return v;
 }
 
 // ------------------------------------------------------------------ instantiations

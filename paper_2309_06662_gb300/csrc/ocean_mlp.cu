@@ -6,12 +6,9 @@
 // Network (see include/ocean.h): x (6 nz) -> H -> H -> H -> y (3 nz), SiLU after each
 // hidden layer.  Layer weights W [in][out]; the GEMMs read W^T [out][in] in the forward
 // pass and W [in][out] in the backward pass, both kept as BF16 copies of the FP32 master.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
-#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -465,24 +462,11 @@ __global__ void __launch_bounds__(TMA_TH) k_gemm_nt_tma(const __grid_constant__ 
 // tensor map of a row-major BF16 matrix [rows][ld] read K columns wide, boxes of 64
 // columns x TBM rows, 128-byte swizzle; false if the driver refuses it
 bool gemm_tensor_map(CUtensorMap* map, const bf16* ptr, int rows, int K, int ld) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    if (!encode) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
-    const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
-    const cuuint32_t es[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const unsigned long long dims[2] = {(unsigned long long)K, (unsigned long long)rows};
+    const unsigned long long strides[1] = {(unsigned long long)ld * sizeof(bf16)};
+    const unsigned box[2] = {(unsigned)TBK, (unsigned)TBM};
+    return oc_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box,
+                           CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 // Self-test of the bounded wait: a barrier that nothing completes; the wait gives up
