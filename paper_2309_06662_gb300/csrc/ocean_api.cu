@@ -513,13 +513,20 @@ bool build_tile_maps(ocean_t m) {
                                         (unsigned long long)m->nz};
     const unsigned long long strides[2] = {(unsigned long long)m->pitch * m->esz,
                                            (unsigned long long)m->plane * m->esz};
-    const unsigned boxTS[3] = {40, 14, 1}, boxU[3] = {36, 8, 1}, boxV[3] = {32, 9, 1};
+    const unsigned boxTS[3] = {40, 14, 1}, boxU[3] = {36, 8, 1}, boxV[3] = {32, 9, 1},
+                   boxMU[3] = {40, 14, 1}, boxMV[3] = {40, 13, 1}, boxC[3] = {36, 9, 1};
+    const CUtensorMapSwizzle no = CU_TENSOR_MAP_SWIZZLE_NONE;
     for (int c = 0; c < 2; ++c) {
         TileMaps& t = m->tmaps[c];
-        if (!oc_encode_tiled(&t.T, dt, 3, m->T[c], dims, strides, boxTS, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-            !oc_encode_tiled(&t.S, dt, 3, m->S[c], dims, strides, boxTS, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-            !oc_encode_tiled(&t.u, dt, 3, m->u[c], dims, strides, boxU, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-            !oc_encode_tiled(&t.v, dt, 3, m->v[c], dims, strides, boxV, CU_TENSOR_MAP_SWIZZLE_NONE))
+        if (!oc_encode_tiled(&t.T, dt, 3, m->T[c], dims, strides, boxTS, no) ||
+            !oc_encode_tiled(&t.S, dt, 3, m->S[c], dims, strides, boxTS, no) ||
+            !oc_encode_tiled(&t.tu, dt, 3, m->u[c], dims, strides, boxU, no) ||
+            !oc_encode_tiled(&t.tv, dt, 3, m->v[c], dims, strides, boxV, no) ||
+            !oc_encode_tiled(&t.mu, dt, 3, m->u[c], dims, strides, boxMU, no) ||
+            !oc_encode_tiled(&t.mv, dt, 3, m->v[c], dims, strides, boxMV, no) ||
+            !oc_encode_tiled(&t.mp, dt, 3, m->p, dims, strides, boxC, no) ||
+            !oc_encode_tiled(&t.mw, dt, 3, m->w, dims, strides, boxC, no) ||
+            !oc_encode_tiled(&t.mnu, dt, 3, m->nu, dims, strides, boxC, no))
             return false;
     }
     return true;

@@ -184,11 +184,12 @@ template <> struct WenoPair<float> {
 // ----------------------------------------------------------------------- launchers
 // Implemented in ocean_kernels.cu, instantiated for double and float.
 
-// Tensor maps (TMA descriptors) of the fields the tracer tile stages, for one buffer
-// parity: 3-D [nz][ny + 2H][pitch] views of T, S, u, v (boxes: T and S 40 x 14 columns x
-// rows, u 36 x 8, v 32 x 9, one level).
-struct __align__(64) TileMaps {
-    CUtensorMap T, S, u, v;
+// Tensor maps (TMA descriptors) of the fields the tile kernels stage, for one buffer
+// parity: 3-D [nz][ny + 2H][pitch] views, one level per copy.  Tracer: T and S (boxes of
+// 40 x 14 columns x rows), u and v faces (36 x 8, 32 x 9).  Momentum: u (40 x 14), v
+// (40 x 13), pressure, w and nu (36 x 9).
+struct __align__(128) TileMaps {
+    CUtensorMap T, S, tu, tv, mu, mv, mp, mw, mnu;
 };
 
 // Encodes a tiled tensor map through the driver's entry point; false if refused.

@@ -295,8 +295,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             bar_expect(&sm.bar[buf], STAGE_BYTES);
             tma_level(&sm.T[buf][0][0], &tm.T, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
             tma_level(&sm.S[buf][0][0], &tm.S, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
-            tma_level(&sm.us[buf][0][0], &tm.u, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
-            tma_level(&sm.vs[buf][0][0], &tm.v, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+            tma_level(&sm.us[buf][0][0], &tm.tu, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+            tma_level(&sm.vs[buf][0][0], &tm.tv, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
         }
     };
     stage(kstart, 0);
@@ -499,13 +499,17 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p,
 
 // ------------------------------------------------------------------ momentum
 
+// TMA destinations first, each buffer a multiple of 128 bytes; every box starts at the
+// column i0-4 (16-byte aligned), so the logical column c of each array sits at c + 2 (u),
+// c + 1 (v), c + 3 (p, w, nu)
 template <typename R>
-struct MomentumSmem {
-    R u[2][TY + 6][TX + 5];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3); levels k, k+1
-    R v[2][TY + 5][TX + 6];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
-    R p[2][TY + 1][TX + 1];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
-    R w[3][TY + 1][TX + 1];   // w on the bottom faces of levels k, k+1, k+2 (ring), same centres
-    R nu[3][TY + 1][TX + 1];  // nu on those faces
+struct __align__(128) MomentumSmem {
+    R u[2][TY + 8][TX + 8];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3); levels k, k+1
+    R v[2][TY + 8][TX + 8];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
+    R p[2][2 * TY][TX + 4];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
+    R w[3][2 * TY][TX + 4];   // w on the bottom faces of levels k, k+1, k+2 (ring), same centres
+    R nu[3][2 * TY][TX + 4];  // nu on those faces
+    unsigned long long bar[2];   // the copies issued at one level (two levels in flight)
     R z[TY + 5][TX + 5];      // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3)
     R K[TY + 1][TX + 1];      // kinetic energy at the centres
     short kbz[TY + 5][TX + 5], kbzin[TY + 5][TX + 5];
@@ -518,7 +522,7 @@ struct MomentumSmem {
 // sum of the solved column Su = sum dz u**.
 template <typename R, bool STEP>
 __device__ __forceinline__ void momentum_tile(
-    const KP<R>& p, const int bx, const int by, const R* __restrict__ u,
+    const KP<R>& p, const TileMaps& tm, const int bx, const int by, const R* __restrict__ u,
     const R* __restrict__ v, const R* __restrict__ w, const R* __restrict__ pr,
     const R* __restrict__ nu, const R* __restrict__ taux_s, const R* __restrict__ tauy_s,
     R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un, R* __restrict__ vn,
@@ -548,37 +552,32 @@ __device__ __forceinline__ void momentum_tile(
     const int kstart = sm.kmin;
     if (kstart >= nz) return;
 
-    // ---- asynchronous staging: u, v, p of a level into buffer b; w, nu of a level into
-    // ring slot r
-    constexpr int TU = (TY + 6) * (TX + 5), TV = (TY + 5) * (TX + 6), TC = (TY + 1) * (TX + 1);
-    auto stage_uvp = [&](int k, int b) {
-        const long Pk = k * P;
-        for (int q = tid; q < TU; q += NT) {
-            const int a = q / (TX + 5), c = q % (TX + 5);
-            cp_async_el(&sm.u[b][a][c], &u[Pk + tix(g, i0 - 2 + c, j0 - 3 + a)]);
-        }
-        for (int q = tid; q < TV; q += NT) {
-            const int a = q / (TX + 6), c = q % (TX + 6);
-            cp_async_el(&sm.v[b][a][c], &v[Pk + tix(g, i0 - 3 + c, j0 - 2 + a)]);
-        }
-        for (int q = tid; q < TC; q += NT) {
-            const int a = q / (TX + 1), c = q % (TX + 1);
-            cp_async_el(&sm.p[b][a][c], &pr[Pk + tix(g, i0 - 1 + c, j0 - 1 + a)]);
-        }
+    // ---- staging by tensor copies one thread issues: u, v, p of level k+1 into buffer b,
+    // w and nu of level k+2 into ring slot r, all completing on the barrier of the level
+    // that issued them (two levels in flight)
+    constexpr int TC = (TY + 1) * (TX + 1);   // centres of the pressure / w / nu tiles
+    constexpr unsigned UVP = (unsigned)sizeof(R) * (40u * 14u + 40u * 13u + 36u * 9u);
+    constexpr unsigned WNU = (unsigned)sizeof(R) * (2u * 36u * 9u);
+    const int yu = j0 + OC_H - 3, yv = j0 + OC_H - 2, yc = j0 + OC_H - 1;
+    auto copy_uvp = [&](int k, int b, unsigned long long* bar) {
+        tma_level(&sm.u[b][0][0], &tm.mu, i0, yu, k, bar);
+        tma_level(&sm.v[b][0][0], &tm.mv, i0, yv, k, bar);
+        tma_level(&sm.p[b][0][0], &tm.mp, i0, yc, k, bar);
     };
-    auto stage_wnu = [&](int k, int r) {
-        const long Pk = k * P;
-        for (int q = tid; q < TC; q += NT) {
-            const int a = q / (TX + 1), c = q % (TX + 1);
-            const long o = Pk + tix(g, i0 - 1 + c, j0 - 1 + a);
-            cp_async_el(&sm.w[r][a][c], &w[o]);
-            cp_async_el(&sm.nu[r][a][c], &nu[o]);
-        }
+    auto copy_wnu = [&](int k, int r, unsigned long long* bar) {
+        tma_level(&sm.w[r][0][0], &tm.mw, i0, yc, k, bar);
+        tma_level(&sm.nu[r][0][0], &tm.mnu, i0, yc, k, bar);
     };
-    stage_uvp(kstart, 0);
-    stage_wnu(kstart, 0);
-    if (kstart + 1 < nz) stage_wnu(kstart + 1, 1);
-    cp_async_commit();
+    if (tid == 0) {
+        bar_init(&sm.bar[0]);
+        bar_init(&sm.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        bar_expect(&sm.bar[0], UVP + WNU * (kstart + 1 < nz ? 2u : 1u));
+        copy_uvp(kstart, 0, &sm.bar[0]);
+        copy_wnu(kstart, 0, &sm.bar[0]);
+        if (kstart + 1 < nz) copy_wnu(kstart + 1, 1, &sm.bar[0]);
+    }
+    __syncthreads();   // the barriers are initialised before anyone waits on them
 
     const int jr = (mine ? j : 0) + OC_H;
     const R rdxc = p.rdxc[jr], fu = p.fu[jr], fv = p.fv[jr];
@@ -594,11 +593,14 @@ __device__ __forceinline__ void momentum_tile(
         const long Pk = k * P;
         const int cb = (k - kstart) & 1;
         const int rc = (k - kstart) % 3, rn = (rc + 1) % 3, rnn = (rc + 2) % 3;
-        cp_async_wait_all();
+        bar_wait(&sm.bar[cb], (unsigned)((k - kstart) >> 1) & 1u);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();   // level k is in; buffers of the previous level are free
-        if (k + 1 < nz) stage_uvp(k + 1, 1 - cb);
-        if (k + 2 < nz) stage_wnu(k + 2, rnn);
-        cp_async_commit();
+        if (tid == 0 && k + 1 < nz) {
+            bar_expect(&sm.bar[1 - cb], UVP + (k + 2 < nz ? WNU : 0u));
+            copy_uvp(k + 1, 1 - cb, &sm.bar[1 - cb]);
+            if (k + 2 < nz) copy_wnu(k + 2, rnn, &sm.bar[1 - cb]);
+        }
         R uhi = R(0), vhi = R(0), gu0 = R(0), gv0 = R(0);
         if (mine && k + 1 < nz) {
             uhi = u[Pk + P + c2];
@@ -617,8 +619,8 @@ __device__ __forceinline__ void momentum_tile(
                 const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
                 // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
                 // v(i-1, jc) = v[a][b]
-                const R circ = p.dy * (sm.v[cb][a][b + 1] - sm.v[cb][a][b])
-                             - (p.dxc[jrc] * sm.u[cb][a + 1][b] - p.dxc[jrc - 1] * sm.u[cb][a][b]);
+                const R circ = p.dy * (sm.v[cb][a][(b + 1) + 1] - sm.v[cb][a][(b) + 1])
+                             - (p.dxc[jrc] * sm.u[cb][a + 1][(b) + 2] - p.dxc[jrc - 1] * sm.u[cb][a][(b) + 2]);
                 zz = circ * p.rAz[jrc];
             }
             sm.z[a][b] = zz;
@@ -626,8 +628,8 @@ __device__ __forceinline__ void momentum_tile(
         for (int q = tid; q < TC; q += NT) {
             const int a = q / (TX + 1), b = q % (TX + 1);
             // centre (i0-1+b, j0-1+a): u at cols b+1, b+2 of row a+2; v at col b+2, rows a+1, a+2
-            const R ua = sm.u[cb][a + 2][b + 1], ub = sm.u[cb][a + 2][b + 2];
-            const R va = sm.v[cb][a + 1][b + 2], vb = sm.v[cb][a + 2][b + 2];
+            const R ua = sm.u[cb][a + 2][(b + 1) + 2], ub = sm.u[cb][a + 2][(b + 2) + 2];
+            const R va = sm.v[cb][a + 1][(b + 2) + 1], vb = sm.v[cb][a + 2][(b + 2) + 1];
             sm.K[a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
         }
         __syncthreads();
@@ -635,12 +637,12 @@ __device__ __forceinline__ void momentum_tile(
             const R rdz = p.rdz[k];
             const bool du_ = k >= ku, dv_ = k >= kv;
             // ---- the two vorticity reconstructions of this thread
-            const R u0 = sm.u[cb][ty + 3][tx + 2];
-            const R v0 = sm.v[cb][ty + 2][tx + 3];
-            const R vh = R(0.25) * (sm.v[cb][ty + 2][tx + 2] + sm.v[cb][ty + 2][tx + 3]
-                                  + sm.v[cb][ty + 3][tx + 2] + sm.v[cb][ty + 3][tx + 3]);
-            const R uh = R(0.25) * (sm.u[cb][ty + 2][tx + 2] + sm.u[cb][ty + 2][tx + 3]
-                                  + sm.u[cb][ty + 3][tx + 2] + sm.u[cb][ty + 3][tx + 3]);
+            const R u0 = sm.u[cb][ty + 3][(tx + 2) + 2];
+            const R v0 = sm.v[cb][ty + 2][(tx + 3) + 1];
+            const R vh = R(0.25) * (sm.v[cb][ty + 2][(tx + 2) + 1] + sm.v[cb][ty + 2][(tx + 3) + 1]
+                                  + sm.v[cb][ty + 3][(tx + 2) + 1] + sm.v[cb][ty + 3][(tx + 3) + 1]);
+            const R uh = R(0.25) * (sm.u[cb][ty + 2][(tx + 2) + 2] + sm.u[cb][ty + 2][(tx + 3) + 2]
+                                  + sm.u[cb][ty + 3][(tx + 2) + 2] + sm.u[cb][ty + 3][(tx + 3) + 2]);
             R qa[5], qb[5];
             unsigned ina = 0, inb = 0;
 #pragma unroll
@@ -656,12 +658,12 @@ __device__ __forceinline__ void momentum_tile(
             WenoPair<R>::run(qa, qb, ina, inb, p.eps, p.linear, ztu, ztv);
             if (du_) {   // ---------------- u at the west face of column (i, j)
                 const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty + 1][tx]) * rdxc;
-                const R dP = (sm.p[cb][ty + 1][tx + 1] - sm.p[cb][ty + 1][tx]) * rdxc;
+                const R dP = (sm.p[cb][ty + 1][(tx + 1) + 3] - sm.p[cb][ty + 1][(tx) + 3]) * rdxc;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[rn][ty + 1][tx] + sm.w[rn][ty + 1][tx + 1]) * (uhi - u0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[rn][ty + 1][(tx) + 3] + sm.w[rn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
                 if (k - 1 >= ku)
-                    dn = R(0.5) * (sm.w[rc][ty + 1][tx] + sm.w[rc][ty + 1][tx + 1]) * (u0 - ulo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[rc][ty + 1][(tx) + 3] + sm.w[rc][ty + 1][(tx + 1) + 3]) * (u0 - ulo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? taux_s[c2] : R(0);
                 const R G = (ztu + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -674,9 +676,9 @@ __device__ __forceinline__ void momentum_tile(
                     sGU += p.dz[k] * gh;
                     const R us = u0 + p.dt * gh;
                     const R lo = k > ku
-                        ? p.dt * R(0.5) * (sm.nu[rc][ty + 1][tx] + sm.nu[rc][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rc][ty + 1][(tx) + 3] + sm.nu[rc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[rn][ty + 1][tx] + sm.nu[rn][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rn][ty + 1][(tx) + 3] + sm.nu[rn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
@@ -686,12 +688,12 @@ __device__ __forceinline__ void momentum_tile(
             }
             if (dv_) {   // ---------------- v at the south face of column (i, j)
                 const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty][tx + 1]) * p.rdy;
-                const R dP = (sm.p[cb][ty + 1][tx + 1] - sm.p[cb][ty][tx + 1]) * p.rdy;
+                const R dP = (sm.p[cb][ty + 1][(tx + 1) + 3] - sm.p[cb][ty][(tx + 1) + 3]) * p.rdy;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[rn][ty][tx + 1] + sm.w[rn][ty + 1][tx + 1]) * (vhi - v0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[rn][ty][(tx + 1) + 3] + sm.w[rn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
                 if (k - 1 >= kv)
-                    dn = R(0.5) * (sm.w[rc][ty][tx + 1] + sm.w[rc][ty + 1][tx + 1]) * (v0 - vlo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[rc][ty][(tx + 1) + 3] + sm.w[rc][ty + 1][(tx + 1) + 3]) * (v0 - vlo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
                 const R G = -(ztv + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -704,9 +706,9 @@ __device__ __forceinline__ void momentum_tile(
                     sGV += p.dz[k] * gh;
                     const R vs = v0 + p.dt * gh;
                     const R lo = k > kv
-                        ? p.dt * R(0.5) * (sm.nu[rc][ty][tx + 1] + sm.nu[rc][ty + 1][tx + 1]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rc][ty][(tx + 1) + 3] + sm.nu[rc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[rn][ty][tx + 1] + sm.nu[rn][ty + 1][tx + 1]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[rn][ty][(tx + 1) + 3] + sm.nu[rn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
@@ -718,7 +720,11 @@ __device__ __forceinline__ void momentum_tile(
             vlo = v0;
         }
     }
-    cp_async_wait_all();
+    __syncthreads();   // every copy waited for: the barriers can be retired
+    if (tid == 0) {
+        bar_inval(&sm.bar[0]);
+        bar_inval(&sm.bar[1]);
+    }
     if (!STEP || !mine) return;
     if (ku < nz) {
         R x = duk;   // level nz-1
@@ -750,14 +756,15 @@ __device__ __forceinline__ void momentum_tile(
 
 template <typename R, bool STEP>
 __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
-    KP<R> p, const R* __restrict__ u, const R* __restrict__ v, const R* __restrict__ w,
+    KP<R> p, const __grid_constant__ TileMaps tm, const R* __restrict__ u,
+    const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
     const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
     R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
     R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
     R* __restrict__ Sv) {
-    momentum_tile<R, STEP>(p, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s, Gup, Gvp,
-                           un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
+    momentum_tile<R, STEP>(p, tm, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s, Gup,
+                           Gvp, un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
 }
 
 // ------------------------------------------------------------------ barotropic mode
@@ -1032,11 +1039,11 @@ template <typename R>
 void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
     if (step)
-        k_momentum<R, true><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
+        k_momentum<R, true><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
                                                    b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
                                                    b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
     else
-        k_momentum<R, false><<<grid, block, 0, s>>>(p, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
+        k_momentum<R, false><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
                                                     b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
                                                     b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
 }
@@ -1351,7 +1358,7 @@ __global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_momentum(
         const EnsItem e = work[it];
         const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        momentum_tile<R, true>(p, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
+        momentum_tile<R, true>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
                                b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
     }
 }
