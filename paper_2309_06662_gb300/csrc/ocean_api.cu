@@ -514,7 +514,8 @@ bool build_tile_maps(ocean_t m) {
     const unsigned long long strides[2] = {(unsigned long long)m->pitch * m->esz,
                                            (unsigned long long)m->plane * m->esz};
     const unsigned boxTS[3] = {40, 14, 1}, boxU[3] = {36, 8, 1}, boxV[3] = {32, 9, 1},
-                   boxMU[3] = {40, 14, 1}, boxMV[3] = {40, 13, 1}, boxC[3] = {36, 9, 1};
+                   boxMU[3] = {40, 14, 1}, boxMV[3] = {40, 13, 1}, boxC[3] = {36, 9, 1},
+                   boxO[3] = {32, 8, 1};
     const CUtensorMapSwizzle no = CU_TENSOR_MAP_SWIZZLE_NONE;
     for (int c = 0; c < 2; ++c) {
         TileMaps& t = m->tmaps[c];
@@ -522,6 +523,10 @@ bool build_tile_maps(ocean_t m) {
             !oc_encode_tiled(&t.S, dt, 3, m->S[c], dims, strides, boxTS, no) ||
             !oc_encode_tiled(&t.tu, dt, 3, m->u[c], dims, strides, boxU, no) ||
             !oc_encode_tiled(&t.tv, dt, 3, m->v[c], dims, strides, boxV, no) ||
+            !oc_encode_tiled(&t.tw, dt, 3, m->w, dims, strides, boxO, no) ||
+            !oc_encode_tiled(&t.tk, dt, 3, m->kap, dims, strides, boxO, no) ||
+            !oc_encode_tiled(&t.tgt, dt, 3, m->GT, dims, strides, boxO, no) ||
+            !oc_encode_tiled(&t.tgs, dt, 3, m->GS, dims, strides, boxO, no) ||
             !oc_encode_tiled(&t.mu, dt, 3, m->u[c], dims, strides, boxMU, no) ||
             !oc_encode_tiled(&t.mv, dt, 3, m->v[c], dims, strides, boxMV, no) ||
             !oc_encode_tiled(&t.mp, dt, 3, m->p, dims, strides, boxC, no) ||

@@ -220,6 +220,7 @@ template <typename R>
 struct __align__(128) TracerSmem {
     R T[2][TY + 8][TX + 8], S[2][TY + 8][TX + 8];     // anomalies of levels k, k+1
     R us[2][TY][TX + 4], vs[2][TY + 1][TX];           // face velocities of levels k, k+1
+    R own[2][4][TY][TX];                              // own columns: w(k+1), kap(k+1), G_T(k), G_S(k)
     unsigned long long bar[2];                        // buffer b's copies have landed
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
@@ -284,19 +285,30 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     constexpr int NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
     constexpr unsigned STAGE_BYTES =
         (unsigned)sizeof(R) * (2u * 14u * 40u + (unsigned)TY * 36u + (unsigned)(TY + 1) * TX);
+    constexpr unsigned OWN_BYTES = (unsigned)sizeof(R) * TY * TX;
     if (tid == 0) {
         bar_init(&sm.bar[0]);
         bar_init(&sm.bar[1]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    // with the own columns' operands of the level: w and the diffusivity on its top face
+    // (level k+1, when there is one), and with STEP G_T and G_S of the previous step
     auto stage = [&](int k, int buf) {
         if (tid == 0) {
-            bar_expect(&sm.bar[buf], STAGE_BYTES);
+            const bool top = k + 1 < nz;
+            const unsigned n_own = (top ? 1u : 0u) + (STEP ? (top ? 1u : 0u) + 2u : 0u);
+            bar_expect(&sm.bar[buf], STAGE_BYTES + n_own * OWN_BYTES);
             tma_level(&sm.T[buf][0][0], &tm.T, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
             tma_level(&sm.S[buf][0][0], &tm.S, i0, j0 + OC_H - 3, k, &sm.bar[buf]);
             tma_level(&sm.us[buf][0][0], &tm.tu, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
             tma_level(&sm.vs[buf][0][0], &tm.tv, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+            if (top) tma_level(&sm.own[buf][0][0][0], &tm.tw, i0 + OC_H, j0 + OC_H, k + 1, &sm.bar[buf]);
+            if (STEP) {
+                if (top) tma_level(&sm.own[buf][1][0][0], &tm.tk, i0 + OC_H, j0 + OC_H, k + 1, &sm.bar[buf]);
+                tma_level(&sm.own[buf][2][0][0], &tm.tgt, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+                tma_level(&sm.own[buf][3][0][0], &tm.tgs, i0 + OC_H, j0 + OC_H, k, &sm.bar[buf]);
+            }
         }
     };
     stage(kstart, 0);
@@ -312,6 +324,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         wS[q] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
     }
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
+    R kcarry = R(0);   // diffusivity on the top face of the previous level
 
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
@@ -324,23 +337,24 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (k + 1 < nz) stage(k + 1, 1 - cb);
-        // own-cell operands of level k, issued before the face work
+        // own-cell operands of level k, from the staged buffers; the diffusivity on the
+        // bottom face is the previous level's top one (read before this level rewrites it)
         const bool live = mine && k >= kb;
         const long ck = Pk + c2;
-        R wt = R(0), k0 = R(0), k1 = R(0), gT0 = R(0), gS0 = R(0), T0 = R(0), S0 = R(0);
+        R wt = R(0), k0 = kcarry, k1 = R(0), gT0 = R(0), gS0 = R(0), T0 = R(0), S0 = R(0);
         if (live) {
             if (k + 1 < nz) {
-                wt = w[ck + P];
-                if (STEP) k1 = kap[ck + P];
+                wt = sm.own[cb][0][ty][tx];
+                if (STEP) k1 = sm.own[cb][1][ty][tx];
             }
             if (STEP) {
-                k0 = kap[ck];
-                gT0 = GTp[ck];
-                gS0 = GSp[ck];
-                T0 = T[ck];
-                S0 = S[ck];
+                gT0 = sm.own[cb][2][ty][tx];
+                gS0 = sm.own[cb][3][ty][tx];
+                T0 = sm.T[cb][ty + 3][tx + 4];
+                S0 = sm.S[cb][ty + 3][tx + 4];
             }
         }
+        kcarry = k1;
         const R dzk = p.dz[k];
         // ---- x- and y-face fluxes, each face once (one job list, so that no warp does
         // more than one job beyond the others)
