@@ -486,14 +486,28 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         bar_inval(&sm.bar[1]);
     }
     if (!STEP || !mine || kb >= nz) return;
+    // back substitution down the column, the coefficients of four levels loaded at once
+    // (the recurrence itself is serial)
     R xT = dTprev, xS = dSprev;   // level nz-1: x = d'
-    for (int k = nz - 2; k >= kb; --k) {
-        const long ck = k * P + c2;
-        const R cc = kap[ck];
-        xT = Tn[ck] - cc * xT;
-        xS = Sn[ck] - cc * xS;
-        Tn[ck] = xT;
-        Sn[ck] = xS;
+    for (int k = nz - 2; k >= kb; k -= 4) {
+        R cc[4], tq[4], sq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k - q) * P + c2;
+            const bool in = k - q >= kb;
+            cc[q] = in ? kap[ck] : R(0);
+            tq[q] = in ? Tn[ck] : R(0);
+            sq[q] = in ? Sn[ck] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (k - q < kb) break;
+            const long ck = (long)(k - q) * P + c2;
+            xT = tq[q] - cc[q] * xT;
+            xS = sq[q] - cc[q] * xS;
+            Tn[ck] = xT;
+            Sn[ck] = xS;
+        }
     }
 }
 
@@ -740,28 +754,36 @@ __device__ __forceinline__ void momentum_tile(
         bar_inval(&sm.bar[1]);
     }
     if (!STEP || !mine) return;
-    if (ku < nz) {
-        R x = duk;   // level nz-1
+    // back substitutions down the column, four levels' coefficients loaded at once
+    auto back = [&](R x, int kf, R* __restrict__ xn, const R* __restrict__ cx) {
         R s = p.dz[nz - 1] * x;
-        for (int k = nz - 2; k >= ku; --k) {
-            const long ck = k * P + c2;
-            x = un[ck] - cu[ck] * x;
-            un[ck] = x;
-            s += p.dz[k] * x;
+        for (int k = nz - 2; k >= kf; k -= 4) {
+            R cq[4], dq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long ck = (long)(k - q) * P + c2;
+                const bool in = k - q >= kf;
+                cq[q] = in ? cx[ck] : R(0);
+                dq[q] = in ? xn[ck] : R(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (k - q < kf) break;
+                x = dq[q] - cq[q] * x;
+                xn[(long)(k - q) * P + c2] = x;
+                s += p.dz[k - q] * x;
+            }
         }
+        return s;
+    };
+    if (ku < nz) {
+        const R s = back(duk, ku, un, cu);   // from level nz-1
         Un[c2] = sUn;
         GU[c2] = sGU;
         Su[c2] = s;
     }
     if (kv < nz) {
-        R x = dvk;
-        R s = p.dz[nz - 1] * x;
-        for (int k = nz - 2; k >= kv; --k) {
-            const long ck = k * P + c2;
-            x = vn[ck] - cv[ck] * x;
-            vn[ck] = x;
-            s += p.dz[k] * x;
-        }
+        const R s = back(dvk, kv, vn, cv);
         Vn[c2] = sVn;
         GV[c2] = sGV;
         Sv[c2] = s;
@@ -997,10 +1019,10 @@ __global__ void k_baro_end(KP<R> p, double* eta, const double* __restrict__ accE
                     Vn, Su, Sv, rHu, rHv, corrU, corrV, rns);
 }
 
-// The correction is a read-modify-write of u and v over the whole water column; a
-// column is split into slabs of CORR_SLAB levels so that more independent loads are in
-// flight than one thread per column would issue.
-constexpr int CORR_SLAB = 8;
+// The correction is a read-modify-write of u and v over the whole water column, split
+// into slabs of CORR_SLAB levels (one slab for the usual column depths: thinner slabs
+// measured slower at 1/12 degree, each re-reading the column's masks and corrections).
+constexpr int CORR_SLAB = 64;
 
 template <typename R>
 __device__ __forceinline__ void correct_col(const KP<R>& p, const long c, const int slab,
