@@ -66,16 +66,29 @@ __device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* 
     const int kb = g.kb[c2], nz = g.nz;
     if (kb >= nz) return;
     const long P = g.plane;
-    // pressure anomaly, integrated downward from the surface
+    // pressure anomaly, integrated downward from the surface (T and S of four levels
+    // loaded at once; the recurrence is serial)
     R bup = buoy_anom(p, T[(nz - 1) * P + c2], S[(nz - 1) * P + c2]);
     R pk = -rmul(bup, p.ptop);
     pr[(nz - 1) * P + c2] = pk;
 #pragma unroll 1
-    for (int k = nz - 2; k >= kb; --k) {
-        R bk = buoy_anom(p, T[k * P + c2], S[k * P + c2]);
-        pk = fma(-rmul(R(0.5), bk + bup), p.dzf[k + 1], pk);
-        pr[k * P + c2] = pk;
-        bup = bk;
+    for (int k4 = nz - 2; k4 >= kb; k4 -= 4) {
+        R tq[4], sq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = k4 - q >= kb;
+            tq[q] = in ? T[(long)(k4 - q) * P + c2] : R(0);
+            sq[q] = in ? S[(long)(k4 - q) * P + c2] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k4 - q;
+            if (k < kb) break;
+            R bk = buoy_anom(p, tq[q], sq[q]);
+            pk = fma(-rmul(R(0.5), bk + bup), p.dzf[k + 1], pk);
+            pr[k * P + c2] = pk;
+            bup = bk;
+        }
     }
     // one upward sweep: w on the bottom faces, integrated from the sea floor, and the
     // Richardson-number closure on the interior faces, from the levels k-1 (kept in
@@ -84,37 +97,54 @@ __device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* 
     R wk = R(0);
     w[kb * P + c2] = wk;
     R Tm = R(0), Sm = R(0), ub = R(0), vb = R(0);
-    for (int k = kb; k < nz; ++k) {
-        const long ck = k * P + c2;
-        const R Tk = T[ck], Sk = S[ck];
-        const R u0 = u[ck], u1 = u[ck + 1], v0 = v[ck], v1 = v[ck + g.pitch];
-        if (k < nz - 1) {
-            R div = dy * p.dz[k] * (u1 - u0) + p.dz[k] * (dxvN * v1 - dxvS * v0);
-            wk = wk - div * rac;
-            w[ck + P] = wk;
+    for (int k4 = kb; k4 < nz; k4 += 4) {
+        R Tq[4], Sq[4], u0q[4], u1q[4], v0q[4], v1q[4];   // four levels' operands at once
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k4 + q) * P + c2;
+            const bool in = k4 + q < nz;
+            Tq[q] = in ? T[ck] : R(0);
+            Sq[q] = in ? S[ck] : R(0);
+            u0q[q] = in ? u[ck] : R(0);
+            u1q[q] = in ? u[ck + 1] : R(0);
+            v0q[q] = in ? v[ck] : R(0);
+            v1q[q] = in ? v[ck + g.pitch] : R(0);
         }
-        const R ua = R(0.5) * (u0 + u1), va = R(0.5) * (v0 + v1);
-        if (k > kb) {
-            R rz = p.rdzf[k];
-            R n2 = p.grav * (p.alpha * ((Tk - Tm) + p.dTref[k])
-                             - p.beta_s * ((Sk - Sm) + p.dSref[k])) * rz;
-            R s2 = ((ua - ub) * (ua - ub) + (va - vb) * (va - vb)) * rz * rz;
-            R kk, nn;
-            if (n2 < R(0)) {
-                kk = p.kappa_conv; nn = p.kappa_conv;
-            } else {
-                R ri = n2 / (s2 > R(1e-14) ? s2 : R(1e-14));
-                R q = R(1) + p.ri_a * ri;
-                nn = p.nu0 / (q * q) + p.nu_b;
-                kk = nn / q + p.kappa_b;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k4 + q;
+            if (k >= nz) break;
+            const long ck = k * P + c2;
+            const R Tk = Tq[q], Sk = Sq[q];
+            const R u0 = u0q[q], u1 = u1q[q], v0 = v0q[q], v1 = v1q[q];
+            if (k < nz - 1) {
+                R div = dy * p.dz[k] * (u1 - u0) + p.dz[k] * (dxvN * v1 - dxvS * v0);
+                wk = wk - div * rac;
+                w[ck + P] = wk;
             }
-            kap[ck] = kk;
-            nu[ck] = nn;
+            const R ua = R(0.5) * (u0 + u1), va = R(0.5) * (v0 + v1);
+            if (k > kb) {
+                R rz = p.rdzf[k];
+                R n2 = p.grav * (p.alpha * ((Tk - Tm) + p.dTref[k])
+                                 - p.beta_s * ((Sk - Sm) + p.dSref[k])) * rz;
+                R s2 = ((ua - ub) * (ua - ub) + (va - vb) * (va - vb)) * rz * rz;
+                R kk, nn;
+                if (n2 < R(0)) {
+                    kk = p.kappa_conv; nn = p.kappa_conv;
+                } else {
+                    R ri = n2 / (s2 > R(1e-14) ? s2 : R(1e-14));
+                    R qr = R(1) + p.ri_a * ri;
+                    nn = p.nu0 / (qr * qr) + p.nu_b;
+                    kk = nn / qr + p.kappa_b;
+                }
+                kap[ck] = kk;
+                nu[ck] = nn;
+            }
+            Tm = Tk;
+            Sm = Sk;
+            ub = ua;
+            vb = va;
         }
-        Tm = Tk;
-        Sm = Sk;
-        ub = ua;
-        vb = va;
     }
 }
 
