@@ -20,7 +20,6 @@ reference` times the CPU oracle instead, on a bounded window of the same workloa
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
@@ -38,14 +37,7 @@ import numpy as np  # noqa: E402
 
 from paper_2309_06662_gb300 import inputs, metrics, roofline  # noqa: E402
 
-WORKLOADS = {
-    "latlon_12th": (inputs.latlon_12th_case, "latlon_1/12deg_4320x1680x48"),
-    "latlon_quarter": (inputs.latlon_quarter_case, "latlon_1/4deg_1440x560x48"),
-    "latlon_1deg": (inputs.latlon_1deg_case, "latlon_1deg_360x160x32"),
-    "box": (inputs.box_case, "box_32x32x8"),
-    "ensemble96": (lambda: inputs.ensemble_cases(96, seed=5), "ensemble_96_basins"),
-    "learned_half": (inputs.latlon_half_case, "latlon_1/2deg_720x320x48_learned_closure"),
-}
+WORKLOADS = inputs.WORKLOADS
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -79,14 +71,6 @@ def measured_tensor_peak():
         if "bf16_tflops" in d:
             return float(d["bf16_tflops"]), "measured bf16_tflops (burst)"
     return 1900.0, "fallback 1.9 PFLOP/s bf16"
-
-
-def source_digest() -> str:
-    h = hashlib.sha256()
-    for name in ("ocean_kernels.cu", "ocean_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2309_06662_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -526,7 +510,7 @@ def main():
     algo = roofline.KERNEL_WORDS[top] * esz * wet
     achieved = algo / (top_ms / 1e3) / 1e9
     traffic = roofline.load_traffic(os.path.join(ROOT, "profiles", "traffic.txt"), wname,
-                                    source_digest())
+                                    roofline.source_digest())
     tr = traffic.get(top) * wet if traffic and top in traffic else None
     step_bytes = roofline.STEP_WORDS_PER_CELL * esz * wet + \
         roofline.barotropic_bytes_per_column(esz, int(p["n_substeps"])) * wet_cols

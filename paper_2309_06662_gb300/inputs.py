@@ -429,3 +429,14 @@ def ensemble_cases(count: int = 96, seed: int = 5, n_lo: int = 32, n_hi: int = 5
         nz = int(levels[int(u[2] * len(levels))])
         out.append(ensemble_member_case(s, nx, ny, nz, 0.05 + 0.15 * u[3], 10.0 + 10.0 * u[4]))
     return out
+
+
+# the benchmark's workloads: name -> (case constructor, workload label)
+WORKLOADS = {
+    "latlon_12th": (latlon_12th_case, "latlon_1/12deg_4320x1680x48"),
+    "latlon_quarter": (latlon_quarter_case, "latlon_1/4deg_1440x560x48"),
+    "latlon_1deg": (latlon_1deg_case, "latlon_1deg_360x160x32"),
+    "box": (box_case, "box_32x32x8"),
+    "ensemble96": (lambda: ensemble_cases(96, seed=5), "ensemble_96_basins"),
+    "learned_half": (latlon_half_case, "latlon_1/2deg_720x320x48_learned_closure"),
+}

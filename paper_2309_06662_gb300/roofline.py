@@ -11,6 +11,7 @@ words per cell, plus the 2-D barotropic state once per step.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 from typing import Dict, Optional
@@ -70,3 +71,13 @@ def load_traffic(path: str, workload: str, source_digest: str) -> Optional[Dict[
                 if d.get("workload") == workload and d.get("source_digest") == source_digest:
                     return d.get("bytes_per_wet_cell")
     return None
+
+
+def source_digest() -> str:
+    """Digest of the 3-D kernels' source: a traffic figure taken on other source is stale."""
+    h = hashlib.sha256()
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for name in ("ocean_kernels.cu", "ocean_internal.cuh"):
+        with open(os.path.join(here, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
