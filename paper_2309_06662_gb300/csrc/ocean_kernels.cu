@@ -168,6 +168,10 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
 // the same thread, so they stay in L2), which keeps shared memory small and occupancy
 // bounded by registers only.
 constexpr int TX = 32, TY = 8, NT = TX * TY;
+// The tracer block has one more warp: its 8 x 33 x-faces and 9 x 32 y-faces (552 WENO
+// pairs per level) then take two rounds of 288 threads instead of three of 256; the
+// extra warp owns no column and only computes faces.
+constexpr int TTY = TY + 1, NTT = TX * TTY;
 // resident blocks per SM the register budget is sized for (FP64 needs more registers)
 template <typename R> struct TileOcc { static constexpr int value = 3; };
 template <> struct TileOcc<double> { static constexpr int value = 1; };
@@ -284,20 +288,20 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int i = i0 + tx, j = j0 + ty;
-    const bool mine = i < g.nx && j < g.ny;
+    const bool mine = ty < TY && i < g.nx && j < g.ny;
     const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
     // ---- 2-D masks of the patch, and the lowest wet level of the whole patch
     if (tid == 0) sm.kmin = nz;
-    for (int q = tid; q < (TY + 6) * (TX + 6); q += NT) {
+    for (int q = tid; q < (TY + 6) * (TX + 6); q += NTT) {
         const int a = q / (TX + 6), b = q % (TX + 6);
         sm.kb[a][b] = g.kb[tix(g, i0 - 3 + b, j0 - 3 + a)];
     }
-    for (int q = tid; q < TY * (TX + 1); q += NT) {
+    for (int q = tid; q < TY * (TX + 1); q += NTT) {
         const int a = q / (TX + 1), b = q % (TX + 1);
         const int fi = i0 + b, fj = j0 + a;
         sm.kbu[a][b] = (fi <= g.nx && fj < g.ny) ? g.kbu[ix2(g, fi, fj)] : (short)nz;
     }
-    for (int q = tid; q < (TY + 1) * TX; q += NT) {
+    for (int q = tid; q < (TY + 1) * TX; q += NTT) {
         const int a = q / TX, b = q % TX;
         const int fi = i0 + b, fj = j0 + a;
         sm.kbv[a][b] = (fi < g.nx && fj <= g.ny) ? g.kbv[ix2(g, fi, fj)] : (short)nz;
@@ -388,7 +392,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         const R dzk = p.dz[k];
         // ---- x- and y-face fluxes, each face once (one job list, so that no warp does
         // more than one job beyond the others)
-        for (int q = tid; q < NXF + NYF; q += NT) {
+        for (int q = tid; q < NXF + NYF; q += NTT) {
             if (q < NXF) {
                 const int a = q / (TX + 1), b = q % (TX + 1);
                 R fU = R(0), fT = R(0), fS = R(0);
@@ -542,7 +546,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
 }
 
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_tracer(KP<R> p,
+__global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_tracer(KP<R> p,
                                                const __grid_constant__ TileMaps tm,
                                                const R* __restrict__ u,
                                                const R* __restrict__ v, const R* __restrict__ w,
@@ -1092,7 +1096,7 @@ void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
 
 template <typename R>
 void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
-    const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
+    const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TTY);
     if (step)
         k_tracer<R, true><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
                                                  b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
@@ -1402,7 +1406,7 @@ __global__ void __launch_bounds__(TPB) k_ens_diag(const EnsMember<R>* __restrict
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_tracer(
+__global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_ens_tracer(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
@@ -1503,7 +1507,7 @@ int ens_blocks_per_sm(int kind) {
     cudaError_t e = cudaSuccess;
     switch (kind) {
         case ENS_DIAG: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_diag<R>, TPB, 0); break;
-        case ENS_TRACER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_tracer<R>, NT, 0); break;
+        case ENS_TRACER: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_tracer<R>, NTT, 0); break;
         case ENS_MOMENTUM: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_momentum<R>, NT, 0); break;
         case ENS_BARO_BEGIN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_baro_begin<R>, TPB, 0); break;
         case ENS_BARO_PASS:
@@ -1524,7 +1528,7 @@ void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwor
     const dim3 tile(TX, TY);
     switch (kind) {
         case ENS_DIAG: k_ens_diag<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
-        case ENS_TRACER: k_ens_tracer<R><<<grid, tile, 0, s>>>(mem, work, nwork, counter); break;
+        case ENS_TRACER: k_ens_tracer<R><<<grid, dim3(TX, TTY), 0, s>>>(mem, work, nwork, counter); break;
         case ENS_MOMENTUM: k_ens_momentum<R><<<grid, tile, 0, s>>>(mem, work, nwork, counter); break;
         case ENS_BARO_BEGIN: k_ens_baro_begin<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
         case ENS_BARO_PASS:
