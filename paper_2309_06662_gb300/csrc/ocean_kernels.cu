@@ -252,14 +252,15 @@ __device__ __forceinline__ void bar_wait(unsigned long long* b, unsigned parity)
 // 33 used), v faces 9 x 32
 template <typename R>
 struct __align__(128) TracerSmem {
-    R T[2][TY + 8][TX + 8], S[2][TY + 8][TX + 8];     // anomalies of levels k, k+1
-    R us[2][TY][TX + 4], vs[2][TY + 1][TX];           // face velocities of levels k, k+1
-    R own[2][4][TY][TX];                              // own columns: w(k+1), kap(k+1), G_T(k), G_S(k)
-    unsigned long long bar[2];                        // buffer b's copies have landed
+    R T[3][TY + 8][TX + 8], S[3][TY + 8][TX + 8];     // anomalies of levels k, k+1, k+2
+    R us[3][TY][TX + 4], vs[3][TY + 1][TX];           // face velocities of those levels
+    R own[3][4][TY][TX];                              // own columns: w(k+1), kap(k+1), G_T(k), G_S(k)
+    unsigned long long bar[3];                        // buffer b's copies have landed
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
-    R fxU[TY][TX + 1], fxT[TY][TX + 1], fxS[TY][TX + 1];   // x-face transport and fluxes
-    R fyV[TY + 1][TX], fyT[TY + 1][TX], fyS[TY + 1][TX];   // y-face transport and fluxes
+    // x- and y-face transport and fluxes of levels k (even) and k+1 (odd)
+    R fxU[2][TY][TX + 1], fxT[2][TY][TX + 1], fxS[2][TY][TX + 1];
+    R fyV[2][TY + 1][TX], fyT[2][TY + 1][TX], fyS[2][TY + 1][TX];
     int kmin;
 };
 
@@ -313,9 +314,9 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     const int kstart = sm.kmin;
     if (kstart >= nz) return;   // the whole patch is land
 
-    // ---- the staged tile (halo 3) and the face velocities stream in one level ahead,
-    // double buffered, as four tensor copies one thread issues per level (rows and
-    // columns beyond the arrays arrive as zeros and feed only threads outside the domain)
+    // ---- the staged tile (halo 3) and the face velocities stream in two levels ahead,
+    // triple buffered, as tensor copies one thread issues per level (rows and columns
+    // beyond the arrays arrive as zeros and feed only threads outside the domain)
     constexpr int NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
     constexpr unsigned STAGE_BYTES =
         (unsigned)sizeof(R) * (2u * 14u * 40u + (unsigned)TY * 36u + (unsigned)(TY + 1) * TX);
@@ -323,6 +324,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     if (tid == 0) {
         bar_init(&sm.bar[0]);
         bar_init(&sm.bar[1]);
+        bar_init(&sm.bar[2]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -346,6 +348,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         }
     };
     stage(kstart, 0);
+    if (kstart + 1 < nz) stage(kstart + 1, 1);
 
     const R rac = p.rAc[(mine ? j : 0) + OC_H];
     // register window of full values at levels k-2 .. k+3 (0 outside the column)
@@ -360,17 +363,14 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
     R kcarry = R(0);   // diffusivity on the top face of the previous level
 
+    // One block barrier per level: the faces of level k go to face buffer k & 1, so a
+    // warp that has finished level k-1 computes level k's faces while others still read
+    // level k-1's; the barrier after the faces publishes them and frees the staging
+    // buffer of level k-1 (read by every thread before it), which takes level k+2.
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        const int cb = (k - kstart) & 1;
-        // ---- level k has landed; start level k+1 into the other buffer (its previous
-        // readers finished before this barrier)
-        bar_wait(&sm.bar[cb], (unsigned)((k - kstart) >> 1) & 1u);
-        // this thread's reads of the other buffer (the previous level) are ordered before
-        // the tensor copy that overwrites it
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (k + 1 < nz) stage(k + 1, 1 - cb);
+        const int lv = k - kstart, cb = lv % 3, fb = lv & 1;
+        bar_wait(&sm.bar[cb], (unsigned)(lv / 3) & 1u);
         // own-cell operands of level k, from the staged buffers; the diffusivity on the
         // bottom face is the previous level's top one (read before this level rewrites it)
         const bool live = mine && k >= kb;
@@ -413,9 +413,9 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                     fT = fU * rT;
                     fS = fU * rS;
                 }
-                sm.fxU[a][b] = fU;
-                sm.fxT[a][b] = fT;
-                sm.fxS[a][b] = fS;
+                sm.fxU[fb][a][b] = fU;
+                sm.fxT[fb][a][b] = fT;
+                sm.fxS[fb][a][b] = fS;
             } else {
                 const int a = (q - NXF) / TX, b = (q - NXF) % TX;
                 R fV = R(0), fT = R(0), fS = R(0);
@@ -437,12 +437,16 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                     fT = fV * rT;
                     fS = fV * rS;
                 }
-                sm.fyV[a][b] = fV;
-                sm.fyT[a][b] = fT;
-                sm.fyS[a][b] = fS;
+                sm.fyV[fb][a][b] = fV;
+                sm.fyT[fb][a][b] = fT;
+                sm.fyS[fb][a][b] = fS;
             }
         }
+        // this thread's reads of level k-1's staging buffer (faces and own cell, before
+        // this point) are ordered before the tensor copy that overwrites it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
+        if (k + 2 < nz) stage(k + 2, (lv + 2) % 3);
         // ---- own cell
         if (live) {
             R ftT = R(0), ftS = R(0);
@@ -465,9 +469,9 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                 ftS = wt * rS;
             }
             const R rdz = p.rdz[k];
-            const R divU = sm.fxU[ty][tx + 1] - sm.fxU[ty][tx] + sm.fyV[ty + 1][tx] - sm.fyV[ty][tx];
-            const R hT = sm.fxT[ty][tx + 1] - sm.fxT[ty][tx] + sm.fyT[ty + 1][tx] - sm.fyT[ty][tx];
-            const R hS = sm.fxS[ty][tx + 1] - sm.fxS[ty][tx] + sm.fyS[ty + 1][tx] - sm.fyS[ty][tx];
+            const R divU = sm.fxU[fb][ty][tx + 1] - sm.fxU[fb][ty][tx] + sm.fyV[fb][ty + 1][tx] - sm.fyV[fb][ty][tx];
+            const R hT = sm.fxT[fb][ty][tx + 1] - sm.fxT[fb][ty][tx] + sm.fyT[fb][ty + 1][tx] - sm.fyT[fb][ty][tx];
+            const R hS = sm.fxS[fb][ty][tx + 1] - sm.fxS[fb][ty][tx] + sm.fyS[fb][ty + 1][tx] - sm.fyS[fb][ty][tx];
             R GT = -((p.Tref[k] * divU + hT) * rac + (ftT - fzT)) * rdz;
             R GS = -((p.Sref[k] * divU + hS) * rac + (ftS - fzS)) * rdz;
             if (dGT) {   // learned-closure corrections, part of G^n
@@ -518,6 +522,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     if (tid == 0) {
         bar_inval(&sm.bar[0]);
         bar_inval(&sm.bar[1]);
+        bar_inval(&sm.bar[2]);
     }
     if (!STEP || !mine || kb >= nz) return;
     // back substitution down the column, the coefficients of four levels loaded at once
