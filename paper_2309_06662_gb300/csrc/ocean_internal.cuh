@@ -164,11 +164,40 @@ __device__ __forceinline__ float2 weno5z_x2(float2 q0, float2 q1, float2 q2, flo
     return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
 }
 
+// third-order WENO-Z of two stencils at once (same definition as weno3)
+__device__ __forceinline__ float2 weno3z_x2(float2 q0, float2 q1, float2 q2, float eps) {
+    const float2 h = f2(0.5f);
+    const float2 p0 = f2mul(f2fma(q1, f2(3.f), f2mul(q0, f2(-1.f))), h);
+    const float2 p1 = f2mul(f2add(q1, q2), h);
+    const float2 e0 = f2fma(q0, f2(-1.f), q1), e1 = f2fma(q1, f2(-1.f), q2);
+    const float2 b0 = f2mul(e0, e0), b1 = f2mul(e1, e1);
+    const float2 tau = make_float2(fabsf(b0.x - b1.x), fabsf(b0.y - b1.y));
+    const float2 r0 = make_float2(fminf(__fdividef(tau.x, b0.x + eps), 1e18f),
+                                  fminf(__fdividef(tau.y, b0.y + eps), 1e18f));
+    const float2 r1 = make_float2(fminf(__fdividef(tau.x, b1.x + eps), 1e18f),
+                                  fminf(__fdividef(tau.y, b1.y + eps), 1e18f));
+    const float2 a0 = f2mul(f2(1.f / 3.f), f2fma(r0, r0, f2(1.f)));
+    const float2 a1 = f2mul(f2(2.f / 3.f), f2fma(r1, r1, f2(1.f)));
+    const float2 num = f2fma(a0, p0, f2mul(a1, p1));
+    const float2 den = f2add(a0, a1);
+    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
+// FP32: every order of the adaptive scheme in packed form.  Both stencils complete:
+// one WENO5 pass.  Otherwise each of the two takes its own order (WENO5, WENO3 or the
+// upwind value) from at most one WENO5 and one WENO3 pass over both, so that a warp
+// whose lanes mix orders runs each pass once.
 template <> struct WenoPair<float> {
     static __device__ __forceinline__ void run(const float* qa, const float* qb, unsigned ina,
                                                unsigned inb, float eps, int linear, float& oa,
                                                float& ob) {
-        if (ina == 31u && inb == 31u && !linear) {
+        if (linear) {
+            oa = weno_adaptive(qa, ina, eps, linear);
+            ob = weno_adaptive(qb, inb, eps, linear);
+            return;
+        }
+        const bool a5 = ina == 31u, b5 = inb == 31u;
+        if (a5 && b5) {
             const float2 o = weno5z_x2(make_float2(qa[0], qb[0]), make_float2(qa[1], qb[1]),
                                        make_float2(qa[2], qb[2]), make_float2(qa[3], qb[3]),
                                        make_float2(qa[4], qb[4]), eps);
@@ -176,8 +205,22 @@ template <> struct WenoPair<float> {
             ob = o.y;
             return;
         }
-        oa = weno_adaptive(qa, ina, eps, linear);
-        ob = weno_adaptive(qb, inb, eps, linear);
+        const bool a3 = !a5 && (ina & 14u) == 14u, b3 = !b5 && (inb & 14u) == 14u;
+        oa = qa[2];
+        ob = qb[2];
+        if (a5 || b5) {
+            const float2 o = weno5z_x2(make_float2(qa[0], qb[0]), make_float2(qa[1], qb[1]),
+                                       make_float2(qa[2], qb[2]), make_float2(qa[3], qb[3]),
+                                       make_float2(qa[4], qb[4]), eps);
+            if (a5) oa = o.x;
+            if (b5) ob = o.y;
+        }
+        if (a3 || b3) {
+            const float2 o = weno3z_x2(make_float2(qa[1], qb[1]), make_float2(qa[2], qb[2]),
+                                       make_float2(qa[3], qb[3]), eps);
+            if (a3) oa = o.x;
+            if (b3) ob = o.y;
+        }
     }
 };
 

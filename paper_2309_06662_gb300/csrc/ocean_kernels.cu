@@ -258,6 +258,8 @@ struct __align__(128) TracerSmem {
     unsigned long long bar[3];                        // buffer b's copies have landed
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
+    // lowest level from which all six cells an x- (y-) face's stencils can touch are wet
+    short kfx[TY][TX + 1], kfy[TY + 1][TX];
     // x- and y-face transport and fluxes of levels k (even) and k+1 (odd)
     R fxU[2][TY][TX + 1], fxT[2][TY][TX + 1], fxS[2][TY][TX + 1];
     R fyV[2][TY + 1][TX], fyT[2][TY + 1][TX], fyS[2][TY + 1][TX];
@@ -310,6 +312,20 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     __syncthreads();
     const int kb = mine ? (int)sm.kb[ty + 3][tx + 3] : nz;
     if (kb < nz) atomicMin(&sm.kmin, kb);
+    for (int q = tid; q < TY * (TX + 1); q += NTT) {
+        const int a = q / (TX + 1), b = q % (TX + 1);
+        short m = sm.kb[a + 3][b];
+#pragma unroll
+        for (int n = 1; n < 6; ++n) m = max(m, sm.kb[a + 3][b + n]);
+        sm.kfx[a][b] = m;
+    }
+    for (int q = tid; q < (TY + 1) * TX; q += NTT) {
+        const int a = q / TX, b = q % TX;
+        short m = sm.kb[a][b + 3];
+#pragma unroll
+        for (int n = 1; n < 6; ++n) m = max(m, sm.kb[a + n][b + 3]);
+        sm.kfy[a][b] = m;
+    }
     __syncthreads();
     const int kstart = sm.kmin;
     if (kstart >= nz) return;   // the whole patch is land
@@ -396,16 +412,17 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             if (q < NXF) {
                 const int a = q / (TX + 1), b = q % (TX + 1);
                 R fU = R(0), fT = R(0), fS = R(0);
-                if (k >= sm.kbu[a][b]) {
+                const bool full = k >= sm.kfx[a][b];   // every stencil point wet
+                if (full || k >= sm.kbu[a][b]) {
                     const R ut = sm.us[cb][a][b];
                     R qT[5], qS[5];
-                    unsigned in = 0;
+                    unsigned in = full ? 31u : 0u;
 #pragma unroll
                     for (int n = 0; n < 5; ++n) {
                         const int col = ut >= R(0) ? b + n : b + 5 - n;
                         qT[n] = sm.T[cb][a + 3][col + 1];
                         qS[n] = sm.S[cb][a + 3][col + 1];
-                        in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
+                        if (!full) in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
                     }
                     R rT, rS;
                     WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
@@ -419,17 +436,18 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             } else {
                 const int a = (q - NXF) / TX, b = (q - NXF) % TX;
                 R fV = R(0), fT = R(0), fS = R(0);
-                if (k >= sm.kbv[a][b]) {
+                const bool full = k >= sm.kfy[a][b];
+                if (full || k >= sm.kbv[a][b]) {
                     const int fj = j0 + a;
                     const R vt = sm.vs[cb][a][b];
                     R qT[5], qS[5];
-                    unsigned in = 0;
+                    unsigned in = full ? 31u : 0u;
 #pragma unroll
                     for (int n = 0; n < 5; ++n) {
                         const int row = vt >= R(0) ? a + n : a + 5 - n;
                         qT[n] = sm.T[cb][row][b + 4];
                         qS[n] = sm.S[cb][row][b + 4];
-                        in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                        if (!full) in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
                     }
                     R rT, rS;
                     WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
@@ -452,8 +470,11 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             R ftT = R(0), ftS = R(0);
             if (k + 1 < nz) {   // flux through the top face (bottom face of cell k+1)
                 const bool pos = wt >= R(0);
+                // all five levels of the stencil in the column: k-2..k+2 upward, k-1..k+3
+                // downward
+                const bool full = pos ? (k - 2 >= kb && k + 2 < nz) : (k - 1 >= kb && k + 3 < nz);
                 R qT[5], qS[5];
-                unsigned in = 0;
+                unsigned in = full ? 31u : 0u;
 #pragma unroll
                 for (int n = 0; n < 5; ++n) {
                     // window index n (level k-2+n) upward, 5-n (level k+3-n) downward; both
@@ -461,7 +482,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                     qT[n] = pos ? wT[n] : wT[5 - n];
                     qS[n] = pos ? wS[n] : wS[5 - n];
                     const int kk = pos ? k - 2 + n : k + 3 - n;
-                    in |= (kk >= kb && kk < nz ? 1u : 0u) << n;
+                    if (!full) in |= (kk >= kb && kk < nz ? 1u : 0u) << n;
                 }
                 R rT, rS;
                 WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
