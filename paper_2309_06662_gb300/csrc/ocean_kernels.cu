@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
 // bounded by registers only.
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 // The tracer block has one more warp: its 8 x 33 x-faces and 9 x 32 y-faces (552 WENO
-// pairs per level) then take two rounds of 288 threads instead of three of 256; the
+// pairs per level) then take two per thread of 288 instead of up to three of 256; the
 // extra warp owns no column and only computes faces.
 constexpr int TTY = TY + 1, NTT = TX * TTY;
 // resident blocks per SM the register budget is sized for (FP64 needs more registers)
@@ -333,7 +333,6 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     // ---- the staged tile (halo 3) and the face velocities stream in two levels ahead,
     // triple buffered, as tensor copies one thread issues per level (rows and columns
     // beyond the arrays arrive as zeros and feed only threads outside the domain)
-    constexpr int NXF = TY * (TX + 1), NYF = (TY + 1) * TX;
     constexpr unsigned STAGE_BYTES =
         (unsigned)sizeof(R) * (2u * 14u * 40u + (unsigned)TY * 36u + (unsigned)(TY + 1) * TX);
     constexpr unsigned OWN_BYTES = (unsigned)sizeof(R) * TY * TX;
@@ -406,59 +405,64 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         }
         kcarry = k1;
         const R dzk = p.dz[k];
-        // ---- x- and y-face fluxes, each face once (one job list, so that no warp does
-        // more than one job beyond the others)
-        for (int q = tid; q < NXF + NYF; q += NTT) {
-            if (q < NXF) {
-                const int a = q / (TX + 1), b = q % (TX + 1);
-                R fU = R(0), fT = R(0), fS = R(0);
-                const bool full = k >= sm.kfx[a][b];   // every stencil point wet
-                if (full || k >= sm.kbu[a][b]) {
-                    const R ut = sm.us[cb][a][b];
-                    R qT[5], qS[5];
-                    unsigned in = full ? 31u : 0u;
+        // ---- x- and y-face fluxes, each face once, by fixed roles: thread (tx, ty < TY)
+        // the west and south faces of its own column; the extra warp the north faces of
+        // the last row and (lanes 0..TY-1) the east faces of the last column.  Two WENO
+        // pairs per thread; the stencil offsets are known at compile time.
+        auto xface = [&](const int a, const int b) {
+            R fU = R(0), fT = R(0), fS = R(0);
+            const bool full = k >= sm.kfx[a][b];   // every stencil point wet
+            if (full || k >= sm.kbu[a][b]) {
+                const R ut = sm.us[cb][a][b];
+                R qT[5], qS[5];
+                unsigned in = full ? 31u : 0u;
 #pragma unroll
-                    for (int n = 0; n < 5; ++n) {
-                        const int col = ut >= R(0) ? b + n : b + 5 - n;
-                        qT[n] = sm.T[cb][a + 3][col + 1];
-                        qS[n] = sm.S[cb][a + 3][col + 1];
-                        if (!full) in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
-                    }
-                    R rT, rS;
-                    WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                    fU = ut * p.dy * dzk;
-                    fT = fU * rT;
-                    fS = fU * rS;
+                for (int n = 0; n < 5; ++n) {
+                    const int col = ut >= R(0) ? b + n : b + 5 - n;
+                    qT[n] = sm.T[cb][a + 3][col + 1];
+                    qS[n] = sm.S[cb][a + 3][col + 1];
+                    if (!full) in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
                 }
-                sm.fxU[fb][a][b] = fU;
-                sm.fxT[fb][a][b] = fT;
-                sm.fxS[fb][a][b] = fS;
-            } else {
-                const int a = (q - NXF) / TX, b = (q - NXF) % TX;
-                R fV = R(0), fT = R(0), fS = R(0);
-                const bool full = k >= sm.kfy[a][b];
-                if (full || k >= sm.kbv[a][b]) {
-                    const int fj = j0 + a;
-                    const R vt = sm.vs[cb][a][b];
-                    R qT[5], qS[5];
-                    unsigned in = full ? 31u : 0u;
-#pragma unroll
-                    for (int n = 0; n < 5; ++n) {
-                        const int row = vt >= R(0) ? a + n : a + 5 - n;
-                        qT[n] = sm.T[cb][row][b + 4];
-                        qS[n] = sm.S[cb][row][b + 4];
-                        if (!full) in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
-                    }
-                    R rT, rS;
-                    WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                    fV = vt * p.dxv[fj + OC_H] * dzk;
-                    fT = fV * rT;
-                    fS = fV * rS;
-                }
-                sm.fyV[fb][a][b] = fV;
-                sm.fyT[fb][a][b] = fT;
-                sm.fyS[fb][a][b] = fS;
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                fU = ut * p.dy * dzk;
+                fT = fU * rT;
+                fS = fU * rS;
             }
+            sm.fxU[fb][a][b] = fU;
+            sm.fxT[fb][a][b] = fT;
+            sm.fxS[fb][a][b] = fS;
+        };
+        auto yface = [&](const int a, const int b) {
+            R fV = R(0), fT = R(0), fS = R(0);
+            const bool full = k >= sm.kfy[a][b];
+            if (full || k >= sm.kbv[a][b]) {
+                const R vt = sm.vs[cb][a][b];
+                R qT[5], qS[5];
+                unsigned in = full ? 31u : 0u;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int row = vt >= R(0) ? a + n : a + 5 - n;
+                    qT[n] = sm.T[cb][row][b + 4];
+                    qS[n] = sm.S[cb][row][b + 4];
+                    if (!full) in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                }
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                fV = vt * p.dxv[j0 + a + OC_H] * dzk;
+                fT = fV * rT;
+                fS = fV * rS;
+            }
+            sm.fyV[fb][a][b] = fV;
+            sm.fyT[fb][a][b] = fT;
+            sm.fyS[fb][a][b] = fS;
+        };
+        if (ty < TY) {
+            xface(ty, tx);
+            yface(ty, tx);
+        } else {
+            yface(TY, tx);
+            if (tx < TY) xface(tx, TX);
         }
         // this thread's reads of level k-1's staging buffer (faces and own cell, before
         // this point) are ordered before the tensor copy that overwrites it
