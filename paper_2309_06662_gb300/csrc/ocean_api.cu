@@ -531,7 +531,9 @@ bool build_tile_maps(ocean_t m) {
             !oc_encode_tiled(&t.mv, dt, 3, m->v[c], dims, strides, boxMV, no) ||
             !oc_encode_tiled(&t.mp, dt, 3, m->p, dims, strides, boxC, no) ||
             !oc_encode_tiled(&t.mw, dt, 3, m->w, dims, strides, boxC, no) ||
-            !oc_encode_tiled(&t.mnu, dt, 3, m->nu, dims, strides, boxC, no))
+            !oc_encode_tiled(&t.mnu, dt, 3, m->nu, dims, strides, boxC, no) ||
+            !oc_encode_tiled(&t.mgu, dt, 3, m->Gu, dims, strides, boxO, no) ||
+            !oc_encode_tiled(&t.mgv, dt, 3, m->Gv, dims, strides, boxO, no))
             return false;
     }
     return true;

@@ -231,9 +231,9 @@ template <> struct WenoPair<float> {
 // parity: 3-D [nz][ny + 2H][pitch] views, one level per copy.  Tracer: T and S (boxes of
 // 40 x 14 columns x rows), u and v faces (36 x 8, 32 x 9), and its own columns' w,
 // diffusivity, G_T and G_S (32 x 8).  Momentum: u (40 x 14), v (40 x 13), pressure, w and
-// nu (36 x 9).
+// nu (36 x 9), and its own columns' G_u and G_v (32 x 8).
 struct __align__(128) TileMaps {
-    CUtensorMap T, S, tu, tv, tw, tk, tgt, tgs, mu, mv, mp, mw, mnu;
+    CUtensorMap T, S, tu, tv, tw, tk, tgt, tgs, mu, mv, mp, mw, mnu, mgu, mgv;
 };
 
 // Encodes a tiled tensor map through the driver's entry point; false if refused.

@@ -175,6 +175,9 @@ constexpr int TTY = TY + 1, NTT = TX * TTY;
 // resident blocks per SM the register budget is sized for (FP64 needs more registers)
 template <typename R> struct TileOcc { static constexpr int value = 3; };
 template <> struct TileOcc<double> { static constexpr int value = 1; };
+// the FP32 momentum tile fits 64 registers: four blocks per SM
+template <typename R> struct MomOcc { static constexpr int value = 4; };
+template <> struct MomOcc<double> { static constexpr int value = 1; };
 
 // padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
 // the domain stage a few columns beyond it, whose values only feed threads that are
@@ -593,17 +596,20 @@ __global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_tracer(KP<R> p,
 
 // TMA destinations first, each buffer a multiple of 128 bytes; every box starts at the
 // column i0-4 (16-byte aligned), so the logical column c of each array sits at c + 2 (u),
-// c + 1 (v), c + 3 (p, w, nu)
+// c + 1 (v), c + 3 (p, w, nu).  Slot s holds one level's tiles; three slots rotate.
 template <typename R>
 struct __align__(128) MomentumSmem {
-    R u[2][TY + 8][TX + 8];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3); levels k, k+1
-    R v[2][TY + 8][TX + 8];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
-    R p[2][2 * TY][TX + 4];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
-    R w[3][2 * TY][TX + 4];   // w on the bottom faces of levels k, k+1, k+2 (ring), same centres
+    R u[3][TY + 8][TX + 8];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3)
+    R v[3][TY + 8][TX + 8];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
+    R p[3][2 * TY][TX + 4];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
+    R w[3][2 * TY][TX + 4];   // w on the level's bottom faces, same centres
     R nu[3][2 * TY][TX + 4];  // nu on those faces
-    unsigned long long bar[2];   // the copies issued at one level (two levels in flight)
-    R z[TY + 5][TX + 5];      // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3)
-    R K[TY + 1][TX + 1];      // kinetic energy at the centres
+    R gu[3][TY][TX], gv[3][TY][TX];   // own columns' G_u, G_v of the previous step
+    unsigned long long bar[3];        // slot s's copies have landed
+    // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3), and the kinetic energy
+    // at the centres, of levels k (even) and k+1 (odd)
+    R z[2][TY + 5][TX + 5];
+    R K[2][TY + 1][TX + 1];
     short kbz[TY + 5][TX + 5], kbzin[TY + 5][TX + 5];
     int kmin;
 };
@@ -644,30 +650,34 @@ __device__ __forceinline__ void momentum_tile(
     const int kstart = sm.kmin;
     if (kstart >= nz) return;
 
-    // ---- staging by tensor copies one thread issues: u, v, p of level k+1 into buffer b,
-    // w and nu of level k+2 into ring slot r, all completing on the barrier of the level
-    // that issued them (two levels in flight)
+    // ---- staging by tensor copies one thread issues: level k's u, v, p, w, nu tiles (and
+    // with STEP its own columns' G^{n-1}) into slot (k - kstart) % 3, two levels ahead.
+    // Level k's own cells read its slot and level k+1's (u, v above, w and nu on the top
+    // face).
     constexpr int TC = (TY + 1) * (TX + 1);   // centres of the pressure / w / nu tiles
-    constexpr unsigned UVP = (unsigned)sizeof(R) * (40u * 14u + 40u * 13u + 36u * 9u);
-    constexpr unsigned WNU = (unsigned)sizeof(R) * (2u * 36u * 9u);
+    constexpr unsigned TILES = (unsigned)sizeof(R) * (40u * 14u + 40u * 13u + 3u * 36u * 9u);
+    constexpr unsigned OWN = (unsigned)sizeof(R) * TY * TX;
     const int yu = j0 + OC_H - 3, yv = j0 + OC_H - 2, yc = j0 + OC_H - 1;
-    auto copy_uvp = [&](int k, int b, unsigned long long* bar) {
-        tma_level(&sm.u[b][0][0], &tm.mu, i0, yu, k, bar);
-        tma_level(&sm.v[b][0][0], &tm.mv, i0, yv, k, bar);
-        tma_level(&sm.p[b][0][0], &tm.mp, i0, yc, k, bar);
-    };
-    auto copy_wnu = [&](int k, int r, unsigned long long* bar) {
-        tma_level(&sm.w[r][0][0], &tm.mw, i0, yc, k, bar);
-        tma_level(&sm.nu[r][0][0], &tm.mnu, i0, yc, k, bar);
+    auto stage = [&](int k, int sl) {
+        unsigned long long* bar = &sm.bar[sl];
+        bar_expect(bar, TILES + (STEP ? 2u * OWN : 0u));
+        tma_level(&sm.u[sl][0][0], &tm.mu, i0, yu, k, bar);
+        tma_level(&sm.v[sl][0][0], &tm.mv, i0, yv, k, bar);
+        tma_level(&sm.p[sl][0][0], &tm.mp, i0, yc, k, bar);
+        tma_level(&sm.w[sl][0][0], &tm.mw, i0, yc, k, bar);
+        tma_level(&sm.nu[sl][0][0], &tm.mnu, i0, yc, k, bar);
+        if (STEP) {
+            tma_level(&sm.gu[sl][0][0], &tm.mgu, i0 + OC_H, j0 + OC_H, k, bar);
+            tma_level(&sm.gv[sl][0][0], &tm.mgv, i0 + OC_H, j0 + OC_H, k, bar);
+        }
     };
     if (tid == 0) {
         bar_init(&sm.bar[0]);
         bar_init(&sm.bar[1]);
+        bar_init(&sm.bar[2]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        bar_expect(&sm.bar[0], UVP + WNU * (kstart + 1 < nz ? 2u : 1u));
-        copy_uvp(kstart, 0, &sm.bar[0]);
-        copy_wnu(kstart, 0, &sm.bar[0]);
-        if (kstart + 1 < nz) copy_wnu(kstart + 1, 1, &sm.bar[0]);
+        stage(kstart, 0);
+        if (kstart + 1 < nz) stage(kstart + 1, 1);
     }
     __syncthreads();   // the barriers are initialised before anyone waits on them
 
@@ -675,33 +685,20 @@ __device__ __forceinline__ void momentum_tile(
     const R rdxc = p.rdxc[jr], fu = p.fu[jr], fv = p.fv[jr];
     R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
-    // own faces: u, v at k-1 (lower); level k comes from the tile, k+1 from global
+    // own faces: u, v at k-1 (lower); levels k and k+1 come from the tiles
     R ulo = R(0), vlo = R(0);
     if (mine && kstart >= 1) {
         ulo = u[(kstart - 1) * P + c2];
         vlo = v[(kstart - 1) * P + c2];
     }
+    // One block barrier per level: corners and kinetic energy of level k go to buffer
+    // k & 1, so a warp that has finished level k-1 computes them while others still read
+    // level k-1's; the barrier after them publishes them and frees the slot of level k-1
+    // (read by every thread before it), which takes level k+2.
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        const int cb = (k - kstart) & 1;
-        const int rc = (k - kstart) % 3, rn = (rc + 1) % 3, rnn = (rc + 2) % 3;
-        bar_wait(&sm.bar[cb], (unsigned)((k - kstart) >> 1) & 1u);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();   // level k is in; buffers of the previous level are free
-        if (tid == 0 && k + 1 < nz) {
-            bar_expect(&sm.bar[1 - cb], UVP + (k + 2 < nz ? WNU : 0u));
-            copy_uvp(k + 1, 1 - cb, &sm.bar[1 - cb]);
-            if (k + 2 < nz) copy_wnu(k + 2, rnn, &sm.bar[1 - cb]);
-        }
-        R uhi = R(0), vhi = R(0), gu0 = R(0), gv0 = R(0);
-        if (mine && k + 1 < nz) {
-            uhi = u[Pk + P + c2];
-            vhi = v[Pk + P + c2];
-        }
-        if (STEP && mine) {
-            if (k >= ku) gu0 = Gup[Pk + c2];
-            if (k >= kv) gv0 = Gvp[Pk + c2];
-        }
+        const int lv = k - kstart, sc = lv % 3, sn = (lv + 1) % 3, fb = lv & 1;
+        bar_wait(&sm.bar[sc], (unsigned)(lv / 3) & 1u);
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
         for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
             const int a = q / (TX + 5), b = q % (TX + 5);
@@ -711,51 +708,60 @@ __device__ __forceinline__ void momentum_tile(
                 const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
                 // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
                 // v(i-1, jc) = v[a][b]
-                const R circ = p.dy * (sm.v[cb][a][(b + 1) + 1] - sm.v[cb][a][(b) + 1])
-                             - (p.dxc[jrc] * sm.u[cb][a + 1][(b) + 2] - p.dxc[jrc - 1] * sm.u[cb][a][(b) + 2]);
+                const R circ = p.dy * (sm.v[sc][a][(b + 1) + 1] - sm.v[sc][a][(b) + 1])
+                             - (p.dxc[jrc] * sm.u[sc][a + 1][(b) + 2] - p.dxc[jrc - 1] * sm.u[sc][a][(b) + 2]);
                 zz = circ * p.rAz[jrc];
             }
-            sm.z[a][b] = zz;
+            sm.z[fb][a][b] = zz;
         }
         for (int q = tid; q < TC; q += NT) {
             const int a = q / (TX + 1), b = q % (TX + 1);
             // centre (i0-1+b, j0-1+a): u at cols b+1, b+2 of row a+2; v at col b+2, rows a+1, a+2
-            const R ua = sm.u[cb][a + 2][(b + 1) + 2], ub = sm.u[cb][a + 2][(b + 2) + 2];
-            const R va = sm.v[cb][a + 1][(b + 2) + 1], vb = sm.v[cb][a + 2][(b + 2) + 1];
-            sm.K[a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
+            const R ua = sm.u[sc][a + 2][(b + 1) + 2], ub = sm.u[sc][a + 2][(b + 2) + 2];
+            const R va = sm.v[sc][a + 1][(b + 2) + 1], vb = sm.v[sc][a + 2][(b + 2) + 1];
+            sm.K[fb][a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
         }
+        // this thread's reads of level k-1's slot are ordered before the tensor copy that
+        // overwrites it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
+        if (tid == 0 && k + 2 < nz) stage(k + 2, (lv + 2) % 3);
+        if (k + 1 < nz) bar_wait(&sm.bar[sn], (unsigned)((lv + 1) / 3) & 1u);
         if (mine) {
             const R rdz = p.rdz[k];
             const bool du_ = k >= ku, dv_ = k >= kv;
+            const R uhi = k + 1 < nz ? sm.u[sn][ty + 3][(tx + 2) + 2] : R(0);
+            const R vhi = k + 1 < nz ? sm.v[sn][ty + 2][(tx + 3) + 1] : R(0);
+            const R gu0 = STEP && du_ ? sm.gu[sc][ty][tx] : R(0);
+            const R gv0 = STEP && dv_ ? sm.gv[sc][ty][tx] : R(0);
             // ---- the two vorticity reconstructions of this thread
-            const R u0 = sm.u[cb][ty + 3][(tx + 2) + 2];
-            const R v0 = sm.v[cb][ty + 2][(tx + 3) + 1];
-            const R vh = R(0.25) * (sm.v[cb][ty + 2][(tx + 2) + 1] + sm.v[cb][ty + 2][(tx + 3) + 1]
-                                  + sm.v[cb][ty + 3][(tx + 2) + 1] + sm.v[cb][ty + 3][(tx + 3) + 1]);
-            const R uh = R(0.25) * (sm.u[cb][ty + 2][(tx + 2) + 2] + sm.u[cb][ty + 2][(tx + 3) + 2]
-                                  + sm.u[cb][ty + 3][(tx + 2) + 2] + sm.u[cb][ty + 3][(tx + 3) + 2]);
+            const R u0 = sm.u[sc][ty + 3][(tx + 2) + 2];
+            const R v0 = sm.v[sc][ty + 2][(tx + 3) + 1];
+            const R vh = R(0.25) * (sm.v[sc][ty + 2][(tx + 2) + 1] + sm.v[sc][ty + 2][(tx + 3) + 1]
+                                  + sm.v[sc][ty + 3][(tx + 2) + 1] + sm.v[sc][ty + 3][(tx + 3) + 1]);
+            const R uh = R(0.25) * (sm.u[sc][ty + 2][(tx + 2) + 2] + sm.u[sc][ty + 2][(tx + 3) + 2]
+                                  + sm.u[sc][ty + 3][(tx + 2) + 2] + sm.u[sc][ty + 3][(tx + 3) + 2]);
             R qa[5], qb[5];
             unsigned ina = 0, inb = 0;
 #pragma unroll
             for (int n = 0; n < 5; ++n) {
                 const int a = vh >= R(0) ? ty + n : ty + 5 - n;   // corner rows j-2.. (u-face)
-                qa[n] = sm.z[a][tx + 2];
+                qa[n] = sm.z[fb][a][tx + 2];
                 ina |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
                 const int b = uh >= R(0) ? tx + n : tx + 5 - n;   // corner cols i-2.. (v-face)
-                qb[n] = sm.z[ty + 2][b];
+                qb[n] = sm.z[fb][ty + 2][b];
                 inb |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
             }
             R ztu, ztv;
             WenoPair<R>::run(qa, qb, ina, inb, p.eps, p.linear, ztu, ztv);
             if (du_) {   // ---------------- u at the west face of column (i, j)
-                const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty + 1][tx]) * rdxc;
-                const R dP = (sm.p[cb][ty + 1][(tx + 1) + 3] - sm.p[cb][ty + 1][(tx) + 3]) * rdxc;
+                const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty + 1][tx]) * rdxc;
+                const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty + 1][(tx) + 3]) * rdxc;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[rn][ty + 1][(tx) + 3] + sm.w[rn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[sn][ty + 1][(tx) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
                 if (k - 1 >= ku)
-                    dn = R(0.5) * (sm.w[rc][ty + 1][(tx) + 3] + sm.w[rc][ty + 1][(tx + 1) + 3]) * (u0 - ulo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[sc][ty + 1][(tx) + 3] + sm.w[sc][ty + 1][(tx + 1) + 3]) * (u0 - ulo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? taux_s[c2] : R(0);
                 const R G = (ztu + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -768,9 +774,9 @@ __device__ __forceinline__ void momentum_tile(
                     sGU += p.dz[k] * gh;
                     const R us = u0 + p.dt * gh;
                     const R lo = k > ku
-                        ? p.dt * R(0.5) * (sm.nu[rc][ty + 1][(tx) + 3] + sm.nu[rc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[sc][ty + 1][(tx) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[rn][ty + 1][(tx) + 3] + sm.nu[rn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[sn][ty + 1][(tx) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
@@ -779,13 +785,13 @@ __device__ __forceinline__ void momentum_tile(
                 }
             }
             if (dv_) {   // ---------------- v at the south face of column (i, j)
-                const R dK = (sm.K[ty + 1][tx + 1] - sm.K[ty][tx + 1]) * p.rdy;
-                const R dP = (sm.p[cb][ty + 1][(tx + 1) + 3] - sm.p[cb][ty][(tx + 1) + 3]) * p.rdy;
+                const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty][tx + 1]) * p.rdy;
+                const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty][(tx + 1) + 3]) * p.rdy;
                 R up = R(0), dn = R(0);
                 if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[rn][ty][(tx + 1) + 3] + sm.w[rn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
+                    up = R(0.5) * (sm.w[sn][ty][(tx + 1) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
                 if (k - 1 >= kv)
-                    dn = R(0.5) * (sm.w[rc][ty][(tx + 1) + 3] + sm.w[rc][ty + 1][(tx + 1) + 3]) * (v0 - vlo) * p.rdzf[k];
+                    dn = R(0.5) * (sm.w[sc][ty][(tx + 1) + 3] + sm.w[sc][ty + 1][(tx + 1) + 3]) * (v0 - vlo) * p.rdzf[k];
                 const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
                 const R G = -(ztv + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -798,9 +804,9 @@ __device__ __forceinline__ void momentum_tile(
                     sGV += p.dz[k] * gh;
                     const R vs = v0 + p.dt * gh;
                     const R lo = k > kv
-                        ? p.dt * R(0.5) * (sm.nu[rc][ty][(tx + 1) + 3] + sm.nu[rc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[sc][ty][(tx + 1) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[rn][ty][(tx + 1) + 3] + sm.nu[rn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
+                        ? p.dt * R(0.5) * (sm.nu[sn][ty][(tx + 1) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
                     const R inv = R(1) / ((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
@@ -816,6 +822,7 @@ __device__ __forceinline__ void momentum_tile(
     if (tid == 0) {
         bar_inval(&sm.bar[0]);
         bar_inval(&sm.bar[1]);
+        bar_inval(&sm.bar[2]);
     }
     if (!STEP || !mine) return;
     // back substitutions down the column, four levels' coefficients loaded at once
@@ -855,7 +862,7 @@ __device__ __forceinline__ void momentum_tile(
 }
 
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_momentum(
+__global__ void __launch_bounds__(NT, MomOcc<R>::value) k_momentum(
     KP<R> p, const __grid_constant__ TileMaps tm, const R* __restrict__ u,
     const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
@@ -1450,7 +1457,7 @@ __global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_ens_tracer(
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT, TileOcc<R>::value) k_ens_momentum(
+__global__ void __launch_bounds__(NT, MomOcc<R>::value) k_ens_momentum(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
