@@ -927,12 +927,22 @@ template <typename R> constexpr size_t baro_smem() { return (3 * BRX * BRY + 3 *
 template <typename R> struct BaroOcc { static constexpr int value = 2; };
 template <> struct BaroOcc<double> { static constexpr int value = 1; };
 
-// padded index of (i, j) with periodic wrap; -1 beyond a wall
+// padded index of (i, j) with periodic wrap; -1 beyond a wall (a region reaches less
+// than one region width beyond the domain, so the wrap is one add or subtract for any
+// domain at least that wide)
 __device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
-    if (g.px) { i %= g.nx; if (i < 0) i += g.nx; }
-    else if (i < 0 || i >= g.nx) return -1;
-    if (g.py) { j %= g.ny; if (j < 0) j += g.ny; }
-    else if (j < 0 || j >= g.ny) return -1;
+    if (g.px) {
+        while (i < 0) i += g.nx;
+        while (i >= g.nx) i -= g.nx;
+    } else if (i < 0 || i >= g.nx) {
+        return -1;
+    }
+    if (g.py) {
+        while (j < 0) j += g.ny;
+        while (j >= g.ny) j -= g.ny;
+    } else if (j < 0 || j >= g.ny) {
+        return -1;
+    }
     jw = j;
     return ix2(g, i, j);
 }
@@ -982,19 +992,22 @@ __device__ __forceinline__ void baro_region(
         ownm |= (own ? 1u : 0u) << r;
         pE[r] = pU[r] = pV[r] = R(0);
         if (c >= 0) {
-            sE[q] = Ea[c];
-            sU[q] = Ua[c];
-            sV[q] = Va[c];
-            const R hu = Hu[c], hv = Hv[c];
+            // every load of the cell issued at once (none waits on another's value)
+            const R e = Ea[c], uu = Ua[c], vv = Va[c], hu = Hu[c], hv = Hv[c];
+            const R gu = GU[c], gv = GV[c], gx = gxe[c], gy = gye[c], rdx = p.rdxc[jw + OC_H];
+            const int kbc = g.kb[c];
+            u0[r] = Un[c];   // used by owned cells only
+            v0[r] = Vn[c];
+            sE[q] = e;
+            sU[q] = uu;
+            sV[q] = vv;
             // U += dtau [-g H_u (gxe + deta_i - deta_{i-1})/dx_c + G_U]
             //    = U + Bu - Au (deta_i - deta_{i-1})
-            Au[r] = hu > R(0) ? dtau * grav * hu * p.rdxc[jw + OC_H] : R(0);
-            Bu[r] = hu > R(0) ? dtau * GU[c] - Au[r] * gxe[c] : R(0);
+            Au[r] = hu > R(0) ? dtau * grav * hu * rdx : R(0);
+            Bu[r] = hu > R(0) ? dtau * gu - Au[r] * gx : R(0);
             Av[r] = hv > R(0) ? dtau * grav * hv * p.rdy : R(0);
-            Bv[r] = hv > R(0) ? dtau * GV[c] - Av[r] * gye[c] : R(0);
-            wetm |= (g.kb[c] < g.nz ? 1u : 0u) << r;
-            u0[r] = own ? Un[c] : R(0);
-            v0[r] = own ? Vn[c] : R(0);
+            Bv[r] = hv > R(0) ? dtau * gv - Av[r] * gy : R(0);
+            wetm |= (kbc < g.nz ? 1u : 0u) << r;
         } else {
             sE[q] = sU[q] = sV[q] = R(0);
             Au[r] = Bu[r] = Av[r] = Bv[r] = u0[r] = v0[r] = R(0);
@@ -1041,9 +1054,11 @@ __device__ __forceinline__ void baro_region(
         Eb[c] = sE[q];
         Ub[c] = sU[q];
         Vb[c] = sV[q];
-        accE[c] += (double)pE[r];
-        accU[c] += (double)pU[r];
-        accV[c] += (double)pV[r];
+        // one thread owns each cell: a reduction in memory is the plain FP64 add, issued
+        // without waiting for the old value
+        atomicAdd(&accE[c], (double)pE[r]);
+        atomicAdd(&accU[c], (double)pU[r]);
+        atomicAdd(&accV[c], (double)pV[r]);
     }
 }
 
