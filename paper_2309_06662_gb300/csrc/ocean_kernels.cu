@@ -1122,8 +1122,23 @@ __device__ __forceinline__ void correct_col(const KP<R>& p, const long c, const 
     const int k0 = slab * CORR_SLAB, k1 = k0 + CORR_SLAB < g.nz ? k0 + CORR_SLAB : g.nz;
     const int ku = g.kbu[c2], kv = g.kbv[c2];
     const R cu = corrU[c2], cv = corrV[c2];
-    for (int k = k0 > ku ? k0 : ku; k < k1; ++k) un[k * P + c2] += cu;
-    for (int k = k0 > kv ? k0 : kv; k < k1; ++k) vn[k * P + c2] += cv;
+    // u and v of four levels loaded at once (eight loads in flight per column)
+    const int kmn = ku < kv ? ku : kv;
+    for (int k = k0 > kmn ? k0 : kmn; k < k1; k += 4) {
+        R uq[4], vq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k + q) * P + c2;
+            uq[q] = k + q < k1 && k + q >= ku ? un[ck] : R(0);
+            vq[q] = k + q < k1 && k + q >= kv ? vn[ck] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k + q) * P + c2;
+            if (k + q < k1 && k + q >= ku) un[ck] = uq[q] + cu;
+            if (k + q < k1 && k + q >= kv) vn[ck] = vq[q] + cv;
+        }
+    }
 }
 
 template <typename R>
