@@ -172,12 +172,10 @@ constexpr int TX = 32, TY = 8, NT = TX * TY;
 // pairs per level) then take two per thread of 288 instead of up to three of 256; the
 // extra warp owns no column and only computes faces.
 constexpr int TTY = TY + 1, NTT = TX * TTY;
-// resident blocks per SM the register budget is sized for (FP64 needs more registers)
-template <typename R> struct TileOcc { static constexpr int value = 3; };
-template <> struct TileOcc<double> { static constexpr int value = 1; };
-// the FP32 momentum tile fits 64 registers: four blocks per SM
-template <typename R> struct MomOcc { static constexpr int value = 4; };
-template <> struct MomOcc<double> { static constexpr int value = 1; };
+// resident blocks per SM the register budget is sized for: the FP32 momentum and tracer
+// tiles fit 64 and 56 registers (four blocks per SM); the FP64 tiles need far more
+template <typename R> struct Occ4 { static constexpr int value = 4; };
+template <> struct Occ4<double> { static constexpr int value = 1; };
 
 // padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
 // the domain stage a few columns beyond it, whose values only feed threads that are
@@ -579,7 +577,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
 }
 
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_tracer(KP<R> p,
+__global__ void __launch_bounds__(NTT, Occ4<R>::value) k_tracer(KP<R> p,
                                                const __grid_constant__ TileMaps tm,
                                                const R* __restrict__ u,
                                                const R* __restrict__ v, const R* __restrict__ w,
@@ -862,7 +860,7 @@ __device__ __forceinline__ void momentum_tile(
 }
 
 template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, MomOcc<R>::value) k_momentum(
+__global__ void __launch_bounds__(NT, Occ4<R>::value) k_momentum(
     KP<R> p, const __grid_constant__ TileMaps tm, const R* __restrict__ u,
     const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
@@ -1473,7 +1471,7 @@ __global__ void __launch_bounds__(TPB) k_ens_diag(const EnsMember<R>* __restrict
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_ens_tracer(
+__global__ void __launch_bounds__(NTT, Occ4<R>::value) k_ens_tracer(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
@@ -1487,7 +1485,7 @@ __global__ void __launch_bounds__(NTT, TileOcc<R>::value) k_ens_tracer(
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT, MomOcc<R>::value) k_ens_momentum(
+__global__ void __launch_bounds__(NT, Occ4<R>::value) k_ens_momentum(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
