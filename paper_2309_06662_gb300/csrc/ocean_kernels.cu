@@ -227,7 +227,9 @@ __device__ __forceinline__ void tma_level(void* dst, const CUtensorMap* map, int
         : "memory");
 }
 // waits (at most ~1 s of SM clock) for phase `parity` of the barrier; on giving up it
-// flags g_tile_err (the host reports OCEAN_ERR_TIMEOUT) and returns
+// flags g_tile_err (the host reports OCEAN_ERR_TIMEOUT) and returns.  Once any wait has
+// given up, every later wait that is not satisfied at once returns too, so that a kernel
+// whose barriers can no longer complete drains in about one time limit.
 __device__ __forceinline__ void bar_wait(unsigned long long* b, unsigned parity) {
     const long long t0 = clock64();
     while (true) {
@@ -239,6 +241,7 @@ __device__ __forceinline__ void bar_wait(unsigned long long* b, unsigned parity)
             : "r"(sm_u32(b)), "r"(parity)
             : "memory");
         if (ok) return;
+        if (*reinterpret_cast<volatile int*>(&g_tile_err)) return;
         if (clock64() - t0 > 2000000000LL) {
             atomicExch(&g_tile_err, 1);
             return;
