@@ -969,9 +969,10 @@ __device__ __forceinline__ void baro_region(
     const int tid = threadIdx.x;
     const int IX = BRX - 2 * BS, IY = BRY - 2 * BS;
     const int i0 = bx * IX - BS, j0 = by * IY - BS;   // region origin
-    // a thread owns the cells (rx, ry0 + r BNT/BRX), r < BC, of one region column
-    const int rx = tid % BRX, ry0 = tid / BRX;
-    constexpr int RS = BNT / BRX;
+    // a thread owns the cells (rx, ry0 + r), r < BC, of one region column: consecutive
+    // rows, so the state of its inner cells' north and south neighbours is in its own
+    // registers; shared memory carries what the neighbouring threads read
+    const int rx = tid % BRX, ry0 = (tid / BRX) * BC;
     if (tid < BRY) {
         int j = j0 + tid;
         if (g.py) { j %= g.ny; if (j < 0) j += g.ny; }
@@ -982,10 +983,11 @@ __device__ __forceinline__ void baro_region(
     }
     R Au[BC], Bu[BC], Av[BC], Bv[BC], u0[BC], v0[BC];
     R pE[BC], pU[BC], pV[BC];
+    R e[BC], uu[BC], vv[BC];   // the thread's own state
     unsigned wetm = 0, ownm = 0;
 #pragma unroll
     for (int r = 0; r < BC; ++r) {
-        const int ry = ry0 + r * RS, q = ry * BRX + rx;
+        const int ry = ry0 + r, q = ry * BRX + rx;
         int jw = 0;
         const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
         const bool own = rx >= BS && rx < BRX - BS && ry >= BS && ry < BRY - BS &&
@@ -994,14 +996,14 @@ __device__ __forceinline__ void baro_region(
         pE[r] = pU[r] = pV[r] = R(0);
         if (c >= 0) {
             // every load of the cell issued at once (none waits on another's value)
-            const R e = Ea[c], uu = Ua[c], vv = Va[c], hu = Hu[c], hv = Hv[c];
+            const R hu = Hu[c], hv = Hv[c];
             const R gu = GU[c], gv = GV[c], gx = gxe[c], gy = gye[c], rdx = p.rdxc[jw + OC_H];
             const int kbc = g.kb[c];
+            e[r] = Ea[c];
+            uu[r] = Ua[c];
+            vv[r] = Va[c];
             u0[r] = Un[c];   // used by owned cells only
             v0[r] = Vn[c];
-            sE[q] = e;
-            sU[q] = uu;
-            sV[q] = vv;
             // U += dtau [-g H_u (gxe + deta_i - deta_{i-1})/dx_c + G_U]
             //    = U + Bu - Au (deta_i - deta_{i-1})
             Au[r] = hu > R(0) ? dtau * grav * hu * rdx : R(0);
@@ -1010,37 +1012,44 @@ __device__ __forceinline__ void baro_region(
             Bv[r] = hv > R(0) ? dtau * gv - Av[r] * gy : R(0);
             wetm |= (kbc < g.nz ? 1u : 0u) << r;
         } else {
-            sE[q] = sU[q] = sV[q] = R(0);
+            e[r] = uu[r] = vv[r] = R(0);
             Au[r] = Bu[r] = Av[r] = Bv[r] = u0[r] = v0[r] = R(0);
         }
+        sE[q] = e[r];
+        sU[q] = uu[r];
+        sV[q] = vv[r];
     }
     __syncthreads();
     for (int m = 0; m < nsub; ++m) {
         // deta^m = deta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]
-        // (each column reads only its own deta here, so it can be overwritten in place)
+        // (the east and north neighbours' U, V are read before anyone rewrites them)
 #pragma unroll
         for (int r = 0; r < BC; ++r) {
-            const int ry = ry0 + r * RS, q = ry * BRX + rx;
+            const int ry = ry0 + r, q = ry * BRX + rx;
             if (rx + 1 < BRX && ry + 1 < BRY && ((wetm >> r) & 1u)) {
-                const R div = p.dy * (sU[q + 1] - sU[q]) + sDN[ry] * sV[q + BRX] - sDS[ry] * sV[q];
-                const R e = sE[q] - sCe[ry] * div;
-                sE[q] = e;
-                pE[r] += e;
+                const R vN = r + 1 < BC ? vv[r + 1] : sV[q + BRX];
+                const R div = p.dy * (sU[q + 1] - uu[r]) + sDN[ry] * vN - sDS[ry] * vv[r];
+                e[r] = e[r] - sCe[ry] * div;
+                sE[q] = e[r];
+                pE[r] += e[r];
             }
         }
         __syncthreads();
-        // U^m, V^m from eta^m (each column reads only its own U, V here)
+        // U^m, V^m from eta^m (the west and south neighbours' eta from the pass above)
 #pragma unroll
         for (int r = 0; r < BC; ++r) {
-            const int ry = ry0 + r * RS, q = ry * BRX + rx;
+            const int ry = ry0 + r, q = ry * BRX + rx;
             if (rx >= 1 && Au[r] != R(0)) {
-                const R un = sU[q] + Bu[r] - Au[r] * (sE[q] - sE[q - 1]);
+                const R un = uu[r] + Bu[r] - Au[r] * (e[r] - sE[q - 1]);
+                uu[r] = un;
                 sU[q] = un;
                 pU[r] += un - u0[r];
             }
             if (ry >= 1 && Av[r] != R(0)) {
-                const R vn = sV[q] + Bv[r] - Av[r] * (sE[q] - sE[q - BRX]);
-                sV[q] = vn;
+                const R eS = r > 0 ? e[r - 1] : sE[q - BRX];
+                const R vn = vv[r] + Bv[r] - Av[r] * (e[r] - eS);
+                vv[r] = vn;
+                if (r == 0) sV[q] = vn;   // only the thread below reads it
                 pV[r] += vn - v0[r];
             }
         }
@@ -1049,12 +1058,12 @@ __device__ __forceinline__ void baro_region(
 #pragma unroll
     for (int r = 0; r < BC; ++r) {
         if (!((ownm >> r) & 1u)) continue;
-        const int ry = ry0 + r * RS, q = ry * BRX + rx;
+        const int ry = ry0 + r;
         int jw = 0;
         const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
-        Eb[c] = sE[q];
-        Ub[c] = sU[q];
-        Vb[c] = sV[q];
+        Eb[c] = e[r];
+        Ub[c] = uu[r];
+        Vb[c] = vv[r];
         // one thread owns each cell: a reduction in memory is the plain FP64 add, issued
         // without waiting for the old value
         atomicAdd(&accE[c], (double)pE[r]);
