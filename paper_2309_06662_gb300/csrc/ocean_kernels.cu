@@ -28,6 +28,10 @@ constexpr int TPB = 128;
 // multiplications that the compiler may not fuse into a neighbouring add
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+// reciprocal of a Thomas pivot (>= 1 by construction): exact in FP64, the fast
+// approximate reciprocal (2 ulp) in the mixed form
+__device__ __forceinline__ double rcp_pivot(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_pivot(float x) { return __fdividef(1.0f, x); }
 
 inline int nblocks(long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
@@ -525,7 +529,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                            + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
                 const R Ss = S0 + p.dt * gS
                            + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
-                const R inv = R(1) / ((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
+                const R inv = rcp_pivot((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
                 cprev = -hi * inv;
                 dTprev = (Ts + lo * dTprev) * inv;
                 dSprev = (Ss + lo * dSprev) * inv;
@@ -778,7 +782,7 @@ __device__ __forceinline__ void momentum_tile(
                         ? p.dt * R(0.5) * (sm.nu[sc][ty + 1][(tx) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
                         ? p.dt * R(0.5) * (sm.nu[sn][ty + 1][(tx) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
-                    const R inv = R(1) / ((R(1) + lo + hi) + lo * cuk);
+                    const R inv = rcp_pivot((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
                     cu[ck] = cuk;
@@ -808,7 +812,7 @@ __device__ __forceinline__ void momentum_tile(
                         ? p.dt * R(0.5) * (sm.nu[sc][ty][(tx + 1) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
                     const R hi = k < nz - 1
                         ? p.dt * R(0.5) * (sm.nu[sn][ty][(tx + 1) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
-                    const R inv = R(1) / ((R(1) + lo + hi) + lo * cvk);
+                    const R inv = rcp_pivot((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
                     cv[ck] = cvk;
@@ -826,39 +830,46 @@ __device__ __forceinline__ void momentum_tile(
         bar_inval(&sm.bar[2]);
     }
     if (!STEP || !mine) return;
-    // back substitutions down the column, four levels' coefficients loaded at once
-    auto back = [&](R x, int kf, R* __restrict__ xn, const R* __restrict__ cx) {
-        R s = p.dz[nz - 1] * x;
-        for (int k = nz - 2; k >= kf; k -= 4) {
-            R cq[4], dq[4];
+    // back substitutions of u and v down the column together, both coefficients of four
+    // levels loaded at once (each recurrence itself is serial)
+    R xu = duk, xv = dvk;   // level nz-1: x = d'
+    R su = p.dz[nz - 1] * xu, sv = p.dz[nz - 1] * xv;
+    const int kf = ku < kv ? ku : kv;
+    for (int k = nz - 2; k >= kf; k -= 4) {
+        R cuq[4], duq[4], cvq[4], dvq[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const long ck = (long)(k - q) * P + c2;
-                const bool in = k - q >= kf;
-                cq[q] = in ? cx[ck] : R(0);
-                dq[q] = in ? xn[ck] : R(0);
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k - q) * P + c2;
+            const bool inu = k - q >= ku, inv = k - q >= kv;
+            cuq[q] = inu ? cu[ck] : R(0);
+            duq[q] = inu ? un[ck] : R(0);
+            cvq[q] = inv ? cv[ck] : R(0);
+            dvq[q] = inv ? vn[ck] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long ck = (long)(k - q) * P + c2;
+            if (k - q >= ku) {
+                xu = duq[q] - cuq[q] * xu;
+                un[ck] = xu;
+                su += p.dz[k - q] * xu;
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (k - q < kf) break;
-                x = dq[q] - cq[q] * x;
-                xn[(long)(k - q) * P + c2] = x;
-                s += p.dz[k - q] * x;
+            if (k - q >= kv) {
+                xv = dvq[q] - cvq[q] * xv;
+                vn[ck] = xv;
+                sv += p.dz[k - q] * xv;
             }
         }
-        return s;
-    };
+    }
     if (ku < nz) {
-        const R s = back(duk, ku, un, cu);   // from level nz-1
         Un[c2] = sUn;
         GU[c2] = sGU;
-        Su[c2] = s;
+        Su[c2] = su;
     }
     if (kv < nz) {
-        const R s = back(dvk, kv, vn, cv);
         Vn[c2] = sVn;
         GV[c2] = sGV;
-        Sv[c2] = s;
+        Sv[c2] = sv;
     }
 }
 
