@@ -616,6 +616,7 @@ struct __align__(128) MomentumSmem {
     R z[2][TY + 5][TX + 5];
     R K[2][TY + 1][TX + 1];
     short kbz[TY + 5][TX + 5], kbzin[TY + 5][TX + 5];
+    R zdxS[TY + 5], zdxN[TY + 5], zrA[TY + 5];   // per corner row: dxc south, north; 1/A_z
     int kmin;
 };
 
@@ -646,6 +647,13 @@ __device__ __forceinline__ void momentum_tile(
         const long c = tix(g, i0 - 2 + b, j0 - 2 + a);
         sm.kbz[a][b] = g.kbz[c];
         sm.kbzin[a][b] = g.kbzin[c];
+    }
+    if (tid < TY + 5) {
+        const int jc = j0 - 2 + tid;
+        const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
+        sm.zdxS[tid] = p.dxc[jrc - 1];
+        sm.zdxN[tid] = p.dxc[jrc];
+        sm.zrA[tid] = p.rAz[jrc];
     }
     const int ku = mine ? (int)g.kbu[c2] : nz, kv = mine ? (int)g.kbv[c2] : nz;
     __syncthreads();
@@ -707,15 +715,13 @@ __device__ __forceinline__ void momentum_tile(
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
         for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
             const int a = q / (TX + 5), b = q % (TX + 5);
-            const int jc = j0 - 2 + a;
             R zz = R(0);
             if (k >= sm.kbz[a][b]) {
-                const int jrc = (jc < g.ny + OC_H - 1 ? jc : g.ny + OC_H - 1) + OC_H;
                 // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
                 // v(i-1, jc) = v[a][b]
                 const R circ = p.dy * (sm.v[sc][a][(b + 1) + 1] - sm.v[sc][a][(b) + 1])
-                             - (p.dxc[jrc] * sm.u[sc][a + 1][(b) + 2] - p.dxc[jrc - 1] * sm.u[sc][a][(b) + 2]);
-                zz = circ * p.rAz[jrc];
+                             - (sm.zdxN[a] * sm.u[sc][a + 1][(b) + 2] - sm.zdxS[a] * sm.u[sc][a][(b) + 2]);
+                zz = circ * sm.zrA[a];
             }
             sm.z[fb][a][b] = zz;
         }
