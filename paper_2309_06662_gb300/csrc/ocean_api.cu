@@ -57,6 +57,7 @@ struct ocean_s {
     void *u[2] = {}, *v[2] = {}, *T[2] = {}, *S[2] = {};
     void *Gu = nullptr, *Gv = nullptr, *GT = nullptr, *GS = nullptr;
     void *w = nullptr, *p = nullptr, *kap = nullptr, *nu = nullptr, *wk = nullptr;
+    double* wind_raw = nullptr;   // staging of the host wind stress, [2][ny][nx]
     // 2-D of element size esz
     void *taux_s = nullptr, *tauy_s = nullptr, *Un = nullptr, *Vn = nullptr, *GU = nullptr,
          *GV = nullptr, *Su = nullptr, *Sv = nullptr, *Ub = nullptr, *Vb = nullptr,
@@ -182,6 +183,7 @@ size_t layout(ocean_t m, char* base) {
     for (int b = 0; b < 2; ++b) { m->u[b] = f3(); m->v[b] = f3(); m->T[b] = f3(); m->S[b] = f3(); }
     m->Gu = f3(); m->Gv = f3(); m->GT = f3(); m->GS = f3();
     m->w = f3(); m->p = f3(); m->kap = f3(); m->nu = f3(); m->wk = f3();
+    m->wind_raw = c.take<double>(2 * (size_t)m->nx * m->ny);
     void** two[] = {&m->taux_s, &m->tauy_s, &m->Un, &m->Vn, &m->GU, &m->GV, &m->Su, &m->Sv,
                     &m->Ub, &m->Vb, &m->dE, &m->paccE, &m->paccU, &m->paccV, &m->gxe, &m->gye,
                     &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv, &m->Ub2, &m->Vb2,
@@ -390,20 +392,32 @@ int build_geometry(ocean_t m, const double* depth) {
     return OCEAN_OK;
 }
 
+// The host arrays go to a device staging area by two copies on the model's stream; a
+// kernel scales them by 1 / (rho0 dz_top) and writes them into the padded fields.
+// Returns once the host arrays have been read.
 int set_wind(ocean_t m, const double* taux, const double* tauy) {
-    const long n2 = m->n2pad;
-    std::vector<double> tx(n2, 0.0), ty(n2, 0.0);
+    const size_t n = (size_t)m->nx * m->ny;
+    double* raw = m->wind_raw;
+    if (taux)
+        OC_CUDA(m, cudaMemcpyAsync(raw, taux, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    if (tauy)
+        OC_CUDA(m, cudaMemcpyAsync(raw + n, tauy, n * sizeof(double), cudaMemcpyHostToDevice,
+                                   m->stream));
     const double s = 1.0 / (m->prm.rho0 * m->dz[m->nz - 1]);
-    for (int j = 0; j < m->ny; ++j)
-        for (int i = 0; i < m->nx; ++i) {
-            const long c = hix2(m, i, j);
-            if (taux) tx[c] = taux[(size_t)j * m->nx + i] * s;
-            if (tauy) ty[c] = tauy[(size_t)j * m->nx + i] * s;
-        }
-    upload_real(m, tx, m->taux_s);
-    upload_real(m, ty, m->tauy_s);
-    return cudaGetLastError() == cudaSuccess ? OCEAN_OK
-                                             : fail(m, OCEAN_ERR_CUDA, "wind stress upload failed");
+    GeoD g{};
+    g.nx = m->nx; g.ny = m->ny; g.nz = m->nz; g.px = m->px; g.py = m->py; g.pitch = m->pitch;
+    g.plane = m->plane;
+    if (m->prec == OCEAN_FP64)
+        launch_wind<double>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
+                            reinterpret_cast<double*>(m->taux_s), reinterpret_cast<double*>(m->tauy_s),
+                            m->stream);
+    else
+        launch_wind<float>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
+                           reinterpret_cast<float*>(m->taux_s), reinterpret_cast<float*>(m->tauy_s),
+                           m->stream);
+    OC_CUDA(m, cudaGetLastError());
+    OC_CUDA(m, cudaStreamSynchronize(m->stream));
+    return OCEAN_OK;
 }
 
 // field location and mask: which lowest-wet-level array applies (0 cell, 1 u, 2 v)

@@ -275,6 +275,11 @@ template <typename R>
 void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s);
 template <typename R>
 void launch_halo2(const GeoD& g, R* f, cudaStream_t s);
+// surface wind stress: o[x|y][column] = (R)(t[x|y][j nx + i] * scale) on the padded
+// plane (zero where t is null)
+template <typename R>
+void launch_wind(const GeoD& g, const double* tx, const double* ty, double scale, R* ox, R* oy,
+                 cudaStream_t s);
 template <typename R>
 int setup_kernel_attributes(int nz);
 

@@ -1257,6 +1257,16 @@ template <typename R> struct PtrPack { R* f[4]; };
 // padded width (so the corners come out right)
 
 template <typename R>
+__global__ void k_wind(GeoD g, const double* __restrict__ tx, const double* __restrict__ ty,
+                       double scale, R* __restrict__ ox, R* __restrict__ oy) {
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long)g.nx * g.ny) return;
+    const long c2 = ix2(g, (int)(c % g.nx), (int)(c / g.nx));
+    ox[c2] = tx ? (R)(tx[c] * scale) : R(0);
+    oy[c2] = ty ? (R)(ty[c] * scale) : R(0);
+}
+
+template <typename R>
 __global__ void k_halo_x_pack(GeoD g, PtrPack<R> pk, int nf, int nlev) {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long per = (long)2 * OC_H * g.ny;
@@ -1309,6 +1319,13 @@ void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s) {
 }
 
 template <typename R>
+void launch_wind(const GeoD& g, const double* tx, const double* ty, double scale, R* ox, R* oy,
+                 cudaStream_t s) {
+    const long n = (long)g.nx * g.ny;
+    k_wind<R><<<nblocks(n, TPB), TPB, 0, s>>>(g, tx, ty, scale, ox, oy);
+}
+
+template <typename R>
 void launch_halo2(const GeoD& g, R* f, cudaStream_t s) {
     halo_pack<R>(g, &f, 1, 1, s);
 }
@@ -1353,16 +1370,21 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
         const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
         const double ac = m.Ac[j + OC_H], av = m.dxv[j + OC_H] * m.dy;
         const R rdx = (R)m.rdxc[j + OC_H];
-        double tcol = 0.0, scol = 0.0;
+        // a column's anomaly content in the path's precision (in the mixed form an FP32
+        // sum of at most nz terms, far below the 1e-6 the mixed conservation holds to),
+        // the sums over columns in compensated FP64; land cells hold 0 and are skipped
+        R tcol = R(0), scol = R(0);
         R ku2 = R(0), kv2 = R(0);
-        for (int k = 0; k < g.nz; ++k) {
+        const int k0 = min(kb, min(ku, kv));
+#pragma unroll 4
+        for (int k = k0; k < g.nz; ++k) {
             const long ck = k * g.plane + c2;
             const R tq = T[ck], sq = S[ck], uq = u[ck], vq = v[ck];
             bad = bad || !isfinite(tq) || !isfinite(sq) || !isfinite(uq) || !isfinite(vq);
             const R dzr = (R)m.dz[k];
             if (k >= kb) {
-                tcol = fma((double)tq, m.dz[k], tcol);
-                scol = fma((double)sq, m.dz[k], scol);
+                tcol = fma(tq, dzr, tcol);
+                scol = fma(sq, dzr, scol);
                 cflr = fmax(cflr, fabs(w[ck]) * (R)m.dtdz[k]);
             }
             if (k >= ku) {
@@ -1375,8 +1397,8 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
             }
         }
         if (kb < g.nz) {
-            cs_add(sT, (tcol + m.colT[kb]) * ac);
-            cs_add(sS, (scol + m.colS[kb]) * ac);
+            cs_add(sT, ((double)tcol + m.colT[kb]) * ac);
+            cs_add(sS, ((double)scol + m.colS[kb]) * ac);
             cs_add(sV, m.colV[kb] * ac);
             cs_add(sE, eta[c2] * ac);
         }
@@ -1671,6 +1693,8 @@ int tile_wait_failed() {
     template void launch_correct<R>(const KP<R>&, const StepBuffers<R>&, cudaStream_t);     \
     template void launch_halo3<R>(const GeoD&, R* const*, int, cudaStream_t);               \
     template void launch_halo2<R>(const GeoD&, R*, cudaStream_t);                           \
+    template void launch_wind<R>(const GeoD&, const double*, const double*, double, R*, R*,  \
+                                 cudaStream_t);                                             \
     template void launch_diagnostics<R>(const GeoD&, const DiagMetrics&, const R*, const R*, \
                                         const R*, const R*, const R*, const double*,        \
                                         double*, double*, cudaStream_t);                \
