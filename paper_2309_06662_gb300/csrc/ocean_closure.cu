@@ -16,10 +16,12 @@ __device__ __forceinline__ float softplus_c(float z) { return z > 20.f ? z : log
 
 // Per interior column c = j nx + i: raw features (T, S, centre u, v on levels; N^2 and
 // shear^2 on bottom faces), z-scored with mu/sigma where the entry counts (wet level or
-// interior face), else 0.  emit(fi, x, k, w, f, gT, gS) receives feature fi = q nz + k,
-// its value, and for q = 0 the level's masks and vertical gradients.
+// interior face), else 0, for the levels [k0, k1).  emit(fi, x, k, w, f, gT, gS) receives
+// feature fi = q nz + k, its value, and for q = 0 the level's masks and vertical
+// gradients.
 template <typename R, typename Emit>
-__device__ __forceinline__ void column_features(const KP<R>& p, long c, const R* __restrict__ u,
+__device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, int k1,
+                                                const R* __restrict__ u,
                                                 const R* __restrict__ v, const R* __restrict__ T,
                                                 const R* __restrict__ S,
                                                 const float* __restrict__ mu,
@@ -28,8 +30,13 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, const R*
     const int i = (int)(c % g.nx), j = (int)(c / g.nx), nz = g.nz;
     const long c2 = ix2(g, i, j), P = g.plane;
     const int kb = g.kb[c2];
-    float ubp = 0.f, vbp = 0.f;
-    for (int k = 0; k < nz; ++k) {
+    float ubp = 0.f, vbp = 0.f;   // centre u, v of level k-1 (0 below the sea floor)
+    if (k0 > 0 && k0 - 1 >= kb) {
+        const long cm = (long)(k0 - 1) * P + c2;
+        ubp = 0.5f * (float)(u[cm] + u[cm + 1]);
+        vbp = 0.5f * (float)(v[cm] + v[cm + g.pitch]);
+    }
+    for (int k = k0; k < k1; ++k) {
         const long ck = k * P + c2;
         const bool w = k >= kb, f = k >= kb + 1;
         const float ub = w ? 0.5f * (float)(u[ck] + u[ck + 1]) : 0.f;
@@ -72,7 +79,7 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const int nz = g.nz;
-    column_features<R>(p, c, u, v, T, S, mu, sigma,
+    column_features<R>(p, c, 0, nz, u, v, T, S, mu, sigma,
                        [&](int fi, float x, int k, bool w, bool f, float gT, float gS) {
                            if (Xf) Xf[c * 6 * nz + fi] = x;
                            if (Xb) Xb[c * 6 * nz + fi] = __float2bfloat16_rn(x);
@@ -87,35 +94,38 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
 
 // Rows of feature matrices and network outputs pass through shared memory, so the
 // row-major [column][feature] arrays are written and read with coalesced accesses
-// (one thread per column would touch one 2- or 4-byte element per row per access): a
-// block of fcols(nz) columns, rows padded by one 4-byte word (no bank conflicts).
-__host__ __device__ inline int fcols(int nz) { return nz <= 48 ? 128 : 32; }
+// (one thread per column would touch one 2- or 4-byte element per row per access).  A
+// block of 32 columns x XQ level ranges: thread (c, q) handles the levels
+// [q L, q L + L) of column c, L = ceil(nz / XQ), so that a column's serial chain of
+// loads is a quarter as long; rows padded by one 4-byte word (no bank conflicts).
+constexpr int XC = 32, XQ = 4;
 
 // BF16 features of the step's network pass (no masks or gradients)
 template <typename R>
-__global__ void __launch_bounds__(128) k_closure_xb(KP<R> p, const R* __restrict__ u,
-                                                    const R* __restrict__ v,
-                                                    const R* __restrict__ T,
-                                                    const R* __restrict__ S,
-                                                    const float* __restrict__ mu,
-                                                    const float* __restrict__ sigma,
-                                                    __nv_bfloat16* __restrict__ Xb) {
+__global__ void __launch_bounds__(XC * XQ) k_closure_xb(KP<R> p, const R* __restrict__ u,
+                                                        const R* __restrict__ v,
+                                                        const R* __restrict__ T,
+                                                        const R* __restrict__ S,
+                                                        const float* __restrict__ mu,
+                                                        const float* __restrict__ sigma,
+                                                        __nv_bfloat16* __restrict__ Xb) {
     extern __shared__ __align__(16) unsigned char fx_raw[];
     __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(fx_raw);
     const GeoD& g = p.g;
-    const int nz = g.nz, F = 6 * nz, ld = F + 2, FC = fcols(nz);
-    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * FC;
-    const int t = threadIdx.x;
-    if (t < FC && c0 + t < ncol) {
-        __nv_bfloat16* row = tile + (long)t * ld;
-        column_features<R>(p, c0 + t, u, v, T, S, mu, sigma,
+    const int nz = g.nz, F = 6 * nz, ld = F + 2;
+    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * XC;
+    const int t = threadIdx.x, tc = t % XC, tq = t / XC;
+    const int L = (nz + XQ - 1) / XQ, k0 = tq * L, k1 = min(k0 + L, nz);
+    if (c0 + tc < ncol && k0 < k1) {
+        __nv_bfloat16* row = tile + (long)tc * ld;
+        column_features<R>(p, c0 + tc, k0, k1, u, v, T, S, mu, sigma,
                            [&](int fi, float x, int, bool, bool, float, float) {
                                row[fi] = __float2bfloat16_rn(x);
                            });
     }
     __syncthreads();
     // the block's rows are contiguous in Xb: copy them out as 4-byte pairs (F is even)
-    const long rows = ncol - c0 < FC ? ncol - c0 : FC;
+    const long rows = ncol - c0 < XC ? ncol - c0 : XC;
     const int pairs = F / 2;
     unsigned* dst = reinterpret_cast<unsigned*>(Xb + c0 * F);
     for (long q = t; q < rows * pairs; q += blockDim.x) {
@@ -126,34 +136,43 @@ __global__ void __launch_bounds__(128) k_closure_xb(KP<R> p, const R* __restrict
 
 // network outputs -> extra diffusivity on the interior wet faces (added to the
 // Richardson-number value already in kap) and tracer corrections; the block's rows of Y
-// come in through shared memory (coalesced)
+// come in through shared memory (coalesced), each column's levels split as above
 template <typename R>
-__global__ void __launch_bounds__(128) k_closure_apply(KP<R> p, const float* __restrict__ Y,
-                                                       float ks, float gt, float gs,
-                                                       R* __restrict__ kap, R* __restrict__ dGT,
-                                                       R* __restrict__ dGS) {
+__global__ void __launch_bounds__(XC * XQ) k_closure_apply(KP<R> p, const float* __restrict__ Y,
+                                                           float ks, float gt, float gs,
+                                                           R* __restrict__ kap,
+                                                           R* __restrict__ dGT,
+                                                           R* __restrict__ dGS) {
     extern __shared__ __align__(16) unsigned char fy_raw[];
     float* tile = reinterpret_cast<float*>(fy_raw);
+    __shared__ int s_ok[XC];
     const GeoD& g = p.g;
-    const int nz = g.nz, F = 3 * nz, ld = F + 1, FC = fcols(nz);
-    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * FC;
-    const int t = threadIdx.x;
-    const long rows = ncol - c0 < FC ? ncol - c0 : FC;
+    const int nz = g.nz, F = 3 * nz, ld = F + 1;
+    const long ncol = (long)g.nx * g.ny, c0 = (long)blockIdx.x * XC;
+    const int t = threadIdx.x, tc = t % XC, tq = t / XC;
+    const long rows = ncol - c0 < XC ? ncol - c0 : XC;
     const float* src = Y + c0 * F;
     for (long q = t; q < rows * F; q += blockDim.x) {
         const long r = q / F;
         tile[r * ld + (q - r * F)] = src[q];
     }
     __syncthreads();
-    if (t >= FC || c0 + t >= ncol) return;
-    const long c = c0 + t;
+    if (tq == 0) {   // a column's outputs are applied only if all of them are finite
+        bool ok = true;
+        const float* y = tile + (long)tc * ld;
+        for (int q = 0; q < F; ++q) ok = ok && isfinite(y[q]);
+        s_ok[tc] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const int L = (nz + XQ - 1) / XQ, k0 = tq * L, k1 = min(k0 + L, nz);
+    if (c0 + tc >= ncol || k0 >= k1) return;
+    const long c = c0 + tc;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j), P = g.plane;
     const int kb = g.kb[c2];
-    const float* y = tile + (long)t * ld;
-    bool ok = true;
-    for (int q = 0; q < F; ++q) ok = ok && isfinite(y[q]);
-    for (int k = 0; k < nz; ++k) {
+    const float* y = tile + (long)tc * ld;
+    const bool ok = s_ok[tc] != 0;
+    for (int k = k0; k < k1; ++k) {
         const long ck = k * P + c2;
         if (ok && k >= kb + 1) kap[ck] = kap[ck] + (R)(ks * softplus_c(y[k]));
         dGT[ck] = (ok && k >= kb) ? (R)(gt * y[nz + k]) : R(0);
@@ -295,9 +314,8 @@ void launch_closure_features(const KP<R>& p, const R* u, const R* v, const R* T,
                              cudaStream_t s) {
     const long ncol = (long)p.g.nx * p.g.ny;
     if (Xb && !Xf && !face && !wet && !dzT && !dzS) {   // the step's BF16 features
-        const int FC = fcols(p.g.nz);
-        const size_t smem = (size_t)FC * (6 * p.g.nz + 2) * sizeof(__nv_bfloat16);
-        k_closure_xb<R><<<(int)((ncol + FC - 1) / FC), 128, smem, s>>>(
+        const size_t smem = (size_t)XC * (6 * p.g.nz + 2) * sizeof(__nv_bfloat16);
+        k_closure_xb<R><<<(int)((ncol + XC - 1) / XC), XC * XQ, smem, s>>>(
             p, u, v, T, S, mu, sigma, reinterpret_cast<__nv_bfloat16*>(Xb));
         return;
     }
@@ -309,14 +327,13 @@ template <typename R>
 void launch_closure_apply(const KP<R>& p, const float* Y, float ks, float gt, float gs, R* kap,
                           R* dGT, R* dGS, cudaStream_t s) {
     const long ncol = (long)p.g.nx * p.g.ny;
-    const int FC = fcols(p.g.nz);
-    const size_t smem = (size_t)FC * (3 * p.g.nz + 1) * sizeof(float);
-    k_closure_apply<R><<<(int)((ncol + FC - 1) / FC), 128, smem, s>>>(p, Y, ks, gt, gs, kap, dGT,
-                                                                       dGS);
+    const size_t smem = (size_t)XC * (3 * p.g.nz + 1) * sizeof(float);
+    k_closure_apply<R><<<(int)((ncol + XC - 1) / XC), XC * XQ, smem, s>>>(p, Y, ks, gt, gs, kap,
+                                                                          dGT, dGS);
 }
 
-// the tiled kernels' shared memory (up to ~75 KB, above the default 48 KB); set before
-// the first launch and outside stream capture
+// the tiled kernels' shared memory (above the default 48 KB for nz > 125); set before the
+// first launch and outside stream capture
 template <typename R>
 int closure_tiles_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_closure_xb<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
