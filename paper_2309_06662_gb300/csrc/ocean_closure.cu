@@ -97,8 +97,8 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
 // (one thread per column would touch one 2- or 4-byte element per row per access).  A
 // block of 32 columns x XQ level ranges: thread (c, q) handles the levels
 // [q L, q L + L) of column c, L = ceil(nz / XQ), so that a column's serial chain of
-// loads is a quarter as long; rows padded by one 4-byte word (no bank conflicts).
-constexpr int XC = 32, XQ = 4;
+// loads is an eighth as long; rows padded by one 4-byte word (no bank conflicts).
+constexpr int XC = 32, XQ = 8;
 
 // BF16 features of the step's network pass (no masks or gradients)
 template <typename R>
