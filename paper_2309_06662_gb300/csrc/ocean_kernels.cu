@@ -101,12 +101,15 @@ __device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* 
     R wk = R(0);
     w[kb * P + c2] = wk;
     R Tm = R(0), Sm = R(0), ub = R(0), vb = R(0);
-    for (int k4 = kb; k4 < nz; k4 += 4) {
+    // every lane of the warp walks the same levels (from the warp's deepest sea floor),
+    // so that each load instruction reads one level's row: coalesced
+    const int kw = __reduce_min_sync(__activemask(), kb);
+    for (int k4 = kw; k4 < nz; k4 += 4) {
         R Tq[4], Sq[4], u0q[4], u1q[4], v0q[4], v1q[4];   // four levels' operands at once
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const long ck = (long)(k4 + q) * P + c2;
-            const bool in = k4 + q < nz;
+            const bool in = k4 + q < nz && k4 + q >= kb;
             Tq[q] = in ? T[ck] : R(0);
             Sq[q] = in ? S[ck] : R(0);
             u0q[q] = in ? u[ck] : R(0);
@@ -118,6 +121,7 @@ __device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* 
         for (int q = 0; q < 4; ++q) {
             const int k = k4 + q;
             if (k >= nz) break;
+            if (k < kb) continue;
             const long ck = k * P + c2;
             const R Tk = Tq[q], Sk = Sq[q];
             const R u0 = u0q[q], u1 = u1q[q], v0 = v0q[q], v1 = v1q[q];
@@ -1149,8 +1153,9 @@ __device__ __forceinline__ void correct_col(const KP<R>& p, const long c, const 
     const int k0 = slab * CORR_SLAB, k1 = k0 + CORR_SLAB < g.nz ? k0 + CORR_SLAB : g.nz;
     const int ku = g.kbu[c2], kv = g.kbv[c2];
     const R cu = corrU[c2], cv = corrV[c2];
-    // u and v of four levels loaded at once (eight loads in flight per column)
-    const int kmn = ku < kv ? ku : kv;
+    // u and v of four levels loaded at once (eight loads in flight per column), every
+    // lane of the warp on the same levels (coalesced)
+    const int kmn = __reduce_min_sync(__activemask(), ku < kv ? ku : kv);
     for (int k = k0 > kmn ? k0 : kmn; k < k1; k += 4) {
         R uq[4], vq[4];
 #pragma unroll
@@ -1375,7 +1380,7 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
         // the sums over columns in compensated FP64; land cells hold 0 and are skipped
         R tcol = R(0), scol = R(0);
         R ku2 = R(0), kv2 = R(0);
-        const int k0 = min(kb, min(ku, kv));
+        const int k0 = __reduce_min_sync(__activemask(), min(kb, min(ku, kv)));   // warp-uniform
 #pragma unroll 4
         for (int k = k0; k < g.nz; ++k) {
             const long ck = k * g.plane + c2;
