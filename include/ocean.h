@@ -157,7 +157,11 @@ int ocean_get_field(ocean_t h, int field, double* host, size_t count);
 int ocean_get_reference(ocean_t h, double* Tref, double* Sref);
 int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref);
 
-/* Replace the surface wind stress (host arrays [ny][nx], copied). */
+/* Replace the surface wind stress (host arrays [ny][nx] in N/m^2, either may be NULL for
+ * zero).  The arrays are copied to a staging area of the model's device memory on the
+ * model's stream, after the work already enqueued there, and scaled into the model's
+ * fields by a kernel; the call returns once the copies have completed, so the caller may
+ * reuse the arrays at once.  Errors: OCEAN_ERR_ARG (null handle), OCEAN_ERR_CUDA. */
 int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy);
 
 /* Advance n >= 0 steps and wait for them; runs the health check when check_every > 0. */
