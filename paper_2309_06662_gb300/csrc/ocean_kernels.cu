@@ -194,20 +194,6 @@ __device__ __forceinline__ long tix(const GeoD& g, int i, int j) {
     return ix2(g, i, j);
 }
 
-// asynchronous global -> shared copies of one element (cp.async, completion tracked per
-// thread by commit/wait groups), so the next level's tile streams in while this level
-// is computed
-__device__ __forceinline__ void cp_async_el(float* dst, const float* src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_el(double* dst, const double* src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // ---- tensor-memory-accelerator copies of tiles, completed on an mbarrier
 __device__ int g_tile_err = 0;   // set when a tile's bounded wait gave up
 
