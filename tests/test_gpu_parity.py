@@ -219,3 +219,34 @@ def test_graph_replayed_step_is_bitwise_the_direct_step():
     assert launches == a.launches
     for f in ("u", "v", "T_anom", "S_anom", "eta", "Gu_prev", "GT_prev"):
         assert np.array_equal(a.get(f), b.get(f)), f
+
+
+@pytest.mark.gpu
+def test_wind_stress_replaced_after_creation_matches_the_oracle_built_with_it():
+    # the upload path of ocean_set_wind_stress (two device copies and a scatter kernel
+    # that scales each column into the padded fields): a model created with one stress
+    # and given another before stepping is the oracle built with the second; null arrays
+    # mean zero stress
+    import ctypes
+    import dataclasses
+    a = _moving_state(inputs.latlon_small_case())
+    rng = np.random.default_rng(11)
+    b = dataclasses.replace(a, taux=rng.normal(0.0, 0.1, a.taux.shape),
+                            tauy=rng.normal(0.0, 0.1, a.tauy.shape))
+    for prec, measure, tol in ((ocean.OCEAN_FP64, max_rel, FP64_TOL),
+                               (ocean.OCEAN_MIXED, rel_l2, MIXED_TOL)):
+        g = ocean.Ocean(a, precision=prec)
+        g.set_wind_stress(b.taux, b.tauy)
+        o = oracle.OracleModel(b)
+        g.step(10)
+        o.step(10)
+        errs = state_errors(g, o, measure)
+        assert all(e <= tol for e in errs.values()), (prec, errs)
+    z = dataclasses.replace(a, taux=np.zeros_like(a.taux), tauy=np.zeros_like(a.tauy))
+    g = ocean.Ocean(a, precision=ocean.OCEAN_FP64)
+    assert ocean.load().ocean_set_wind_stress(g._h, None, None) == 0
+    o = oracle.OracleModel(z)
+    g.step(10)
+    o.step(10)
+    errs = state_errors(g, o)
+    assert all(e <= FP64_TOL for e in errs.values()), errs
