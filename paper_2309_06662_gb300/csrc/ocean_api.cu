@@ -678,14 +678,13 @@ template <typename R>
 void enqueue_diagnostics(ocean_t m) {
     const KP<R> k = make_kp<R>(m, m->nstep == 0);
     const StepBuffers<R> b = make_bufs<R>(m);
-    launch_diag<R>(k, b, m->stream);   // w of the current state for the CFL number
     const size_t nr = (size_t)m->ny + 2 * OC_H;
     const int nz = m->nz;
     const double* cols = m->dlev + 4 * nz;
     DiagMetrics dm{m->drow, m->drow + nr, m->drow + 2 * nr, m->dlev, m->dlev + nz,
                    m->dlev + 2 * nz, m->dlev + 3 * nz, cols, cols + nz + 1, cols + 2 * (nz + 1),
                    m->dy, 1.0 / m->dy, m->prm.dt};
-    launch_diagnostics<R>(k.g, dm, b.u, b.v, b.T, b.S, b.w, m->eta, m->diag_part, m->diag_out,
+    launch_diagnostics<R>(k.g, dm, b.u, b.v, b.T, b.S, m->eta, m->diag_part, m->diag_out,
                           m->stream);
 }
 

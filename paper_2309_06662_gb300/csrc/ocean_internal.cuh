@@ -299,8 +299,8 @@ struct DiagMetrics {
 size_t diag_partials_bytes();
 template <typename R>
 void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v,
-                        const R* T, const R* S, const R* w, const double* eta,
-                        double* partials, double* out, cudaStream_t s);
+                        const R* T, const R* S, const double* eta, double* partials,
+                        double* out, cudaStream_t s);
 
 // Sets the message ocean_last_error(NULL) returns (entry points without a handle).
 extern "C" void oc_set_last_error(const char* msg);

@@ -1347,8 +1347,8 @@ __device__ __forceinline__ void cs_merge(CSum& a, const CSum& b) {
 template <typename R>
 __global__ void __launch_bounds__(OC_DIAG_THREADS, 4) k_diag_sums(
     GeoD g, DiagMetrics m, const R* __restrict__ u, const R* __restrict__ v,
-    const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ w,
-    const double* __restrict__ eta, double* __restrict__ partials) {
+    const R* __restrict__ T, const R* __restrict__ S, const double* __restrict__ eta,
+    double* __restrict__ partials) {
     CSum sT{0, 0}, sS{0, 0}, sE{0, 0}, sK{0, 0}, sV{0, 0};
     R cflr = R(0);
     bool bad = false;
@@ -1361,6 +1361,12 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS, 4) k_diag_sums(
         const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
         const double ac = m.Ac[j + OC_H], av = m.dxv[j + OC_H] * m.dy;
         const R rdx = (R)m.rdxc[j + OC_H];
+        // w of the current state for its CFL number, integrated up from the sea floor as
+        // the diagnostics kernel does (same operands and order): w = 0 on the floor,
+        // w_{k+1} = w_k - rac (dy dz_k (u_{i+1} - u_i) + dz_k (dxv_{j+1} v_{j+1} - dxv_j v_j))
+        const R dyr = (R)m.dy, dxvS = (R)m.dxv[j + OC_H], dxvN = (R)m.dxv[j + 1 + OC_H];
+        const R rac = (R)(1.0 / m.Ac[j + OC_H]);
+        R wk = R(0);
         // a column's anomaly content in the path's precision (in the mixed form an FP32
         // sum of at most nz terms, far below the 1e-6 the mixed conservation holds to),
         // the sums over columns in compensated FP64; land cells hold 0 and are skipped
@@ -1376,7 +1382,11 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS, 4) k_diag_sums(
             if (k >= kb) {
                 tcol = fma(tq, dzr, tcol);
                 scol = fma(sq, dzr, scol);
-                cflr = fmax(cflr, fabs(w[ck]) * (R)m.dtdz[k]);
+                cflr = fmax(cflr, fabs(wk) * (R)m.dtdz[k]);   // w on the level's floor
+                if (k < g.nz - 1) {
+                    const R div = dyr * dzr * (u[ck + 1] - uq) + dzr * (dxvN * v[ck + g.pitch] - dxvS * vq);
+                    wk = wk - div * rac;
+                }
             }
             if (k >= ku) {
                 ku2 += uq * uq * dzr;
@@ -1468,9 +1478,9 @@ size_t diag_partials_bytes() { return (size_t)OC_DIAG_BLOCKS * 12 * sizeof(doubl
 
 template <typename R>
 void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v, const R* T,
-                        const R* S, const R* w, const double* eta, double* partials,
-                        double* out, cudaStream_t s) {
-    k_diag_sums<R><<<OC_DIAG_BLOCKS, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, w, eta, partials);
+                        const R* S, const double* eta, double* partials, double* out,
+                        cudaStream_t s) {
+    k_diag_sums<R><<<OC_DIAG_BLOCKS, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
     k_diag_final<<<1, FIN_TH, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
 }
 
@@ -1687,8 +1697,8 @@ int tile_wait_failed() {
     template void launch_wind<R>(const GeoD&, const double*, const double*, double, R*, R*,  \
                                  cudaStream_t);                                             \
     template void launch_diagnostics<R>(const GeoD&, const DiagMetrics&, const R*, const R*, \
-                                        const R*, const R*, const R*, const double*,        \
-                                        double*, double*, cudaStream_t);                \
+                                        const R*, const R*, const double*, double*, double*, \
+                                        cudaStream_t);                \
     template int ens_blocks_per_sm<R>(int);                                                 \
     template void launch_ens<R>(int, const EnsMember<R>*, const EnsItem*, int, int, int*,   \
                                 int, int, cudaStream_t);
