@@ -294,7 +294,7 @@ struct DiagMetrics {
 // Conservation/health reduction; `partials` is device scratch of at least
 // diag_partials_bytes() bytes; `out` (device) receives 8 doubles:
 // {sum T dV, sum S dV, sum eta dA, KE, max CFL, nonfinite, wet volume, 0}.
-#define OC_DIAG_BLOCKS 608   /* one wave: 4 resident blocks on each of the 152 SMs */
+#define OC_DIAG_BLOCKS 456   /* one wave: 3 resident blocks on each of the 152 SMs */
 #define OC_DIAG_THREADS 256
 size_t diag_partials_bytes();
 template <typename R>

@@ -1345,7 +1345,7 @@ __device__ __forceinline__ void cs_merge(CSum& a, const CSum& b) {
 // and the CFL number in the state's own precision; then Neumaier-compensated FP64 sums
 // over the columns.
 template <typename R>
-__global__ void __launch_bounds__(OC_DIAG_THREADS, 4) k_diag_sums(
+__global__ void __launch_bounds__(OC_DIAG_THREADS, 3) k_diag_sums(
     GeoD g, DiagMetrics m, const R* __restrict__ u, const R* __restrict__ v,
     const R* __restrict__ T, const R* __restrict__ S, const double* __restrict__ eta,
     double* __restrict__ partials) {
