@@ -18,7 +18,7 @@
 //   k_correct   barotropic correction of u and v
 //   k_halo*     periodic halo copies
 // One thread owns one water column; threads of a warp hold neighbouring columns of a
-// row, so every level access is coalesced.
+// row and walk the same levels, so every level access is coalesced.
 #include "ocean_internal.cuh"
 
 namespace {
@@ -167,14 +167,15 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
 
 // ------------------------------------------------------------------ tile layout
 
-// The tracer and momentum kernels are 2.5-D tiled: a block of TX x TY threads owns a
-// TX x TY patch of columns and marches up through the levels.  At each level it stages
-// the patch (plus the halo its stencils reach) in shared memory, computes every face
-// flux / corner vorticity once, then each thread finishes its own cell.  Vertical
+// The tracer and momentum kernels are 2.5-D tiled: a block owns a TX x TY patch of
+// columns and marches up through the levels.  Each level's tiles (the patch plus the
+// halo its stencils reach, and the patch's own operands) arrive in shared memory by
+// tensor copies two levels ahead, in three rotating slots; the block computes every
+// face flux / corner vorticity of the level once, one block barrier publishes them and
+// frees the slot of the level before, and each thread finishes its own cell.  Vertical
 // stencils use a per-thread register window.  The Thomas coefficients of the implicit
 // solve go to global scratch (one value per level and column, written and read back by
-// the same thread, so they stay in L2), which keeps shared memory small and occupancy
-// bounded by registers only.
+// the same thread, so they stay in L2).
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 // The tracer block has one more warp: its 8 x 33 x-faces and 9 x 32 y-faces (552 WENO
 // pairs per level) then take two per thread of 288 instead of up to three of 256; the

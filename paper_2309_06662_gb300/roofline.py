@@ -14,6 +14,7 @@ from __future__ import annotations
 import hashlib
 import json
 import os
+import re
 from typing import Dict, Optional
 
 import numpy as np
@@ -74,10 +75,14 @@ def load_traffic(path: str, workload: str, source_digest: str) -> Optional[Dict[
 
 
 def source_digest() -> str:
-    """Digest of the 3-D kernels' source: a traffic figure taken on other source is stale."""
+    """Digest of the 3-D kernels' source code (comments and layout left out): a traffic
+    figure taken on other code is stale."""
     h = hashlib.sha256()
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
     for name in ("ocean_kernels.cu", "ocean_internal.cuh"):
-        with open(os.path.join(here, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(here, name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                  # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
