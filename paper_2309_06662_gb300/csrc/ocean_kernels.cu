@@ -691,6 +691,9 @@ __device__ __forceinline__ void momentum_tile(
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
     // own faces: u, v at k-1 (lower); levels k and k+1 come from the tiles
     R ulo = R(0), vlo = R(0);
+    // carried up one level: the vertical advection through the top face (the next
+    // level's bottom-face term) and the sum of the two nu on the top face
+    R upu = R(0), upv = R(0), nsu = R(0), nsv = R(0);
     if (mine && kstart >= 1) {
         ulo = u[(kstart - 1) * P + c2];
         vlo = v[(kstart - 1) * P + c2];
@@ -759,11 +762,11 @@ __device__ __forceinline__ void momentum_tile(
             if (du_) {   // ---------------- u at the west face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty + 1][tx]) * rdxc;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty + 1][(tx) + 3]) * rdxc;
-                R up = R(0), dn = R(0);
+                R up = R(0);
                 if (k + 1 < nz)
                     up = R(0.5) * (sm.w[sn][ty + 1][(tx) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
-                if (k - 1 >= ku)
-                    dn = R(0.5) * (sm.w[sc][ty + 1][(tx) + 3] + sm.w[sc][ty + 1][(tx + 1) + 3]) * (u0 - ulo) * p.rdzf[k];
+                const R dn = k - 1 >= ku ? upu : R(0);   // the level below's top-face term
+                upu = up;
                 const R wind = k == nz - 1 ? taux_s[c2] : R(0);
                 const R G = (ztu + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -775,10 +778,10 @@ __device__ __forceinline__ void momentum_tile(
                     sUn += p.dz[k] * u0;
                     sGU += p.dz[k] * gh;
                     const R us = u0 + p.dt * gh;
-                    const R lo = k > ku
-                        ? p.dt * R(0.5) * (sm.nu[sc][ty + 1][(tx) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
-                    const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[sn][ty + 1][(tx) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
+                    const R nt = k < nz - 1 ? sm.nu[sn][ty + 1][(tx) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3] : R(0);
+                    const R lo = k > ku ? p.dt * R(0.5) * nsu * rdz * p.rdzf[k] : R(0);
+                    const R hi = k < nz - 1 ? p.dt * R(0.5) * nt * rdz * p.rdzf[k + 1] : R(0);
+                    nsu = nt;
                     const R inv = rcp_pivot((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
@@ -789,11 +792,11 @@ __device__ __forceinline__ void momentum_tile(
             if (dv_) {   // ---------------- v at the south face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty][tx + 1]) * p.rdy;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty][(tx + 1) + 3]) * p.rdy;
-                R up = R(0), dn = R(0);
+                R up = R(0);
                 if (k + 1 < nz)
                     up = R(0.5) * (sm.w[sn][ty][(tx + 1) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
-                if (k - 1 >= kv)
-                    dn = R(0.5) * (sm.w[sc][ty][(tx + 1) + 3] + sm.w[sc][ty + 1][(tx + 1) + 3]) * (v0 - vlo) * p.rdzf[k];
+                const R dn = k - 1 >= kv ? upv : R(0);
+                upv = up;
                 const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
                 const R G = -(ztv + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
                 const long ck = Pk + c2;
@@ -805,10 +808,10 @@ __device__ __forceinline__ void momentum_tile(
                     sVn += p.dz[k] * v0;
                     sGV += p.dz[k] * gh;
                     const R vs = v0 + p.dt * gh;
-                    const R lo = k > kv
-                        ? p.dt * R(0.5) * (sm.nu[sc][ty][(tx + 1) + 3] + sm.nu[sc][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k] : R(0);
-                    const R hi = k < nz - 1
-                        ? p.dt * R(0.5) * (sm.nu[sn][ty][(tx + 1) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3]) * rdz * p.rdzf[k + 1] : R(0);
+                    const R nt = k < nz - 1 ? sm.nu[sn][ty][(tx + 1) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3] : R(0);
+                    const R lo = k > kv ? p.dt * R(0.5) * nsv * rdz * p.rdzf[k] : R(0);
+                    const R hi = k < nz - 1 ? p.dt * R(0.5) * nt * rdz * p.rdzf[k + 1] : R(0);
+                    nsv = nt;
                     const R inv = rcp_pivot((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
