@@ -446,13 +446,23 @@ __global__ void __launch_bounds__(TMA_TH) k_gemm_nt_tma(const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!*abandon) {
+        // the tile's bias in shared memory (the operand stages are free once `done` has
+        // completed): every row reads the same 128 values
+        Epi ee = e;
+        if (e.bias && e.mode != EPI_SILU_BWD) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            float* sb = reinterpret_cast<float*>(base);
+            for (int q = tid; q < TBN; q += TMA_TH) sb[q] = n0 + q < N ? e.bias[n0 + q] : 0.f;
+            __syncthreads();
+            ee.bias = sb - n0;   // indexed by the matrix column n0 + c
+        }
         const int quarter = warp & 3, half = warp >> 2;
         const int row = quarter * 32 + lane, m = m0 + row;
 #pragma unroll 1
         for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
             unsigned r[32];
             tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
-            if (m < M) epi_run32(e, m, n0 + c0, N, r);
+            if (m < M) epi_run32(ee, m, n0 + c0, N, r);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
