@@ -458,11 +458,44 @@ __global__ void __launch_bounds__(TMA_TH) k_gemm_nt_tma(const __grid_constant__ 
         }
         const int quarter = warp & 3, half = warp >> 2;
         const int row = quarter * 32 + lane, m = m0 + row;
+        if (e.mode == EPI_SILU && !e.outF && !e.outT && e.bias) {
+            // the network's hidden layers: SiLU in BF16 through a shared-memory tile, so
+            // that the rows leave as whole 256-byte segments (one thread per row would
+            // write 32 rows per store instruction); rows padded by 16 bytes
+            constexpr int LDT = TBN * 2 + 16;
+            unsigned char* tile = base + 1024;
 #pragma unroll 1
-        for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
-            unsigned r[32];
-            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
-            if (m < M) epi_run32(ee, m, n0 + c0, N, r);
+            for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
+                unsigned r[32];
+                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
+                unsigned pk[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + 2 * j;
+                    const float b0 = n < N ? ee.bias[n] : 0.f, b1 = n + 1 < N ? ee.bias[n + 1] : 0.f;
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(
+                        silu_f(__uint_as_float(r[2 * j]) + b0), silu_f(__uint_as_float(r[2 * j + 1]) + b1));
+                    pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(tile + row * LDT + c0 * 2);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            }
+            __syncthreads();
+            // 16 chunks of 16 bytes per row; the leading dimension and N are multiples of 8
+            for (int q = tid; q < TBM * (TBN / 8); q += TMA_TH) {
+                const int rr = q / (TBN / 8), cc = (q % (TBN / 8)) * 8;
+                if (m0 + rr < M && n0 + cc < N)
+                    *reinterpret_cast<uint4*>(e.outB + (long)(m0 + rr) * e.ldB + n0 + cc) =
+                        *reinterpret_cast<const uint4*>(tile + rr * LDT + cc * 2);
+            }
+        } else {
+#pragma unroll 1
+            for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
+                unsigned r[32];
+                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
+                if (m < M) epi_run32(ee, m, n0 + c0, N, r);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
