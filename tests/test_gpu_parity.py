@@ -72,7 +72,8 @@ def test_latlon_small_mixed_50_steps():
                                             ((33, 9, 3), (True, True)),
                                             ((5, 6, 1), (False, False)),
                                             ((64, 4, 2), (True, False))])
-def test_ragged_and_degenerate_shapes_fp64(shape, periodic):
+@pytest.mark.parametrize("precision", [ocean.OCEAN_FP64, ocean.OCEAN_MIXED])
+def test_ragged_and_degenerate_shapes(shape, periodic, precision):
     nx, ny, nz = shape
     rng = np.random.default_rng(nx * 100 + ny)
     T = 10 + 5 * rng.random((nz, ny, nx))
@@ -81,9 +82,13 @@ def test_ragged_and_degenerate_shapes_fp64(shape, periodic):
                  v=0.05 * rng.standard_normal((nz, ny, nx)), dt=300.0, n_substeps=10)
     c.depth[:] = 4000.0 * (0.3 + 0.7 * rng.random((ny, nx)))
     c.depth[rng.random((ny, nx)) < 0.15] = 0.0
-    g, o = run_pair(c, ocean.OCEAN_FP64, 10)
-    errs = state_errors(g, o)
-    assert all(e <= FP64_TOL for e in errs.values()), errs
+    g, o = run_pair(c, precision, 10)
+    if precision == ocean.OCEAN_FP64:
+        errs = state_errors(g, o)
+        assert all(e <= FP64_TOL for e in errs.values()), errs
+    else:
+        errs = state_errors(g, o, rel_l2)
+        assert all(e <= MIXED_TOL for e in errs.values()), errs
 
 
 def test_all_land_domain_is_inert():
