@@ -528,6 +528,225 @@ __global__ void k_wait_selftest(long long limit, int* timed_out) {
     if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
 }
 
+// ------------------------------------------------------------------ GEMM: persistent tcgen05
+//
+// The network's forward pass (bias + SiLU to BF16, or bias to FP32) as a persistent,
+// warp-specialised kernel: each block walks the 128 x 128 output tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; warp 0 issues the tensor copies of every K step into a
+// ring of PGS stages, warp 1 issues the MMAs into one of two TMEM accumulators (128
+// columns each), and warps 2..5 drain an accumulator (each its 32 TMEM lanes) while the
+// MMAs of the next tile fill the other.  Barriers: full/empty per stage (copies landed /
+// MMAs done with the stage), accf/acce per accumulator (MMAs of a tile done / its four
+// epilogue warps have read it).  The hidden layers' BF16 rows go out through a
+// warp-private shared-memory tile as whole 256-byte row segments.  Every wait is bounded;
+// after one gives up, all later waits of the block return at once and the block exits
+// (the closure's error status is set).
+
+constexpr int PGS = 2, PG_TH = 192, PG_LDT = TBN * 2 + 16;
+constexpr size_t PG_STAGE = 4 * 32 * (size_t)PG_LDT;              // four warps x 32 rows
+constexpr size_t PG_SMEM = 1024 + 2 * PGS * (size_t)TILE_BYTES + PG_STAGE + 256 * 4 + 256;
+
+__device__ __forceinline__ bool pg_wait(unsigned bar, unsigned parity, volatile int* abandon) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abandon) return false;
+        if (clock64() - t0 > 2000000000LL) {
+            *abandon = 1;
+            atomicExch(&g_tc_err, 1);
+            return false;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ CUtensorMap tA,
+                                                      const __grid_constant__ CUtensorMap tB,
+                                                      int M, int N, int K, Epi e) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        ((unsigned long long)tc_raw + 1023) & ~1023ull);
+    auto sA = [&](int st) { return base + st * TILE_BYTES; };
+    auto sB = [&](int st) { return base + (PGS + st) * TILE_BYTES; };
+    unsigned char* stage = base + 2 * PGS * TILE_BYTES;
+    float* sbias = reinterpret_cast<float*>(stage + PG_STAGE);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sbias + 256);
+    unsigned long long* empty = full + PGS;
+    unsigned long long* accf = empty + PGS;
+    unsigned long long* acce = accf + 2;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(acce + 2);
+    volatile int* abandon = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntn = (N + TBN - 1) / TBN, ntiles = ((M + TBM - 1) / TBM) * ntn;
+    const int nk = (K + TBK - 1) / TBK;
+
+    for (int q = tid; q < 256; q += PG_TH) sbias[q] = (e.bias && q < N) ? e.bias[q] : 0.f;
+    if (tid == 0) {
+        for (int st = 0; st < PGS; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&accf[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&acce[b])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abandon = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(2u * TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---- copies
+            int g = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x) {
+                const int m0 = (t / ntn) * TBM, n0 = (t % ntn) * TBN;
+                for (int kt = 0; kt < nk; ++kt, ++g) {
+                    const int st = g % PGS, use = g / PGS;
+                    if (g >= PGS && !pg_wait(smem_u32(&empty[st]), (unsigned)(use - 1) & 1u, abandon))
+                        break;
+                    mbar_expect(smem_u32(&full[st]), 2u * TILE_BYTES);
+                    tma_load_2d(smem_u32(sA(st)), &tA, kt * TBK, m0, smem_u32(&full[st]));
+                    tma_load_2d(smem_u32(sB(st)), &tB, kt * TBK, n0, smem_u32(&full[st]));
+                }
+            }
+            // copies still in flight when the block gave up: wait (bounded) for them
+            if (*abandon)
+                for (int gg = (g > PGS ? g - PGS : 0); gg < g; ++gg) {
+                    const long long t0 = clock64();
+                    unsigned ok = 0;
+                    while (!ok && clock64() - t0 < 2000000000LL)
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                            " selp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(ok)
+                            : "r"(smem_u32(&full[gg % PGS])), "r"((unsigned)(gg / PGS) & 1u)
+                            : "memory");
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---- MMAs
+            int g = 0, i = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !pg_wait(smem_u32(&acce[b]), (unsigned)((i >> 1) - 1) & 1u, abandon))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned acc_addr = tmem + (unsigned)(b * (int)TMEM_COLS);
+                bool fine = true;
+                for (int kt = 0; kt < nk; ++kt, ++g) {
+                    const int st = g % PGS;
+                    if (!pg_wait(smem_u32(&full[st]), (unsigned)(g / PGS) & 1u, abandon)) {
+                        fine = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned long long ad = sw128_desc(smem_u32(sA(st)));
+                    const unsigned long long bd = sw128_desc(smem_u32(sB(st)));
+#pragma unroll
+                    for (int k = 0; k < TBK / 16; ++k) {
+                        const unsigned acc = (kt > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+                            "l"(ad + 2ull * k), "l"(bd + 2ull * k), "r"(TC_IDESC), "r"(acc));
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                            smem_u32(&empty[st]))
+                        : "memory");
+                }
+                if (!fine) break;
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                        smem_u32(&accf[b]))
+                    : "memory");
+            }
+        }
+    } else {   // ---- epilogue: warps 2..5, each the TMEM lanes 32 (warp % 4) ..
+        const int quarter = warp & 3, row = quarter * 32 + lane;
+        unsigned char* mine = stage + (size_t)(warp - 2) * 32 * PG_LDT;   // this warp's rows
+        const bool silu = e.mode == EPI_SILU;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int b = i & 1, m0 = (t / ntn) * TBM, n0 = (t % ntn) * TBN, m = m0 + row;
+            if (!pg_wait(smem_u32(&accf[b]), (unsigned)(i >> 1) & 1u, abandon)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+            for (int c0 = 0; c0 < TBN; c0 += 32) {
+                unsigned r[32];
+                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * (int)TMEM_COLS + c0), r);
+                if (silu) {
+                    unsigned pk[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + c0 + 2 * j;
+                        const float z0 = __uint_as_float(r[2 * j]) + (n < N ? sbias[n] : 0.f);
+                        const float z1 = __uint_as_float(r[2 * j + 1]) + (n + 1 < N ? sbias[n + 1] : 0.f);
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(silu_f(z0), silu_f(z1));
+                        pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(mine + lane * PG_LDT + c0 * 2);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                } else if (m < M) {
+                    if (n0 + c0 + 32 <= N) {   // ldF is a multiple of 4: 16-byte vectors
+                        float4* o4 = reinterpret_cast<float4*>(e.outF + (long)m * e.ldF + n0 + c0);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int n = n0 + c0 + 4 * q;
+                            o4[q] = make_float4(__uint_as_float(r[4 * q]) + sbias[n],
+                                                __uint_as_float(r[4 * q + 1]) + sbias[n + 1],
+                                                __uint_as_float(r[4 * q + 2]) + sbias[n + 2],
+                                                __uint_as_float(r[4 * q + 3]) + sbias[n + 3]);
+                        }
+                    } else {
+                        for (int j = 0; j < 32; ++j) {
+                            const int n = n0 + c0 + j;
+                            if (n < N) e.outF[(long)m * e.ldF + n] = __uint_as_float(r[j]) + sbias[n];
+                        }
+                    }
+                }
+            }
+            // the accumulator is read: the MMAs of tile i + 2 may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acce[b]))
+                             : "memory");
+            if (silu) {   // this warp's 32 rows out as 256-byte segments, two rows per store
+                for (int q = lane; q < 32 * (TBN / 8); q += 32) {
+                    const int rr = q / (TBN / 8), cc = (q % (TBN / 8)) * 8;
+                    if (m0 + quarter * 32 + rr < M && n0 + cc < N)
+                        *reinterpret_cast<uint4*>(e.outB + (long)(m0 + quarter * 32 + rr) * e.ldB + n0 + cc) =
+                            *reinterpret_cast<const uint4*>(mine + rr * PG_LDT + cc * 2);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(2u * TMEM_COLS));
+}
+
 // A [M][lda], B [N][ldb] row-major BF16 (lda, ldb and K multiples of 8, 16-byte aligned
 // rows): TMA-fed when the driver encodes both tensor maps, else staged by cp.async
 void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& e,
@@ -538,6 +757,27 @@ void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K
         k_gemm_nt_tma<<<grid, TMA_TH, TMA_SMEM, s>>>(ta, tb, M, N, K, e);
     else
         k_gemm_nt_tc<<<grid, TTH, TC_SMEM, s>>>(A, lda, B, ldb, M, N, K, e);
+}
+
+// the network's forward GEMMs (bias + SiLU to BF16 rows, or bias to FP32 rows): the
+// persistent kernel on two blocks per SM when both tensor maps encode and N <= 256, else
+// gemm_nt
+void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
+                     const Epi& e, cudaStream_t s) {
+    const bool plain = (e.mode == EPI_SILU && e.outB && !e.outF && !e.outT) ||
+                       (e.mode == EPI_F32 && e.outF && (e.ldF % 4) == 0);
+    CUtensorMap ta, tb;
+    if (plain && N <= 256 && gemm_tensor_map(&ta, A, M, K, lda) &&
+        gemm_tensor_map(&tb, B, N, K, ldb)) {
+        const int tiles = ((M + TBM - 1) / TBM) * ((N + TBN - 1) / TBN);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+        k_gemm_nt_pers<<<grid, PG_TH, PG_SMEM, s>>>(ta, tb, M, N, K, e);
+        return;
+    }
+    gemm_nt(A, lda, B, ldb, M, N, K, e, s);
 }
 
 // ------------------------------------------------------------------ elementwise kernels
@@ -697,6 +937,9 @@ int closure_gemm_setup() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gemm_nt_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TMA_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_nt_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PG_SMEM);
     return (int)e;
 }
 
@@ -747,7 +990,7 @@ void closure_forward(const void* Xb, int M, const void* const* Wt, const float* 
             e.outF = Y;
             e.ldF = dims[l + 1];
         }
-        gemm_nt(a, lda, reinterpret_cast<const bf16*>(Wt[l]), dims[l], M, dims[l + 1], dims[l], e, s);
+        gemm_nt_forward(a, lda, reinterpret_cast<const bf16*>(Wt[l]), dims[l], M, dims[l + 1], dims[l], e, s);
         if (l < 3) {
             a = H[l & 1];
             lda = dims[l + 1];
