@@ -542,16 +542,18 @@ __global__ void k_wait_selftest(long long limit, int* timed_out) {
 // warp-specialised kernel: each block walks the 128 x 128 output tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...; warp 0 issues the tensor copies of every K step into a
 // ring of PGS stages, warp 1 issues the MMAs into one of two TMEM accumulators (128
-// columns each), and warps 2..5 drain an accumulator (each its 32 TMEM lanes) while the
-// MMAs of the next tile fill the other.  Barriers: full/empty per stage (copies landed /
-// MMAs done with the stage), accf/acce per accumulator (MMAs of a tile done / its four
-// epilogue warps have read it).  The hidden layers' BF16 rows go out through a
+// columns each), and warps 2..9 drain an accumulator (each its 32 TMEM lanes and one
+// column half) while the MMAs of the next tile fill the other.  Barriers: full/empty per
+// stage (copies landed / MMAs done with the stage), accf/acce per accumulator (MMAs of a
+// tile done / its eight epilogue warps have read it).  The hidden layers' BF16 rows go out through a
 // warp-private shared-memory tile as whole 256-byte row segments.  Every wait is bounded;
 // after one gives up, all later waits of the block return at once and the block exits
 // (the closure's error status is set).
 
-constexpr int PGS = 2, PG_TH = 192, PG_LDT = TBN * 2 + 16;
-constexpr size_t PG_STAGE = 4 * 32 * (size_t)PG_LDT;              // four warps x 32 rows
+// eight epilogue warps: two per TMEM lane quarter, each draining one column half
+// five operand stages (one block per SM): enough copies in flight to keep the MMAs fed
+constexpr int PGS = 5, PG_EW = 8, PG_TH = (2 + PG_EW) * 32, PG_LDT = TBN + 16;
+constexpr size_t PG_STAGE = PG_EW * 32 * (size_t)PG_LDT;          // per warp 32 rows x 64 columns
 constexpr size_t PG_SMEM = 1024 + 2 * PGS * (size_t)TILE_BYTES + PG_STAGE + 256 * 4 + 256;
 
 __device__ __forceinline__ bool pg_wait(unsigned bar, unsigned parity, volatile int* abandon) {
@@ -602,7 +604,8 @@ __global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ 
         }
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&accf[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&acce[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acce[b])),
+                         "r"((unsigned)PG_EW));
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         *abandon = 0;
@@ -685,8 +688,8 @@ __global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ 
                     : "memory");
             }
         }
-    } else {   // ---- epilogue: warps 2..5, each the TMEM lanes 32 (warp % 4) ..
-        const int quarter = warp & 3, row = quarter * 32 + lane;
+    } else {   // ---- epilogue: warps 2..9, the TMEM lanes 32 (warp % 4) .., column half
+        const int quarter = warp & 3, row = quarter * 32 + lane, ch = ((warp - 2) / 4) * (TBN / 2);
         unsigned char* mine = stage + (size_t)(warp - 2) * 32 * PG_LDT;   // this warp's rows
         const bool silu = e.mode == EPI_SILU;
         int i = 0;
@@ -695,7 +698,7 @@ __global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ 
             if (!pg_wait(smem_u32(&accf[b]), (unsigned)(i >> 1) & 1u, abandon)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
-            for (int c0 = 0; c0 < TBN; c0 += 32) {
+            for (int c0 = ch; c0 < ch + TBN / 2; c0 += 32) {
                 unsigned r[32];
                 tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * (int)TMEM_COLS + c0), r);
                 if (silu) {
@@ -708,7 +711,7 @@ __global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ 
                         const __nv_bfloat162 h2 = __floats2bfloat162_rn(silu_bf16(z0), silu_bf16(z1));
                         pk[j] = *reinterpret_cast<const unsigned*>(&h2);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(mine + lane * PG_LDT + c0 * 2);
+                    uint4* dst = reinterpret_cast<uint4*>(mine + lane * PG_LDT + (c0 - ch) * 2);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
@@ -737,11 +740,11 @@ __global__ void __launch_bounds__(PG_TH) k_gemm_nt_pers(const __grid_constant__ 
             if (lane == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acce[b]))
                              : "memory");
-            if (silu) {   // this warp's 32 rows out as 256-byte segments, two rows per store
-                for (int q = lane; q < 32 * (TBN / 8); q += 32) {
-                    const int rr = q / (TBN / 8), cc = (q % (TBN / 8)) * 8;
-                    if (m0 + quarter * 32 + rr < M && n0 + cc < N)
-                        *reinterpret_cast<uint4*>(e.outB + (long)(m0 + quarter * 32 + rr) * e.ldB + n0 + cc) =
+            if (silu) {   // this warp's 32 half rows out as 128-byte segments, four per store
+                for (int q = lane; q < 32 * (TBN / 16); q += 32) {
+                    const int rr = q / (TBN / 16), cc = (q % (TBN / 16)) * 8;
+                    if (m0 + quarter * 32 + rr < M && n0 + ch + cc < N)
+                        *reinterpret_cast<uint4*>(e.outB + (long)(m0 + quarter * 32 + rr) * e.ldB + n0 + ch + cc) =
                             *reinterpret_cast<const uint4*>(mine + rr * PG_LDT + cc * 2);
                 }
                 __syncwarp();
@@ -768,7 +771,7 @@ void gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K
 }
 
 // the network's forward GEMMs (bias + SiLU to BF16 rows, or bias to FP32 rows): the
-// persistent kernel on two blocks per SM when both tensor maps encode and N <= 256, else
+// persistent kernel, one block per SM, when both tensor maps encode and N <= 256, else
 // gemm_nt
 void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
                      const Epi& e, cudaStream_t s) {
@@ -781,7 +784,7 @@ void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int 
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+        const int grid = tiles < sms ? tiles : sms;
         k_gemm_nt_pers<<<grid, PG_TH, PG_SMEM, s>>>(ta, tb, M, N, K, e);
         return;
     }
