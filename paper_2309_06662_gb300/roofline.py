@@ -74,11 +74,12 @@ def load_traffic(path: str, workload: str, source_digest: str) -> Optional[Dict[
     return None
 
 
-def source_digest() -> str:
+def source_digest(csrc: Optional[str] = None) -> str:
     """Digest of the 3-D kernels' source code (comments and layout left out): a traffic
-    figure taken on other code is stale."""
+    figure taken on other code is stale.  `csrc`: the source folder (default: this
+    package's)."""
     h = hashlib.sha256()
-    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    here = csrc or os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
     for name in ("ocean_kernels.cu", "ocean_internal.cuh"):
         with open(os.path.join(here, name)) as f:
             text = f.read()
