@@ -177,7 +177,12 @@ int ocean_sync(ocean_t h);
  * state without stepping (fields OCEAN_W .. OCEAN_GS). */
 int ocean_tendencies(ocean_t h);
 
-/* Conservation and health diagnostics of the current state (synchronous). */
+/* Conservation and health diagnostics of the current state (synchronous): total tracer
+ * contents and volume (compensated FP64 over columns), kinetic energy, the largest
+ * advective CFL number (w integrated from the current u, v inside the same reduction,
+ * so the fields OCEAN_W .. OCEAN_NU are left as the last ocean_tendencies or step made
+ * them), and whether any state value is not finite.  Errors: OCEAN_ERR_ARG (null
+ * arguments), OCEAN_ERR_CUDA. */
 int ocean_diagnostics(ocean_t h, ocean_diag* out);
 
 long ocean_get_step(ocean_t h);
