@@ -290,28 +290,35 @@ class Ocean:
         return self._h
 
     def shape(self, name: str):
+        """Shape of field `name` as it crosses the ABI: (nz, ny, nx) or (ny, nx)."""
         return (self.ny, self.nx) if name in FIELDS_2D else (self.nz, self.ny, self.nx)
 
     def set(self, name: str, arr) -> None:
+        """Copy a host field in (ocean_set_field; FP64, [k][j][i], k = 0 bottom)."""
         a = np.ascontiguousarray(arr, dtype=np.float64)
         assert a.shape == self.shape(name), (name, a.shape)
         _check(load().ocean_set_field(self._h, FIELD[name], _dp(a), a.size), self._h)
 
     def get(self, name: str) -> np.ndarray:
+        """Copy a field out (ocean_get_field) as a new FP64 array."""
         out = np.zeros(self.shape(name))
         _check(load().ocean_get_field(self._h, FIELD[name], _dp(out), out.size), self._h)
         return out
 
     def step(self, n: int = 1) -> None:
+        """Advance n steps and wait for them (ocean_step, with the health check)."""
         _check(load().ocean_step(self._h, int(n)), self._h)
 
     def step_async(self, n: int = 1) -> None:
+        """Enqueue n steps on the model's stream without waiting (ocean_step_async)."""
         _check(load().ocean_step_async(self._h, int(n)), self._h)
 
     def sync(self) -> None:
+        """Wait for the model's stream; device waits that gave up raise OceanError."""
         _check(load().ocean_sync(self._h), self._h)
 
     def tendencies(self) -> None:
+        """Diagnostics and tendencies G^n of the current state without stepping."""
         _check(load().ocean_tendencies(self._h), self._h)
 
     def get_reference(self):
@@ -393,11 +400,13 @@ class Ocean:
         return t
 
     def set_wind_stress(self, taux, tauy) -> None:
+        """Replace the surface wind stress ([ny][nx], N/m^2); the arrays are copied."""
         tx = np.ascontiguousarray(taux, dtype=np.float64)
         ty = np.ascontiguousarray(tauy, dtype=np.float64)
         _check(load().ocean_set_wind_stress(self._h, _dp(tx), _dp(ty)), self._h)
 
     def diagnostics(self) -> Dict[str, float]:
+        """Conservation and health sums of the current state (ocean_diagnostics)."""
         d = OceanDiag()
         _check(load().ocean_diagnostics(self._h, ctypes.byref(d)), self._h)
         return dict(step=d.step, tracer_T=d.tracer_T, tracer_S=d.tracer_S,
