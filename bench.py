@@ -266,6 +266,24 @@ def learned_main(args, case, wname, rank, world, local, dist):
             barrier()
         res[name] = dict(ms=ev0.elapsed_time(ev1) / args.steps, launches=m.launches - l0,
                          clocks=clk.summary(), healthy=not m.diagnostics()["nonfinite"])
+        if closure == ocean.OCEAN_CLOSURE_LEARNED:
+            # end to end through the C ABI, per step: the wind stress from pinned host
+            # memory, one step with the network in the loop, the diagnostics back
+            taux = torch.from_numpy(np.ascontiguousarray(case.taux)).pin_memory().numpy()
+            tauy = torch.from_numpy(np.ascontiguousarray(case.tauy)).pin_memory().numpy()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                m.set_wind_stress(taux, tauy)
+                m.step_async(1)
+                d = m.diagnostics()
+            barrier()
+            e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist)
+            res[name]["e2e"] = {"value": cells / e2e_s * world, "unit": "cell-updates/s",
+                                "h2d_bytes_per_step": int(taux.nbytes + tauy.nbytes),
+                                "d2h_bytes_per_step": 8 * 8, "healthy": not d["nonfinite"],
+                                "what": "per step: wind stress host->device, one step with "
+                                        "the network, diagnostics device->host"}
         m.close()
         del m
         torch.cuda.empty_cache()
@@ -315,7 +333,7 @@ def learned_main(args, case, wname, rank, world, local, dist):
                          "frac": achieved / peak, "traffic": None,
                          "algorithmic_flops_per_chain": flops, "ms_per_chain": ms_net,
                          "peak_source": src},
-            "e2e": None,
+            "e2e": res["learned"]["e2e"],
             "gpu_launches": res["learned"]["launches"],
             "clocks": res["learned"]["clocks"],
             "healthy": res["learned"]["healthy"],
