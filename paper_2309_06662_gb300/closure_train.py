@@ -58,6 +58,7 @@ CONFIGS = {
 
 
 def fine_model(cfg: Dict, seed: int):
+    """The fine model of the pair (and the matching coarse case) for one seed."""
     fine_c, coarse_c = inputs.latlon_pair(cfg["nxc"], cfg["nyc"], cfg["nz"], cfg["lat"],
                                           cfg["r"], seed, cfg["dt"], cfg["ns_coarse"],
                                           cfg["ns_fine"])
@@ -75,6 +76,7 @@ def coarse_model(coarse_c, fine, hidden: int = 0):
 
 
 def check_finite(model, what: str) -> None:
+    """Raise if the model's state is no longer finite."""
     d = model.diagnostics()
     if d["nonfinite"]:
         raise RuntimeError(f"{what}: the state is not finite at step {d['step']} "
@@ -109,6 +111,7 @@ def split_east(d, cols, nx: int, frac: float):
 
 
 def concat(parts):
+    """Concatenate per-snapshot training tensors along the column axis."""
     import torch
     return {k: torch.cat([p[k] for p in parts]).contiguous() for k in parts[0]}
 
@@ -142,6 +145,7 @@ def feature_stats(d):
 
 
 def normalise(d, mu, sd):
+    """z-score the features of a training set with the given statistics."""
     import torch
     m = torch.tensor(mu, dtype=torch.float32, device="cuda")
     s = torch.tensor(sd, dtype=torch.float32, device="cuda")
@@ -240,14 +244,19 @@ def gate_heads(params, nz: int, terms, base):
 
 
 def fmt_terms(t) -> str:
+    """The four loss terms (fT, fS, gT, gS) as one short string."""
     return "/".join(f"{t[k]:.3g}" for k in ("fT", "fS", "gT", "gS"))
 
 
 def wet_rms(a: np.ndarray, b: np.ndarray, wet: np.ndarray) -> float:
+    """Root-mean-square difference of two fields over the wet cells."""
     return float(np.sqrt(np.mean((a - b)[wet] ** 2)))
 
 
 def run(cfg: Dict, log=print) -> Dict:
+    """The whole pipeline for one configuration: fine runs, coarse-grained targets,
+    training with a held-out longitude band, a priori evaluation on another seed and
+    online runs of the coarse model with and without the network; returns the results."""
     import torch
     r, nz, H = cfg["r"], cfg["nz"], cfg["hidden"]
     t0 = time.time()
@@ -351,6 +360,7 @@ def run(cfg: Dict, log=print) -> Dict:
 
 
 def main():
+    """Command line: run one configuration and print (or write) its results."""
     ap = argparse.ArgumentParser(description="Train and evaluate the learned closure.")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="half")
     ap.add_argument("--out", default=None, help="write the results as JSON")

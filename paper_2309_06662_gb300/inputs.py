@@ -167,9 +167,11 @@ class Case:
 
     @property
     def cells(self) -> int:
+        """Grid cells, land included."""
         return self.nx * self.ny * self.nz
 
     def with_params(self, **kw) -> "Case":
+        """A copy of the case with some model parameters replaced."""
         p = dict(self.params)
         p.update(kw)
         return replace(self, params=p)

@@ -55,6 +55,7 @@ def wet_cells(depth: np.ndarray, z_faces: np.ndarray, min_depth: float) -> int:
 
 
 def wet_columns(depth: np.ndarray, min_depth: float, z_faces: np.ndarray) -> int:
+    """Number of wet columns: deep enough and with a wet top level."""
     zc_top = 0.5 * (z_faces[-1] + z_faces[-2])
     return int(np.count_nonzero((depth >= min_depth) & (zc_top > -depth)))
 
