@@ -164,7 +164,17 @@ int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref);
  * reuse the arrays at once.  Errors: OCEAN_ERR_ARG (null handle), OCEAN_ERR_CUDA. */
 int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy);
 
-/* Advance n >= 0 steps and wait for them; runs the health check when check_every > 0. */
+/* Advance n >= 0 steps and wait for them; runs the health check when check_every > 0.
+ * One step n -> n+1 is the sequence of the paper's Sec. "New numerical methods for finite
+ * volume fluid dynamics on the sphere" and Sec. "Optimization of ocean free surface
+ * dynamics": the pressure and vertical-diffusivity intermediates of the state at n (Sec.
+ * "Starting from scratch with Julia"), WENO tracer and vector-invariant momentum
+ * tendencies, the quasi-second-order Adams-Bashforth predictor, backward-Euler vertical
+ * diffusion (one tridiagonal solve per column), the split-explicit barotropic sub-cycle
+ * with its time-averaging filter, and the barotropic correction of u, v.  The first step
+ * of a model (step counter 0) is forward Euler.  Errors: OCEAN_ERR_ARG (null handle,
+ * n < 0), OCEAN_ERR_CUDA, OCEAN_ERR_NONFINITE (health check), OCEAN_ERR_TIMEOUT (a
+ * bounded device wait gave up). */
 int ocean_step(ocean_t h, int n);
 
 /* Enqueue n steps on the handle's stream and return without waiting. */
@@ -177,7 +187,11 @@ int ocean_sync(ocean_t h);
  * state without stepping (fields OCEAN_W .. OCEAN_GS). */
 int ocean_tendencies(ocean_t h);
 
-/* Conservation and health diagnostics of the current state (synchronous): total tracer
+/* Conservation and health diagnostics of the current state (synchronous).  The paper
+ * measures conservation only implicitly (its runs are long and stable, Sec. "How
+ * performance was measured"); these sums are the check that a finite-volume step in
+ * flux form with a closed basin keeps sum T dV, sum S dV and sum eta dA fixed to
+ * roundoff.  Total tracer
  * contents and volume (compensated FP64 over columns), kinetic energy, the largest
  * advective CFL number (w integrated from the current u, v inside the same reduction,
  * so the fields OCEAN_W .. OCEAN_NU are left as the last ocean_tendencies or step made
@@ -319,16 +333,19 @@ int ocean_closure_targets(ocean_t coarse, const float* d_GTm, const float* d_GSm
                           const float* d_FT, const float* d_FS, float* d_GTt, float* d_GSt);
 
 /* The batched tridiagonal solve above, for callers that cannot allocate device memory:
- * code that runs while a CUDA graph is being captured (allocation cannot be captured),
- * code embedded in a framework that owns every allocation on the device, or a runtime
- * with a fixed memory budget.  It allocates nothing: the Thomas coefficients go to one
+ * code embedded in a host framework whose caching allocator owns the device's free
+ * memory (a cudaMalloc of ours could fail, or fragment its pool), a runtime with a fixed
+ * memory budget set at start-up, or a latency-bound loop that must not make the
+ * device-synchronising cudaMalloc/cudaFree calls.  It allocates nothing: the Thomas coefficients go to one
  * static device array of OCEAN_TRIDIAG_STATIC_WORDS 8-byte words (16 MiB) that every GPU
  * loading the library holds until the process exits.  Same arguments, layout and result
  * as ocean_tridiag_batched, with n >= 1 and n * nsys at most OCEAN_TRIDIAG_STATIC_WORDS
  * (OCEAN_FP64) or twice that (OCEAN_MIXED); larger requests return OCEAN_ERR_ARG with a
  * message and launch nothing.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) while that device is current; make that first call
- * before any stream capture.  All calls share the array and it keeps the last call's
+ * address (cudaGetSymbolAddress) while that device is current and keeps it for the
+ * life of the process; make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) invalidates the kept address: later calls in the same process are
+ * then invalid.  All calls share the array and it keeps the last call's
  * contents (nothing needs clearing: every value read is first written by the same
  * call); calls that overlap on the GPU race on it.  The paper has no counterpart. */
 #define OCEAN_TRIDIAG_STATIC_WORDS (1 << 21)

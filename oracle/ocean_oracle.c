@@ -9,9 +9,14 @@
  * with the CUDA path: every index, metric and formula below is written out again from
  * the discrete equations.
  *
- * The paper names the ingredients but prints no formula; the discrete reading used
- * here (every constant, stencil and boundary rule) is written out in the function
- * comments and in the design notes of the repository.  Summary of the step n -> n+1:
+ * The paper names the ingredients but prints no formula, constant or stencil; every
+ * reading taken here is stated in the comment of the function that uses it: full-cell
+ * bathymetry (a cell is wet when its centre lies above the sea floor), product-form
+ * spherical metrics, Coriolis 2 Omega sin(phi) at the row (u) and face (v) latitudes,
+ * free-slip corner vorticity, WENO-Z weights with eps = 1e-30, zero advective flux at the
+ * sea floor and the surface, the Pacanowski-Philander constants, chi = 0.1 with a
+ * forward-Euler first step, and equal averaging weights over the sub-cycle (or the
+ * power-law shape, see ora_filter_weights).  Summary of the step n -> n+1:
  *   1. buoyancy b = g[alpha(T-T0) - beta_s(S-S0)] (linear equation of state);
  *      hydrostatic pressure p, summed top -> bottom (the "hydrostatic pressure"
  *      intermediate of Sec. "Starting from scratch with Julia");

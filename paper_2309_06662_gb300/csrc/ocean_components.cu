@@ -96,10 +96,10 @@ int ocean_tridiag_batched(const void* d_a, const void* d_b, const void* d_c, con
 // ---------------------------------------------------------------------------------
 // Batched tridiagonal solve without any allocation.
 //
-// For callers that must not allocate device memory: code running while a CUDA graph
-// is being captured (an allocation is not a capturable operation), code embedded in
-// another framework that owns every allocation on the device, or a runtime with a fixed
-// memory budget.  The solve above keeps the Thomas coefficients c' in a per-thread
+// For callers that must not allocate device memory: code embedded in another framework
+// whose caching allocator owns the device's free memory, a runtime with a fixed memory
+// budget, or a latency-bound loop that must not make the device-synchronising
+// cudaMalloc/cudaFree calls.  The solve above keeps the Thomas coefficients c' in a per-thread
 // local-memory frame that the driver sets aside at launch; this variant keeps them,
 // level-major, in one file-scope device array instead, so the call needs no memory
 // beyond the caller's inputs and outputs and this module's static storage.
@@ -141,6 +141,7 @@ __global__ void k_tridiag_static(const R* __restrict__ a, const R* __restrict__ 
 }
 
 // device address of the static array on the current device, looked up once per device
+// and kept for the life of the process (a device reset would make it stale)
 std::mutex g_static_mu;
 void* g_static_ptr[128];
 

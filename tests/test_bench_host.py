@@ -69,7 +69,8 @@ def test_traffic_summary_reads_ncu_csv_and_matches_the_code_digest(tmp_path):
     # used only while the kernels' code digest matches the one recorded with it
     import csv
     sys.path.insert(0, ROOT)
-    from paper_2309_06662_gb300 import ncu_summary, roofline
+    import bench
+    from paper_2309_06662_gb300 import roofline
     hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context",
            "Stream", "Block Size", "Grid Size", "Device", "CC", "Section Name",
            "Metric Name", "Metric Unit", "Metric Value"]
@@ -87,7 +88,7 @@ def test_traffic_summary_reads_ncu_csv_and_matches_the_code_digest(tmp_path):
                                     ("gpu__time_duration.sum", "ns", "1000")):
                 w.writerow([str(lid), "1", "p", "h", "void <unnamed>::" + k + "(KP<T1>)", "1",
                             "13", "(32, 8, 1)", "(1, 1, 1)", "0", "10.3", "s", name, unit, val])
-    out = ncu_summary.traffic(str(path), "box", "box")
+    out = bench.ncu_traffic(str(path), "box", "box")
     line = [l for l in out.splitlines() if l.startswith("traffic_json:")][0]
     d = json.loads(line.split(":", 1)[1])
     from paper_2309_06662_gb300 import inputs

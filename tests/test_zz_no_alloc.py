@@ -1,6 +1,6 @@
 """ocean_tridiag_batched_static: the batched tridiagonal solve for callers that cannot
-allocate device memory (for example code running during CUDA graph capture, or inside a
-framework that owns every allocation).  It must give the same solution as
+allocate device memory (for example code inside a host framework whose allocator owns
+the device's free memory, or a runtime with a fixed memory budget).  It must give the same solution as
 ocean_tridiag_batched, call after call, and refuse requests larger than its static
 scratch before launching anything.
 
