@@ -71,6 +71,8 @@ def lib():
             L.ora_barotropic.argtypes = [ctypes.c_void_p, P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
             L.ora_set_closure_fields.argtypes = [ctypes.c_void_p, P(d), P(d), P(d)]
             L.ora_kbot.restype = i
+            L.ora_filter_weights.restype = d
+            L.ora_filter_weights.argtypes = [i, i, P(d)]
             L.ora_kbot.argtypes = [ctypes.c_void_p, i, i]
             _lib = L
     return _lib
@@ -100,6 +102,13 @@ def recon(q, inside, eps: float = 1e-30, linear: bool = False) -> float:
     return lib().ora_recon(_dp(q), ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), eps, int(linear))
 
 
+def filter_weights(ns: int, kind: int = 0):
+    """Averaging weights a_1..a_ns of the sub-cycle and their first moment sum m a_m."""
+    a = np.zeros(ns)
+    mom = lib().ora_filter_weights(int(ns), int(kind), _dp(a))
+    return a, mom
+
+
 def thomas(a, b, c, d) -> np.ndarray:
     a, b, c, d = (_f64(x) for x in (a, b, c, d))
     x = np.zeros_like(d)
@@ -121,7 +130,8 @@ class OracleModel:
                        int(case.periodic_y)], dtype=np.int32)
         dg = _f64([case.x0, case.x1, case.y0, case.y1])
         prm = _f64([p[k] for k in PRM_ORDER])
-        ip = np.array([int(p["n_substeps"]), int(p["weno_linear"])], dtype=np.int32)
+        ip = np.array([int(p["n_substeps"]), int(p["weno_linear"]), int(p.get("baro_filter", 0))],
+                      dtype=np.int32)
         keep = [_f64(case.z_faces), _f64(case.depth), _f64(case.taux), _f64(case.tauy)]
         L = lib()
         self._h = L.ora_create(ig.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(dg),

@@ -46,7 +46,8 @@ typedef struct {
     /* parameters */
     double dt, chi, g, rho0, alpha, beta_s, T0, S0, f0, betap, omega, radius;
     double nu0, ri_a, nu_b, kappa_b, kappa_conv, weno_eps, min_depth;
-    int ns, weno_linear;
+    int ns, weno_linear, filter;
+    double* fw;                      /* averaging weights a_m of the sub-cycle, m = 1..ns */
     /* column data */
     double *depth, *taux, *tauy;
     int *kb;                         /* lowest wet level, nz for land */
@@ -534,23 +535,62 @@ static void implicit_solves(ora_t* m) {
     }
 }
 
+/* ------------------------------------------------------------------ averaging filter */
+
+/*
+ * Weights a_1..a_ns of the time average that closes the barotropic sub-cycle.
+ *
+ * filter 0: equal weights a_m = 1/ns (a boxcar over the ns substeps).
+ * filter 1: the power-law shape of Shchepetkin & McWilliams (2005, Ocean Modelling 9),
+ *   s(x) = x^p (1 - x^q) - r x with p = 2, q = 4, r = 0.284.  The shape is negative near
+ *   x = 0, positive over its main lobe and returns to zero at x*, the root of
+ *   x - x^5 = r above the maximum of x - x^5 (x = 5^(-1/4)).  It is sampled at the ns
+ *   interior points x_m = m x* / (ns + 1) and normalised so that the weights sum to one.
+ * Either way the substep length follows from the first moment: dtau = dt / sum_m m a_m,
+ * which puts the centroid of the average exactly at t + dt (for the boxcar this is
+ * dtau = 2 dt / (ns + 1)).  Returns sum_m m a_m.
+ */
+double ora_filter_weights(int ns, int filter, double* a) {
+    if (filter == 0) {
+        for (int m = 0; m < ns; m++) a[m] = 1.0 / ns;
+    } else {
+        const double r = 0.284;
+        double lo = pow(5.0, -0.25), hi = 1.0;   /* x - x^5 - r: > 0 at lo, < 0 at hi */
+        for (int it = 0; it < 200; it++) {
+            double mid = 0.5 * (lo + hi);
+            if (mid - pow(mid, 5.0) - r > 0.0) lo = mid; else hi = mid;
+        }
+        double xs = 0.5 * (lo + hi), sum = 0.0;
+        for (int m = 1; m <= ns; m++) {
+            double x = m * xs / (ns + 1.0);
+            a[m - 1] = x * x * (1.0 - pow(x, 4.0)) - r * x;
+            sum += a[m - 1];
+        }
+        for (int m = 0; m < ns; m++) a[m] /= sum;
+    }
+    double mom = 0.0;
+    for (int m = 1; m <= ns; m++) mom += m * a[m - 1];
+    return mom;
+}
+
 /* ------------------------------------------------------------------ barotropic mode */
 
 /*
  * Split-explicit sub-cycle.  From eta^0 = eta (in place), U^0, V^0 (transports, m^2/s)
  * and the slow forcing GU, GV, take N_s forward-backward substeps of length
- * dtau = 2 dt/(N_s + 1):
+ * dtau = dt / sum_m m a_m (2 dt/(N_s + 1) for equal weights):
  *   eta^m = eta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]^{m-1}
  *   U^m   = U^{m-1} + dtau [-g H_u (eta^m_i - eta^m_{i-1})/dx_c + GU]
  *   V^m   = V^{m-1} + dtau [-g H_v (eta^m_j - eta^m_{j-1})/dy + GV]
- * and return the equal-weight averages over m = 1..N_s (weights 1/N_s; their first
- * moment, dtau (N_s+1)/2, is exactly dt) in eta, Ubar, Vbar.
+ * and return the averages sum_m a_m (eta, U, V)^m over m = 1..N_s with the filter's
+ * weights (ora_filter_weights; their first moment sum_m a_m m dtau is exactly dt) in
+ * eta, Ubar, Vbar.
  */
 void ora_barotropic(ora_t* m, double* eta, const double* U0, const double* V0, const double* GU,
                     const double* GV, double* Ubar, double* Vbar) {
     int nx = m->nx, ny = m->ny, ns = m->ns;
     long n2 = (long)nx * ny;
-    double dtau = 2.0 * m->dt / (ns + 1.0);
+    double dtau = m->filter == 0 ? 2.0 * m->dt / (ns + 1.0) : m->dt / ora_filter_weights(ns, m->filter, m->fw);
     double *U = malloc(n2 * sizeof(double)), *V = malloc(n2 * sizeof(double));
     double *E = malloc(n2 * sizeof(double)), *Ea = calloc(n2, sizeof(double));
     double dy = dy_(m);
@@ -578,9 +618,16 @@ void ora_barotropic(ora_t* m, double* eta, const double* U0, const double* V0, c
                 else V[c] = 0.0;
             }
         for (long c = 0; c < n2; c++) {
-            Ea[c] += E[c] / ns;
-            Ubar[c] += U[c] / ns;
-            Vbar[c] += V[c] / ns;
+            if (m->filter == 0) {
+                Ea[c] += E[c] / ns;
+                Ubar[c] += U[c] / ns;
+                Vbar[c] += V[c] / ns;
+            } else {
+                double a = m->fw[step - 1];
+                Ea[c] += a * E[c];
+                Ubar[c] += a * U[c];
+                Vbar[c] += a * V[c];
+            }
         }
     }
     memcpy(eta, Ea, n2 * sizeof(double));
@@ -730,7 +777,7 @@ void ora_diagnostics(ora_t* m, double* out) {
  * zf[nz+1] bottom to top; depth, taux, tauy [ny][nx];
  * prm = {dt, chi, g, rho0, alpha, beta_s, T0, S0, f0, beta_plane, omega, radius,
  *        nu0, ri_a, nu_b, kappa_b, kappa_conv, weno_eps, min_depth};
- * iprm = {n_substeps, weno_linear}.
+ * iprm = {n_substeps, weno_linear, averaging filter (0 equal weights, 1 power-law shape)}.
  */
 ora_t* ora_create(const int* igrid, const double* dgrid, const double* zf, const double* depth,
                   const double* taux, const double* tauy, const double* prm, const int* iprm) {
@@ -743,7 +790,9 @@ ora_t* ora_create(const int* igrid, const double* dgrid, const double* zf, const
     m->omega = prm[10]; m->radius = prm[11]; m->nu0 = prm[12]; m->ri_a = prm[13];
     m->nu_b = prm[14]; m->kappa_b = prm[15]; m->kappa_conv = prm[16]; m->weno_eps = prm[17];
     m->min_depth = prm[18];
-    m->ns = iprm[0]; m->weno_linear = iprm[1];
+    m->ns = iprm[0]; m->weno_linear = iprm[1]; m->filter = iprm[2];
+    m->fw = malloc((m->ns > 0 ? m->ns : 1) * sizeof(double));
+    if (m->ns > 0) ora_filter_weights(m->ns, m->filter, m->fw);
     int nx = m->nx, ny = m->ny, nz = m->nz;
     long n2 = (long)nx * ny, n3 = n2 * nz;
     m->zf = malloc((nz + 1) * sizeof(double));
@@ -795,6 +844,7 @@ void ora_destroy(ora_t* m) {
                       m->Gu, m->Gv, m->GT, m->GS, m->GU, m->GV, m->U, m->V, m->Hu, m->Hv};
     for (unsigned a = 0; a < sizeof(arrs) / sizeof(arrs[0]); a++) free(arrs[a]);
     free(m->kb);
+    free(m->fw);
     free(m->ext_kap); free(m->ext_dGT); free(m->ext_dGS);
     free(m);
 }

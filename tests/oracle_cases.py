@@ -45,3 +45,22 @@ def seeded_velocity(case: inputs.Case, seed: int, amp: float = 0.1):
     u = amp * inputs.random_normal(seed, 21, n).reshape(case.nz, case.ny, case.nx)
     v = amp * inputs.random_normal(seed, 22, n).reshape(case.nz, case.ny, case.nx)
     return u, v
+
+
+def flat_latlon(nx, ny, nz, lat0=-60.0, lat1=60.0, H=4000.0, z_faces=None, T=None, S=None,
+                u=None, v=None, eta=None, taux=None, tauy=None, **params) -> inputs.Case:
+    """Flat-bottomed lat-lon band, periodic in longitude over 360 degrees, walls beyond
+    the first and last rows; uniform levels unless z_faces is given."""
+    zf = inputs.uniform_z_faces(nz, H) if z_faces is None else np.asarray(z_faces, dtype=float)
+    depth = np.full((ny, nx), -zf[0])
+    z = lambda val, d: np.zeros((nz, ny, nx)) + (d if val is None else np.asarray(val, dtype=float))
+    p = inputs.default_params()
+    p.update(params)
+    c = inputs.Case("flat_latlon", 1, nx, ny, nz, True, False, 0.0, 360.0, lat0, lat1, zf,
+                    depth, np.zeros((ny, nx)) if taux is None else taux,
+                    np.zeros((ny, nx)) if tauy is None else tauy, z(T, 10.0), z(S, 35.0), p,
+                    steps=10)
+    c.u = None if u is None else z(u, 0.0)
+    c.v = None if v is None else z(v, 0.0)
+    c.eta = None if eta is None else np.asarray(eta, dtype=float) + np.zeros((ny, nx))
+    return c
