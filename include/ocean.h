@@ -110,7 +110,19 @@ typedef struct {
     const double* tauy;
     int closure_hidden;     /* hidden width of the learned closure to reserve memory for
                                (0 = none; otherwise a multiple of 16) */
+    int baro_filter;        /* time average closing the barotropic sub-cycle:
+                               OCEAN_FILTER_BOXCAR or OCEAN_FILTER_POWER_LAW */
 } ocean_params;
+
+/* Averaging filters of the split-explicit sub-cycle (Sec. "Optimization of ocean free
+ * surface dynamics": the fast mode is sub-cycled and averaged back onto the baroclinic
+ * step).  Both are weights a_1..a_Ns with sum 1; the substep is dtau = dt / sum_m m a_m,
+ * which puts the average's centroid at t + dt.  BOXCAR: a_m = 1/Ns (dtau = 2 dt/(Ns+1)).
+ * POWER_LAW: the shape x^2 (1 - x^4) - 0.284 x of Shchepetkin & McWilliams (2005) over its
+ * support (0, xs), sampled at m xs/(Ns+1) and normalised (a short negative lobe, then one
+ * positive lobe; it damps the unresolved fast modes more than the boxcar). */
+#define OCEAN_FILTER_BOXCAR 0
+#define OCEAN_FILTER_POWER_LAW 1
 
 typedef struct {
     long step;              /* completed steps */

@@ -65,6 +65,8 @@ struct ocean_s {
          *gye = nullptr, *corrU = nullptr, *corrV = nullptr, *Hu = nullptr, *Hv = nullptr,
          *rHu = nullptr, *rHv = nullptr, *Ub2 = nullptr, *Vb2 = nullptr, *dE2 = nullptr;
     double *eta = nullptr, *accE = nullptr, *accU = nullptr, *accV = nullptr;
+    void* fw = nullptr;        // averaging weights of the sub-cycle (power-law filter), R[ns]
+    double fmom = 0;           // their first moment sum_m m a_m
     short *kb = nullptr, *kbu = nullptr, *kbv = nullptr, *kbz = nullptr, *kbzin = nullptr;
     void* rowm = nullptr;   // 7 row arrays of (ny + 2H) elements
     void* levm = nullptr;   // 8 level arrays of nz elements
@@ -148,6 +150,8 @@ int validate(const ocean_grid* g, const ocean_params* p) {
     if (p->check_every < 0) return fail(nullptr, OCEAN_ERR_ARG, "check_every must be >= 0");
     if (p->closure_hidden < 0 || p->closure_hidden % 16)
         return fail(nullptr, OCEAN_ERR_ARG, "closure_hidden must be 0 or a positive multiple of 16");
+    if (p->baro_filter != OCEAN_FILTER_BOXCAR && p->baro_filter != OCEAN_FILTER_POWER_LAW)
+        return fail(nullptr, OCEAN_ERR_ARG, "unknown baro_filter %d", p->baro_filter);
     return OCEAN_OK;
 }
 
@@ -189,6 +193,7 @@ size_t layout(ocean_t m, char* base) {
                     &m->corrU, &m->corrV, &m->Hu, &m->Hv, &m->rHu, &m->rHv, &m->Ub2, &m->Vb2,
                     &m->dE2};
     for (void** q : two) *q = f2();
+    m->fw = c.take<char>((size_t)m->prm.n_substeps * e);
     m->eta = c.take<double>(n2); m->accE = c.take<double>(n2);
     m->accU = c.take<double>(n2); m->accV = c.take<double>(n2);
     m->kb = c.take<short>(n2); m->kbu = c.take<short>(n2); m->kbv = c.take<short>(n2);
@@ -337,6 +342,10 @@ int build_geometry(ocean_t m, const double* depth) {
     }
     upload_bytes(m, m->drow, drow.data(), drow.size() * sizeof(double));
     upload_levels(m);
+    // ---- averaging weights of the sub-cycle
+    std::vector<double> fw((size_t)p.n_substeps);
+    m->fmom = baro_filter_weights(p.n_substeps, p.baro_filter, fw.data());
+    upload_real(m, fw, m->fw);
     // ---- masks
     const long n2 = m->n2pad;
     std::vector<short> kbi((size_t)nx * ny);
@@ -514,6 +523,8 @@ StepBuffers<R> make_bufs(const ocean_t m, int cur = -1) {
     b.Ub2 = P(m->Ub2); b.Vb2 = P(m->Vb2); b.dE2 = P(m->dE2);
     b.Hu = P(m->Hu); b.Hv = P(m->Hv); b.rHu = P(m->rHu); b.rHv = P(m->rHv);
     b.eta = m->eta; b.accE = m->accE; b.accU = m->accU; b.accV = m->accV;
+    b.fw = m->prm.baro_filter == OCEAN_FILTER_BOXCAR ? nullptr : reinterpret_cast<const R*>(m->fw);
+    b.fmom = m->fmom;
     b.tm = m->tmaps[c];
     return b;
 }

@@ -255,6 +255,10 @@ template <typename R> struct StepBuffers {
     R *Ub2, *Vb2, *dE2;        // second buffers of the barotropic state (passes ping-pong)
     const R *Hu, *Hv, *rHu, *rHv;
     double *eta, *accE, *accU, *accV;
+    // averaging weights a_m of the sub-cycle (null: equal weights 1/N_s) and their first
+    // moment sum_m m a_m (the substep is dt / fmom)
+    const R* fw;
+    double fmom;
     TileMaps tm;               // tensor maps of the state read by the tracer tile
 };
 
@@ -271,6 +275,9 @@ template <typename R>
 void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s);
 // kernel launches of one barotropic sub-cycle of ns substeps, halos excluded
 int baro_passes(int ns);
+// averaging weights a_1..a_ns of the sub-cycle for filter `kind` (OCEAN_FILTER_*) into a;
+// returns their first moment sum_m m a_m
+double baro_filter_weights(int ns, int kind, double* a);
 template <typename R>
 void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s);
 template <typename R>

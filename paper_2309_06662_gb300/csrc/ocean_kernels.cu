@@ -959,8 +959,10 @@ __device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
     return ix2(g, i, j);
 }
 
-// region (bx, by): the interior [bx IX, bx IX + IX) x [by IY, by IY + IY) and its halo
-template <typename R>
+// region (bx, by): the interior [bx IX, bx IX + IX) x [by IY, by IY + IY) and its halo.
+// WEIGHTED: the partial sums take substep m with the filter's weight fw[m] (the pass's own
+// weights), else with weight 1 (equal weights, scaled by 1/N_s at the end)
+template <typename R, bool WEIGHTED = false>
 __device__ __forceinline__ void baro_region(
     const KP<R>& p, const int bx, const int by, const R* __restrict__ Ea,
     const R* __restrict__ Ua, const R* __restrict__ Va, R* __restrict__ Eb, R* __restrict__ Ub,
@@ -968,7 +970,7 @@ __device__ __forceinline__ void baro_region(
     const R* __restrict__ Hu, const R* __restrict__ Hv, const R* __restrict__ GU,
     const R* __restrict__ GV, const R* __restrict__ Un, const R* __restrict__ Vn,
     double* __restrict__ accE, double* __restrict__ accU, double* __restrict__ accV, int nsub,
-    R dtau, R grav) {
+    R dtau, R grav, const R* __restrict__ fw = nullptr) {
     extern __shared__ __align__(16) unsigned char bsm[];
     R* sE = reinterpret_cast<R*>(bsm);
     R* sU = sE + BRX * BRY;
@@ -1032,6 +1034,7 @@ __device__ __forceinline__ void baro_region(
     }
     __syncthreads();
     for (int m = 0; m < nsub; ++m) {
+        const R wm = WEIGHTED ? fw[m] : R(1);
         // deta^m = deta^{m-1} - dtau/A_c [dy (U_{i+1} - U_i) + dxv_{j+1} V_{j+1} - dxv_j V_j]
         // (the east and north neighbours' U, V are read before anyone rewrites them)
 #pragma unroll
@@ -1042,7 +1045,8 @@ __device__ __forceinline__ void baro_region(
                 const R div = p.dy * (sU[q + 1] - uu[r]) + sDN[ry] * vN - sDS[ry] * vv[r];
                 e[r] = e[r] - sCe[ry] * div;
                 sE[q] = e[r];
-                pE[r] += e[r];
+                if (WEIGHTED) pE[r] = fma(wm, e[r], pE[r]);
+                else pE[r] += e[r];
             }
         }
         __syncthreads();
@@ -1054,14 +1058,16 @@ __device__ __forceinline__ void baro_region(
                 const R un = uu[r] + Bu[r] - Au[r] * (e[r] - sE[q - 1]);
                 uu[r] = un;
                 sU[q] = un;
-                pU[r] += un - u0[r];
+                if (WEIGHTED) pU[r] = fma(wm, un - u0[r], pU[r]);
+                else pU[r] += un - u0[r];
             }
             if (ry >= 1 && Av[r] != R(0)) {
                 const R eS = r > 0 ? e[r - 1] : sE[q - BRX];
                 const R vn = vv[r] + Bv[r] - Av[r] * (e[r] - eS);
                 vv[r] = vn;
                 if (r == 0) sV[q] = vn;   // only the thread below reads it
-                pV[r] += vn - v0[r];
+                if (WEIGHTED) pV[r] = fma(wm, vn - v0[r], pV[r]);
+                else pV[r] += vn - v0[r];
             }
         }
         __syncthreads();
@@ -1083,20 +1089,21 @@ __device__ __forceinline__ void baro_region(
     }
 }
 
-template <typename R>
+template <typename R, bool WEIGHTED>
 __global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_baro_pass(
     KP<R> p, const R* __restrict__ Ea, const R* __restrict__ Ua, const R* __restrict__ Va,
     R* __restrict__ Eb, R* __restrict__ Ub, R* __restrict__ Vb, const R* __restrict__ gxe,
     const R* __restrict__ gye, const R* __restrict__ Hu, const R* __restrict__ Hv,
     const R* __restrict__ GU, const R* __restrict__ GV, const R* __restrict__ Un,
     const R* __restrict__ Vn, double* __restrict__ accE, double* __restrict__ accU,
-    double* __restrict__ accV, int nsub, R dtau, R grav) {
-    baro_region<R>(p, blockIdx.x, blockIdx.y, Ea, Ua, Va, Eb, Ub, Vb, gxe, gye, Hu, Hv, GU, GV,
-                   Un, Vn, accE, accU, accV, nsub, dtau, grav);
+    double* __restrict__ accV, int nsub, R dtau, R grav, const R* __restrict__ fw) {
+    baro_region<R, WEIGHTED>(p, blockIdx.x, blockIdx.y, Ea, Ua, Va, Eb, Ub, Vb, gxe, gye, Hu, Hv,
+                             GU, GV, Un, Vn, accE, accU, accV, nsub, dtau, grav, fw);
 }
 
-// eta^{n+1} = eta^n + mean(deta) in FP64; correction of the depth-integrated velocity
-// (Ubar - sum dz u**)/H_u with Ubar = U^n + mean(U - U^n)
+// eta^{n+1} = eta^n + sum_m a_m deta^m in FP64; correction of the depth-integrated
+// velocity (Ubar - sum dz u**)/H_u with Ubar = U^n + sum_m a_m (U^m - U^n); `rns` scales
+// the accumulated sums (1/N_s for equal weights, 1 when the passes applied the weights)
 template <typename R>
 __device__ __forceinline__ void baro_end_col(const KP<R>& p, const long c, double* eta,
                                              const double* __restrict__ accE,
@@ -1213,7 +1220,7 @@ void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double d
     const GeoD& g = p.g;
     const long n = (long)g.nx * g.ny;
     const int nbk = nblocks(n, TPB);
-    const R dtau = (R)(2.0 * dt / (ns + 1.0));
+    const R dtau = b.fw ? (R)(dt / b.fmom) : (R)(2.0 * dt / (ns + 1.0));
     if (g.px || g.py) launch_halo2<double>(g, b.eta, s);
     k_baro_begin<R><<<nbk, TPB, 0, s>>>(p, b.Un, b.Vn, b.eta, b.Hu, b.Hv, b.Ub, b.Vb, b.dE,
                                        b.paccE, b.paccU, b.paccV, b.accE, b.accU, b.accV, b.gxe,
@@ -1224,19 +1231,57 @@ void launch_barotropic(const KP<R>& p, const StepBuffers<R>& b, int ns, double d
     R *Ea = b.dE, *Ua = b.Ub, *Va = b.Vb, *Eb = b.dE2, *Ub = b.Ub2, *Vb = b.Vb2;
     for (int m0 = 0; m0 < ns; m0 += BS) {
         const int nsub = ns - m0 < BS ? ns - m0 : BS;
-        k_baro_pass<R><<<grid, BNT, smem, s>>>(p, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye, b.Hu,
-                                               b.Hv, b.GU, b.GV, b.Un, b.Vn, b.accE, b.accU,
-                                               b.accV, nsub, dtau, grav);
+        if (b.fw)
+            k_baro_pass<R, true><<<grid, BNT, smem, s>>>(p, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye,
+                                                         b.Hu, b.Hv, b.GU, b.GV, b.Un, b.Vn,
+                                                         b.accE, b.accU, b.accV, nsub, dtau,
+                                                         grav, b.fw + m0);
+        else
+            k_baro_pass<R, false><<<grid, BNT, smem, s>>>(p, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye,
+                                                          b.Hu, b.Hv, b.GU, b.GV, b.Un, b.Vn,
+                                                          b.accE, b.accU, b.accV, nsub, dtau,
+                                                          grav, nullptr);
         R* t;
         t = Ea; Ea = Eb; Eb = t;
         t = Ua; Ua = Ub; Ub = t;
         t = Va; Va = Vb; Vb = t;
     }
     k_baro_end<R><<<nbk, TPB, 0, s>>>(p, b.eta, b.accE, b.accU, b.accV, b.Un, b.Vn, b.Su, b.Sv,
-                                     b.rHu, b.rHv, b.corrU, b.corrV, 1.0 / ns);
+                                     b.rHu, b.rHv, b.corrU, b.corrV, b.fw ? 1.0 : 1.0 / ns);
 }
 
 int baro_passes(int ns) { return (ns + BS - 1) / BS; }
+
+// The averaging weights.  Equal weights: a_m = 1/ns.  Power law: the shape
+// s(x) = x^2 (1 - x^4) - r x, r = 0.284 (Shchepetkin & McWilliams 2005), whose support
+// ends at xs, the root of x - x^5 = r beyond the maximum of x - x^5 at 5^(-1/4); Newton's
+// iteration from x = 1 (where x - x^5 - r < 0 and the function is concave and falling)
+// converges monotonically to it.  Sampled at m xs/(ns + 1), normalised to sum 1.
+double baro_filter_weights(int ns, int kind, double* a) {
+    if (kind == OCEAN_FILTER_POWER_LAW) {
+        const double r = 0.284;
+        double x = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            const double x4 = x * x * x * x;
+            const double f = x - x4 * x - r, df = 1.0 - 5.0 * x4;
+            const double nx = x - f / df;
+            if (nx == x) break;
+            x = nx;
+        }
+        double sum = 0.0;
+        for (int m = 1; m <= ns; ++m) {
+            const double xm = x * m / (ns + 1.0), x2 = xm * xm;
+            a[m - 1] = x2 * (1.0 - x2 * x2) - r * xm;
+            sum += a[m - 1];
+        }
+        for (int m = 0; m < ns; ++m) a[m] /= sum;
+    } else {
+        for (int m = 0; m < ns; ++m) a[m] = 1.0 / ns;
+    }
+    double mom = 0.0;
+    for (int m = 1; m <= ns; ++m) mom += m * a[m - 1];
+    return mom;
+}
 
 template <typename R>
 void launch_correct(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
@@ -1668,7 +1713,9 @@ template <typename R>
 int setup_kernel_attributes(int nz) {
     (void)nz;
     const int bytes = (int)baro_smem<R>();
-    cudaError_t e = cudaFuncSetAttribute(k_baro_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_baro_pass<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_baro_pass<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ens_baro_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return (int)e;

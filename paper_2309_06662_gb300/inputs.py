@@ -311,6 +311,14 @@ def latlon_half_case(seed: int = 4, lat: float = 80.0) -> Case:
     return latlon_case(720, 320, 48, lat, seed, 480.0, 60, 2000, "latlon_half")
 
 
+def latlon_half70_case(seed: int = 3) -> Case:
+    """1/2-degree restriction of the 1/12-degree recipe: 720 x 280 x 48, 70S-70N, the same
+    seeded random-field bathymetry and forcing recipe generated at 1/2 degree, dt = 480 s
+    (the 1/2-degree step of this recipe, below the internal-wave limit next to 70 degrees),
+    60 substeps, 200 steps; the size at which the oracle runs the recipe."""
+    return latlon_case(720, 280, 48, 70.0, seed, 480.0, 60, 200, "latlon_half70")
+
+
 def latlon_small_case(nx: int = 72, ny: int = 40, nz: int = 12, seed: int = 7,
                       lat: float = 70.0, dt: float = 1800.0, n_substeps: int = 20) -> Case:
     """A small lat-lon case (5 degree) with the same recipe, for fast parity runs."""

@@ -36,3 +36,20 @@ def run_pair(case, precision: int, steps: int, params=None):
 
 def state_errors(m_gpu, m_ora, measure=max_rel, fields=STATE):
     return {f: measure(m_gpu.get(f), m_ora.get(f)) for f in fields}
+
+
+def field_error_table(get_a, get_b, wet_T, T_init=None, S_init=None, fields=STATE):
+    """Per-field errors of model a against reference b: relative L2 and max-relative
+    (max |a - b| / max |b|) over each field, plus both measures on the tracer anomalies
+    T - T_init and S - S_init over the wet cells (the mean of T hides the errors of what
+    moved).  get_a, get_b: field name -> array."""
+    out = {}
+    for f in fields:
+        a, b = get_a(f), get_b(f)
+        out[f] = {"rel_l2": rel_l2(a, b), "max_rel": max_rel(a, b)}
+        if f in ("T", "S"):
+            init = T_init if f == "T" else S_init
+            if init is not None:
+                da, db = (a - init)[wet_T], (b - init)[wet_T]
+                out[f + "_anom"] = {"rel_l2": rel_l2(da, db), "max_rel": max_rel(da, db)}
+    return out
