@@ -134,34 +134,48 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-// fifth-order WENO-Z of two stencils at once (same definition as weno5)
+// approximate reciprocal of the special-function unit (rcp.approx)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// fifth-order WENO-Z of two stencils at once (same definition as weno5, rearranged):
+// with the second differences A_r and first differences B_r of the three candidate
+// stencils, 4 beta_r = (13/3) A_r^2 + B_r^2, so tau5/(beta_r + eps) = 4 (beta_0 - beta_2)
+// / (4 beta_r + 4 eps) needs no division by 4; the candidates are formed times 6 and the
+// weighted sum divided by 6 at the end.  tau/(beta+eps) squared is clamped at 1e36 (see
+// WenoRatio: the clamp leaves the value unchanged) so that the weights stay finite.
 __device__ __forceinline__ float2 weno5z_x2(float2 q0, float2 q1, float2 q2, float2 q3,
                                             float2 q4, float eps) {
-    const float2 s6 = f2(1.0f / 6.0f), c13 = f2(13.0f / 12.0f), qr = f2(0.25f);
-    const float2 p0 = f2mul(f2fma(q0, f2(2.f), f2fma(q1, f2(-7.f), f2mul(q2, f2(11.f)))), s6);
-    const float2 p1 = f2mul(f2fma(q1, f2(-1.f), f2fma(q2, f2(5.f), f2mul(q3, f2(2.f)))), s6);
-    const float2 p2 = f2mul(f2fma(q2, f2(2.f), f2fma(q3, f2(5.f), f2mul(q4, f2(-1.f)))), s6);
-    float2 a = f2add(f2fma(q1, f2(-2.f), q0), q2), b = f2fma(q2, f2(3.f), f2fma(q1, f2(-4.f), q0));
-    const float2 b0 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
-    a = f2add(f2fma(q2, f2(-2.f), q1), q3);
-    b = f2add(q1, f2mul(q3, f2(-1.f)));
-    const float2 b1 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
-    a = f2add(f2fma(q3, f2(-2.f), q2), q4);
-    b = f2fma(q3, f2(-4.f), f2fma(q2, f2(3.f), q4));
-    const float2 b2 = f2fma(f2mul(a, a), c13, f2mul(f2mul(b, b), qr));
-    const float2 tau = make_float2(fabsf(b0.x - b2.x), fabsf(b0.y - b2.y));
-    const float2 r0 = make_float2(fminf(__fdividef(tau.x, b0.x + eps), 1e18f),
-                                  fminf(__fdividef(tau.y, b0.y + eps), 1e18f));
-    const float2 r1 = make_float2(fminf(__fdividef(tau.x, b1.x + eps), 1e18f),
-                                  fminf(__fdividef(tau.y, b1.y + eps), 1e18f));
-    const float2 r2 = make_float2(fminf(__fdividef(tau.x, b2.x + eps), 1e18f),
-                                  fminf(__fdividef(tau.y, b2.y + eps), 1e18f));
-    const float2 a0 = f2mul(f2(0.1f), f2fma(r0, r0, f2(1.f)));
-    const float2 a1 = f2mul(f2(0.6f), f2fma(r1, r1, f2(1.f)));
-    const float2 a2 = f2mul(f2(0.3f), f2fma(r2, r2, f2(1.f)));
-    const float2 num = f2fma(a0, p0, f2fma(a1, p1, f2mul(a2, p2)));
+    const float2 P0 = f2fma(q0, f2(2.f), f2fma(q1, f2(-7.f), f2mul(q2, f2(11.f))));
+    const float2 P1 = f2fma(q1, f2(-1.f), f2fma(q2, f2(5.f), f2mul(q3, f2(2.f))));
+    const float2 P2 = f2fma(q2, f2(2.f), f2fma(q3, f2(5.f), f2mul(q4, f2(-1.f))));
+    const float2 A0 = f2add(f2fma(q1, f2(-2.f), q0), q2);
+    const float2 A1 = f2add(f2fma(q2, f2(-2.f), q1), q3);
+    const float2 A2 = f2add(f2fma(q3, f2(-2.f), q2), q4);
+    const float2 B0 = f2fma(f2fma(q1, f2(-1.f), q2), f2(2.f), A0);   // q0 - 4 q1 + 3 q2
+    const float2 B1 = f2fma(q3, f2(-1.f), q1);                        // q1 - q3
+    const float2 B2 = f2fma(f2fma(q3, f2(-1.f), q2), f2(2.f), A2);   // 3 q2 - 4 q3 + q4
+    const float2 c = f2(13.f / 3.f);
+    const float2 b0 = f2fma(f2mul(A0, A0), c, f2mul(B0, B0));
+    const float2 b1 = f2fma(f2mul(A1, A1), c, f2mul(B1, B1));
+    const float2 b2 = f2fma(f2mul(A2, A2), c, f2mul(B2, B2));
+    const float2 d = f2fma(b2, f2(-1.f), b0);
+    const float2 e4 = f2(4.f * eps);
+    auto alpha = [&](float2 b, float dr) {
+        const float2 be = f2add(b, e4);
+        const float2 r = f2mul(d, make_float2(rcp_approx(be.x), rcp_approx(be.y)));
+        float2 r2 = f2mul(r, r);
+        r2.x = fminf(r2.x, 1e36f);
+        r2.y = fminf(r2.y, 1e36f);
+        return f2fma(r2, f2(dr), f2(dr));
+    };
+    const float2 a0 = alpha(b0, 0.1f), a1 = alpha(b1, 0.6f), a2 = alpha(b2, 0.3f);
+    const float2 num = f2fma(a0, P0, f2fma(a1, P1, f2mul(a2, P2)));
     const float2 den = f2add(f2add(a0, a1), a2);
-    return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    return f2mul(f2mul(num, make_float2(rcp_approx(den.x), rcp_approx(den.y))), f2(1.f / 6.f));
 }
 
 // third-order WENO-Z of two stencils at once (same definition as weno3)
