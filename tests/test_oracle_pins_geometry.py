@@ -335,3 +335,32 @@ def test_inertial_oscillation_with_power_law_average():
         m.step(1)
         assert np.max(np.abs(m.get("u") - w[k].real)) < 1e-12
         assert np.max(np.abs(m.get("v") - w[k].imag)) < 1e-12
+
+
+# ----------------------------------------------------------------------------- masks and flags
+
+
+def test_full_cell_bathymetry_masks():
+    # a cell is wet when its centre lies above the sea floor, and columns shallower than
+    # min_depth are land: with faces at -4000, -3000, ..., 0 (centres -3500 .. -500), a
+    # depth of 2600 m wets the three top cells (kb = 1), 500 m wets none (the centre sits
+    # exactly on the floor), 40 m is land
+    nx, ny, nz = 5, 1, 4
+    c = flat_box(nx, ny, nz, H=4000.0)
+    c.depth[0, :] = [4000.0, 2600.0, 501.0, 500.0, 40.0]
+    m = oracle.OracleModel(c)
+    assert [m.kbot(i, 0) for i in range(nx)] == [0, 1, 3, 4, 4]
+    # u-faces are wet where both neighbouring cells are: Hu is the wet thickness
+    Hu = m.get("Hu")[0]
+    assert list(Hu[1:]) == [3000.0, 1000.0, 0.0, 0.0]
+    assert Hu[0] == 0.0
+
+
+def test_nonfinite_state_is_flagged():
+    c = flat_box(4, 4, 3)
+    m = oracle.OracleModel(c)
+    assert not m.diagnostics()["nonfinite"]
+    T = m.get("T")
+    T[1, 2, 2] = np.nan
+    m.set("T", T)
+    assert m.diagnostics()["nonfinite"]
