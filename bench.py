@@ -13,7 +13,11 @@ the ECCO2-forced realistic domain of the paper (Sec. "How performance was measur
 
 Prints one JSON line.  `value` is whole-job cell-updates/s (grid cells, land included,
 times steps, summed over ranks, over the max-over-ranks device time), state resident in
-HBM.  `e2e` is the same metric through the C ABI with host buffers: every step uploads
+HBM.  The default run also measures every other configuration (`configs`: the 1-degree
+grid in the mixed form and in FP64, the aqua-planet per-GPU workload of the paper's weak
+scaling, the 96-basin ensemble against its members one by one, the learned closure
+against the Richardson-number step) and the per-field difference of the mixed form from
+the FP64 path (`errors`).  `e2e` is the same metric through the C ABI with host buffers: every step uploads
 the surface wind stress from host memory and reads the diagnostics back.  `--impl
 reference` times the CPU oracle instead, on a bounded window of the same workload.
 """
@@ -313,6 +317,8 @@ def parse():
                     help="steps of the mixed-vs-FP64 comparison (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations in the default run")
     return ap.parse_args()
 
 
@@ -383,6 +389,104 @@ def mixed_vs_fp64(case, steps: int):
     return out
 
 
+def single_model(case, precision: int, steps: int, warmup: int, local: int, dist=None):
+    """Device-resident timing of one model (CUDA events on its stream around `steps`
+    graph-replayed steps after `warmup`), the per-phase times of up to 5 more steps, the
+    roofline of the heaviest single-kernel phase and the clocks seen."""
+    import torch
+    from paper_2309_06662_gb300 import ocean
+    p = case.params
+    esz = 8 if precision == ocean.OCEAN_FP64 else 4
+    wet = roofline.wet_cells(case.depth, case.z_faces, p["min_depth"])
+    wet_cols = roofline.wet_columns(case.depth, p["min_depth"], case.z_faces)
+    m = ocean.Ocean(case, precision=precision)
+    m.step_async(max(1, warmup))
+    m.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = m.launches
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        m.step_async(steps)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dist)
+    launches = m.launches - l0
+    m.profile(True)
+    m.step_async(min(steps, 5))
+    m.sync()
+    phases, nprof = m.phase_times()
+    m.profile(False)
+    healthy = not m.diagnostics()["nonfinite"]
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+    peak, peak_src = measured_peaks()
+    fr = {}
+    for k in roofline.KERNEL_WORDS:
+        t = phases[k] / nprof
+        gbs = roofline.KERNEL_WORDS[k] * esz * wet / (t / 1e3) / 1e9
+        fr[k] = {"ms": round(t, 4), "GBs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    tb = phases["barotropic"] / nprof
+    bb = roofline.barotropic_bytes_per_column(esz, int(p["n_substeps"])) * wet_cols
+    fr["barotropic"] = {"ms": round(tb, 4), "GBs": round(bb / (tb / 1e3) / 1e9, 1),
+                        "frac": round(bb / (tb / 1e3) / 1e9 / peak, 3)}
+    top = max(roofline.KERNEL_WORDS, key=lambda k: fr[k]["ms"])
+    step_bytes = roofline.STEP_WORDS_PER_CELL * esz * wet + bb
+    return {"value": metrics.cell_updates_per_s(case.nx, case.ny, case.nz, ms / 1e3),
+            "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps,
+            "sypd": metrics.sypd(p["dt"], ms / 1e3), "dt_s": p["dt"],
+            "roofline": {"bound": "hbm", "kernel": top, "frac": fr[top]["frac"],
+                         "achieved": fr[top]["GBs"], "peak": peak, "unit": "GB/s",
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak,
+            "phases": fr, "gpu_launches": launches, "healthy": healthy,
+            "clocks": clk.summary()}
+
+
+def other_configs(args, rank, world, local, dist):
+    """Every other configuration of the benchmark, measured in the default run: the
+    1-degree grid in the mixed form and in FP64 side by side, the aqua-planet per-GPU
+    workload of the paper's weak scaling (FP64 as the paper ran it, and mixed), the
+    96-basin ensemble against its members stepped one by one, and the 1/2-degree step
+    with the learned closure against the Richardson-number step."""
+    import torch
+    from paper_2309_06662_gb300 import ocean
+    out = {}
+    c1 = inputs.latlon_1deg_case()
+    mixed = single_model(c1, ocean.OCEAN_MIXED, 50, 5, local, dist)
+    fp64 = single_model(c1, ocean.OCEAN_FP64, 10, 2, local, dist)
+    out["latlon_1deg_360x160x32"] = {"mixed": mixed, "fp64": fp64,
+                                     "mixed_over_fp64": mixed["value"] / fp64["value"]}
+    ap = inputs.aquaplanet_case()
+    apf = single_model(ap, ocean.OCEAN_FP64, 5, 1, local, dist)
+    apm = single_model(ap, ocean.OCEAN_MIXED, 20, 3, local, dist)
+    out["aquaplanet_1/6deg_2160x900x100"] = {
+        "fp64": apf, "mixed": apm, "mixed_over_fp64": apm["value"] / apf["value"],
+        "paper_per_gpu_context": "3.4e8 cell-updates/s per A100 in FP64 (768 A100s, 2.1e11 cells, "
+                                 "0.81 s per step; other hardware, context only)"}
+    keep = lambda d, ks: {k: d[k] for k in ks if k in d}
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup, sub.e2e_steps = 10, 3, 2
+    ens = ensemble_main(sub, inputs.ensemble_cases(96, seed=5), "ensemble_96_basins", rank,
+                        world, local, dist, with_cpu=False)
+    torch.cuda.empty_cache()
+    if ens is not None:
+        out["ensemble_96_basins"] = keep(ens, ["value", "unit", "ms_per_step", "one_by_one",
+                                               "roofline", "step_hbm", "e2e", "gpu_launches",
+                                               "clocks", "config"])
+    lrn = learned_main(sub, inputs.latlon_half_case(), WORKLOADS["learned_half"][1], rank, world,
+                       local, dist, with_cpu=False)
+    torch.cuda.empty_cache()
+    if lrn is not None:
+        out["learned_half_720x320x48"] = keep(lrn, ["value", "unit", "ms_per_step", "sypd",
+                                                    "richardson_only", "roofline", "e2e",
+                                                    "gpu_launches", "clocks", "healthy", "config"])
+    return out
+
+
 def config_block(case, wname, precision):
     p = case.params
     return {"workload": wname, "nx": case.nx, "ny": case.ny, "nz": case.nz,
@@ -391,7 +495,7 @@ def config_block(case, wname, precision):
             "l2": "inputs larger than L2 (every 3-D field > 1 GB)"}
 
 
-def learned_main(args, case, wname, rank, world, local, dist):
+def learned_main(args, case, wname, rank, world, local, dist, with_cpu=True):
     """The 1/2-degree step with the learned closure in the loop (seeded network, feature
     statistics of the initial state), against the same step with the Richardson-number
     closure alone; the closure network's GEMM chain timed on all columns."""
@@ -474,7 +578,7 @@ def learned_main(args, case, wname, rank, world, local, dist):
     ms = max_over_ranks(res["learned"]["ms"], dist)
     p = case.params
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and with_cpu:
         cpu = run_oracle_sample(case, args.cpu_seconds)
         cpu.pop("s_per_step", None)
         cpu["sample"] += " (Richardson-number closure: the oracle of the learned step is numpy, see oracle/closure.py)"
@@ -504,13 +608,11 @@ def learned_main(args, case, wname, rank, world, local, dist):
             "healthy": res["learned"]["healthy"],
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+        return line
+    return None
 
 
-def ensemble_main(args, cases, wname, rank, world, local, dist):
+def ensemble_main(args, cases, wname, rank, world, local, dist, with_cpu=True):
     """The batched ensemble: all members advanced by one graph launch per step, against
     the same members stepped one after another with ocean_step."""
     import torch
@@ -576,7 +678,7 @@ def ensemble_main(args, cases, wname, rank, world, local, dist):
     shapes = E.launch_shapes()
     E.close()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and with_cpu:
         cpu = run_oracle_sample(cases[0], args.cpu_seconds)
         cpu.pop("s_per_step", None)
         cpu["sample"] += " (member 0 of the ensemble)"
@@ -615,10 +717,8 @@ def ensemble_main(args, cases, wname, rank, world, local, dist):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+        return line
+    return None
 
 
 def ncu_cli(argv) -> bool:
@@ -658,11 +758,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     make, wname = WORKLOADS[args.workload]
-    if args.workload == "ensemble96":
-        ensemble_main(args, make(), wname, rank, world, local, dist)
-        return
-    if args.workload == "learned_half":
-        learned_main(args, make(), wname, rank, world, local, dist)
+    if args.workload in ("ensemble96", "learned_half"):
+        fn = ensemble_main if args.workload == "ensemble96" else learned_main
+        line = fn(args, make(), wname, rank, world, local, dist)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
         return
     case = make()
     p = case.params
@@ -761,6 +864,9 @@ def main():
                 "mixed_over_fp64": value / v64}
 
     errors = mixed_vs_fp64(case, args.error_steps) if rank == 0 and args.error_steps > 0 else None
+    configs = None
+    if args.workload == "latlon_12th" and not args.no_configs:
+        configs = other_configs(args, rank, world, local, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -790,6 +896,7 @@ def main():
             "phases": phase_frac,
             "fp64": fp64,
             "errors": errors,
+            "configs": configs,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s",
                     "h2d_bytes_per_step": int(taux.nbytes + tauy.nbytes),
                     "d2h_bytes_per_step": 8 * 8, "healthy": healthy,

@@ -319,6 +319,43 @@ def latlon_half70_case(seed: int = 3) -> Case:
     return latlon_case(720, 280, 48, 70.0, seed, 480.0, 60, 200, "latlon_half70")
 
 
+def aquaplanet_case(nx: int = 2160, ny: int = 900, nz: int = 100, seed: int = 8,
+                    dt: float = 240.0, n_substeps: int = 30, depth: float = 4000.0,
+                    ridge_deg: float = 1.0) -> Case:
+    """The per-GPU workload of the paper's aqua-planet weak-scaling runs (Sec. "How
+    performance was measured": global, 75S-75N, 100 levels, idealised bathymetry with two
+    ridges that divide the world ocean into two basins; each GPU holds the equivalent of a
+    global 1/6-degree grid).  The ridge geometry is not given; here: a flat 4000 m ocean
+    with two land ridges `ridge_deg` wide at 0 and 90 degrees east, from the northern edge
+    down to 35S, so that the basins meet in a circumpolar channel south of 35S.  Stretched
+    levels, zonal wind 0.1 cos(3 phi) N/m^2, T linear 20 -> 2 C in depth scaled towards
+    the poles by cos(phi) (cold high latitudes) plus 0.05 C of seeded noise, S 34.5 -> 35;
+    dt = 240 s (below the internal-wave limit of the 4.8 km zonal spacing at 75 degrees),
+    30 substeps, 500 steps (the paper's averaging window)."""
+    lat = 75.0
+    zf = stretched_z_faces(nz, depth, 3.0)
+    dlon, dlat = 360.0 / nx, 2.0 * lat / ny
+    lonc = (np.arange(nx) + 0.5) * dlon
+    latc = -lat + (np.arange(ny) + 0.5) * dlat
+    d = np.full((ny, nx), depth)
+    for lon0 in (0.0, 90.0):
+        dl = np.abs((lonc - lon0 + 180.0) % 360.0 - 180.0)
+        ridge = dl <= max(0.5 * ridge_deg, 0.5 * dlon)   # at least the nearest cells
+        d[np.ix_(latc > -35.0, ridge)] = 0.0
+    phi = np.deg2rad(latc)
+    taux = np.repeat((0.1 * np.cos(3.0 * phi))[:, None], nx, axis=1)
+    tauy = np.zeros((ny, nx))
+    T, S = _stratified(zf, ny, nx, seed, 20.0, 2.0, 34.5, 35.0, 0.05,
+                       grid=(0.0, dlon, -lat, dlat, True), noise_deg=1.0)
+    # warm low latitudes, cold high latitudes: the top-to-bottom contrast shrinks with
+    # cos(phi) toward the poles (the deep value stays at 2 C)
+    T = 2.0 + (T - 2.0) * np.cos(phi)[None, :, None]
+    p = default_params()
+    p.update(dt=dt, n_substeps=n_substeps)
+    return Case("aquaplanet", 1, nx, ny, nz, True, False, 0.0, 360.0, -lat, lat, zf, d, taux,
+                tauy, T, S, p, steps=500)
+
+
 def latlon_small_case(nx: int = 72, ny: int = 40, nz: int = 12, seed: int = 7,
                       lat: float = 70.0, dt: float = 1800.0, n_substeps: int = 20) -> Case:
     """A small lat-lon case (5 degree) with the same recipe, for fast parity runs."""
@@ -449,4 +486,5 @@ WORKLOADS = {
     "box": (box_case, "box_32x32x8"),
     "ensemble96": (lambda: ensemble_cases(96, seed=5), "ensemble_96_basins"),
     "learned_half": (latlon_half_case, "latlon_1/2deg_720x320x48_learned_closure"),
+    "aquaplanet_6th": (aquaplanet_case, "aquaplanet_1/6deg_2160x900x100"),
 }

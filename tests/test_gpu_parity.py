@@ -72,6 +72,21 @@ def test_latlon_small_mixed_50_steps():
 
 
 @pytest.mark.parametrize("precision", [ocean.OCEAN_FP64, ocean.OCEAN_MIXED])
+def test_aquaplanet_recipe_matches_oracle(precision):
+    # the aqua-planet geometry (two ridges dividing the ocean into two basins that meet
+    # south of 35S, 75S-75N) at 5 degrees: the periodic wrap through the ridges
+    c = inputs.aquaplanet_case(nx=72, ny=30, nz=10, dt=1800.0, n_substeps=20)
+    assert (c.depth == 0).any()
+    g, o = run_pair(c, precision, 20)
+    if precision == ocean.OCEAN_FP64:
+        errs = state_errors(g, o)
+        assert all(e <= FP64_TOL for e in errs.values()), errs
+    else:
+        errs = state_errors(g, o, rel_l2)
+        assert all(e <= MIXED_TOL for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("precision", [ocean.OCEAN_FP64, ocean.OCEAN_MIXED])
 def test_power_law_filter_matches_oracle(precision):
     # the sub-cycle averaged with the power-law weights (substep from their first moment)
     for c, steps in ((inputs.box_case().with_params(baro_filter=1), 60),
