@@ -67,6 +67,10 @@ def lib():
             L.ora_weno3.argtypes = [P(d), d, i]
             L.ora_recon.restype = d
             L.ora_recon.argtypes = [P(d), P(i), d, i]
+            L.ora_recon_coef.restype = d
+            L.ora_recon_coef.argtypes = [P(d), P(i), P(d), d, d, i]
+            L.ora_weno_coeffs.argtypes = [P(d), d, i, P(d)]
+            L.ora_vertical_advection_column.argtypes = [i, P(d), P(d), i, P(d), i, i, d, P(d)]
             L.ora_thomas.argtypes = [i, P(d), P(d), P(d), P(d), P(d)]
             L.ora_barotropic.argtypes = [ctypes.c_void_p, P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
             L.ora_set_closure_fields.argtypes = [ctypes.c_void_p, P(d), P(d), P(d)]
@@ -102,6 +106,35 @@ def recon(q, inside, eps: float = 1e-30, linear: bool = False) -> float:
     return lib().ora_recon(_dp(q), ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), eps, int(linear))
 
 
+def recon_coef(q, inside, edges, xf: float, eps: float = 1e-30, linear: bool = False) -> float:
+    """Adaptive-order WENO-Z at xf of an ordered five-cell stencil with edges[0..5] (the
+    candidates and ideal weights of that non-uniform stencil)."""
+    q, e = _f64(q), _f64(edges)
+    ins = np.ascontiguousarray(inside, dtype=np.int32)
+    return lib().ora_recon_coef(_dp(q), ins.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(e),
+                                float(xf), eps, int(linear))
+
+
+def weno_coeffs(edges, xf: float, five: bool = True):
+    """Stretched-stencil coefficients: (c [3][3], d [3], c3 [2][2], d3 [2])."""
+    e = _f64(edges)
+    out = np.zeros(18)
+    lib().ora_weno_coeffs(_dp(e), float(xf), int(five), _dp(out))
+    return out[:9].reshape(3, 3), out[9:12], out[12:16].reshape(2, 2), out[16:18]
+
+
+def vertical_advection_column(z_faces, F, k0: int, w_faces, vertical_weno: int = 1,
+                              momentum_vadv: int = 1, eps: float = 1e-30) -> np.ndarray:
+    """w dF/dz of one velocity column as the momentum tendency computes it (levels k0..nz-1;
+    w_faces[k] on the bottom face of level k, nz + 1 values)."""
+    zf, F, wf = _f64(z_faces), _f64(F), _f64(w_faces)
+    nz = len(F)
+    out = np.zeros(nz)
+    lib().ora_vertical_advection_column(nz, _dp(zf), _dp(F), int(k0), _dp(wf), int(vertical_weno),
+                                        int(momentum_vadv), eps, _dp(out))
+    return out
+
+
 def filter_weights(ns: int, kind: int = 0):
     """Averaging weights a_1..a_ns of the sub-cycle and their first moment sum m a_m."""
     a = np.zeros(ns)
@@ -130,7 +163,8 @@ class OracleModel:
                        int(case.periodic_y)], dtype=np.int32)
         dg = _f64([case.x0, case.x1, case.y0, case.y1])
         prm = _f64([p[k] for k in PRM_ORDER])
-        ip = np.array([int(p["n_substeps"]), int(p["weno_linear"]), int(p.get("baro_filter", 0))],
+        ip = np.array([int(p["n_substeps"]), int(p["weno_linear"]), int(p.get("baro_filter", 0)),
+                       int(p.get("vertical_weno", 0)), int(p.get("momentum_vadv", 0))],
                       dtype=np.int32)
         keep = [_f64(case.z_faces), _f64(case.depth), _f64(case.taux), _f64(case.tauy)]
         L = lib()

@@ -47,6 +47,8 @@ typedef struct {
     double dt, chi, g, rho0, alpha, beta_s, T0, S0, f0, betap, omega, radius;
     double nu0, ri_a, nu_b, kappa_b, kappa_conv, weno_eps, min_depth;
     int ns, weno_linear, filter;
+    int vweno;                       /* vertical WENO: 0 index-space, 1 from the level thicknesses */
+    int mom_vadv;                    /* vertical momentum advection: 0 centred, 1 WENO flux form */
     double* fw;                      /* averaging weights a_m of the sub-cycle, m = 1..ns */
     /* column data */
     double *depth, *taux, *tauy;
@@ -222,6 +224,155 @@ double ora_recon(const double* q, const int* in, double eps, int linear) {
     return q[2];
 }
 
+/* ------------------------------------------------------------------ WENO on stretched levels */
+
+/*
+ * Reconstruction weights on a non-uniform stencil (the "stretched" reading of the
+ * adaptive WENO of Sec. "New numerical methods for finite volume fluid dynamics on the
+ * sphere").  The n cells of the stencil span the edges e[0..n], monotone in either
+ * direction.  c[0..n-1] are the weights for which sum_j c_j qbar_j is the value at x = xf
+ * of the polynomial of degree n-1 whose means over the n cells are qbar_j.  With
+ * p(x) = sum_m a_m ((x - xf)/h)^m the cell means are M a with
+ *   M[j][m] = mean over cell j of ((x - xf)/h)^m
+ *           = (s_{j+1}^{m+1} - s_j^{m+1}) / ((m+1)(s_{j+1} - s_j)),  s = (e - xf)/h,
+ * and the value at xf is a_0, the first entry of M^{-1} qbar; so c is the first row of
+ * M^{-1}, the solution of M^T c = (1, 0, ..., 0).  Gaussian elimination with partial
+ * pivoting; h is the mean cell width (the weights do not depend on it).
+ */
+static void recon_weights(int n, const double* e, double xf, double* c) {
+    double A[5][6];
+    double h = fabs(e[n] - e[0]) / n;
+    for (int j = 0; j < n; j++) {
+        double s0 = (e[j] - xf) / h, s1 = (e[j + 1] - xf) / h;
+        double p0 = s0, p1 = s1;   /* s^{m+1} */
+        for (int m = 0; m < n; m++) {
+            A[m][j] = (p1 - p0) / ((m + 1) * (s1 - s0));   /* row m of M^T */
+            p0 *= s0;
+            p1 *= s1;
+        }
+    }
+    for (int m = 0; m < n; m++) A[m][n] = (m == 0) ? 1.0 : 0.0;
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int r = col + 1; r < n; r++)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        for (int t = 0; t <= n; t++) { double x = A[col][t]; A[col][t] = A[piv][t]; A[piv][t] = x; }
+        for (int r = col + 1; r < n; r++) {
+            double f = A[r][col] / A[col][col];
+            for (int t = col; t <= n; t++) A[r][t] -= f * A[col][t];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = A[r][n];
+        for (int t = r + 1; t < n; t++) s -= A[r][t] * c[t];
+        c[r] = s / A[r][r];
+    }
+}
+
+/*
+ * Coefficients of the reconstruction at the face xf downstream of cell 2 of an ordered
+ * five-cell stencil with edges e[0..5] (upwind to downwind): the three third-order
+ * candidates on cells {0,1,2}, {1,2,3}, {2,3,4}; the ideal weights d_r for which
+ * sum_r d_r (candidate r) is the fifth-order reconstruction on all five cells (d_0 and d_2
+ * from its outermost weights, d_1 = 1 - d_0 - d_2); and the same for the third-order
+ * scheme on cells 1..3 (candidates on {1,2} and {2,3}).  Only the parts whose edges lie
+ * inside [0, nz] are computed: five = 0 skips the fifth-order part.
+ */
+typedef struct { double c[3][3], d[3], c3[2][2], d3[2]; } wcoef_t;
+
+void ora_weno_coeffs(const double* e, double xf, int five, double* out /* 18 values */) {
+    wcoef_t w;
+    memset(&w, 0, sizeof(w));
+    if (five) {
+        double c5[5];
+        for (int r = 0; r < 3; r++) recon_weights(3, e + r, xf, w.c[r]);
+        recon_weights(5, e, xf, c5);
+        w.d[0] = c5[0] / w.c[0][0];
+        w.d[2] = c5[4] / w.c[2][2];
+        w.d[1] = 1.0 - w.d[0] - w.d[2];
+    }
+    double c3[3];
+    recon_weights(2, e + 1, xf, w.c3[0]);
+    recon_weights(2, e + 2, xf, w.c3[1]);
+    recon_weights(3, e + 1, xf, c3);
+    w.d3[0] = c3[0] / w.c3[0][0];
+    w.d3[1] = 1.0 - w.d3[0];
+    memcpy(out, &w, sizeof(w));
+}
+
+/* WENO-Z of an ordered stencil with the coefficients of ora_weno_coeffs: candidates and
+ * ideal weights from the level thicknesses, smoothness indicators and tau5 in index space
+ * (the Jiang-Shu forms of ora_weno5).  The reading: the indicators only rank the
+ * candidates, so they keep their uniform form while the candidates and weights carry the
+ * grid. */
+static double weno5_coef(const double* q, const wcoef_t* w, double eps, int linear) {
+    double p[3];
+    for (int r = 0; r < 3; r++) p[r] = w->c[r][0] * q[r] + w->c[r][1] * q[r + 1] + w->c[r][2] * q[r + 2];
+    if (linear) return w->d[0] * p[0] + w->d[1] * p[1] + w->d[2] * p[2];
+    double a = q[0] - 2.0 * q[1] + q[2], bb = q[0] - 4.0 * q[1] + 3.0 * q[2];
+    double b0 = 13.0 / 12.0 * a * a + 0.25 * bb * bb;
+    a = q[1] - 2.0 * q[2] + q[3]; bb = q[1] - q[3];
+    double b1 = 13.0 / 12.0 * a * a + 0.25 * bb * bb;
+    a = q[2] - 2.0 * q[3] + q[4]; bb = 3.0 * q[2] - 4.0 * q[3] + q[4];
+    double b2 = 13.0 / 12.0 * a * a + 0.25 * bb * bb;
+    double tau = fabs(b0 - b2);
+    double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+    double a0 = w->d[0] * (1.0 + r0 * r0), a1 = w->d[1] * (1.0 + r1 * r1), a2 = w->d[2] * (1.0 + r2 * r2);
+    return (a0 * p[0] + a1 * p[1] + a2 * p[2]) / (a0 + a1 + a2);
+}
+/* third order on q[1..3] with the stretched candidates and weights */
+static double weno3_coef(const double* q, const wcoef_t* w, double eps, int linear) {
+    double p0 = w->c3[0][0] * q[1] + w->c3[0][1] * q[2];
+    double p1 = w->c3[1][0] * q[2] + w->c3[1][1] * q[3];
+    if (linear) return w->d3[0] * p0 + w->d3[1] * p1;
+    double b0 = (q[2] - q[1]) * (q[2] - q[1]);
+    double b1 = (q[3] - q[2]) * (q[3] - q[2]);
+    double tau = fabs(b0 - b1);
+    double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps);
+    double a0 = w->d3[0] * (1.0 + r0 * r0), a1 = w->d3[1] * (1.0 + r1 * r1);
+    return (a0 * p0 + a1 * p1) / (a0 + a1);
+}
+
+/* Adaptive order with stretched coefficients (same order selection as ora_recon). */
+double ora_recon_coef(const double* q, const int* in, const double* e, double xf, double eps,
+                      int linear) {
+    double wc[18];
+    if (in[0] && in[1] && in[2] && in[3] && in[4]) {
+        ora_weno_coeffs(e, xf, 1, wc);
+        return weno5_coef(q, (const wcoef_t*)wc, eps, linear);
+    }
+    if (in[1] && in[2] && in[3]) {
+        ora_weno_coeffs(e, xf, 0, wc);
+        return weno3_coef(q, (const wcoef_t*)wc, eps, linear);
+    }
+    return q[2];
+}
+
+/*
+ * Reconstruction at the level face zf[kf] (bottom face of level kf) of one column of a
+ * field, F[base + k s] for k in [k0, nz) (levels outside that range are not in the
+ * fluid), upwind by the sign of the face velocity wt (wt >= 0 takes the levels below).
+ * vweno = 0: index-space coefficients (ora_recon); 1: coefficients of the level
+ * thicknesses (ora_recon_coef).
+ */
+static double recon_vertical(const ora_t* m, const double* F, long base, long s, int kf, int k0,
+                             double wt) {
+    double q[5], e[6];
+    int in[5];
+    int pos = wt >= 0.0;
+    for (int n = 0; n < 5; n++) {
+        int kk = pos ? kf - 3 + n : kf + 2 - n;
+        in[n] = kk >= k0 && kk < m->nz;
+        q[n] = in[n] ? F[base + (long)kk * s] : 0.0;
+    }
+    if (!m->vweno) return ora_recon(q, in, m->weno_eps, m->weno_linear);
+    for (int n = 0; n < 6; n++) {
+        int ke = pos ? kf - 3 + n : kf + 3 - n;   /* edge n of the ordered stencil */
+        e[n] = (ke >= 0 && ke <= m->nz) ? m->zf[ke] : 0.0;   /* unused when outside */
+    }
+    return ora_recon_coef(q, in, e, m->zf[kf], m->weno_eps, m->weno_linear);
+}
+
 /* ------------------------------------------------------------------ diagnostics */
 
 static double buoy(const ora_t* m, double T, double S) {
@@ -315,15 +466,11 @@ static double flux_y(const ora_t* m, const double* C, int i, int j, int k) {
 }
 /* flux through the bottom face of cell k: zero at the sea floor and at the surface */
 static double flux_z(const ora_t* m, const double* C, int i, int j, int k) {
-    if (k >= m->nz || k <= kbot(m, i, j)) return 0.0;
+    int kb = kbot(m, i, j);
+    if (k >= m->nz || k <= kb) return 0.0;
     double wt = cval(m, m->w, i, j, k);
-    double q[5]; int in[5];
-    for (int n = 0; n < 5; n++) {
-        int kk = wt >= 0.0 ? k - 3 + n : k + 2 - n;
-        q[n] = cval(m, C, i, j, kk);
-        in[n] = wet(m, i, j, kk);
-    }
-    return wt * area_c(m, j) * ora_recon(q, in, m->weno_eps, m->weno_linear);
+    long s = (long)m->nx * m->ny;
+    return wt * area_c(m, j) * recon_vertical(m, C, at3(m, i, j, 0), s, k, kb, wt);
 }
 
 static void tracer_tendency(ora_t* m, const double* C, double* G) {
@@ -362,6 +509,64 @@ static double kin(const ora_t* m, int i, int j, int k) {
     return 0.25 * (ua * ua + ub * ub) + 0.25 * (va * va + vb * vb);
 }
 
+/*
+ * Vertical advection term of the vector-invariant momentum equation, w du/dz, at level k
+ * of a velocity column F[base + k s] whose wet levels are [k0, nz), with the column's
+ * face velocities wbot (bottom face of level k) and wtop (top face).
+ * mom_vadv = 0, centred:  1/2 [wtop (F_{k+1} - F_k)/dzf_{k+1} + wbot (F_k - F_{k-1})/dzf_k].
+ * mom_vadv = 1, WENO flux form (the vertical part of the WENO vector-invariant scheme):
+ *   [wtop F~_{k+1/2} - wbot F~_{k-1/2} - F_k (wtop - wbot)] / dz_k,
+ * F~ the upwind reconstruction at the face (recon_vertical, same order reduction and
+ * coefficients as the tracers).  Faces at the top of the column and below its lowest wet
+ * level carry no flux (wtop, wbot = 0 there).  Both forms equal w dF/dz for a linear
+ * profile and constant w on uniform levels; the flux form vanishes for a uniform
+ * profile whatever w does.
+ */
+static double vertical_advection(const ora_t* m, const double* F, long base, long s, int k, int k0,
+                                 double wbot, double wtop) {
+    int nz = m->nz;
+    double fk = F[base + (long)k * s];
+    if (k + 1 >= nz) wtop = 0.0;
+    if (k <= k0) wbot = 0.0;
+    if (!m->mom_vadv) {
+        double up = 0.0, dn = 0.0;
+        if (k + 1 < nz) up = wtop * (F[base + (long)(k + 1) * s] - fk) / dz_f(m, k + 1);
+        if (k > k0) dn = wbot * (fk - F[base + (long)(k - 1) * s]) / dz_f(m, k);
+        return 0.5 * (up + dn);
+    }
+    double ft = (k + 1 < nz) ? wtop * recon_vertical(m, F, base, s, k + 1, k0, wtop) : 0.0;
+    double fb = (k > k0) ? wbot * recon_vertical(m, F, base, s, k, k0, wbot) : 0.0;
+    return (ft - fb - fk * (wtop - wbot)) / m->dz[k];
+}
+
+/*
+ * The vertical advection term of one velocity column alone (the tests' handle on
+ * vertical_advection): levels zf[0..nz] bottom to top, F[0..nz-1], wet levels [k0, nz),
+ * wf[k] the velocity on the bottom face of level k (wf[nz] on the surface), scheme
+ * switches as in ora_create; out[k] for k in [k0, nz).
+ */
+void ora_vertical_advection_column(int nz, const double* zf, const double* F, int k0,
+                                   const double* wf, int vweno, int mom_vadv, double eps,
+                                   double* out) {
+    ora_t m;
+    memset(&m, 0, sizeof(m));
+    m.nz = nz;
+    m.zf = (double*)zf;
+    m.zc = malloc(nz * sizeof(double));
+    m.dz = malloc(nz * sizeof(double));
+    for (int k = 0; k < nz; k++) {
+        m.zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+        m.dz[k] = zf[k + 1] - zf[k];
+    }
+    m.vweno = vweno;
+    m.mom_vadv = mom_vadv;
+    m.weno_eps = eps;
+    for (int k = k0; k < nz; k++)
+        out[k] = vertical_advection(&m, F, 0, 1, k, k0, wf[k], wf[k + 1]);
+    free(m.zc);
+    free(m.dz);
+}
+
 static void momentum_tendency(ora_t* m) {
     int nx = m->nx, ny = m->ny, nz = m->nz;
 #pragma omp parallel for schedule(static)
@@ -373,7 +578,6 @@ static void momentum_tendency(ora_t* m) {
                 /* ---- u at the west face of cell (i, j) */
                 m->Gu[c] = 0.0;
                 if (uwet(m, i, j, k)) {
-                    double u0 = m->u[c];
                     double vh = 0.25 * (vval(m, m->v, i - 1, j, k) + vval(m, m->v, i, j, k)
                                       + vval(m, m->v, i - 1, j + 1, k) + vval(m, m->v, i, j + 1, k));
                     for (int n = 0; n < 5; n++) {
@@ -385,20 +589,16 @@ static void momentum_tendency(ora_t* m) {
                     double dxc = dx_c(m, j);
                     double dK = (kin(m, i, j, k) - kin(m, i - 1, j, k)) / dxc;
                     double dP = (cval(m, m->p, i, j, k) - cval(m, m->p, i - 1, j, k)) / dxc;
-                    double up = 0.0, dn = 0.0;
-                    if (k + 1 < nz && uwet(m, i, j, k + 1))
-                        up = 0.5 * (cval(m, m->w, i - 1, j, k + 1) + cval(m, m->w, i, j, k + 1))
-                           * (uval(m, m->u, i, j, k + 1) - u0) / dz_f(m, k + 1);
-                    if (k - 1 >= 0 && uwet(m, i, j, k - 1))
-                        dn = 0.5 * (cval(m, m->w, i - 1, j, k) + cval(m, m->w, i, j, k))
-                           * (u0 - uval(m, m->u, i, j, k - 1)) / dz_f(m, k);
+                    int k0 = kbot(m, i - 1, j) > kbot(m, i, j) ? kbot(m, i - 1, j) : kbot(m, i, j);
+                    double wt = k + 1 < nz ? 0.5 * (cval(m, m->w, i - 1, j, k + 1) + cval(m, m->w, i, j, k + 1)) : 0.0;
+                    double wb = 0.5 * (cval(m, m->w, i - 1, j, k) + cval(m, m->w, i, j, k));
+                    double va = vertical_advection(m, m->u, at3(m, i, j, 0), (long)nx * ny, k, k0, wb, wt);
                     double wind = (k == nz - 1) ? m->taux[j * nx + i] / (m->rho0 * m->dz[nz - 1]) : 0.0;
-                    m->Gu[c] = (zt + f_u(m, j)) * vh - dK - 0.5 * (up + dn) - dP + wind;
+                    m->Gu[c] = (zt + f_u(m, j)) * vh - dK - va - dP + wind;
                 }
                 /* ---- v at the south face of cell (i, j) */
                 m->Gv[c] = 0.0;
                 if (vwet(m, i, j, k)) {
-                    double v0 = m->v[c];
                     double uh = 0.25 * (uval(m, m->u, i, j - 1, k) + uval(m, m->u, i + 1, j - 1, k)
                                       + uval(m, m->u, i, j, k) + uval(m, m->u, i + 1, j, k));
                     for (int n = 0; n < 5; n++) {
@@ -410,15 +610,12 @@ static void momentum_tendency(ora_t* m) {
                     double dy = dy_(m);
                     double dK = (kin(m, i, j, k) - kin(m, i, j - 1, k)) / dy;
                     double dP = (cval(m, m->p, i, j, k) - cval(m, m->p, i, j - 1, k)) / dy;
-                    double up = 0.0, dn = 0.0;
-                    if (k + 1 < nz && vwet(m, i, j, k + 1))
-                        up = 0.5 * (cval(m, m->w, i, j - 1, k + 1) + cval(m, m->w, i, j, k + 1))
-                           * (vval(m, m->v, i, j, k + 1) - v0) / dz_f(m, k + 1);
-                    if (k - 1 >= 0 && vwet(m, i, j, k - 1))
-                        dn = 0.5 * (cval(m, m->w, i, j - 1, k) + cval(m, m->w, i, j, k))
-                           * (v0 - vval(m, m->v, i, j, k - 1)) / dz_f(m, k);
+                    int k0 = kbot(m, i, j - 1) > kbot(m, i, j) ? kbot(m, i, j - 1) : kbot(m, i, j);
+                    double wt = k + 1 < nz ? 0.5 * (cval(m, m->w, i, j - 1, k + 1) + cval(m, m->w, i, j, k + 1)) : 0.0;
+                    double wb = 0.5 * (cval(m, m->w, i, j - 1, k) + cval(m, m->w, i, j, k));
+                    double va = vertical_advection(m, m->v, at3(m, i, j, 0), (long)nx * ny, k, k0, wb, wt);
                     double wind = (k == nz - 1) ? m->tauy[j * nx + i] / (m->rho0 * m->dz[nz - 1]) : 0.0;
-                    m->Gv[c] = -(zt + f_v(m, j)) * uh - dK - 0.5 * (up + dn) - dP + wind;
+                    m->Gv[c] = -(zt + f_v(m, j)) * uh - dK - va - dP + wind;
                 }
             }
 }
@@ -777,7 +974,9 @@ void ora_diagnostics(ora_t* m, double* out) {
  * zf[nz+1] bottom to top; depth, taux, tauy [ny][nx];
  * prm = {dt, chi, g, rho0, alpha, beta_s, T0, S0, f0, beta_plane, omega, radius,
  *        nu0, ri_a, nu_b, kappa_b, kappa_conv, weno_eps, min_depth};
- * iprm = {n_substeps, weno_linear, averaging filter (0 equal weights, 1 power-law shape)}.
+ * iprm = {n_substeps, weno_linear, averaging filter (0 equal weights, 1 power-law shape),
+ *         vertical WENO coefficients (0 index space, 1 from the level thicknesses),
+ *         vertical momentum advection (0 centred, 1 WENO flux form)}.
  */
 ora_t* ora_create(const int* igrid, const double* dgrid, const double* zf, const double* depth,
                   const double* taux, const double* tauy, const double* prm, const int* iprm) {
@@ -791,6 +990,7 @@ ora_t* ora_create(const int* igrid, const double* dgrid, const double* zf, const
     m->nu_b = prm[14]; m->kappa_b = prm[15]; m->kappa_conv = prm[16]; m->weno_eps = prm[17];
     m->min_depth = prm[18];
     m->ns = iprm[0]; m->weno_linear = iprm[1]; m->filter = iprm[2];
+    m->vweno = iprm[3]; m->mom_vadv = iprm[4];
     m->fw = malloc((m->ns > 0 ? m->ns : 1) * sizeof(double));
     if (m->ns > 0) ora_filter_weights(m->ns, m->filter, m->fw);
     int nx = m->nx, ny = m->ny, nz = m->nz;

@@ -136,6 +136,7 @@ def default_params() -> Dict[str, float]:
         f0=1e-4, beta_plane=2e-11, omega=7.292115e-5, radius=6.371e6,
         nu0=1e-2, ri_a=5.0, nu_b=1e-4, kappa_b=1e-5, kappa_conv=0.1,
         weno_eps=1e-30, weno_linear=0, min_depth=50.0, baro_filter=0,
+        vertical_weno=0, momentum_vadv=0,
     )
 
 
