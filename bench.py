@@ -446,15 +446,22 @@ def single_model(case, precision: int, steps: int, warmup: int, local: int, dist
             "clocks": clk.summary()}
 
 
-def other_configs(args, rank, world, local, dist):
+def other_configs(args, rank, world, local, dist, case12=None):
     """Every other configuration of the benchmark, measured in the default run: the
-    1-degree grid in the mixed form and in FP64 side by side, the aqua-planet per-GPU
-    workload of the paper's weak scaling (FP64 as the paper ran it, and mixed), the
-    96-basin ensemble against its members stepped one by one, and the 1/2-degree step
-    with the learned closure against the Richardson-number step."""
+    1/12-degree step with the optional vertical schemes (stretched-level WENO
+    coefficients, WENO vertical momentum advection), the 1-degree grid in the mixed form
+    and in FP64 side by side, the aqua-planet per-GPU workload of the paper's weak scaling
+    (FP64 as the paper ran it, and mixed), the 96-basin ensemble against its members
+    stepped one by one, and the 1/2-degree step with the learned closure against the
+    Richardson-number step."""
     import torch
     from paper_2309_06662_gb300 import ocean
     out = {}
+    if case12 is not None:
+        vs = single_model(case12.with_params(vertical_weno=1, momentum_vadv=1), ocean.OCEAN_MIXED,
+                          10, 3, local, dist)
+        vs["schemes"] = "vertical_weno=STRETCHED, momentum_vadv=WENO"
+        out["latlon_12th_vertical_weno"] = vs
     c1 = inputs.latlon_1deg_case()
     mixed = single_model(c1, ocean.OCEAN_MIXED, 50, 5, local, dist)
     fp64 = single_model(c1, ocean.OCEAN_FP64, 10, 2, local, dist)
@@ -866,7 +873,7 @@ def main():
     errors = mixed_vs_fp64(case, args.error_steps) if rank == 0 and args.error_steps > 0 else None
     configs = None
     if args.workload == "latlon_12th" and not args.no_configs:
-        configs = other_configs(args, rank, world, local, dist)
+        configs = other_configs(args, rank, world, local, dist, case12=case)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

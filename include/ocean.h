@@ -112,6 +112,10 @@ typedef struct {
                                (0 = none; otherwise a multiple of 16) */
     int baro_filter;        /* time average closing the barotropic sub-cycle:
                                OCEAN_FILTER_BOXCAR or OCEAN_FILTER_POWER_LAW */
+    int vertical_weno;      /* coefficients of the vertical WENO reconstructions:
+                               OCEAN_VWENO_INDEX or OCEAN_VWENO_STRETCHED */
+    int momentum_vadv;      /* vertical momentum advection: OCEAN_VADV_CENTRED or
+                               OCEAN_VADV_WENO */
 } ocean_params;
 
 /* Averaging filters of the split-explicit sub-cycle (Sec. "Optimization of ocean free
@@ -123,6 +127,26 @@ typedef struct {
  * positive lobe; it damps the unresolved fast modes more than the boxcar). */
 #define OCEAN_FILTER_BOXCAR 0
 #define OCEAN_FILTER_POWER_LAW 1
+
+/* Vertical reconstructions on stretched levels (the adaptive WENO of Sec. "New numerical
+ * methods for finite volume fluid dynamics on the sphere" on a non-uniform grid).  INDEX:
+ * the uniform-grid coefficients in level index space.  STRETCHED: the candidate
+ * polynomials and ideal weights of each level face from the actual level thicknesses
+ * (fifth order on smoothly stretched levels); the smoothness indicators keep their
+ * index-space form.  Applies to the vertical tracer fluxes and, with OCEAN_VADV_WENO, to
+ * the vertical momentum advection. */
+#define OCEAN_VWENO_INDEX 0
+#define OCEAN_VWENO_STRETCHED 1
+
+/* Vertical advection term w du/dz of the vector-invariant momentum equation (Sec. "New
+ * numerical methods for finite volume fluid dynamics on the sphere").  CENTRED:
+ * 1/2 [w_top (u_{k+1} - u_k)/dzf_{k+1} + w_bot (u_k - u_{k-1})/dzf_k].  WENO: the flux form
+ * [w_top u~_top - w_bot u~_bot - u_k (w_top - w_bot)] / dz_k with u~ the upwind WENO
+ * reconstruction at the level faces (adaptive order at the column ends).  w at a u-face is
+ * the mean of the two neighbouring columns' w; no flux through the surface or below the
+ * face's lowest wet level.  The batched ensemble runs the defaults (INDEX, CENTRED). */
+#define OCEAN_VADV_CENTRED 0
+#define OCEAN_VADV_WENO 1
 
 typedef struct {
     long step;              /* completed steps */

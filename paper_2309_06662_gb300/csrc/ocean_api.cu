@@ -66,10 +66,12 @@ struct ocean_s {
          *rHu = nullptr, *rHv = nullptr, *Ub2 = nullptr, *Vb2 = nullptr, *dE2 = nullptr;
     double *eta = nullptr, *accE = nullptr, *accU = nullptr, *accV = nullptr;
     void* fw = nullptr;        // averaging weights of the sub-cycle (power-law filter), R[ns]
+    void* vw = nullptr;        // vertical WENO coefficients of each level face, R[(nz+1)*2][OC_VWROW]
     double fmom = 0;           // their first moment sum_m m a_m
     short *kb = nullptr, *kbu = nullptr, *kbv = nullptr, *kbz = nullptr, *kbzin = nullptr;
     void* rowm = nullptr;   // 7 row arrays of (ny + 2H) elements
     void* levm = nullptr;   // 8 level arrays of nz elements
+    void* lvt = nullptr;    // per-level rows of OC_LVROW constants of the tile kernels
     double *drow = nullptr, *dlev = nullptr;
     double *diag_part = nullptr, *diag_out = nullptr;
     // host-side copies
@@ -152,6 +154,10 @@ int validate(const ocean_grid* g, const ocean_params* p) {
         return fail(nullptr, OCEAN_ERR_ARG, "closure_hidden must be 0 or a positive multiple of 16");
     if (p->baro_filter != OCEAN_FILTER_BOXCAR && p->baro_filter != OCEAN_FILTER_POWER_LAW)
         return fail(nullptr, OCEAN_ERR_ARG, "unknown baro_filter %d", p->baro_filter);
+    if (p->vertical_weno != OCEAN_VWENO_INDEX && p->vertical_weno != OCEAN_VWENO_STRETCHED)
+        return fail(nullptr, OCEAN_ERR_ARG, "unknown vertical_weno %d", p->vertical_weno);
+    if (p->momentum_vadv != OCEAN_VADV_CENTRED && p->momentum_vadv != OCEAN_VADV_WENO)
+        return fail(nullptr, OCEAN_ERR_ARG, "unknown momentum_vadv %d", p->momentum_vadv);
     return OCEAN_OK;
 }
 
@@ -194,6 +200,7 @@ size_t layout(ocean_t m, char* base) {
                     &m->dE2};
     for (void** q : two) *q = f2();
     m->fw = c.take<char>((size_t)m->prm.n_substeps * e);
+    m->vw = c.take<char>(((size_t)m->nz + 1) * 2 * OC_VWROW * e);
     m->eta = c.take<double>(n2); m->accE = c.take<double>(n2);
     m->accU = c.take<double>(n2); m->accV = c.take<double>(n2);
     m->kb = c.take<short>(n2); m->kbu = c.take<short>(n2); m->kbv = c.take<short>(n2);
@@ -201,6 +208,7 @@ size_t layout(ocean_t m, char* base) {
     const size_t nr = (size_t)m->ny + 2 * OC_H;
     m->rowm = c.take<char>(7 * nr * e);
     m->levm = c.take<char>(8 * (size_t)m->nz * e);
+    m->lvt = c.take<char>((size_t)OC_LVROW * m->nz * e);
     m->drow = c.take<double>(3 * nr);
     m->dlev = c.take<double>(4 * (size_t)m->nz + 3 * ((size_t)m->nz + 1));
     m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes()));
@@ -261,6 +269,70 @@ void upload_real(ocean_t m, const std::vector<double>& src, void* dst) {
     else upload_conv<float>(m, src, dst);
 }
 
+// Weights c[0..n-1] for which sum_j c_j qbar_j is the value at xf of the polynomial of
+// degree n-1 with means qbar_j over the n cells between the edges e[0..n] (monotone in
+// either direction): with the primitive P(x) = int_{e_0}^x p, known at the edges as
+// P(e_m) = sum_{j<m} (e_{j+1} - e_j) qbar_j, interpolate P by the Lagrange polynomial
+// through the n+1 edges and differentiate: p(xf) = sum_m P(e_m) L_m'(xf), so
+// c_j = (e_{j+1} - e_j) sum_{m>j} L_m'(xf).  Coordinates are shifted to xf and scaled by
+// the mean cell width first (the weights do not depend on either).
+void face_weights(int n, const double* e, double xf, double* c) {
+    double s[6], dL[6];
+    const double h = std::fabs(e[n] - e[0]) / n;
+    for (int m = 0; m <= n; ++m) s[m] = (e[m] - xf) / h;
+    for (int m = 0; m <= n; ++m) {
+        double den = 1.0, num = 0.0;
+        for (int l = 0; l <= n; ++l) {
+            if (l == m) continue;
+            den *= s[m] - s[l];
+            double pr = 1.0;   // prod over q != m, l of (0 - s_q)
+            for (int q = 0; q <= n; ++q)
+                if (q != m && q != l) pr *= -s[q];
+            num += pr;
+        }
+        dL[m] = num / den / h;
+    }
+    for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int m = j + 1; m <= n; ++m) acc += dL[m];
+        c[j] = (e[j + 1] - e[j]) * acc;
+    }
+}
+
+// One row of the vertical WENO table: the reconstruction at level face kf upwind by
+// direction dir (0: the face velocity is >= 0 and the stencil lies below, cells kf-3 ..
+// kf+1; 1: above, cells kf+2 .. kf-2), ordered from upwind to downwind.  The fifth-order
+// part is filled when all six edges exist, the third-order part when its four do; the
+// kernels use a part only where its stencil lies in the fluid, so inside the grid.
+void vw_row(const std::vector<double>& zf, int kf, int dir, double* row) {
+    const int nz = (int)zf.size() - 1;
+    for (int n = 0; n < OC_VWROW; ++n) row[n] = 0.0;
+    double e[6];
+    bool have[6];
+    for (int n = 0; n < 6; ++n) {
+        const int ke = dir == 0 ? kf - 3 + n : kf + 3 - n;
+        have[n] = ke >= 0 && ke <= nz;
+        e[n] = have[n] ? zf[ke] : 0.0;
+    }
+    const double xf = zf[kf];
+    if (have[0] && have[5]) {
+        double c5[5];
+        for (int r = 0; r < 3; ++r) face_weights(3, e + r, xf, row + 3 * r);
+        face_weights(5, e, xf, c5);
+        row[9] = c5[0] / row[0];
+        row[11] = c5[4] / row[8];
+        row[10] = 1.0 - row[9] - row[11];
+    }
+    if (have[1] && have[4]) {
+        double c3[3];
+        face_weights(2, e + 1, xf, row + 12);
+        face_weights(2, e + 2, xf, row + 14);
+        face_weights(3, e + 1, xf, c3);
+        row[16] = c3[0] / row[12];
+        row[17] = 1.0 - row[16];
+    }
+}
+
 void upload_levels(ocean_t m) {
     const int nz = m->nz;
     std::vector<double> lv(8 * (size_t)nz, 0.0), dl(4 * (size_t)nz + 3 * ((size_t)nz + 1), 0.0);
@@ -290,6 +362,29 @@ void upload_levels(ocean_t m) {
     }
     upload_real(m, lv, m->levm);
     upload_bytes(m, m->dlev, dl.data(), dl.size() * sizeof(double));
+    // rows of the tile kernels (LevelRow): dz, 1/dz, dt/(dz dzf) below and above, Tref,
+    // Sref, and those factors times the reference profiles' level differences
+    std::vector<double> rows((size_t)OC_LVROW * nz, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        double* r = rows.data() + (size_t)k * OC_LVROW;
+        const double alo = k > 0 ? m->prm.dt / (m->dz[k] * (m->zc[k] - m->zc[k - 1])) : 0.0;
+        const double ahi = k < nz - 1 ? m->prm.dt / (m->dz[k] * (m->zc[k + 1] - m->zc[k])) : 0.0;
+        r[0] = m->dz[k];
+        r[1] = 1.0 / m->dz[k];
+        r[2] = alo;
+        r[3] = ahi;
+        r[4] = m->Tref[k];
+        r[5] = m->Sref[k];
+        r[6] = k < nz - 1 ? ahi * (m->Tref[k + 1] - m->Tref[k]) : 0.0;
+        r[7] = k > 0 ? alo * (m->Tref[k] - m->Tref[k - 1]) : 0.0;
+        r[8] = k < nz - 1 ? ahi * (m->Sref[k + 1] - m->Sref[k]) : 0.0;
+        r[9] = k > 0 ? alo * (m->Sref[k] - m->Sref[k - 1]) : 0.0;
+    }
+    upload_real(m, rows, m->lvt);
+    std::vector<double> vw(((size_t)nz + 1) * 2 * OC_VWROW);
+    for (int kf = 0; kf <= nz; ++kf)
+        for (int dir = 0; dir < 2; ++dir) vw_row(m->zf, kf, dir, vw.data() + ((size_t)kf * 2 + dir) * OC_VWROW);
+    upload_real(m, vw, m->vw);
 }
 
 // metrics, masks, column depths; host FP64, uploaded once
@@ -502,6 +597,10 @@ KP<R> make_kp(const ocean_t m, bool first) {
     k.kappa_conv = (R)p.kappa_conv; k.eps = (R)p.weno_eps;
     k.ptop = (R)(m->zf[nz] - m->zc[nz - 1]);
     k.linear = p.weno_linear;
+    k.vw = reinterpret_cast<const R*>(m->vw);
+    k.vweno = p.vertical_weno;
+    k.mvadv = p.momentum_vadv;
+    k.lvt = reinterpret_cast<const R*>(m->lvt);
     return k;
 }
 

@@ -210,6 +210,8 @@ int ocean_ensemble_create(int members, const ocean_grid* grids, const double* co
             return efail(OCEAN_ERR_ARG, "member %d: ensemble members must be closed basins", m);
         if (p.closure != OCEAN_CLOSURE_RI || p.closure_hidden != 0)
             return efail(OCEAN_ERR_ARG, "member %d: ensemble members use the Richardson-number closure", m);
+        if (p.vertical_weno != OCEAN_VWENO_INDEX || p.momentum_vadv != OCEAN_VADV_CENTRED)
+            return efail(OCEAN_ERR_ARG, "member %d: ensemble members use the default vertical schemes", m);
         if (p.baro_filter != OCEAN_FILTER_BOXCAR)
             return efail(OCEAN_ERR_ARG, "member %d: ensemble members average the sub-cycle with equal weights", m);
         if (p.precision != params[0].precision || p.dt != params[0].dt ||

@@ -48,7 +48,46 @@ struct KP {
     R nu0, ri_a, nu_b, kappa_b, kappa_conv;
     R eps, ptop;
     int linear;
+    // vertical schemes: vweno = 1 takes the vertical WENO coefficients of each level face
+    // from vw (rows of OC_VWROW values, row (kf * 2 + dir) for face kf = 0..nz, dir 0 when
+    // the face velocity is >= 0: c[3][3], d[3], c3[2][2], d3[2], 0, 0); mvadv = 1: the WENO
+    // flux form of the vertical momentum advection
+    const R* vw;
+    int vweno, mvadv;
+    // per-level rows of OC_LVROW values (see LevelRow)
+    const R* lvt;
 };
+
+// One level's constants for the tile kernels, one row of KP::lvt: dz_k, 1/dz_k; the
+// implicit solve's factors alo = dt/(dz_k dzf_k) (0 at k = 0) and ahi = dt/(dz_k dzf_{k+1})
+// (0 at the top); Tref_k, Sref_k; and the diffusion of the reference profiles
+// hdT = ahi (Tref_{k+1} - Tref_k), ldT = alo (Tref_k - Tref_{k-1}), likewise for S.
+#define OC_LVROW 16
+template <typename R>
+struct LevelRow {
+    R dz, rdz, alo, ahi, Tref, Sref, hdT, ldT, hdS, ldS;
+};
+
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+__device__ __forceinline__ float2 make_vec2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 make_vec2(double a, double b) { return make_double2(a, b); }
+
+// the first ten values of row k, by 16-byte loads through the read-only path
+__device__ __forceinline__ LevelRow<float> load_level_row(const float* t, int k) {
+    const float4* r = reinterpret_cast<const float4*>(t + (size_t)k * OC_LVROW);
+    const float4 a = __ldg(r), b = __ldg(r + 1);
+    const float2 c = __ldg(reinterpret_cast<const float2*>(r + 2));
+    return {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+}
+__device__ __forceinline__ LevelRow<double> load_level_row(const double* t, int k) {
+    const double2* r = reinterpret_cast<const double2*>(t + (size_t)k * OC_LVROW);
+    const double2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3), e = __ldg(r + 4);
+    return {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, e.x, e.y};
+}
+
+#define OC_VWROW 20
 
 // ----------------------------------------------------------------------- WENO-Z
 
@@ -112,6 +151,57 @@ template <typename R>
 __device__ __forceinline__ R weno_adaptive(const R* q, unsigned in, R eps, int linear) {
     if (in == 31u) return weno5(q[0], q[1], q[2], q[3], q[4], eps, linear);
     if ((in & 14u) == 14u) return weno3(q[1], q[2], q[3], eps, linear);
+    return q[2];
+}
+
+// ----------------------------------------------------------------- stretched-level WENO
+// The same reconstructions with the candidates and ideal weights of one stencil of
+// stretched levels (a row of the vw table: c[r][0..2] the candidate r's weights on its
+// three cells, d[r] the ideal weights, c3 and d3 those of the third-order scheme on the
+// central three cells).  The smoothness indicators keep their index-space form.
+template <typename R>
+__device__ __forceinline__ R weno5_row(const R* q, const R* c, R eps, int linear) {
+    R p0 = c[0] * q[0] + c[1] * q[1] + c[2] * q[2];
+    R p1 = c[3] * q[1] + c[4] * q[2] + c[5] * q[3];
+    R p2 = c[6] * q[2] + c[7] * q[3] + c[8] * q[4];
+    if (linear) return c[9] * p0 + c[10] * p1 + c[11] * p2;
+    const R c13 = R(13) / R(12);
+    R a = q[0] - R(2) * q[1] + q[2], b = q[0] - R(4) * q[1] + R(3) * q[2];
+    R b0 = c13 * a * a + R(0.25) * b * b;
+    a = q[1] - R(2) * q[2] + q[3]; b = q[1] - q[3];
+    R b1 = c13 * a * a + R(0.25) * b * b;
+    a = q[2] - R(2) * q[3] + q[4]; b = R(3) * q[2] - R(4) * q[3] + q[4];
+    R b2 = c13 * a * a + R(0.25) * b * b;
+    R tau = fabs(b0 - b2);
+    R r0 = WenoRatio<R>::clamp(tau / (b0 + eps));
+    R r1 = WenoRatio<R>::clamp(tau / (b1 + eps));
+    R r2 = WenoRatio<R>::clamp(tau / (b2 + eps));
+    R a0 = c[9] * (R(1) + r0 * r0);
+    R a1 = c[10] * (R(1) + r1 * r1);
+    R a2 = c[11] * (R(1) + r2 * r2);
+    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
+// third order on q[1..3]
+template <typename R>
+__device__ __forceinline__ R weno3_row(const R* q, const R* c, R eps, int linear) {
+    R p0 = c[12] * q[1] + c[13] * q[2];
+    R p1 = c[14] * q[2] + c[15] * q[3];
+    if (linear) return c[16] * p0 + c[17] * p1;
+    R b0 = (q[2] - q[1]) * (q[2] - q[1]);
+    R b1 = (q[3] - q[2]) * (q[3] - q[2]);
+    R tau = fabs(b0 - b1);
+    R r0 = WenoRatio<R>::clamp(tau / (b0 + eps));
+    R r1 = WenoRatio<R>::clamp(tau / (b1 + eps));
+    R a0 = c[16] * (R(1) + r0 * r0);
+    R a1 = c[17] * (R(1) + r1 * r1);
+    return (a0 * p0 + a1 * p1) / (a0 + a1);
+}
+
+template <typename R>
+__device__ __forceinline__ R weno_adaptive_row(const R* q, unsigned in, const R* c, R eps, int linear) {
+    if (in == 31u) return weno5_row(q, c, eps, linear);
+    if ((in & 14u) == 14u) return weno3_row(q, c, eps, linear);
     return q[2];
 }
 
@@ -235,6 +325,74 @@ template <> struct WenoPair<float> {
             if (a3) oa = o.x;
             if (b3) ob = o.y;
         }
+    }
+};
+
+// Stretched-level pairs: stencil a with table row ca, stencil b with row cb (the two
+// rows may differ, e.g. u- and v-faces with opposite vertical velocities).
+template <typename R> struct WenoPairRow {
+    static __device__ __forceinline__ void run(const R* qa, const R* qb, unsigned ina,
+                                               unsigned inb, const R* ca, const R* cb, R eps,
+                                               int linear, R& oa, R& ob) {
+        oa = weno_adaptive_row(qa, ina, ca, eps, linear);
+        ob = weno_adaptive_row(qb, inb, cb, eps, linear);
+    }
+};
+
+__device__ __forceinline__ float2 ldrow2(const float* ca, const float* cb, int n) {
+    return make_float2(__ldg(ca + n), __ldg(cb + n));
+}
+
+// packed fifth-order WENO-Z with per-lane rows (same definition as weno5_row); the
+// indicators are formed as in weno5z_x2 (4 beta_r, no division by 4)
+__device__ __forceinline__ float2 weno5z_x2_row(float2 q0, float2 q1, float2 q2, float2 q3,
+                                                float2 q4, const float* ca, const float* cb,
+                                                float eps) {
+    const float2 P0 = f2fma(q0, ldrow2(ca, cb, 0), f2fma(q1, ldrow2(ca, cb, 1), f2mul(q2, ldrow2(ca, cb, 2))));
+    const float2 P1 = f2fma(q1, ldrow2(ca, cb, 3), f2fma(q2, ldrow2(ca, cb, 4), f2mul(q3, ldrow2(ca, cb, 5))));
+    const float2 P2 = f2fma(q2, ldrow2(ca, cb, 6), f2fma(q3, ldrow2(ca, cb, 7), f2mul(q4, ldrow2(ca, cb, 8))));
+    const float2 A0 = f2add(f2fma(q1, f2(-2.f), q0), q2);
+    const float2 A1 = f2add(f2fma(q2, f2(-2.f), q1), q3);
+    const float2 A2 = f2add(f2fma(q3, f2(-2.f), q2), q4);
+    const float2 B0 = f2fma(f2fma(q1, f2(-1.f), q2), f2(2.f), A0);
+    const float2 B1 = f2fma(q3, f2(-1.f), q1);
+    const float2 B2 = f2fma(f2fma(q3, f2(-1.f), q2), f2(2.f), A2);
+    const float2 c = f2(13.f / 3.f);
+    const float2 b0 = f2fma(f2mul(A0, A0), c, f2mul(B0, B0));
+    const float2 b1 = f2fma(f2mul(A1, A1), c, f2mul(B1, B1));
+    const float2 b2 = f2fma(f2mul(A2, A2), c, f2mul(B2, B2));
+    const float2 d = f2fma(b2, f2(-1.f), b0);
+    const float2 e4 = f2(4.f * eps);
+    auto alpha = [&](float2 b, float2 dr) {
+        const float2 be = f2add(b, e4);
+        const float2 r = f2mul(d, make_float2(rcp_approx(be.x), rcp_approx(be.y)));
+        float2 r2 = f2mul(r, r);
+        r2.x = fminf(r2.x, 1e36f);
+        r2.y = fminf(r2.y, 1e36f);
+        return f2fma(r2, dr, dr);
+    };
+    const float2 a0 = alpha(b0, ldrow2(ca, cb, 9)), a1 = alpha(b1, ldrow2(ca, cb, 10)),
+                 a2 = alpha(b2, ldrow2(ca, cb, 11));
+    const float2 num = f2fma(a0, P0, f2fma(a1, P1, f2mul(a2, P2)));
+    const float2 den = f2add(f2add(a0, a1), a2);
+    return f2mul(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+}
+
+template <> struct WenoPairRow<float> {
+    static __device__ __forceinline__ void run(const float* qa, const float* qb, unsigned ina,
+                                               unsigned inb, const float* ca, const float* cb,
+                                               float eps, int linear, float& oa, float& ob) {
+        const bool a5 = ina == 31u, b5 = inb == 31u;
+        if (linear || !(a5 || b5)) {   // ideal weights, or neither stencil complete
+            oa = weno_adaptive_row(qa, ina, ca, eps, linear);
+            ob = weno_adaptive_row(qb, inb, cb, eps, linear);
+            return;
+        }
+        const float2 o = weno5z_x2_row(make_float2(qa[0], qb[0]), make_float2(qa[1], qb[1]),
+                                       make_float2(qa[2], qb[2]), make_float2(qa[3], qb[3]),
+                                       make_float2(qa[4], qb[4]), ca, cb, eps);
+        oa = a5 ? o.x : weno_adaptive_row(qa, ina, ca, eps, linear);
+        ob = b5 ? o.y : weno_adaptive_row(qb, inb, cb, eps, linear);
     }
 };
 

@@ -185,6 +185,9 @@ constexpr int TTY = TY + 1, NTT = TX * TTY;
 // tiles fit 64 and 56 registers (four blocks per SM); the FP64 tiles need far more
 template <typename R> struct Occ4 { static constexpr int value = 4; };
 template <> struct Occ4<double> { static constexpr int value = 1; };
+// the variants with the optional vertical schemes keep more registers: 3 blocks per SM
+template <typename R, bool X> struct OccX { static constexpr int value = X ? 3 : Occ4<R>::value; };
+template <bool X> struct OccX<double, X> { static constexpr int value = 1; };
 
 // padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
 // the domain stage a few columns beyond it, whose values only feed threads that are
@@ -251,17 +254,18 @@ __device__ __forceinline__ void bar_wait(unsigned long long* b, unsigned parity)
 // 33 used), v faces 9 x 32
 template <typename R>
 struct __align__(128) TracerSmem {
+    using R2 = typename Vec2<R>::type;
     R T[3][TY + 8][TX + 8], S[3][TY + 8][TX + 8];     // anomalies of levels k, k+1, k+2
     R us[3][TY][TX + 4], vs[3][TY + 1][TX];           // face velocities of those levels
     R own[3][4][TY][TX];                              // own columns: w(k+1), kap(k+1), G_T(k), G_S(k)
+    // x- and y-face transports and (T, S) fluxes of levels k (even) and k+1 (odd)
+    R2 fxTS[2][TY][TX + 1], fyTS[2][TY + 1][TX];
+    R fxU[2][TY][TX + 1], fyV[2][TY + 1][TX];
     unsigned long long bar[3];                        // buffer b's copies have landed
     short kb[TY + 6][TX + 6];                         // lowest wet level of those columns
     short kbu[TY][TX + 1], kbv[TY + 1][TX];           // lowest wet level of the faces
     // lowest level from which all six cells an x- (y-) face's stencils can touch are wet
     short kfx[TY][TX + 1], kfy[TY + 1][TX];
-    // x- and y-face transport and fluxes of levels k (even) and k+1 (odd)
-    R fxU[2][TY][TX + 1], fxT[2][TY][TX + 1], fxS[2][TY][TX + 1];
-    R fyV[2][TY + 1][TX], fyT[2][TY + 1][TX], fyS[2][TY + 1][TX];
     int kmin;
 };
 
@@ -274,7 +278,8 @@ struct __align__(128) TracerSmem {
 // (WENO is translation-equivariant, so adding U Tref(k) gives the flux of T itself);
 // vertical ones reconstruct full values, since the reference varies along the column.
 // tile (bx, by): columns [bx TX, bx TX + TX) x [by TY, by TY + TY)
-template <typename R, bool STEP>
+// SV: the vertical reconstructions take the stretched-level coefficients of p.vw.
+template <typename R, bool STEP, bool SV>
 __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, const int bx,
                                             const int by,
                                             const R* __restrict__ u, const R* __restrict__ v,
@@ -283,6 +288,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                                             R* __restrict__ GTp, R* __restrict__ GSp,
                                             R* __restrict__ Tn, R* __restrict__ Sn,
                                             const R* __restrict__ dGT, const R* __restrict__ dGS) {
+    using R2 = typename Vec2<R>::type;
     __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
@@ -376,6 +382,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     }
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
     R kcarry = R(0);   // diffusivity on the top face of the previous level
+    int cb = 0;                 // staging slot of level k: (k - kstart) mod 3
+    unsigned phase = 0;         // bit s: parity of slot s's next completion
 
     // One block barrier per level: the faces of level k go to face buffer k & 1, so a
     // warp that has finished level k-1 computes level k's faces while others still read
@@ -383,10 +391,90 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     // buffer of level k-1 (read by every thread before it), which takes level k+2.
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        const int lv = k - kstart, cb = lv % 3, fb = lv & 1;
-        bar_wait(&sm.bar[cb], (unsigned)(lv / 3) & 1u);
-        // own-cell operands of level k, from the staged buffers; the diffusivity on the
-        // bottom face is the previous level's top one (read before this level rewrites it)
+        const int fb = (k - kstart) & 1;
+        bar_wait(&sm.bar[cb], (phase >> cb) & 1u);
+        phase ^= 1u << cb;
+        const R dzk = __ldg(p.lvt + (size_t)k * OC_LVROW);   // dz of the level (row k, first value)
+        // ---- x- and y-face fluxes, each face once, by fixed roles: thread (tx, ty < TY)
+        // the west and south faces of its own column; the extra warp the north faces of the last row and (lanes 0..TY-1) the east faces
+        // of the last column.  Two WENO pairs per thread; the stencil offsets are known at
+        // compile time.
+        auto xface = [&](const int a, const int b) {
+            R fU = R(0), fT = R(0), fS = R(0);
+            const bool full = k >= sm.kfx[a][b];   // every stencil point wet
+            if (full || k >= sm.kbu[a][b]) {
+                const R ut = sm.us[cb][a][b];
+                const bool pos = ut >= R(0);
+                // upwind to downwind: columns b .. b+4 (ut >= 0) or b+5 .. b+1
+                const R* tT = &sm.T[cb][a + 3][pos ? b + 1 : b + 6];
+                const R* tS = &sm.S[cb][a + 3][pos ? b + 1 : b + 6];
+                const int st = pos ? 1 : -1;
+                R qT[5], qS[5];
+                unsigned in = full ? 31u : 0u;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    qT[n] = tT[n * st];
+                    qS[n] = tS[n * st];
+                    if (!full) {
+                        const int col = pos ? b + n : b + 5 - n;
+                        in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
+                    }
+                }
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                fU = ut * p.dy * dzk;
+                fT = fU * rT;
+                fS = fU * rS;
+            }
+            sm.fxU[fb][a][b] = fU;
+            sm.fxTS[fb][a][b] = make_vec2(fT, fS);
+        };
+        auto yface = [&](const int a, const int b) {
+            R fV = R(0), fT = R(0), fS = R(0);
+            const bool full = k >= sm.kfy[a][b];
+            if (full || k >= sm.kbv[a][b]) {
+                const R vt = sm.vs[cb][a][b];
+                const bool pos = vt >= R(0);
+                // rows a .. a+4 (vt >= 0) or a+5 .. a+1
+                const R* tT = &sm.T[cb][pos ? a : a + 5][b + 4];
+                const R* tS = &sm.S[cb][pos ? a : a + 5][b + 4];
+                const int st = pos ? (TX + 8) : -(TX + 8);
+                R qT[5], qS[5];
+                unsigned in = full ? 31u : 0u;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    qT[n] = tT[n * st];
+                    qS[n] = tS[n * st];
+                    if (!full) {
+                        const int row = pos ? a + n : a + 5 - n;
+                        in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
+                    }
+                }
+                R rT, rS;
+                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                fV = vt * p.dxv[j0 + a + OC_H] * dzk;
+                fT = fV * rT;
+                fS = fV * rS;
+            }
+            sm.fyV[fb][a][b] = fV;
+            sm.fyTS[fb][a][b] = make_vec2(fT, fS);
+        };
+        if (ty < TY) {
+            xface(ty, tx);
+            yface(ty, tx);
+        } else {
+            yface(TY, tx);
+            if (tx < TY) xface(tx, TX);
+        }
+        // this thread's reads of level k-1's staging buffer (faces and own cell, before
+        // this point) are ordered before the tensor copy that overwrites it
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        const int c2s = cb == 0 ? 2 : cb - 1;   // slot of level k+2: (k - kstart + 2) mod 3
+        if (k + 2 < nz) stage(k + 2, c2s);
+        // own-cell operands of level k, from its staging slot (rewritten only by the copy of
+        // level k+3, issued after the next level's barrier); the diffusivity on the bottom
+        // face is the previous level's top one
         const bool live = mine && k >= kb;
         const long ck = Pk + c2;
         R wt = R(0), k0 = kcarry, k1 = R(0), gT0 = R(0), gS0 = R(0), T0 = R(0), S0 = R(0);
@@ -403,73 +491,11 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             }
         }
         kcarry = k1;
-        const R dzk = p.dz[k];
-        // ---- x- and y-face fluxes, each face once, by fixed roles: thread (tx, ty < TY)
-        // the west and south faces of its own column; the extra warp the north faces of
-        // the last row and (lanes 0..TY-1) the east faces of the last column.  Two WENO
-        // pairs per thread; the stencil offsets are known at compile time.
-        auto xface = [&](const int a, const int b) {
-            R fU = R(0), fT = R(0), fS = R(0);
-            const bool full = k >= sm.kfx[a][b];   // every stencil point wet
-            if (full || k >= sm.kbu[a][b]) {
-                const R ut = sm.us[cb][a][b];
-                R qT[5], qS[5];
-                unsigned in = full ? 31u : 0u;
-#pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int col = ut >= R(0) ? b + n : b + 5 - n;
-                    qT[n] = sm.T[cb][a + 3][col + 1];
-                    qS[n] = sm.S[cb][a + 3][col + 1];
-                    if (!full) in |= (k >= sm.kb[a + 3][col] ? 1u : 0u) << n;
-                }
-                R rT, rS;
-                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                fU = ut * p.dy * dzk;
-                fT = fU * rT;
-                fS = fU * rS;
-            }
-            sm.fxU[fb][a][b] = fU;
-            sm.fxT[fb][a][b] = fT;
-            sm.fxS[fb][a][b] = fS;
-        };
-        auto yface = [&](const int a, const int b) {
-            R fV = R(0), fT = R(0), fS = R(0);
-            const bool full = k >= sm.kfy[a][b];
-            if (full || k >= sm.kbv[a][b]) {
-                const R vt = sm.vs[cb][a][b];
-                R qT[5], qS[5];
-                unsigned in = full ? 31u : 0u;
-#pragma unroll
-                for (int n = 0; n < 5; ++n) {
-                    const int row = vt >= R(0) ? a + n : a + 5 - n;
-                    qT[n] = sm.T[cb][row][b + 4];
-                    qS[n] = sm.S[cb][row][b + 4];
-                    if (!full) in |= (k >= sm.kb[row][b + 3] ? 1u : 0u) << n;
-                }
-                R rT, rS;
-                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                fV = vt * p.dxv[j0 + a + OC_H] * dzk;
-                fT = fV * rT;
-                fS = fV * rS;
-            }
-            sm.fyV[fb][a][b] = fV;
-            sm.fyT[fb][a][b] = fT;
-            sm.fyS[fb][a][b] = fS;
-        };
-        if (ty < TY) {
-            xface(ty, tx);
-            yface(ty, tx);
-        } else {
-            yface(TY, tx);
-            if (tx < TY) xface(tx, TX);
-        }
-        // this thread's reads of level k-1's staging buffer (faces and own cell, before
-        // this point) are ordered before the tensor copy that overwrites it
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (k + 2 < nz) stage(k + 2, (lv + 2) % 3);
         // ---- own cell
         if (live) {
+            // level constants: 1/dz, the implicit solve's off-diagonal factors dt/(dz dzf)
+            // below and above, Tref, Sref and the diffusion of the reference profiles
+            const LevelRow<R> L = load_level_row(p.lvt, k);
             R ftT = R(0), ftS = R(0);
             if (k + 1 < nz) {   // flux through the top face (bottom face of cell k+1)
                 const bool pos = wt >= R(0);
@@ -488,16 +514,25 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                     if (!full) in |= (kk >= kb && kk < nz ? 1u : 0u) << n;
                 }
                 R rT, rS;
-                WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                if (SV) {
+                    const R* row = p.vw + ((k + 1) * 2 + (pos ? 0 : 1)) * OC_VWROW;
+                    WenoPairRow<R>::run(qT, qS, in, in, row, row, p.eps, p.linear, rT, rS);
+                } else {
+                    WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
+                }
                 ftT = wt * rT;
                 ftS = wt * rS;
             }
-            const R rdz = p.rdz[k];
-            const R divU = sm.fxU[fb][ty][tx + 1] - sm.fxU[fb][ty][tx] + sm.fyV[fb][ty + 1][tx] - sm.fyV[fb][ty][tx];
-            const R hT = sm.fxT[fb][ty][tx + 1] - sm.fxT[fb][ty][tx] + sm.fyT[fb][ty + 1][tx] - sm.fyT[fb][ty][tx];
-            const R hS = sm.fxS[fb][ty][tx + 1] - sm.fxS[fb][ty][tx] + sm.fyS[fb][ty + 1][tx] - sm.fyS[fb][ty][tx];
-            R GT = -((p.Tref[k] * divU + hT) * rac + (ftT - fzT)) * rdz;
-            R GS = -((p.Sref[k] * divU + hS) * rac + (ftS - fzS)) * rdz;
+            const R rdz = L.rdz;
+            const R eU = sm.fxU[fb][ty][tx + 1], nV = sm.fyV[fb][ty + 1][tx];
+            const R wU = sm.fxU[fb][ty][tx], sV = sm.fyV[fb][ty][tx];
+            const R2 eTS = sm.fxTS[fb][ty][tx + 1], nTS = sm.fyTS[fb][ty + 1][tx];
+            const R2 wTS = sm.fxTS[fb][ty][tx], sTS = sm.fyTS[fb][ty][tx];
+            const R divU = eU - wU + nV - sV;
+            const R hT = eTS.x - wTS.x + nTS.x - sTS.x;
+            const R hS = eTS.y - wTS.y + nTS.y - sTS.y;
+            R GT = -((L.Tref * divU + hT) * rac + (ftT - fzT)) * rdz;
+            R GS = -((L.Sref * divU + hS) * rac + (ftS - fzS)) * rdz;
             if (dGT) {   // learned-closure corrections, part of G^n
                 GT += dGT[ck];
                 GS += dGS[ck];
@@ -512,14 +547,13 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                 const R gS = p.ca * GS - p.cb * gS0;
                 GTp[ck] = GT;
                 GSp[ck] = GS;
-                const R lo = k > kb ? p.dt * k0 * rdz * p.rdzf[k] : R(0);
-                const R hi = k < nz - 1 ? p.dt * k1 * rdz * p.rdzf[k + 1] : R(0);
+                // lo, hi: dt kap / (dz dzf) on the bottom and top faces (zero at the ends)
+                const R lo = k > kb ? k0 * L.alo : R(0);
+                const R hi = k1 * L.ahi;   // kap on the surface face is zero
                 // the diffusion of the reference profile moves to the right-hand side:
                 // (I - dt D) T'^{n+1} = T'* + dt D Tref
-                const R Ts = T0 + p.dt * gT
-                           + (k < nz - 1 ? hi * p.dTref[k + 1] : R(0)) - (k > kb ? lo * p.dTref[k] : R(0));
-                const R Ss = S0 + p.dt * gS
-                           + (k < nz - 1 ? hi * p.dSref[k + 1] : R(0)) - (k > kb ? lo * p.dSref[k] : R(0));
+                const R Ts = T0 + p.dt * gT + k1 * L.hdT - (k > kb ? k0 * L.ldT : R(0));
+                const R Ss = S0 + p.dt * gS + k1 * L.hdS - (k > kb ? k0 * L.ldS : R(0));
                 const R inv = rcp_pivot((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
                 cprev = -hi * inv;
                 dTprev = (Ts + lo * dTprev) * inv;
@@ -529,6 +563,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                 Sn[ck] = dSprev;
             }
         }
+        cb = cb == 2 ? 0 : cb + 1;
         // ---- slide the vertical window up one level
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
@@ -574,8 +609,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     }
 }
 
-template <typename R, bool STEP>
-__global__ void __launch_bounds__(NTT, Occ4<R>::value) k_tracer(KP<R> p,
+template <typename R, bool STEP, bool SV>
+__global__ void __launch_bounds__(NTT, (OccX<R, SV>::value)) k_tracer(KP<R> p,
                                                const __grid_constant__ TileMaps tm,
                                                const R* __restrict__ u,
                                                const R* __restrict__ v, const R* __restrict__ w,
@@ -584,8 +619,8 @@ __global__ void __launch_bounds__(NTT, Occ4<R>::value) k_tracer(KP<R> p,
                                                R* __restrict__ GSp, R* __restrict__ Tn,
                                                R* __restrict__ Sn, const R* __restrict__ dGT,
                                                const R* __restrict__ dGS) {
-    tracer_tile<R, STEP>(p, tm, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn, Sn,
-                         dGT, dGS);
+    tracer_tile<R, STEP, SV>(p, tm, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn,
+                             Sn, dGT, dGS);
 }
 
 // ------------------------------------------------------------------ momentum
@@ -614,8 +649,10 @@ struct __align__(128) MomentumSmem {
 // STEP = false: G^n of u, v into un, vn.  STEP = true: quasi-AB2 predictor, G^{n-1} <-
 // G^n, the column sums U^n = sum dz u^n and G_U = sum dz G^ of the barotropic mode, the
 // backward-Euler vertical viscosity (Thomas: c' in cu/cv scratch, d' in un/vn) and the
-// sum of the solved column Su = sum dz u**.
-template <typename R, bool STEP>
+// sum of the solved column Su = sum dz u**.  VA: the vertical advection in the WENO flux
+// form (own-column windows of u and v over levels k-2 .. k+3 in registers, the bottom
+// face's flux carried up from the level below), else centred.
+template <typename R, bool STEP, bool VA>
 __device__ __forceinline__ void momentum_tile(
     const KP<R>& p, const TileMaps& tm, const int bx, const int by, const R* __restrict__ u,
     const R* __restrict__ v, const R* __restrict__ w, const R* __restrict__ pr,
@@ -687,6 +724,23 @@ __device__ __forceinline__ void momentum_tile(
 
     const int jr = (mine ? j : 0) + OC_H;
     const R rdxc = p.rdxc[jr], fu = p.fu[jr], fv = p.fv[jr];
+    // the corners and kinetic-energy centres this thread computes on every level: fixed
+    // for the whole march (two slots each; the second only for the first threads), so
+    // their indices, shared-memory offsets and corner masks are formed once
+    constexpr int NCR = (TY + 5) * (TX + 5);
+    static_assert(NCR <= 2 * NT && TC <= 2 * NT, "two corner and two centre slots per thread");
+    // corner slot: lowest active level << 16 | row << 8 | column (-1: none); centre slot:
+    // row << 8 | column (-1: none)
+    int zs[2], ko[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = tid + r * NT;
+        const bool okz = q < NCR, okk = q < TC;
+        const int a = okz ? q / (TX + 5) : 0, b = okz ? q % (TX + 5) : 0;
+        zs[r] = okz ? ((int)sm.kbz[a][b] << 16) | (a << 8) | b : -1;
+        const int ca = okk ? q / (TX + 1) : 0, cb = okk ? q % (TX + 1) : 0;
+        ko[r] = okk ? (ca << 8) | cb : -1;
+    }
     R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
     // own faces: u, v at k-1 (lower); levels k and k+1 come from the tiles
@@ -698,6 +752,18 @@ __device__ __forceinline__ void momentum_tile(
         ulo = u[(kstart - 1) * P + c2];
         vlo = v[(kstart - 1) * P + c2];
     }
+    // WENO vertical advection: own u- and v-face values at levels k-2 .. k+3 (0 outside
+    // the face's wet levels), and the flux and w of the bottom face
+    R wu[6], wv[6];
+    R fbu = R(0), fbv = R(0), wbu = R(0), wbv = R(0);
+    if (VA) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int kk = kstart - 2 + q;
+            wu[q] = mine && kk >= ku && kk < nz ? u[kk * P + c2] : R(0);
+            wv[q] = mine && kk >= kv && kk < nz ? v[kk * P + c2] : R(0);
+        }
+    }
     // One block barrier per level: corners and kinetic energy of level k go to buffer
     // k & 1, so a warp that has finished level k-1 computes them while others still read
     // level k-1's; the barrier after them publishes them and frees the slot of level k-1
@@ -707,20 +773,26 @@ __device__ __forceinline__ void momentum_tile(
         const int lv = k - kstart, sc = lv % 3, sn = (lv + 1) % 3, fb = lv & 1;
         bar_wait(&sm.bar[sc], (unsigned)(lv / 3) & 1u);
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
-        for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
-            const int a = q / (TX + 5), b = q % (TX + 5);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (zs[r] < 0) continue;
+            const int a = (zs[r] >> 8) & 255, b = zs[r] & 255;
+            const R* us = &sm.u[sc][a][b];
+            const R* vs = &sm.v[sc][a][b];
             R zz = R(0);
-            if (k >= sm.kbz[a][b]) {
+            if (k >= (zs[r] >> 16)) {
                 // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
-                // v(i-1, jc) = v[a][b]
-                const R circ = p.dy * (sm.v[sc][a][(b + 1) + 1] - sm.v[sc][a][(b) + 1])
-                             - (sm.zdxN[a] * sm.u[sc][a + 1][(b) + 2] - sm.zdxS[a] * sm.u[sc][a][(b) + 2]);
+                // v(i-1, jc) = v[a][b]  (tile columns offset by 2 for u, 1 for v)
+                const R circ = p.dy * (vs[2] - vs[1])
+                             - (sm.zdxN[a] * us[(TX + 8) + 2] - sm.zdxS[a] * us[2]);
                 zz = circ * sm.zrA[a];
             }
             sm.z[fb][a][b] = zz;
         }
-        for (int q = tid; q < TC; q += NT) {
-            const int a = q / (TX + 1), b = q % (TX + 1);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (ko[r] < 0) continue;
+            const int a = ko[r] >> 8, b = ko[r] & 255;
             // centre (i0-1+b, j0-1+a): u at cols b+1, b+2 of row a+2; v at col b+2, rows a+1, a+2
             const R ua = sm.u[sc][a + 2][(b + 1) + 2], ub = sm.u[sc][a + 2][(b + 2) + 2];
             const R va = sm.v[sc][a + 1][(b + 2) + 1], vb = sm.v[sc][a + 2][(b + 2) + 1];
@@ -759,16 +831,55 @@ __device__ __forceinline__ void momentum_tile(
             }
             R ztu, ztv;
             WenoPair<R>::run(qa, qb, ina, inb, p.eps, p.linear, ztu, ztv);
+            // WENO flux form of the vertical advection:
+            // [w_top u~_top - w_bot u~_bot - u_k (w_top - w_bot)] / dz_k, u~ upwind by w
+            R vau = R(0), vav = R(0);
+            if (VA) {
+                R wtu = R(0), wtv = R(0), ftu = R(0), ftv = R(0);
+                if (k + 1 < nz) {
+                    wtu = R(0.5) * (sm.w[sn][ty + 1][(tx) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]);
+                    wtv = R(0.5) * (sm.w[sn][ty][(tx + 1) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]);
+                    const bool pu = wtu >= R(0), pv = wtv >= R(0);
+                    R ra[5], rb[5];
+                    unsigned ia = 0, ib = 0;
+#pragma unroll
+                    for (int n = 0; n < 5; ++n) {
+                        // window index n (level k-2+n) upward, 5-n (level k+3-n) downward
+                        ra[n] = pu ? wu[n] : wu[5 - n];
+                        rb[n] = pv ? wv[n] : wv[5 - n];
+                        const int la = pu ? k - 2 + n : k + 3 - n, lb = pv ? k - 2 + n : k + 3 - n;
+                        ia |= (la >= ku && la < nz ? 1u : 0u) << n;
+                        ib |= (lb >= kv && lb < nz ? 1u : 0u) << n;
+                    }
+                    R xu, xv;
+                    if (p.vweno)
+                        WenoPairRow<R>::run(ra, rb, ia, ib, p.vw + ((k + 1) * 2 + (pu ? 0 : 1)) * OC_VWROW,
+                                            p.vw + ((k + 1) * 2 + (pv ? 0 : 1)) * OC_VWROW, p.eps,
+                                            p.linear, xu, xv);
+                    else
+                        WenoPair<R>::run(ra, rb, ia, ib, p.eps, p.linear, xu, xv);
+                    ftu = wtu * xu;
+                    ftv = wtv * xv;
+                }
+                const bool bu = k > ku, bv = k > kv;   // faces below the lowest wet level carry nothing
+                vau = (ftu - (bu ? fbu : R(0)) - u0 * (wtu - (bu ? wbu : R(0)))) * rdz;
+                vav = (ftv - (bv ? fbv : R(0)) - v0 * (wtv - (bv ? wbv : R(0)))) * rdz;
+                fbu = ftu; wbu = wtu; fbv = ftv; wbv = wtv;
+            }
             if (du_) {   // ---------------- u at the west face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty + 1][tx]) * rdxc;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty + 1][(tx) + 3]) * rdxc;
-                R up = R(0);
-                if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[sn][ty + 1][(tx) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
-                const R dn = k - 1 >= ku ? upu : R(0);   // the level below's top-face term
-                upu = up;
+                R vadv = vau;
+                if (!VA) {
+                    R up = R(0);
+                    if (k + 1 < nz)
+                        up = R(0.5) * (sm.w[sn][ty + 1][(tx) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (uhi - u0) * p.rdzf[k + 1];
+                    const R dn = k - 1 >= ku ? upu : R(0);   // the level below's top-face term
+                    upu = up;
+                    vadv = R(0.5) * (up + dn);
+                }
                 const R wind = k == nz - 1 ? taux_s[c2] : R(0);
-                const R G = (ztu + fu) * vh - dK - R(0.5) * (up + dn) - dP + wind;
+                const R G = (ztu + fu) * vh - dK - vadv - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
                     un[ck] = G;
@@ -792,13 +903,17 @@ __device__ __forceinline__ void momentum_tile(
             if (dv_) {   // ---------------- v at the south face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty][tx + 1]) * p.rdy;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty][(tx + 1) + 3]) * p.rdy;
-                R up = R(0);
-                if (k + 1 < nz)
-                    up = R(0.5) * (sm.w[sn][ty][(tx + 1) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
-                const R dn = k - 1 >= kv ? upv : R(0);
-                upv = up;
+                R vadv = vav;
+                if (!VA) {
+                    R up = R(0);
+                    if (k + 1 < nz)
+                        up = R(0.5) * (sm.w[sn][ty][(tx + 1) + 3] + sm.w[sn][ty + 1][(tx + 1) + 3]) * (vhi - v0) * p.rdzf[k + 1];
+                    const R dn = k - 1 >= kv ? upv : R(0);
+                    upv = up;
+                    vadv = R(0.5) * (up + dn);
+                }
                 const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
-                const R G = -(ztv + fv) * uh - dK - R(0.5) * (up + dn) - dP + wind;
+                const R G = -(ztv + fv) * uh - dK - vadv - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
                     vn[ck] = G;
@@ -821,6 +936,16 @@ __device__ __forceinline__ void momentum_tile(
             }
             ulo = u0;
             vlo = v0;
+        }
+        if (VA) {   // slide the windows up one level
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                wu[q] = wu[q + 1];
+                wv[q] = wv[q + 1];
+            }
+            const int kk = k + 4;
+            wu[5] = mine && kk >= ku && kk < nz ? u[kk * P + c2] : R(0);
+            wv[5] = mine && kk >= kv && kk < nz ? v[kk * P + c2] : R(0);
         }
     }
     __syncthreads();   // every copy waited for: the barriers can be retired
@@ -873,8 +998,8 @@ __device__ __forceinline__ void momentum_tile(
     }
 }
 
-template <typename R, bool STEP>
-__global__ void __launch_bounds__(NT, Occ4<R>::value) k_momentum(
+template <typename R, bool STEP, bool VA>
+__global__ void __launch_bounds__(NT, (OccX<R, VA>::value)) k_momentum(
     KP<R> p, const __grid_constant__ TileMaps tm, const R* __restrict__ u,
     const R* __restrict__ v, const R* __restrict__ w,
     const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
@@ -882,8 +1007,8 @@ __global__ void __launch_bounds__(NT, Occ4<R>::value) k_momentum(
     R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
     R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
     R* __restrict__ Sv) {
-    momentum_tile<R, STEP>(p, tm, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s, Gup,
-                           Gvp, un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
+    momentum_tile<R, STEP, VA>(p, tm, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s,
+                               Gup, Gvp, un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
 }
 
 // ------------------------------------------------------------------ barotropic mode
@@ -1193,25 +1318,34 @@ void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
 template <typename R>
 void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TTY);
-    if (step)
-        k_tracer<R, true><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
-                                                 b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
-    else
-        k_tracer<R, false><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
-                                                  b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
+    auto go = [&](auto kern) {
+        kern<<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS, b.Tn,
+                                    b.Sn, b.dGT, b.dGS);
+    };
+    if (p.vweno) {
+        if (step) go(k_tracer<R, true, true>);
+        else go(k_tracer<R, false, true>);
+    } else {
+        if (step) go(k_tracer<R, true, false>);
+        else go(k_tracer<R, false, false>);
+    }
 }
 
 template <typename R>
 void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
-    if (step)
-        k_momentum<R, true><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
-                                                   b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
-                                                   b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
-    else
-        k_momentum<R, false><<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
-                                                    b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap,
-                                                    b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
+    auto go = [&](auto kern) {
+        kern<<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
+                                    b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su,
+                                    b.Sv);
+    };
+    if (p.mvadv) {
+        if (step) go(k_momentum<R, true, true>);
+        else go(k_momentum<R, false, true>);
+    } else {
+        if (step) go(k_momentum<R, true, false>);
+        else go(k_momentum<R, false, false>);
+    }
 }
 
 template <typename R>
@@ -1580,8 +1714,8 @@ __global__ void __launch_bounds__(NTT, Occ4<R>::value) k_ens_tracer(
         const EnsItem e = work[it];
         const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        tracer_tile<R, true>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS,
-                             b.Tn, b.Sn, b.dGT, b.dGS);
+        tracer_tile<R, true, false>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
+                                    b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
     }
 }
 
@@ -1594,8 +1728,9 @@ __global__ void __launch_bounds__(NT, Occ4<R>::value) k_ens_momentum(
         const EnsItem e = work[it];
         const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        momentum_tile<R, true>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
-                               b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv);
+        momentum_tile<R, true, false>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
+                                      b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn,
+                                      b.GU, b.GV, b.Su, b.Sv);
     }
 }
 

@@ -50,7 +50,8 @@ class OceanParams(ctypes.Structure):
                 ("kappa_conv", c_double), ("weno_eps", c_double), ("weno_linear", c_int),
                 ("min_depth", c_double), ("precision", c_int), ("closure", c_int),
                 ("check_every", c_int), ("taux", POINTER(c_double)), ("tauy", POINTER(c_double)),
-                ("closure_hidden", c_int), ("baro_filter", c_int)]
+                ("closure_hidden", c_int), ("baro_filter", c_int), ("vertical_weno", c_int),
+                ("momentum_vadv", c_int)]
 
 
 class OceanBatch(ctypes.Structure):
@@ -206,7 +207,8 @@ def make_params(p: Dict[str, float], precision: int, taux=None, tauy=None, closu
         p["nu_b"], p["kappa_b"], p["kappa_conv"], p["weno_eps"], int(p["weno_linear"]),
         p["min_depth"], precision, closure, check_every,
         _dp(tx) if tx is not None else None, _dp(ty) if ty is not None else None,
-        closure_hidden, int(p.get("baro_filter", 0)))
+        closure_hidden, int(p.get("baro_filter", 0)), int(p.get("vertical_weno", 0)),
+        int(p.get("momentum_vadv", 0)))
     return prm, keep
 
 

@@ -104,6 +104,42 @@ def test_power_law_filter_matches_oracle(precision):
         assert max_rel(b.get("eta"), o.get("eta")) > 1e3 * FP64_TOL
 
 
+VERTICAL_SCHEMES = [dict(vertical_weno=1, momentum_vadv=0), dict(vertical_weno=0, momentum_vadv=1),
+                    dict(vertical_weno=1, momentum_vadv=1)]
+
+
+@pytest.mark.parametrize("scheme", VERTICAL_SCHEMES)
+def test_vertical_schemes_tendencies_fp64(scheme):
+    # stretched levels (5000 m in 12 levels, 40 m to 1270 m thick): the stretched-level
+    # vertical WENO coefficients and the WENO flux form of the vertical momentum advection
+    c = _moving_state(inputs.latlon_small_case()).with_params(**scheme)
+    g, o = run_pair(c, ocean.OCEAN_FP64, 0)
+    g.tendencies()
+    o.tendencies()
+    for f in ("Gu", "Gv", "GT", "GS"):
+        err = max_rel(g.get(f), o.get(f))
+        assert err < 1e-12, (scheme, f, err)
+    # and the scheme changed the tendencies against the defaults
+    d = oracle.OracleModel(c.with_params(vertical_weno=0, momentum_vadv=0))
+    d.tendencies()
+    field = "GT" if scheme["vertical_weno"] and not scheme["momentum_vadv"] else "Gu"
+    assert max_rel(d.get(field), o.get(field)) > 1e-6, scheme
+
+
+@pytest.mark.parametrize("scheme", VERTICAL_SCHEMES)
+@pytest.mark.parametrize("precision", [ocean.OCEAN_FP64, ocean.OCEAN_MIXED])
+def test_vertical_schemes_match_oracle(scheme, precision):
+    for c, steps in ((_moving_state(inputs.latlon_small_case()).with_params(**scheme), 40),
+                     (inputs.box_case().with_params(**scheme), 60)):
+        g, o = run_pair(c, precision, steps)
+        if precision == ocean.OCEAN_FP64:
+            errs = state_errors(g, o)
+            assert all(e <= FP64_TOL for e in errs.values()), (c.name, scheme, errs)
+        else:
+            errs = state_errors(g, o, rel_l2)
+            assert all(e <= MIXED_TOL for e in errs.values()), (c.name, scheme, errs)
+
+
 @pytest.mark.parametrize("shape,periodic", [((37, 23, 5), (False, False)),
                                             ((33, 9, 3), (True, True)),
                                             ((5, 6, 1), (False, False)),
