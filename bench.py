@@ -152,12 +152,7 @@ def oracle_sample(case):
     return case, f"the full {case.nx}x{case.ny}x{case.nz} workload"
 
 
-def run_oracle_sample(case, seconds: float, warmup: int = 1, steps_cap: int = 10_000):
-    """Time the CPU oracle on the bounded sample for about `seconds`; cell-updates/s."""
-    import oracle
-    sample, desc = oracle_sample(case)
-    m = oracle.OracleModel(sample)
-    m.step(warmup)   # the forward-Euler first step stays outside the timing
+def _time_oracle(m, seconds: float, steps_cap: int):
     t0 = time.perf_counter()
     n = 0
     while n < steps_cap:
@@ -165,12 +160,31 @@ def run_oracle_sample(case, seconds: float, warmup: int = 1, steps_cap: int = 10
         n += 1
         if time.perf_counter() - t0 >= seconds and n >= 2:
             break
-    dt = time.perf_counter() - t0
+    return n, time.perf_counter() - t0
+
+
+def run_oracle_sample(case, seconds: float, warmup: int = 1, steps_cap: int = 10_000,
+                      single_thread: bool = True):
+    """Time the CPU oracle on the bounded sample for about `seconds` on all host cores
+    (and, unless single_thread is False, for a third of that on one core); cell-updates/s."""
+    import oracle
+    sample, desc = oracle_sample(case)
+    m = oracle.OracleModel(sample)
+    m.step(warmup)   # the forward-Euler first step stays outside the timing
+    cores = oracle.get_threads()
+    n, dt = _time_oracle(m, seconds, steps_cap)
     cells = sample.nx * sample.ny * sample.nz
-    return {"value": cells * n / dt, "unit": "cell-updates/s", "kind": "oracle",
-            "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
-            "sample": f"{desc}; {n} steps in {dt:.1f} s (plain FP64 C, OpenMP over rows)",
-            "s_per_step": dt / n}
+    out = {"value": cells * n / dt, "unit": "cell-updates/s", "kind": "oracle",
+           "cores": cores,
+           "sample": f"{desc}; {n} steps in {dt:.1f} s (plain FP64 C, OpenMP over rows)",
+           "s_per_step": dt / n}
+    if single_thread:
+        oracle.set_threads(1)
+        n1, dt1 = _time_oracle(m, seconds / 3, steps_cap)
+        oracle.set_threads(cores)
+        out["single_thread"] = {"value": cells * n1 / dt1, "cores": 1,
+                                "sample": f"the same window, {n1} steps in {dt1:.1f} s on one core"}
+    return out
 
 
 

@@ -78,6 +78,8 @@ def lib():
             L.ora_filter_weights.restype = d
             L.ora_filter_weights.argtypes = [i, i, P(d)]
             L.ora_kbot.argtypes = [ctypes.c_void_p, i, i]
+            L.ora_set_threads.argtypes = [i]
+            L.ora_get_threads.restype = i
             _lib = L
     return _lib
 
@@ -133,6 +135,15 @@ def vertical_advection_column(z_faces, F, k0: int, w_faces, vertical_weno: int =
     lib().ora_vertical_advection_column(nz, _dp(zf), _dp(F), int(k0), _dp(wf), int(vertical_weno),
                                         int(momentum_vadv), eps, _dp(out))
     return out
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP row loops."""
+    lib().ora_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().ora_get_threads())
 
 
 def filter_weights(ns: int, kind: int = 0):
