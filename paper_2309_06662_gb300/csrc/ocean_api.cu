@@ -362,7 +362,7 @@ void upload_levels(ocean_t m) {
     }
     upload_real(m, lv, m->levm);
     upload_bytes(m, m->dlev, dl.data(), dl.size() * sizeof(double));
-    // rows of the tile kernels (LevelRow): dz, 1/dz, dt/(dz dzf) below and above, Tref,
+    // rows of the tile kernels (KP::lvt): dz, 1/dz, dt/(dz dzf) below and above, Tref,
     // Sref, and those factors times the reference profiles' level differences
     std::vector<double> rows((size_t)OC_LVROW * nz, 0.0);
     for (int k = 0; k < nz; ++k) {

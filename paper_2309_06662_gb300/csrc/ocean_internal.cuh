@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "ocean.h"
 
@@ -58,36 +59,21 @@ struct KP {
     const R* lvt;
 };
 
-// One level's constants for the tile kernels, one row of KP::lvt: dz_k, 1/dz_k; the
-// implicit solve's factors alo = dt/(dz_k dzf_k) (0 at k = 0) and ahi = dt/(dz_k dzf_{k+1})
-// (0 at the top); Tref_k, Sref_k; and the diffusion of the reference profiles
-// hdT = ahi (Tref_{k+1} - Tref_k), ldT = alo (Tref_k - Tref_{k-1}), likewise for S.
+// One level's constants for the tile kernels, one row of KP::lvt (OC_LVROW values):
+// dz_k, 1/dz_k; the implicit solve's factors alo = dt/(dz_k dzf_k) (0 at k = 0) and
+// ahi = dt/(dz_k dzf_{k+1}) (0 at the top); Tref_k, Sref_k; and the diffusion of the
+// reference profiles hdT = ahi (Tref_{k+1} - Tref_k), ldT = alo (Tref_k - Tref_{k-1}),
+// hdS, ldS likewise for S; the rest zero.  The kernels read each value where they use
+// it (short live ranges keep the tiles free of register spills).
 #define OC_LVROW 16
-template <typename R>
-struct LevelRow {
-    R dz, rdz, alo, ahi, Tref, Sref, hdT, ldT, hdS, ldS;
-};
+// values per row of KP::vw
+#define OC_VWROW 20
 
 template <typename R> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 __device__ __forceinline__ float2 make_vec2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 make_vec2(double a, double b) { return make_double2(a, b); }
-
-// the first ten values of row k, by 16-byte loads through the read-only path
-__device__ __forceinline__ LevelRow<float> load_level_row(const float* t, int k) {
-    const float4* r = reinterpret_cast<const float4*>(t + (size_t)k * OC_LVROW);
-    const float4 a = __ldg(r), b = __ldg(r + 1);
-    const float2 c = __ldg(reinterpret_cast<const float2*>(r + 2));
-    return {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
-}
-__device__ __forceinline__ LevelRow<double> load_level_row(const double* t, int k) {
-    const double2* r = reinterpret_cast<const double2*>(t + (size_t)k * OC_LVROW);
-    const double2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3), e = __ldg(r + 4);
-    return {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, e.x, e.y};
-}
-
-#define OC_VWROW 20
 
 // ----------------------------------------------------------------------- WENO-Z
 
@@ -231,28 +217,38 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// fifth-order WENO-Z of two stencils at once (same definition as weno5, rearranged):
-// with the second differences A_r and first differences B_r of the three candidate
-// stencils, 4 beta_r = (13/3) A_r^2 + B_r^2, so tau5/(beta_r + eps) = 4 (beta_0 - beta_2)
-// / (4 beta_r + 4 eps) needs no division by 4; the candidates are formed times 6 and the
-// weighted sum divided by 6 at the end.  tau/(beta+eps) squared is clamped at 1e36 (see
-// WenoRatio: the clamp leaves the value unchanged) so that the weights stay finite.
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+
+// fifth-order WENO-Z of two stencils at once (same definition as weno5, rearranged in
+// first differences D_n = q_{n+1} - q_n):
+//   second differences A_r = D_{r+1} - D_r; B_0 = A_0 + 2 D_1, B_1 = -(D_1 + D_2),
+//   B_2 = A_2 - 2 D_2, with 4 beta_r = (13/3) A_r^2 + B_r^2, so tau5/(beta_r + eps) =
+//   4 (beta_0 - beta_2) / (4 beta_r + 4 eps) needs no division by 4;
+//   the candidates as 6 p_r = 6 q_2 + delta_r, delta_0 = 3 D_1 + 2 A_0,
+//   delta_1 = 2 D_2 + D_1, delta_2 = 3 D_2 - A_2;
+//   the value q_2 + sum_r alpha_r delta_r / (6 sum_r alpha_r).
+// tau/(beta+eps) squared is clamped at 1e36 (see WenoRatio: the clamp leaves the value
+// unchanged) so that the weights stay finite.
 __device__ __forceinline__ float2 weno5z_x2(float2 q0, float2 q1, float2 q2, float2 q3,
                                             float2 q4, float eps) {
-    const float2 P0 = f2fma(q0, f2(2.f), f2fma(q1, f2(-7.f), f2mul(q2, f2(11.f))));
-    const float2 P1 = f2fma(q1, f2(-1.f), f2fma(q2, f2(5.f), f2mul(q3, f2(2.f))));
-    const float2 P2 = f2fma(q2, f2(2.f), f2fma(q3, f2(5.f), f2mul(q4, f2(-1.f))));
-    const float2 A0 = f2add(f2fma(q1, f2(-2.f), q0), q2);
-    const float2 A1 = f2add(f2fma(q2, f2(-2.f), q1), q3);
-    const float2 A2 = f2add(f2fma(q3, f2(-2.f), q2), q4);
-    const float2 B0 = f2fma(f2fma(q1, f2(-1.f), q2), f2(2.f), A0);   // q0 - 4 q1 + 3 q2
-    const float2 B1 = f2fma(q3, f2(-1.f), q1);                        // q1 - q3
-    const float2 B2 = f2fma(f2fma(q3, f2(-1.f), q2), f2(2.f), A2);   // 3 q2 - 4 q3 + q4
+    const float2 D0 = f2sub(q1, q0), D1 = f2sub(q2, q1), D2 = f2sub(q3, q2), D3 = f2sub(q4, q3);
+    const float2 A0 = f2sub(D1, D0), A1 = f2sub(D2, D1), A2 = f2sub(D3, D2);
+    const float2 B0 = f2fma(D1, f2(2.f), A0);
+    const float2 E1 = f2add(D1, D2);                 // -B_1
+    const float2 B2 = f2fma(D2, f2(-2.f), A2);
     const float2 c = f2(13.f / 3.f);
     const float2 b0 = f2fma(f2mul(A0, A0), c, f2mul(B0, B0));
-    const float2 b1 = f2fma(f2mul(A1, A1), c, f2mul(B1, B1));
+    const float2 b1 = f2fma(f2mul(A1, A1), c, f2mul(E1, E1));
     const float2 b2 = f2fma(f2mul(A2, A2), c, f2mul(B2, B2));
-    const float2 d = f2fma(b2, f2(-1.f), b0);
+    const float2 d = f2sub(b0, b2);
     const float2 e4 = f2(4.f * eps);
     auto alpha = [&](float2 b, float dr) {
         const float2 be = f2add(b, e4);
@@ -263,9 +259,13 @@ __device__ __forceinline__ float2 weno5z_x2(float2 q0, float2 q1, float2 q2, flo
         return f2fma(r2, f2(dr), f2(dr));
     };
     const float2 a0 = alpha(b0, 0.1f), a1 = alpha(b1, 0.6f), a2 = alpha(b2, 0.3f);
-    const float2 num = f2fma(a0, P0, f2fma(a1, P1, f2mul(a2, P2)));
-    const float2 den = f2add(f2add(a0, a1), a2);
-    return f2mul(f2mul(num, make_float2(rcp_approx(den.x), rcp_approx(den.y))), f2(1.f / 6.f));
+    const float2 t3 = f2(3.f);
+    const float2 g0 = f2fma(D1, t3, f2add(A0, A0));
+    const float2 g1 = f2add(E1, D2);
+    const float2 g2 = f2sub(f2mul(D2, t3), A2);
+    const float2 num = f2fma(a0, g0, f2fma(a1, g1, f2mul(a2, g2)));
+    const float2 den = f2mul(f2add(f2add(a0, a1), a2), f2(6.f));
+    return f2fma(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)), q2);
 }
 
 // third-order WENO-Z of two stencils at once (same definition as weno3)
@@ -433,6 +433,29 @@ template <typename R> struct StepBuffers {
     double fmom;
     TileMaps tm;               // tensor maps of the state read by the tracer tile
 };
+
+// The field pointers of the two tile kernels, passed as one block: a kernel parameter for
+// the single model (the code reads them from the parameter bank where used), a copy in
+// shared memory for an ensemble item.
+template <typename R> struct TracerArgs {
+    const R *u, *v, *w, *T, *S;
+    R *kap, *GTp, *GSp, *Tn, *Sn;
+    const R *dGT, *dGS;
+};
+template <typename R> struct MomentumArgs {
+    const R *u, *v, *w, *pr, *nu, *taux_s, *tauy_s;
+    R *Gup, *Gvp, *un, *vn, *cu, *cv, *Un, *Vn, *GU, *GV, *Su, *Sv;
+};
+template <typename R>
+__host__ __device__ inline TracerArgs<R> tracer_args(const StepBuffers<R>& b) {
+    return TracerArgs<R>{b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS, b.Tn, b.Sn, b.dGT, b.dGS};
+}
+// the v-viscosity's Thomas coefficients go to the scratch field wk, the u-viscosity's to kap
+template <typename R>
+__host__ __device__ inline MomentumArgs<R> momentum_args(const StepBuffers<R>& b) {
+    return MomentumArgs<R>{b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu, b.Gv, b.un, b.vn,
+                           b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su, b.Sv};
+}
 
 template <typename R>
 void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s);

@@ -281,13 +281,7 @@ struct __align__(128) TracerSmem {
 // SV: the vertical reconstructions take the stretched-level coefficients of p.vw.
 template <typename R, bool STEP, bool SV>
 __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, const int bx,
-                                            const int by,
-                                            const R* __restrict__ u, const R* __restrict__ v,
-                                            const R* __restrict__ w, const R* __restrict__ T,
-                                            const R* __restrict__ S, R* __restrict__ kap,
-                                            R* __restrict__ GTp, R* __restrict__ GSp,
-                                            R* __restrict__ Tn, R* __restrict__ Sn,
-                                            const R* __restrict__ dGT, const R* __restrict__ dGS) {
+                                            const int by, const TracerArgs<R>& a) {
     using R2 = typename Vec2<R>::type;
     __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
@@ -348,7 +342,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    // with the own columns' operands of the level: w and the diffusivity on its top face
+    // with the own columns' operands of the level: a.w and the diffusivity on its top face
     // (level k+1, when there is one), and with STEP G_T and G_S of the previous step
     auto stage = [&](int k, int buf) {
         if (tid == 0) {
@@ -377,8 +371,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     for (int q = 0; q < 6; ++q) {
         const int kk = kstart - 2 + q;
         const bool ok = mine && kk >= kb && kk < nz;
-        wT[q] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
-        wS[q] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
+        wT[q] = ok ? a.T[kk * P + c2] + p.Tref[kk] : R(0);
+        wS[q] = ok ? a.S[kk * P + c2] + p.Sref[kk] : R(0);
     }
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
     R kcarry = R(0);   // diffusivity on the top face of the previous level
@@ -493,9 +487,10 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         kcarry = k1;
         // ---- own cell
         if (live) {
-            // level constants: 1/dz, the implicit solve's off-diagonal factors dt/(dz dzf)
-            // below and above, Tref, Sref and the diffusion of the reference profiles
-            const LevelRow<R> L = load_level_row(p.lvt, k);
+            // level constants (row k of the level table, read where used): 1/dz, the
+            // implicit solve's off-diagonal factors dt/(dz dzf) below and above, Tref, Sref
+            // and the diffusion of the reference profiles
+            const R* L = p.lvt + (size_t)k * OC_LVROW;
             R ftT = R(0), ftS = R(0);
             if (k + 1 < nz) {   // flux through the top face (bottom face of cell k+1)
                 const bool pos = wt >= R(0);
@@ -523,7 +518,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                 ftT = wt * rT;
                 ftS = wt * rS;
             }
-            const R rdz = L.rdz;
+            const R rdz = __ldg(L + 1);
             const R eU = sm.fxU[fb][ty][tx + 1], nV = sm.fyV[fb][ty + 1][tx];
             const R wU = sm.fxU[fb][ty][tx], sV = sm.fyV[fb][ty][tx];
             const R2 eTS = sm.fxTS[fb][ty][tx + 1], nTS = sm.fyTS[fb][ty + 1][tx];
@@ -531,36 +526,36 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             const R divU = eU - wU + nV - sV;
             const R hT = eTS.x - wTS.x + nTS.x - sTS.x;
             const R hS = eTS.y - wTS.y + nTS.y - sTS.y;
-            R GT = -((L.Tref * divU + hT) * rac + (ftT - fzT)) * rdz;
-            R GS = -((L.Sref * divU + hS) * rac + (ftS - fzS)) * rdz;
-            if (dGT) {   // learned-closure corrections, part of G^n
-                GT += dGT[ck];
-                GS += dGS[ck];
+            R GT = -((__ldg(L + 4) * divU + hT) * rac + (ftT - fzT)) * rdz;
+            R GS = -((__ldg(L + 5) * divU + hS) * rac + (ftS - fzS)) * rdz;
+            if (a.dGT) {   // learned-closure corrections, part of G^n
+                GT += a.dGT[ck];
+                GS += a.dGS[ck];
             }
             fzT = ftT;
             fzS = ftS;
             if (!STEP) {
-                Tn[ck] = GT;
-                Sn[ck] = GS;
+                a.Tn[ck] = GT;
+                a.Sn[ck] = GS;
             } else {
                 const R gT = p.ca * GT - p.cb * gT0;
                 const R gS = p.ca * GS - p.cb * gS0;
-                GTp[ck] = GT;
-                GSp[ck] = GS;
-                // lo, hi: dt kap / (dz dzf) on the bottom and top faces (zero at the ends)
-                const R lo = k > kb ? k0 * L.alo : R(0);
-                const R hi = k1 * L.ahi;   // kap on the surface face is zero
+                a.GTp[ck] = GT;
+                a.GSp[ck] = GS;
+                // lo, hi: dt a.kap / (dz dzf) on the bottom and top faces (zero at the ends)
+                const R lo = k > kb ? k0 * __ldg(L + 2) : R(0);
+                const R hi = k1 * __ldg(L + 3);   // a.kap on the surface face is zero
                 // the diffusion of the reference profile moves to the right-hand side:
-                // (I - dt D) T'^{n+1} = T'* + dt D Tref
-                const R Ts = T0 + p.dt * gT + k1 * L.hdT - (k > kb ? k0 * L.ldT : R(0));
-                const R Ss = S0 + p.dt * gS + k1 * L.hdS - (k > kb ? k0 * L.ldS : R(0));
+                // (I - dt D) a.T'^{n+1} = a.T'* + dt D Tref
+                const R Ts = T0 + p.dt * gT + k1 * __ldg(L + 6) - (k > kb ? k0 * __ldg(L + 7) : R(0));
+                const R Ss = S0 + p.dt * gS + k1 * __ldg(L + 8) - (k > kb ? k0 * __ldg(L + 9) : R(0));
                 const R inv = rcp_pivot((R(1) + lo + hi) + lo * cprev);   // b_k - a_k c'_{k-1}
                 cprev = -hi * inv;
                 dTprev = (Ts + lo * dTprev) * inv;
                 dSprev = (Ss + lo * dSprev) * inv;
-                kap[ck] = cprev;
-                Tn[ck] = dTprev;
-                Sn[ck] = dSprev;
+                a.kap[ck] = cprev;
+                a.Tn[ck] = dTprev;
+                a.Sn[ck] = dSprev;
             }
         }
         cb = cb == 2 ? 0 : cb + 1;
@@ -573,8 +568,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         {
             const int kk = k + 4;
             const bool ok = mine && kk >= kb && kk < nz;
-            wT[5] = ok ? T[kk * P + c2] + p.Tref[kk] : R(0);
-            wS[5] = ok ? S[kk * P + c2] + p.Sref[kk] : R(0);
+            wT[5] = ok ? a.T[kk * P + c2] + p.Tref[kk] : R(0);
+            wS[5] = ok ? a.S[kk * P + c2] + p.Sref[kk] : R(0);
         }
     }
     __syncthreads();   // every copy waited for: the barriers can be retired
@@ -593,9 +588,9 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         for (int q = 0; q < 4; ++q) {
             const long ck = (long)(k - q) * P + c2;
             const bool in = k - q >= kb;
-            cc[q] = in ? kap[ck] : R(0);
-            tq[q] = in ? Tn[ck] : R(0);
-            sq[q] = in ? Sn[ck] : R(0);
+            cc[q] = in ? a.kap[ck] : R(0);
+            tq[q] = in ? a.Tn[ck] : R(0);
+            sq[q] = in ? a.Sn[ck] : R(0);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -603,24 +598,16 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             const long ck = (long)(k - q) * P + c2;
             xT = tq[q] - cc[q] * xT;
             xS = sq[q] - cc[q] * xS;
-            Tn[ck] = xT;
-            Sn[ck] = xS;
+            a.Tn[ck] = xT;
+            a.Sn[ck] = xS;
         }
     }
 }
 
 template <typename R, bool STEP, bool SV>
-__global__ void __launch_bounds__(NTT, (OccX<R, SV>::value)) k_tracer(KP<R> p,
-                                               const __grid_constant__ TileMaps tm,
-                                               const R* __restrict__ u,
-                                               const R* __restrict__ v, const R* __restrict__ w,
-                                               const R* __restrict__ T, const R* __restrict__ S,
-                                               R* __restrict__ kap, R* __restrict__ GTp,
-                                               R* __restrict__ GSp, R* __restrict__ Tn,
-                                               R* __restrict__ Sn, const R* __restrict__ dGT,
-                                               const R* __restrict__ dGS) {
-    tracer_tile<R, STEP, SV>(p, tm, blockIdx.x, blockIdx.y, u, v, w, T, S, kap, GTp, GSp, Tn,
-                             Sn, dGT, dGS);
+__global__ void __launch_bounds__(NTT, (OccX<R, SV>::value)) k_tracer(
+    KP<R> p, const __grid_constant__ TileMaps tm, const __grid_constant__ TracerArgs<R> a) {
+    tracer_tile<R, STEP, SV>(p, tm, blockIdx.x, blockIdx.y, a);
 }
 
 // ------------------------------------------------------------------ momentum
@@ -653,13 +640,8 @@ struct __align__(128) MomentumSmem {
 // form (own-column windows of u and v over levels k-2 .. k+3 in registers, the bottom
 // face's flux carried up from the level below), else centred.
 template <typename R, bool STEP, bool VA>
-__device__ __forceinline__ void momentum_tile(
-    const KP<R>& p, const TileMaps& tm, const int bx, const int by, const R* __restrict__ u,
-    const R* __restrict__ v, const R* __restrict__ w, const R* __restrict__ pr,
-    const R* __restrict__ nu, const R* __restrict__ taux_s, const R* __restrict__ tauy_s,
-    R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un, R* __restrict__ vn,
-    R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un, R* __restrict__ Vn,
-    R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su, R* __restrict__ Sv) {
+__device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm, const int bx,
+                                              const int by, const MomentumArgs<R>& a) {
     __shared__ MomentumSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
@@ -691,11 +673,11 @@ __device__ __forceinline__ void momentum_tile(
     const int kstart = sm.kmin;
     if (kstart >= nz) return;
 
-    // ---- staging by tensor copies one thread issues: level k's u, v, p, w, nu tiles (and
+    // ---- staging by tensor copies one thread issues: level k's a.u, a.v, p, a.w, a.nu tiles (and
     // with STEP its own columns' G^{n-1}) into slot (k - kstart) % 3, two levels ahead.
-    // Level k's own cells read its slot and level k+1's (u, v above, w and nu on the top
+    // Level k's own cells read its slot and level k+1's (a.u, a.v above, a.w and a.nu on the top
     // face).
-    constexpr int TC = (TY + 1) * (TX + 1);   // centres of the pressure / w / nu tiles
+    constexpr int TC = (TY + 1) * (TX + 1);   // centres of the pressure / a.w / a.nu tiles
     constexpr unsigned TILES = (unsigned)sizeof(R) * (40u * 14u + 40u * 13u + 3u * 36u * 9u);
     constexpr unsigned OWN = (unsigned)sizeof(R) * TY * TX;
     const int yu = j0 + OC_H - 3, yv = j0 + OC_H - 2, yc = j0 + OC_H - 1;
@@ -729,83 +711,89 @@ __device__ __forceinline__ void momentum_tile(
     // their indices, shared-memory offsets and corner masks are formed once
     constexpr int NCR = (TY + 5) * (TX + 5);
     static_assert(NCR <= 2 * NT && TC <= 2 * NT, "two corner and two centre slots per thread");
+    // the lowest level from which all six corners of this thread's a.u-face (a.v-face)
+    // vorticity stencils touch the fluid
+    int kzu = 0, kzv = 0;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        kzu = max(kzu, (int)sm.kbzin[ty + n][tx + 2]);
+        kzv = max(kzv, (int)sm.kbzin[ty + 2][tx + n]);
+    }
     // corner slot: lowest active level << 16 | row << 8 | column (-1: none); centre slot:
     // row << 8 | column (-1: none)
-    int zs[2], ko[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int q = tid + r * NT;
-        const bool okz = q < NCR, okk = q < TC;
-        const int a = okz ? q / (TX + 5) : 0, b = okz ? q % (TX + 5) : 0;
-        zs[r] = okz ? ((int)sm.kbz[a][b] << 16) | (a << 8) | b : -1;
-        const int ca = okk ? q / (TX + 1) : 0, cb = okk ? q % (TX + 1) : 0;
-        ko[r] = okk ? (ca << 8) | cb : -1;
-    }
+    auto zslot = [&](int q) {
+        if (q >= NCR) return -1;
+        const int a = q / (TX + 5), b = q % (TX + 5);
+        return ((int)sm.kbz[a][b] << 16) | (a << 8) | b;
+    };
+    auto kslot = [&](int q) { return q < TC ? ((q / (TX + 1)) << 8) | (q % (TX + 1)) : -1; };
+    const int zs0 = zslot(tid), zs1 = zslot(tid + NT), ko0 = kslot(tid), ko1 = kslot(tid + NT);
     R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
-    // own faces: u, v at k-1 (lower); levels k and k+1 come from the tiles
-    R ulo = R(0), vlo = R(0);
     // carried up one level: the vertical advection through the top face (the next
-    // level's bottom-face term) and the sum of the two nu on the top face
+    // level's bottom-face term) and the sum of the two a.nu on the top face
     R upu = R(0), upv = R(0), nsu = R(0), nsv = R(0);
-    if (mine && kstart >= 1) {
-        ulo = u[(kstart - 1) * P + c2];
-        vlo = v[(kstart - 1) * P + c2];
-    }
-    // WENO vertical advection: own u- and v-face values at levels k-2 .. k+3 (0 outside
-    // the face's wet levels), and the flux and w of the bottom face
+    // WENO vertical advection: own a.u- and a.v-face values at levels k-2 .. k+3 (0 outside
+    // the face's wet levels), and the flux and a.w of the bottom face
     R wu[6], wv[6];
     R fbu = R(0), fbv = R(0), wbu = R(0), wbv = R(0);
     if (VA) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const int kk = kstart - 2 + q;
-            wu[q] = mine && kk >= ku && kk < nz ? u[kk * P + c2] : R(0);
-            wv[q] = mine && kk >= kv && kk < nz ? v[kk * P + c2] : R(0);
+            wu[q] = mine && kk >= ku && kk < nz ? a.u[kk * P + c2] : R(0);
+            wv[q] = mine && kk >= kv && kk < nz ? a.v[kk * P + c2] : R(0);
         }
     }
+    int r3 = 0, q3 = 0;   // (k - kstart) mod 3 and div 3
     // One block barrier per level: corners and kinetic energy of level k go to buffer
     // k & 1, so a warp that has finished level k-1 computes them while others still read
     // level k-1's; the barrier after them publishes them and frees the slot of level k-1
     // (read by every thread before it), which takes level k+2.
     for (int k = kstart; k < nz; ++k) {
         const long Pk = k * P;
-        const int lv = k - kstart, sc = lv % 3, sn = (lv + 1) % 3, fb = lv & 1;
-        bar_wait(&sm.bar[sc], (unsigned)(lv / 3) & 1u);
+        // slots of levels k, k+1, k+2 and the parities of their completions, from the
+        // running quotient and remainder of (k - kstart) / 3
+        const int sc = r3, sn = r3 == 2 ? 0 : r3 + 1, s2 = r3 == 0 ? 2 : r3 - 1, fb = (k - kstart) & 1;
+        const unsigned pc = (unsigned)q3 & 1u, pn = (unsigned)(r3 == 2 ? q3 + 1 : q3) & 1u;
+        bar_wait(&sm.bar[sc], pc);
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            if (zs[r] < 0) continue;
-            const int a = (zs[r] >> 8) & 255, b = zs[r] & 255;
+        auto corner = [&](const int zsr) {
+            const int a = (zsr >> 8) & 255, b = zsr & 255;
             const R* us = &sm.u[sc][a][b];
             const R* vs = &sm.v[sc][a][b];
             R zz = R(0);
-            if (k >= (zs[r] >> 16)) {
-                // u(i, jc) = u[a + 1][b], u(i, jc-1) = u[a][b]; v(i, jc) = v[a][b + 1],
-                // v(i-1, jc) = v[a][b]  (tile columns offset by 2 for u, 1 for v)
+            if (k >= (zsr >> 16)) {
+                // a.u(i, jc) = a.u[a + 1][b], a.u(i, jc-1) = a.u[a][b]; a.v(i, jc) = a.v[a][b + 1],
+                // a.v(i-1, jc) = a.v[a][b]  (tile columns offset by 2 for a.u, 1 for a.v)
                 const R circ = p.dy * (vs[2] - vs[1])
                              - (sm.zdxN[a] * us[(TX + 8) + 2] - sm.zdxS[a] * us[2]);
                 zz = circ * sm.zrA[a];
             }
             sm.z[fb][a][b] = zz;
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            if (ko[r] < 0) continue;
-            const int a = ko[r] >> 8, b = ko[r] & 255;
-            // centre (i0-1+b, j0-1+a): u at cols b+1, b+2 of row a+2; v at col b+2, rows a+1, a+2
+        };
+        corner(zs0);
+        if (zs1 >= 0) corner(zs1);
+        auto centre = [&](const int kor) {
+            const int a = kor >> 8, b = kor & 255;
+            // centre (i0-1+b, j0-1+a): a.u at cols b+1, b+2 of row a+2; a.v at col b+2, rows a+1, a+2
             const R ua = sm.u[sc][a + 2][(b + 1) + 2], ub = sm.u[sc][a + 2][(b + 2) + 2];
             const R va = sm.v[sc][a + 1][(b + 2) + 1], vb = sm.v[sc][a + 2][(b + 2) + 1];
             sm.K[fb][a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
-        }
+        };
+        centre(ko0);
+        if (ko1 >= 0) centre(ko1);
         // this thread's reads of level k-1's slot are ordered before the tensor copy that
         // overwrites it
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        if (tid == 0 && k + 2 < nz) stage(k + 2, (lv + 2) % 3);
-        if (k + 1 < nz) bar_wait(&sm.bar[sn], (unsigned)((lv + 1) / 3) & 1u);
+        if (tid == 0 && k + 2 < nz) stage(k + 2, s2);
+        if (k + 1 < nz) bar_wait(&sm.bar[sn], pn);
         if (mine) {
-            const R rdz = p.rdz[k];
+            // level constants (row k of the level table, read where used): dz, 1/dz and the
+            // implicit solve's factors dt/(dz dzf) below and above
+            const R* L = p.lvt + (size_t)k * OC_LVROW;
+            const R rdz = __ldg(L + 1);
             const bool du_ = k >= ku, dv_ = k >= kv;
             const R uhi = k + 1 < nz ? sm.u[sn][ty + 3][(tx + 2) + 2] : R(0);
             const R vhi = k + 1 < nz ? sm.v[sn][ty + 2][(tx + 3) + 1] : R(0);
@@ -819,20 +807,38 @@ __device__ __forceinline__ void momentum_tile(
             const R uh = R(0.25) * (sm.u[sc][ty + 2][(tx + 2) + 2] + sm.u[sc][ty + 2][(tx + 3) + 2]
                                   + sm.u[sc][ty + 3][(tx + 2) + 2] + sm.u[sc][ty + 3][(tx + 3) + 2]);
             R qa[5], qb[5];
-            unsigned ina = 0, inb = 0;
+            // upwind to downwind: corner rows j-2 .. j+2 (vh >= 0) or j+3 .. j-1 at the
+            // a.u-face's column; corner columns i-2 .. i+2 (uh >= 0) or i+3 .. i-1 on the
+            // a.v-face's row.  A stencil whose six corners all touch the fluid needs no mask.
+            const bool pa = vh >= R(0), pb = uh >= R(0);
+            const R* za = &sm.z[fb][pa ? ty : ty + 5][tx + 2];
+            const R* zb = &sm.z[fb][ty + 2][pb ? tx : tx + 5];
+            const int sa = pa ? (TX + 5) : -(TX + 5), sb = pb ? 1 : -1;
+            const bool fa = k >= kzu, fbb = k >= kzv;
+            unsigned ina = fa ? 31u : 0u, inb = fbb ? 31u : 0u;
 #pragma unroll
             for (int n = 0; n < 5; ++n) {
-                const int a = vh >= R(0) ? ty + n : ty + 5 - n;   // corner rows j-2.. (u-face)
-                qa[n] = sm.z[fb][a][tx + 2];
-                ina |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
-                const int b = uh >= R(0) ? tx + n : tx + 5 - n;   // corner cols i-2.. (v-face)
-                qb[n] = sm.z[fb][ty + 2][b];
-                inb |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
+                qa[n] = za[n * sa];
+                qb[n] = zb[n * sb];
+            }
+            if (!fa) {
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int a = pa ? ty + n : ty + 5 - n;
+                    ina |= (k >= sm.kbzin[a][tx + 2] ? 1u : 0u) << n;
+                }
+            }
+            if (!fbb) {
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    const int b = pb ? tx + n : tx + 5 - n;
+                    inb |= (k >= sm.kbzin[ty + 2][b] ? 1u : 0u) << n;
+                }
             }
             R ztu, ztv;
             WenoPair<R>::run(qa, qb, ina, inb, p.eps, p.linear, ztu, ztv);
             // WENO flux form of the vertical advection:
-            // [w_top u~_top - w_bot u~_bot - u_k (w_top - w_bot)] / dz_k, u~ upwind by w
+            // [w_top a.u~_top - w_bot a.u~_bot - u_k (w_top - w_bot)] / dz_k, a.u~ upwind by a.w
             R vau = R(0), vav = R(0);
             if (VA) {
                 R wtu = R(0), wtv = R(0), ftu = R(0), ftv = R(0);
@@ -866,7 +872,7 @@ __device__ __forceinline__ void momentum_tile(
                 vav = (ftv - (bv ? fbv : R(0)) - v0 * (wtv - (bv ? wbv : R(0)))) * rdz;
                 fbu = ftu; wbu = wtu; fbv = ftv; wbv = wtv;
             }
-            if (du_) {   // ---------------- u at the west face of column (i, j)
+            if (du_) {   // ---------------- a.u at the west face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty + 1][tx]) * rdxc;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty + 1][(tx) + 3]) * rdxc;
                 R vadv = vau;
@@ -878,29 +884,29 @@ __device__ __forceinline__ void momentum_tile(
                     upu = up;
                     vadv = R(0.5) * (up + dn);
                 }
-                const R wind = k == nz - 1 ? taux_s[c2] : R(0);
+                const R wind = k == nz - 1 ? a.taux_s[c2] : R(0);
                 const R G = (ztu + fu) * vh - dK - vadv - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
-                    un[ck] = G;
+                    a.un[ck] = G;
                 } else {
                     const R gh = p.ca * G - p.cb * gu0;
-                    Gup[ck] = G;
-                    sUn += p.dz[k] * u0;
-                    sGU += p.dz[k] * gh;
+                    a.Gup[ck] = G;
+                    sUn += __ldg(L) * u0;
+                    sGU += __ldg(L) * gh;
                     const R us = u0 + p.dt * gh;
                     const R nt = k < nz - 1 ? sm.nu[sn][ty + 1][(tx) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3] : R(0);
-                    const R lo = k > ku ? p.dt * R(0.5) * nsu * rdz * p.rdzf[k] : R(0);
-                    const R hi = k < nz - 1 ? p.dt * R(0.5) * nt * rdz * p.rdzf[k + 1] : R(0);
+                    const R lo = k > ku ? R(0.5) * nsu * __ldg(L + 2) : R(0);
+                    const R hi = R(0.5) * nt * __ldg(L + 3);   // zero at the surface
                     nsu = nt;
                     const R inv = rcp_pivot((R(1) + lo + hi) + lo * cuk);
                     cuk = -hi * inv;
                     duk = (us + lo * duk) * inv;
-                    cu[ck] = cuk;
-                    un[ck] = duk;
+                    a.cu[ck] = cuk;
+                    a.un[ck] = duk;
                 }
             }
-            if (dv_) {   // ---------------- v at the south face of column (i, j)
+            if (dv_) {   // ---------------- a.v at the south face of column (i, j)
                 const R dK = (sm.K[fb][ty + 1][tx + 1] - sm.K[fb][ty][tx + 1]) * p.rdy;
                 const R dP = (sm.p[sc][ty + 1][(tx + 1) + 3] - sm.p[sc][ty][(tx + 1) + 3]) * p.rdy;
                 R vadv = vav;
@@ -912,30 +918,28 @@ __device__ __forceinline__ void momentum_tile(
                     upv = up;
                     vadv = R(0.5) * (up + dn);
                 }
-                const R wind = k == nz - 1 ? tauy_s[c2] : R(0);
+                const R wind = k == nz - 1 ? a.tauy_s[c2] : R(0);
                 const R G = -(ztv + fv) * uh - dK - vadv - dP + wind;
                 const long ck = Pk + c2;
                 if (!STEP) {
-                    vn[ck] = G;
+                    a.vn[ck] = G;
                 } else {
                     const R gh = p.ca * G - p.cb * gv0;
-                    Gvp[ck] = G;
-                    sVn += p.dz[k] * v0;
-                    sGV += p.dz[k] * gh;
+                    a.Gvp[ck] = G;
+                    sVn += __ldg(L) * v0;
+                    sGV += __ldg(L) * gh;
                     const R vs = v0 + p.dt * gh;
                     const R nt = k < nz - 1 ? sm.nu[sn][ty][(tx + 1) + 3] + sm.nu[sn][ty + 1][(tx + 1) + 3] : R(0);
-                    const R lo = k > kv ? p.dt * R(0.5) * nsv * rdz * p.rdzf[k] : R(0);
-                    const R hi = k < nz - 1 ? p.dt * R(0.5) * nt * rdz * p.rdzf[k + 1] : R(0);
+                    const R lo = k > kv ? R(0.5) * nsv * __ldg(L + 2) : R(0);
+                    const R hi = R(0.5) * nt * __ldg(L + 3);   // zero at the surface
                     nsv = nt;
                     const R inv = rcp_pivot((R(1) + lo + hi) + lo * cvk);
                     cvk = -hi * inv;
                     dvk = (vs + lo * dvk) * inv;
-                    cv[ck] = cvk;
-                    vn[ck] = dvk;
+                    a.cv[ck] = cvk;
+                    a.vn[ck] = dvk;
                 }
             }
-            ulo = u0;
-            vlo = v0;
         }
         if (VA) {   // slide the windows up one level
 #pragma unroll
@@ -944,8 +948,12 @@ __device__ __forceinline__ void momentum_tile(
                 wv[q] = wv[q + 1];
             }
             const int kk = k + 4;
-            wu[5] = mine && kk >= ku && kk < nz ? u[kk * P + c2] : R(0);
-            wv[5] = mine && kk >= kv && kk < nz ? v[kk * P + c2] : R(0);
+            wu[5] = mine && kk >= ku && kk < nz ? a.u[kk * P + c2] : R(0);
+            wv[5] = mine && kk >= kv && kk < nz ? a.v[kk * P + c2] : R(0);
+        }
+        if (++r3 == 3) {
+            r3 = 0;
+            ++q3;
         }
     }
     __syncthreads();   // every copy waited for: the barriers can be retired
@@ -955,7 +963,7 @@ __device__ __forceinline__ void momentum_tile(
         bar_inval(&sm.bar[2]);
     }
     if (!STEP || !mine) return;
-    // back substitutions of u and v down the column together, both coefficients of four
+    // back substitutions of a.u and a.v down the column together, both coefficients of four
     // levels loaded at once (each recurrence itself is serial)
     R xu = duk, xv = dvk;   // level nz-1: x = d'
     R su = p.dz[nz - 1] * xu, sv = p.dz[nz - 1] * xv;
@@ -966,49 +974,42 @@ __device__ __forceinline__ void momentum_tile(
         for (int q = 0; q < 4; ++q) {
             const long ck = (long)(k - q) * P + c2;
             const bool inu = k - q >= ku, inv = k - q >= kv;
-            cuq[q] = inu ? cu[ck] : R(0);
-            duq[q] = inu ? un[ck] : R(0);
-            cvq[q] = inv ? cv[ck] : R(0);
-            dvq[q] = inv ? vn[ck] : R(0);
+            cuq[q] = inu ? a.cu[ck] : R(0);
+            duq[q] = inu ? a.un[ck] : R(0);
+            cvq[q] = inv ? a.cv[ck] : R(0);
+            dvq[q] = inv ? a.vn[ck] : R(0);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const long ck = (long)(k - q) * P + c2;
             if (k - q >= ku) {
                 xu = duq[q] - cuq[q] * xu;
-                un[ck] = xu;
+                a.un[ck] = xu;
                 su += p.dz[k - q] * xu;
             }
             if (k - q >= kv) {
                 xv = dvq[q] - cvq[q] * xv;
-                vn[ck] = xv;
+                a.vn[ck] = xv;
                 sv += p.dz[k - q] * xv;
             }
         }
     }
     if (ku < nz) {
-        Un[c2] = sUn;
-        GU[c2] = sGU;
-        Su[c2] = su;
+        a.Un[c2] = sUn;
+        a.GU[c2] = sGU;
+        a.Su[c2] = su;
     }
     if (kv < nz) {
-        Vn[c2] = sVn;
-        GV[c2] = sGV;
-        Sv[c2] = sv;
+        a.Vn[c2] = sVn;
+        a.GV[c2] = sGV;
+        a.Sv[c2] = sv;
     }
 }
 
 template <typename R, bool STEP, bool VA>
 __global__ void __launch_bounds__(NT, (OccX<R, VA>::value)) k_momentum(
-    KP<R> p, const __grid_constant__ TileMaps tm, const R* __restrict__ u,
-    const R* __restrict__ v, const R* __restrict__ w,
-    const R* __restrict__ pr, const R* __restrict__ nu, const R* __restrict__ taux_s,
-    const R* __restrict__ tauy_s, R* __restrict__ Gup, R* __restrict__ Gvp, R* __restrict__ un,
-    R* __restrict__ vn, R* __restrict__ cu, R* __restrict__ cv, R* __restrict__ Un,
-    R* __restrict__ Vn, R* __restrict__ GU, R* __restrict__ GV, R* __restrict__ Su,
-    R* __restrict__ Sv) {
-    momentum_tile<R, STEP, VA>(p, tm, blockIdx.x, blockIdx.y, u, v, w, pr, nu, taux_s, tauy_s,
-                               Gup, Gvp, un, vn, cu, cv, Un, Vn, GU, GV, Su, Sv);
+    KP<R> p, const __grid_constant__ TileMaps tm, const __grid_constant__ MomentumArgs<R> a) {
+    momentum_tile<R, STEP, VA>(p, tm, blockIdx.x, blockIdx.y, a);
 }
 
 // ------------------------------------------------------------------ barotropic mode
@@ -1318,10 +1319,8 @@ void launch_diag(const KP<R>& p, const StepBuffers<R>& b, cudaStream_t s) {
 template <typename R>
 void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TTY);
-    auto go = [&](auto kern) {
-        kern<<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT, b.GS, b.Tn,
-                                    b.Sn, b.dGT, b.dGS);
-    };
+    const TracerArgs<R> a = tracer_args(b);
+    auto go = [&](auto kern) { kern<<<grid, block, 0, s>>>(p, b.tm, a); };
     if (p.vweno) {
         if (step) go(k_tracer<R, true, true>);
         else go(k_tracer<R, false, true>);
@@ -1334,11 +1333,8 @@ void launch_tracer(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStrea
 template <typename R>
 void launch_momentum(const KP<R>& p, const StepBuffers<R>& b, bool step, cudaStream_t s) {
     const dim3 grid((p.g.nx + TX - 1) / TX, (p.g.ny + TY - 1) / TY), block(TX, TY);
-    auto go = [&](auto kern) {
-        kern<<<grid, block, 0, s>>>(p, b.tm, b.u, b.v, b.w, b.p, b.nu, b.taux_s, b.tauy_s, b.Gu,
-                                    b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn, b.GU, b.GV, b.Su,
-                                    b.Sv);
-    };
+    const MomentumArgs<R> a = momentum_args(b);
+    auto go = [&](auto kern) { kern<<<grid, block, 0, s>>>(p, b.tm, a); };
     if (p.mvadv) {
         if (step) go(k_momentum<R, true, true>);
         else go(k_momentum<R, false, true>);
@@ -1706,31 +1702,26 @@ __global__ void __launch_bounds__(TPB) k_ens_diag(const EnsMember<R>* __restrict
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NTT, Occ4<R>::value) k_ens_tracer(
+__global__ void __launch_bounds__(NTT, (OccX<R, true>::value)) k_ens_tracer(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
     for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
         const EnsItem e = work[it];
-        const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        tracer_tile<R, true, false>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.T, b.S, b.kap, b.GT,
-                                    b.GS, b.Tn, b.Sn, b.dGT, b.dGS);
+        tracer_tile<R, true, false>(mem[e.m].k, b.tm, e.a, e.b, tracer_args(b));
     }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT, Occ4<R>::value) k_ens_momentum(
+__global__ void __launch_bounds__(NT, (OccX<R, true>::value)) k_ens_momentum(
     const EnsMember<R>* __restrict__ mem, const EnsItem* __restrict__ work, int nwork,
     int* counter) {
     __shared__ int s_next;
     for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
         const EnsItem e = work[it];
-        const KP<R>& p = mem[e.m].k;
         const StepBuffers<R>& b = mem[e.m].b;
-        momentum_tile<R, true, false>(p, b.tm, e.a, e.b, b.u, b.v, b.w, b.p, b.nu, b.taux_s,
-                                      b.tauy_s, b.Gu, b.Gv, b.un, b.vn, b.kap, b.wk, b.Un, b.Vn,
-                                      b.GU, b.GV, b.Su, b.Sv);
+        momentum_tile<R, true, false>(mem[e.m].k, b.tm, e.a, e.b, momentum_args(b));
     }
 }
 
