@@ -228,12 +228,13 @@ def train(net, d, sc, epochs: int, batch: int, lr: float, val=None, ev=None, see
     return hist, vhist, best, best_terms
 
 
-def gate_heads(params, nz: int, terms, base):
-    """Switch off the output heads that do not beat "no network" on validation columns:
-    returns the gated parameters and which heads stay on."""
+def gate_heads(params, nz: int, terms, base, corrections: bool = True):
+    """Switch off the output heads that do not beat "no network" on validation columns
+    (and the correction head when it was not fitted): returns the gated parameters and
+    which heads stay on."""
     W, b = (x.copy() for x in params[-1])
     keep = dict(diffusivity=terms["fT"] + terms["fS"] < base["fT"] + base["fS"],
-                corrections=terms["gT"] + terms["gS"] < base["gT"] + base["gS"])
+                corrections=corrections and terms["gT"] + terms["gS"] < base["gT"] + base["gS"])
     if not keep["diffusivity"]:
         W[:, :nz] = 0.0
         b[:nz] = -30.0
@@ -285,16 +286,23 @@ def run(cfg: Dict, log=print) -> Dict:
     dims = [6 * nz, H, H, H, 3 * nz]
     net = ocean.MLP(nz, H, cfg["batch"], inputs.mlp_seeded_params(cfg["train_seeds"][0], dims))
     vev = ocean.MLP(nz, H, val["X"].shape[0])
-    train_base = baseline_loss(data, sc)
-    val_base = baseline_loss(val, sc)
+    # fit_corrections = False: the tendency-correction terms leave the training loss (their
+    # normalisation made huge), so the shared layers serve the diffusivity alone and the
+    # correction head stays off; the training and validation losses are those of tsc
+    fit_corr = cfg.get("fit_corrections", True)
+    tsc = dict(sc) if fit_corr else dict(sc, sGT=1e30, sGS=1e30)
+    train_base = baseline_loss(data, tsc)
+    val_base = baseline_loss(val, tsc)
     torch.cuda.synchronize()
     t1 = time.time()
-    hist, vhist, trained, vterms = train(net, data, sc, cfg["epochs"], cfg["batch"], cfg["lr"],
-                                         val, vev)
+    hist, vhist, trained, _ = train(net, data, tsc, cfg["epochs"], cfg["batch"], cfg["lr"],
+                                    val, vev, seed=cfg.get("train_seed", 0))
     torch.cuda.synchronize()
     train_s = time.time() - t1
+    vev.set_params(trained)
+    vterms = loss_terms(vev.forward(val["X"]), val, sc)
     vbase_terms = loss_terms(None, val, sc)
-    trained, heads = gate_heads(trained, nz, vterms, vbase_terms)
+    trained, heads = gate_heads(trained, nz, vterms, vbase_terms, corrections=fit_corr)
     steps = cfg["epochs"] * (ncols // cfg["batch"])
     log(f"training: {steps} Adam steps in {train_s:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}"
         f" (no network: {train_base:.4g}); validation best {min(vhist):.4g} at epoch "
