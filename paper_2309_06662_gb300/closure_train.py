@@ -233,8 +233,11 @@ def gate_heads(params, nz: int, terms, base, corrections: bool = True):
     (and the correction head when it was not fitted): returns the gated parameters and
     which heads stay on."""
     W, b = (x.copy() for x in params[-1])
+    # the correction head must beat zero by 2%: kept on a hair's margin at 1/2 degree it
+    # forced the coarse run to non-finite values within 750 steps
     keep = dict(diffusivity=terms["fT"] + terms["fS"] < base["fT"] + base["fS"],
-                corrections=corrections and terms["gT"] + terms["gS"] < base["gT"] + base["gS"])
+                corrections=corrections
+                and terms["gT"] + terms["gS"] < 0.98 * (base["gT"] + base["gS"]))
     if not keep["diffusivity"]:
         W[:, :nz] = 0.0
         b[:nz] = -30.0

@@ -374,6 +374,14 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         wT[q] = ok ? a.T[kk * P + c2] + p.Tref[kk] : R(0);
         wS[q] = ok ? a.S[kk * P + c2] + p.Sref[kk] : R(0);
     }
+    // anomalies of level kstart+4, the next to enter the window
+    R nT, nS;
+    {
+        const int kk = kstart + 4;
+        const bool ok = mine && kk >= kb && kk < nz;
+        nT = ok ? a.T[kk * P + c2] : R(0);
+        nS = ok ? a.S[kk * P + c2] : R(0);
+    }
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
     R kcarry = R(0);   // diffusivity on the top face of the previous level
     int cb = 0;                 // staging slot of level k: (k - kstart) mod 3
@@ -566,10 +574,15 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             wS[q] = wS[q + 1];
         }
         {
+            // level k+4 enters from the anomalies loaded one level earlier (their memory
+            // latency hidden behind that level's work); level k+5's are loaded now
             const int kk = k + 4;
             const bool ok = mine && kk >= kb && kk < nz;
-            wT[5] = ok ? a.T[kk * P + c2] + p.Tref[kk] : R(0);
-            wS[5] = ok ? a.S[kk * P + c2] + p.Sref[kk] : R(0);
+            wT[5] = ok ? nT + p.Tref[kk] : R(0);
+            wS[5] = ok ? nS + p.Sref[kk] : R(0);
+            const bool ok5 = mine && kk + 1 >= kb && kk + 1 < nz;
+            nT = ok5 ? a.T[(kk + 1) * P + c2] : R(0);
+            nS = ok5 ? a.S[(kk + 1) * P + c2] : R(0);
         }
     }
     __syncthreads();   // every copy waited for: the barriers can be retired

@@ -42,9 +42,14 @@ def test_vertical_fluxes_beat_the_richardson_closure_on_another_seed(result):
 
 
 @pytest.mark.gpu
-def test_online_runs_stay_finite_and_no_worse(result):
+def test_online_runs_stay_finite_and_beat_the_richardson_closure(result):
+    # coarse runs from the coarse-grained state of the held-out seed, compared with that
+    # run's later coarse-grained states: the learned diffusivity keeps temperature closer
+    # to the fine run at every check (measured: 0.7-1.0% lower RMS over three held-out
+    # seeds, 0.9% with this one); salinity, whose vertical flux the shared diffusivity
+    # fits worse, stays within 0.1%
     assert result["online"]
     for row in result["online"]:
         assert row["finite_learned"] and row["finite_richardson"], row
-        assert row["rms_T_learned"] <= 1.05 * row["rms_T_richardson"], row
-        assert row["rms_S_learned"] <= 1.05 * row["rms_S_richardson"], row
+        assert row["rms_T_learned"] < 0.995 * row["rms_T_richardson"], row
+        assert row["rms_S_learned"] <= 1.001 * row["rms_S_richardson"], row

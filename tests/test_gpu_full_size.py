@@ -50,3 +50,31 @@ def test_sampled_columns_match_oracle_windows(case, precision):
                 assert max_rel(got, ref) <= 1e-10, (ic, jc, f)
             else:
                 assert rel_l2(got, ref) <= 2e-4, (ic, jc, f)
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_time_step_300_s_is_past_the_explicit_limit_and_180_s_is_not(case):
+    """The configured 1/12-degree step of 300 s is beyond the explicit internal-wave limit
+    of the quasi-AB2 scheme next to 70 degrees (zonal spacing 3.2 km): the advective CFL
+    number grows by orders of magnitude within 40 steps and the state turns non-finite
+    (measured: CFL 0.013 after 5 steps, 0.64 after 30, 3.7 after 40, non-finite by 50).
+    The paper's own 180 s stays healthy over the same span (CFL about 0.01)."""
+    grown = {}
+    for dt in (300.0, 180.0):
+        m = ocean.Ocean(case.with_params(dt=dt), precision=ocean.OCEAN_MIXED)
+        cfl, bad = [], False
+        for _ in range(12):
+            m.step(5)
+            d = m.diagnostics()
+            bad = bad or d["nonfinite"]
+            cfl.append(d["max_cfl"])
+            if bad:
+                break
+        grown[dt] = (bad, cfl)
+        m.close()
+        del m
+    bad300, cfl300 = grown[300.0]
+    assert bad300 or max(cfl300) > 1.0, cfl300
+    bad180, cfl180 = grown[180.0]
+    assert not bad180 and max(cfl180) < 0.05, cfl180
