@@ -211,7 +211,7 @@ size_t layout(ocean_t m, char* base) {
     m->lvt = c.take<char>((size_t)OC_LVROW * m->nz * e);
     m->drow = c.take<double>(3 * nr);
     m->dlev = c.take<double>(4 * (size_t)m->nz + 3 * ((size_t)m->nz + 1));
-    m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes()));
+    m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes((long)m->nx * m->ny)));
     m->diag_out = c.take<double>(8);
     m->cl_mu = c.take<float>(6 * (size_t)m->nz);
     m->cl_sigma = c.take<float>(6 * (size_t)m->nz);

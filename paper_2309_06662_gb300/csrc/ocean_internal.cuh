@@ -494,11 +494,10 @@ struct DiagMetrics {
 };
 
 // Conservation/health reduction; `partials` is device scratch of at least
-// diag_partials_bytes() bytes; `out` (device) receives 8 doubles:
+// diag_partials_bytes(nx * ny) bytes; `out` (device) receives 8 doubles:
 // {sum T dV, sum S dV, sum eta dA, KE, max CFL, nonfinite, wet volume, 0}.
-#define OC_DIAG_BLOCKS 456   /* one wave: 3 resident blocks on each of the 152 SMs */
 #define OC_DIAG_THREADS 256
-size_t diag_partials_bytes();
+size_t diag_partials_bytes(long ncol);   // one partial per block of OC_DIAG_THREADS columns
 template <typename R>
 void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v,
                         const R* T, const R* S, const double* eta, double* partials,

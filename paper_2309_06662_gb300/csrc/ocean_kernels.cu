@@ -1532,22 +1532,28 @@ __device__ __forceinline__ void cs_merge(CSum& a, const CSum& b) {
     a.c += b.c;
 }
 
-// Per column: T' dz, S' dz summed in FP64 (one fused multiply-add per cell, exact
-// products), plus the reference part and the volume from the per-kb sums; kinetic energy
-// and the CFL number in the state's own precision; then Neumaier-compensated FP64 sums
-// over the columns.
-template <typename R>
-__global__ void __launch_bounds__(OC_DIAG_THREADS, 3) k_diag_sums(
+// One column per thread: the column's T' dz, S' dz in the path's precision from its
+// lowest wet level (in the mixed form an FP32 sum of at most nz terms, far below the 1e-6
+// the mixed conservation holds to), plus the reference part and the volume from the
+// per-kb sums, in FP64; kinetic energy and the CFL number in the state's own precision.
+// The block's columns are then summed in FP64 by a pairwise tree in a fixed order (warp
+// shuffles, then the eight warp sums): its rounding error is at most log2(256) units of
+// FP64 roundoff of the summed magnitudes, and the cheap FP64 adds keep GB300's slow FP64
+// rate off the path.  The blocks' partial sums are merged with Neumaier compensation by
+// k_diag_final.
+// IDX: the element index type (32-bit offsets when every field fits, fewer registers)
+template <typename R, typename IDX>
+__global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     GeoD g, DiagMetrics m, const R* __restrict__ u, const R* __restrict__ v,
     const R* __restrict__ T, const R* __restrict__ S, const double* __restrict__ eta,
     double* __restrict__ partials) {
-    CSum sT{0, 0}, sS{0, 0}, sE{0, 0}, sK{0, 0}, sV{0, 0};
+    double vT = 0.0, vS = 0.0, vE = 0.0, vK = 0.0, vV = 0.0;
     R cflr = R(0);
     bool bad = false;
     const long ncol = (long)g.nx * g.ny;
-    const R dtr = (R)m.dt, rdyr = (R)m.rdy;
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncol;
-         c += (long)gridDim.x * blockDim.x) {
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncol) {
+        const R dtr = (R)m.dt, rdyr = (R)m.rdy;
         const int i = (int)(c % g.nx), j = (int)(c / g.nx);
         const long c2 = ix2(g, i, j);
         const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
@@ -1559,24 +1565,25 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS, 3) k_diag_sums(
         const R dyr = (R)m.dy, dxvS = (R)m.dxv[j + OC_H], dxvN = (R)m.dxv[j + 1 + OC_H];
         const R rac = (R)(1.0 / m.Ac[j + OC_H]);
         R wk = R(0);
-        // a column's anomaly content in the path's precision (in the mixed form an FP32
-        // sum of at most nz terms, far below the 1e-6 the mixed conservation holds to),
-        // the sums over columns in compensated FP64; land cells hold 0 and are skipped
+        // land cells hold 0 and are skipped
         R tcol = R(0), scol = R(0);
         R ku2 = R(0), kv2 = R(0);
         const int k0 = __reduce_min_sync(__activemask(), min(kb, min(ku, kv)));   // warp-uniform
+        const IDX plane = (IDX)g.plane, pitch = (IDX)g.pitch;
+        IDX ck = (IDX)k0 * plane + (IDX)c2;
 #pragma unroll 4
-        for (int k = k0; k < g.nz; ++k) {
-            const long ck = k * g.plane + c2;
+        for (int k = k0; k < g.nz; ++k, ck += plane) {
             const R tq = T[ck], sq = S[ck], uq = u[ck], vq = v[ck];
-            bad = bad || !isfinite(tq) || !isfinite(sq) || !isfinite(uq) || !isfinite(vq);
+            // one test for the four values (a NaN or infinity in any makes the sum
+            // non-finite; physical values are far from overflowing it)
+            bad = bad || !isfinite(tq + sq + uq + vq);
             const R dzr = (R)m.dz[k];
             if (k >= kb) {
                 tcol = fma(tq, dzr, tcol);
                 scol = fma(sq, dzr, scol);
                 cflr = fmax(cflr, fabs(wk) * (R)m.dtdz[k]);   // w on the level's floor
                 if (k < g.nz - 1) {
-                    const R div = dyr * dzr * (u[ck + 1] - uq) + dzr * (dxvN * v[ck + g.pitch] - dxvS * vq);
+                    const R div = dyr * dzr * (u[ck + 1] - uq) + dzr * (dxvN * v[ck + pitch] - dxvS * vq);
                     wk = wk - div * rac;
                 }
             }
@@ -1590,37 +1597,52 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS, 3) k_diag_sums(
             }
         }
         if (kb < g.nz) {
-            cs_add(sT, ((double)tcol + m.colT[kb]) * ac);
-            cs_add(sS, ((double)scol + m.colS[kb]) * ac);
-            cs_add(sV, m.colV[kb] * ac);
-            cs_add(sE, eta[c2] * ac);
+            vT = ((double)tcol + m.colT[kb]) * ac;
+            vS = ((double)scol + m.colS[kb]) * ac;
+            vV = m.colV[kb] * ac;
+            vE = eta[c2] * ac;
         }
-        cs_add(sK, 0.5 * ((double)ku2 * ac + (double)kv2 * av));
+        vK = 0.5 * ((double)ku2 * ac + (double)kv2 * av);
         bad = bad || !isfinite(eta[c2]);
     }
-    const double cfl = (double)cflr;
-    // block reduction in a fixed order
-    __shared__ CSum red[5][OC_DIAG_THREADS];
-    __shared__ double rc[OC_DIAG_THREADS];
-    __shared__ int rb[OC_DIAG_THREADS];
-    const int t = threadIdx.x;
-    red[0][t] = sT; red[1][t] = sS; red[2][t] = sE; red[3][t] = sK; red[4][t] = sV;
-    rc[t] = cfl;
-    rb[t] = bad ? 1 : 0;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (t < h) {
-            for (int q = 0; q < 5; ++q) cs_merge(red[q][t], red[q][t + h]);
-            rc[t] = fmax(rc[t], rc[t + h]);
-            rb[t] |= rb[t + h];
-        }
-        __syncthreads();
+    double cfl = (double)cflr;
+    int nb = bad ? 1 : 0;
+    // pairwise tree over the warp (lane l adds lane l + off), then over the warps
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        vT += __shfl_down_sync(0xffffffffu, vT, off);
+        vS += __shfl_down_sync(0xffffffffu, vS, off);
+        vE += __shfl_down_sync(0xffffffffu, vE, off);
+        vK += __shfl_down_sync(0xffffffffu, vK, off);
+        vV += __shfl_down_sync(0xffffffffu, vV, off);
+        cfl = fmax(cfl, __shfl_down_sync(0xffffffffu, cfl, off));
+        nb |= __shfl_down_sync(0xffffffffu, nb, off);
     }
-    if (t == 0) {
+    constexpr int NW = OC_DIAG_THREADS / 32;
+    __shared__ double ws[7][NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        ws[0][wid] = vT; ws[1][wid] = vS; ws[2][wid] = vE; ws[3][wid] = vK; ws[4][wid] = vV;
+        ws[5][wid] = cfl; ws[6][wid] = (double)nb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double* o = partials + (long)blockIdx.x * 12;
-        for (int q = 0; q < 5; ++q) { o[2 * q] = red[q][0].s; o[2 * q + 1] = red[q][0].c; }
-        o[10] = rc[0];
-        o[11] = (double)rb[0];
+        for (int q = 0; q < 5; ++q) {
+            double a[NW];
+            for (int w = 0; w < NW; ++w) a[w] = ws[q][w];
+            for (int h = NW / 2; h > 0; h >>= 1)
+                for (int w = 0; w < h; ++w) a[w] += a[w + h];
+            o[2 * q] = a[0];
+            o[2 * q + 1] = 0.0;   // compensation term of the block sum (merged by k_diag_final)
+        }
+        double cm = 0.0, bm = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            cm = fmax(cm, ws[5][w]);
+            bm = fmax(bm, ws[6][w]);
+        }
+        o[10] = cm;
+        o[11] = bm;
     }
 }
 
@@ -1666,14 +1688,21 @@ __global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict_
 
 }  // namespace
 
-size_t diag_partials_bytes() { return (size_t)OC_DIAG_BLOCKS * 12 * sizeof(double); }
+size_t diag_partials_bytes(long ncol) {
+    return (size_t)((ncol + OC_DIAG_THREADS - 1) / OC_DIAG_THREADS) * 12 * sizeof(double);
+}
 
 template <typename R>
 void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R* v, const R* T,
                         const R* S, const double* eta, double* partials, double* out,
                         cudaStream_t s) {
-    k_diag_sums<R><<<OC_DIAG_BLOCKS, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
-    k_diag_final<<<1, FIN_TH, 0, s>>>(partials, OC_DIAG_BLOCKS, out);
+    const long ncol = (long)g.nx * g.ny;
+    const int nblk = (int)((ncol + OC_DIAG_THREADS - 1) / OC_DIAG_THREADS);
+    if ((unsigned long long)g.plane * g.nz < (1ull << 32))
+        k_diag_sums<R, unsigned><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
+    else
+        k_diag_sums<R, long><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
+    k_diag_final<<<1, FIN_TH, 0, s>>>(partials, nblk, out);
 }
 
 // ------------------------------------------------------------------ batched ensemble
