@@ -497,7 +497,7 @@ def other_configs(args, rank, world, local, dist, case12=None):
     if ens is not None:
         out["ensemble_96_basins"] = keep(ens, ["value", "unit", "ms_per_step", "one_by_one",
                                                "roofline", "step_hbm", "e2e", "gpu_launches",
-                                               "clocks", "config"])
+                                               "clocks", "config", "autotune"])
     lrn = learned_main(sub, inputs.latlon_half_case(), WORKLOADS["learned_half"][1], rank, world,
                        local, dist, with_cpu=False)
     torch.cuda.empty_cache()
@@ -649,7 +649,9 @@ def ensemble_main(args, cases, wname, rank, world, local, dist, with_cpu=True):
     wet_cols = sum(roofline.wet_columns(c.depth, c.params["min_depth"], c.z_faces) for c in cases)
     E = ocean.Ensemble(cases)
     stream = torch.cuda.ExternalStream(E.stream)
-    tuned = E.autotune(reps=2)           # real steps: part of the warm-up
+    # real steps, part of the warm-up: the barotropic region shape, then the launch shapes
+    tuned = E.autotune_regions(reps=1)
+    tuned += E.autotune(reps=2)
     E.step(max(1, args.warmup))
     barrier()
     launches0 = E.launches
@@ -697,6 +699,7 @@ def ensemble_main(args, cases, wname, rank, world, local, dist, with_cpu=True):
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     healthy = all(not d["nonfinite"] and d["max_cfl"] < 1.0 for d in diags)
     shapes = E.launch_shapes()
+    region_bs, region_ms = E.region_substeps, E.region_times()
     E.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and with_cpu:
@@ -721,7 +724,9 @@ def ensemble_main(args, cases, wname, rank, world, local, dist, with_cpu=True):
             "one_by_one": {"ms_per_step": ms_seq, "value": cells / (ms_seq / 1e3),
                            "ensemble_speedup": ms_seq / ms},
             "autotune": {"steps": tuned, "shapes": shapes,
-                         "kind_ms": {k: round(v, 4) for k, v in kinds.items()}},
+                         "kind_ms": {k: round(v, 4) for k, v in kinds.items()},
+                         "region_substeps": region_bs,
+                         "region_pass_ms": {str(k): round(v, 4) for k, v in region_ms.items()}},
             "step_hbm": {"algorithmic_bytes": step_bytes,
                          "GBs": step_bytes / (ms_all / 1e3) / 1e9,
                          "frac": step_bytes / (ms_all / 1e3) / 1e9 / peak, "of": peak_src},

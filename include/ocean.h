@@ -426,6 +426,22 @@ int ocean_ensemble_step_async(ocean_ensemble_t e, int n);
  * keeps the fastest per kind and rebuilds the step graphs.  *steps_taken receives the
  * number of steps run (may be NULL). */
 int ocean_ensemble_autotune(ocean_ensemble_t e, int reps, int* steps_taken);
+/* Autotuner of the barotropic region shape, the one-GPU form of the paper's barotropic
+ * halo as wide as the sub-cycle (Sec. "Optimization of ocean free surface dynamics"): a
+ * region of 64 x 32 columns advances bs substeps per pass over HBM, with a halo of bs
+ * columns, so a wider halo means fewer passes but a smaller interior.  For each bs of 4, 6
+ * and 8 it runs reps real steps (they advance the ensemble) and times the sub-cycle's
+ * passes, then keeps the fastest and rebuilds the step graphs.  Results under different bs
+ * agree to rounding (the FP32 partial averages of a pass are added into the FP64
+ * accumulators once per pass), not bit for bit.  *steps_taken may be NULL. */
+int ocean_ensemble_autotune_regions(ocean_ensemble_t e, int reps, int* steps_taken);
+/* The halo width (substeps per pass) in use; set it to 4, 6 or 8 (OCEAN_ERR_ARG
+ * otherwise).  The default is 6, the single model's. */
+int ocean_ensemble_region_substeps(ocean_ensemble_t e);
+int ocean_ensemble_set_region_substeps(ocean_ensemble_t e, int bs);
+/* Best sub-cycle time (ms per step) the region autotuner measured for bs = 4, 6, 8 (three
+ * floats; 0 before tuning). */
+int ocean_ensemble_region_times(ocean_ensemble_t e, float* ms);
 /* Launch shape of each kernel kind (OCEAN_ENS_NKIND entries each): blocks per launch,
  * 1 if the atomic-counter schedule is used, and the number of work items. */
 #define OCEAN_ENS_NKIND 7   /* diag, tracer, momentum, baro begin, baro pass, baro end, correct */

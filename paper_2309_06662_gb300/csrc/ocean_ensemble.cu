@@ -27,6 +27,10 @@ struct ocean_ensemble_s {
     int nlaunch = 0;
     int grid[ENS_NKIND] = {}, dyn[ENS_NKIND] = {}, maxres[ENS_NKIND] = {};
     float tuned_ms[ENS_NKIND] = {};   // best time of each kind's launches in autotuning
+    // barotropic regions: the work lists cut for each halo width of ENS_REGION_BS (after
+    // the other kinds' in d_work) and the one in use
+    int off_bp[3] = {}, cnt_bp[3] = {}, bsi = 1;
+    float region_ms[3] = {};          // best sub-cycle pass time of each halo width
     cudaGraphExec_t graph[2] = {};
     long launches = 0;
 };
@@ -77,14 +81,25 @@ void build_work(ocean_ensemble_t e, std::vector<EnsItem> (&w)[ENS_NKIND]) {
                 w[ENS_TRACER].push_back(it);
                 w[ENS_MOMENTUM].push_back(it);
             }
-        const int nrx = (I.nx + sh.region_x - 1) / sh.region_x;
-        const int nry = (I.ny + sh.region_y - 1) / sh.region_y;
-        for (int ry = 0; ry < nry; ++ry)
-            for (int rx = 0; rx < nrx; ++rx) w[ENS_BARO_PASS].push_back({m, rx, ry, 1});
     }
     for (auto& v : w)
         std::stable_sort(v.begin(), v.end(),
                          [](const EnsItem& a, const EnsItem& b) { return a.cost > b.cost; });
+}
+
+// the barotropic region items of every member for halo width bs (regions of
+// (region_w - 2 bs) x (region_h - 2 bs) interior columns)
+std::vector<EnsItem> region_work(ocean_ensemble_t e, int bs) {
+    const EnsShape sh = ens_shape();
+    const int ix = sh.region_w - 2 * bs, iy = sh.region_h - 2 * bs;
+    std::vector<EnsItem> w;
+    for (int m = 0; m < e->M; ++m) {
+        const OcMemberInfo I = oc_member_info(e->mem[m]);
+        const int nrx = (I.nx + ix - 1) / ix, nry = (I.ny + iy - 1) / iy;
+        for (int ry = 0; ry < nry; ++ry)
+            for (int rx = 0; rx < nrx; ++rx) w.push_back({m, rx, ry, 1});
+    }
+    return w;
 }
 
 // table v (= 2 first + cur) starts at byte v * tab_bytes, where the kernels look for it
@@ -112,13 +127,13 @@ void enqueue_t(ocean_ensemble_t e, int variant, const int* grid, const int* dyn,
         reinterpret_cast<const EnsMember<R>*>(e->d_tab + (size_t)variant * e->tab_bytes);
     cudaMemsetAsync(e->d_counters, 0, sizeof(int) * e->nlaunch, s);
     int li = 0;
+    const int bs = ENS_REGION_BS[e->bsi];
     auto run = [&](int kind, int odd, int nsub) {
         launch_ens<R>(kind, tab, e->d_work + e->off[kind], e->cnt[kind], grid[kind],
-                      dyn[kind] ? e->d_counters + li : nullptr, odd, nsub, s);
+                      dyn[kind] ? e->d_counters + li : nullptr, odd, nsub, bs, s);
         ++li;
     };
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
-    const EnsShape sh = ens_shape();
     mark(0);
     run(ENS_DIAG, 0, 0);
     mark(1);
@@ -128,8 +143,8 @@ void enqueue_t(ocean_ensemble_t e, int variant, const int* grid, const int* dyn,
     mark(3);
     run(ENS_BARO_BEGIN, 0, 0);
     mark(4);
-    for (int p = 0, m0 = 0; m0 < e->ns; ++p, m0 += sh.pass_substeps)
-        run(ENS_BARO_PASS, p & 1, std::min(sh.pass_substeps, e->ns - m0));
+    for (int p = 0, m0 = 0; m0 < e->ns; ++p, m0 += bs)
+        run(ENS_BARO_PASS, p & 1, std::min(bs, e->ns - m0));
     mark(5);
     run(ENS_BARO_END, 0, 0);
     mark(6);
@@ -191,6 +206,20 @@ void default_shapes(ocean_ensemble_t e) {
         e->grid[k] = std::max(1, std::min(e->cnt[k], e->maxres[k] * e->nsm));
         e->dyn[k] = 1;
     }
+}
+
+// use the barotropic regions of halo width ENS_REGION_BS[i]: their work list, the number of
+// passes of a step, and the default launch shape of the pass kind
+void set_region(ocean_ensemble_t e, int i) {
+    e->bsi = i;
+    e->off[ENS_BARO_PASS] = e->off_bp[i];
+    e->cnt[ENS_BARO_PASS] = e->cnt_bp[i];
+    e->npass = (e->ns + ENS_REGION_BS[i] - 1) / ENS_REGION_BS[i];
+    e->nlaunch = 6 + e->npass;
+    const int k = ENS_BARO_PASS;
+    e->grid[k] = std::max(1, std::min(e->cnt[k], e->maxres[k] * e->nsm));
+    e->dyn[k] = 1;
+    drop_graphs(e);
 }
 
 }  // namespace
@@ -261,14 +290,20 @@ int ocean_ensemble_create(int members, const ocean_grid* grids, const double* co
         e->cnt[k] = (int)w[k].size();
         all.insert(all.end(), w[k].begin(), w[k].end());
     }
-    const EnsShape sh = ens_shape();
-    e->npass = (e->ns + sh.pass_substeps - 1) / sh.pass_substeps;
-    e->nlaunch = 6 + e->npass;
+    int max_launch = 0;
+    for (int i = 0; i < 3; ++i) {
+        const std::vector<EnsItem> r = region_work(e, ENS_REGION_BS[i]);
+        e->off_bp[i] = (int)all.size();
+        e->cnt_bp[i] = (int)r.size();
+        all.insert(all.end(), r.begin(), r.end());
+        max_launch = std::max(max_launch, 6 + (e->ns + ENS_REGION_BS[i] - 1) / ENS_REGION_BS[i]);
+        if (ENS_REGION_BS[i] == ens_shape().pass_substeps) e->bsi = i;
+    }
     e->tab_bytes = align256(members * (e->prec == OCEAN_FP64 ? sizeof(EnsMember<double>)
                                                             : sizeof(EnsMember<float>)));
     if ((ce = cudaMalloc(&e->d_tab, 4 * e->tab_bytes)) != cudaSuccess ||
         (ce = cudaMalloc(&e->d_work, all.size() * sizeof(EnsItem))) != cudaSuccess ||
-        (ce = cudaMalloc(&e->d_counters, sizeof(int) * e->nlaunch)) != cudaSuccess)
+        (ce = cudaMalloc(&e->d_counters, sizeof(int) * max_launch)) != cudaSuccess)
         return bail(efail(OCEAN_ERR_OOM, "ensemble tables: %s", cudaGetErrorString(ce)));
     ce = cudaMemcpy(e->d_work, all.data(), all.size() * sizeof(EnsItem), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return bail(efail(OCEAN_ERR_CUDA, "work list upload: %s", cudaGetErrorString(ce)));
@@ -281,6 +316,7 @@ int ocean_ensemble_create(int members, const ocean_grid* grids, const double* co
         e->maxres[k] = e->prec == OCEAN_FP64 ? ens_blocks_per_sm<double>(k) : ens_blocks_per_sm<float>(k);
         if (e->maxres[k] < 1) return bail(efail(OCEAN_ERR_CUDA, "ensemble kernel %d cannot be resident", k));
     }
+    set_region(e, e->bsi);
     default_shapes(e);
     *out = e;
     return OCEAN_OK;
@@ -389,6 +425,62 @@ int ocean_ensemble_autotune(ocean_ensemble_t e, int reps, int* steps_taken) {
         e->tuned_ms[k] = ms[k][b];
     }
     drop_graphs(e);
+    return OCEAN_OK;
+}
+
+int ocean_ensemble_autotune_regions(ocean_ensemble_t e, int reps, int* steps_taken) {
+    if (!e) return efail(OCEAN_ERR_ARG, "null ensemble");
+    if (reps < 1) return efail(OCEAN_ERR_ARG, "reps must be >= 1");
+    if (steps_taken) *steps_taken = 0;
+    cudaEvent_t ev[8];
+    for (auto& x : ev) cudaEventCreate(&x);
+    int rc = OCEAN_OK, taken = 0;
+    for (int i = 0; i < 3 && rc == OCEAN_OK; ++i) {
+        if (ENS_REGION_BS[i] > e->ns && i != e->bsi) {   // a wider halo than the sub-cycle
+            e->region_ms[i] = 3.4e38f;
+            continue;
+        }
+        set_region(e, i);
+        float ms = 3.4e38f;
+        for (int r = 0; r < reps && rc == OCEAN_OK; ++r) {
+            rc = step_one(e, e->grid, e->dyn, ev);
+            if (rc) break;
+            ++taken;
+            if (cudaEventSynchronize(ev[7]) != cudaSuccess) {
+                rc = efail(OCEAN_ERR_CUDA, "region autotune step failed: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ev[4], ev[5]);   // the sub-cycle's passes
+            ms = std::min(ms, x);
+        }
+        e->region_ms[i] = ms;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (steps_taken) *steps_taken = taken;
+    if (rc) return rc;
+    int b = 0;
+    for (int i = 1; i < 3; ++i)
+        if (e->region_ms[i] < e->region_ms[b]) b = i;
+    set_region(e, b);
+    return OCEAN_OK;
+}
+
+int ocean_ensemble_region_substeps(ocean_ensemble_t e) { return e ? ENS_REGION_BS[e->bsi] : 0; }
+
+int ocean_ensemble_set_region_substeps(ocean_ensemble_t e, int bs) {
+    if (!e) return efail(OCEAN_ERR_ARG, "null ensemble");
+    for (int i = 0; i < 3; ++i)
+        if (ENS_REGION_BS[i] == bs) {
+            set_region(e, i);
+            return OCEAN_OK;
+        }
+    return efail(OCEAN_ERR_ARG, "region substeps %d: choose 4, 6 or 8", bs);
+}
+
+int ocean_ensemble_region_times(ocean_ensemble_t e, float* ms) {
+    if (!e || !ms) return efail(OCEAN_ERR_ARG, "null argument");
+    for (int i = 0; i < 3; ++i) ms[i] = e->region_ms[i];
     return OCEAN_OK;
 }
 

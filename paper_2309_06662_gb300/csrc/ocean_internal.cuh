@@ -551,17 +551,24 @@ enum {
 };
 // Units of work: columns per chunk of the column kernels, tile and region interiors,
 // substeps per barotropic pass, levels per slab of the correction.
-struct EnsShape { int chunk, tile_x, tile_y, region_x, region_y, pass_substeps, corr_slab; };
+// chunk: columns of a 2-D item; tile_x, tile_y: a tile item's columns; region_w, region_h:
+// a barotropic region including its halo; pass_substeps: the default halo width (= the
+// substeps of one pass); corr_slab: levels of a correction item
+struct EnsShape { int chunk, tile_x, tile_y, region_w, region_h, pass_substeps, corr_slab; };
+// halo widths (substeps per barotropic pass) the ensemble's autotuner chooses among; a
+// region's interior is (region_w - 2 bs) x (region_h - 2 bs)
+constexpr int ENS_REGION_BS[3] = {4, 6, 8};
 EnsShape ens_shape();
 // Resident blocks per SM of each ensemble kernel (occupancy calculator).
 template <typename R> int ens_blocks_per_sm(int kind);
 // One persistent launch of kind `kind` over work[0..nwork): `grid` blocks; items taken in
 // order from an atomic counter if `counter` (zeroed beforehand), else blockIdx.x +
 // n gridDim.x.  For ENS_BARO_PASS: `odd` selects the ping-pong direction, `nsub` the
-// substeps of this pass.
+// substeps of this pass (at most `bs`, the halo width of the regions the work items were
+// cut for).
 template <typename R>
 void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwork, int grid,
-                int* counter, int odd, int nsub, cudaStream_t s);
+                int* counter, int odd, int nsub, int bs, cudaStream_t s);
 
 // Model internals the ensemble builds on (ocean_api.cu): a model in a caller-provided
 // arena on a caller's stream; its sizes and step state; the lowest wet level of column

@@ -1109,7 +1109,7 @@ __device__ __forceinline__ void baro_region(
     const R* __restrict__ Hu, const R* __restrict__ Hv, const R* __restrict__ GU,
     const R* __restrict__ GV, const R* __restrict__ Un, const R* __restrict__ Vn,
     double* __restrict__ accE, double* __restrict__ accU, double* __restrict__ accV, int nsub,
-    R dtau, R grav, const R* __restrict__ fw = nullptr) {
+    R dtau, R grav, const int bs, const R* __restrict__ fw = nullptr) {
     extern __shared__ __align__(16) unsigned char bsm[];
     R* sE = reinterpret_cast<R*>(bsm);
     R* sU = sE + BRX * BRY;
@@ -1119,8 +1119,8 @@ __device__ __forceinline__ void baro_region(
     R* sCe = sDS + BRY;
     const GeoD& g = p.g;
     const int tid = threadIdx.x;
-    const int IX = BRX - 2 * BS, IY = BRY - 2 * BS;
-    const int i0 = bx * IX - BS, j0 = by * IY - BS;   // region origin
+    const int IX = BRX - 2 * bs, IY = BRY - 2 * bs;   // interior; the halo is bs >= nsub wide
+    const int i0 = bx * IX - bs, j0 = by * IY - bs;   // region origin
     // a thread owns the cells (rx, ry0 + r), r < BC, of one region column: consecutive
     // rows, so the state of its inner cells' north and south neighbours is in its own
     // registers; shared memory carries what the neighbouring threads read
@@ -1142,7 +1142,7 @@ __device__ __forceinline__ void baro_region(
         const int ry = ry0 + r, q = ry * BRX + rx;
         int jw = 0;
         const long c = wrap_ix(g, i0 + rx, j0 + ry, jw);
-        const bool own = rx >= BS && rx < BRX - BS && ry >= BS && ry < BRY - BS &&
+        const bool own = rx >= bs && rx < BRX - bs && ry >= bs && ry < BRY - bs &&
                          i0 + rx < g.nx && j0 + ry < g.ny;
         ownm |= (own ? 1u : 0u) << r;
         pE[r] = pU[r] = pV[r] = R(0);
@@ -1237,7 +1237,7 @@ __global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_baro_pass(
     const R* __restrict__ Vn, double* __restrict__ accE, double* __restrict__ accU,
     double* __restrict__ accV, int nsub, R dtau, R grav, const R* __restrict__ fw) {
     baro_region<R, WEIGHTED>(p, blockIdx.x, blockIdx.y, Ea, Ua, Va, Eb, Ub, Vb, gxe, gye, Hu, Hv,
-                             GU, GV, Un, Vn, accE, accU, accV, nsub, dtau, grav, fw);
+                             GU, GV, Un, Vn, accE, accU, accV, nsub, dtau, grav, BS, fw);
 }
 
 // eta^{n+1} = eta^n + sum_m a_m deta^m in FP64; correction of the depth-integrated
@@ -1787,7 +1787,7 @@ template <typename R>
 __global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_ens_baro_pass(const EnsMember<R>* __restrict__ mem,
                                                        const EnsItem* __restrict__ work,
                                                        int nwork, int* counter, int odd,
-                                                       int nsub) {
+                                                       int nsub, int bs) {
     __shared__ int s_next;
     for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
         const EnsItem e = work[it];
@@ -1800,7 +1800,7 @@ __global__ void __launch_bounds__(BNT, BaroOcc<R>::value) k_ens_baro_pass(const 
             Eb = b.dE; Ub = b.Ub; Vb = b.Vb;
         }
         baro_region<R>(p, e.a, e.b, Ea, Ua, Va, Eb, Ub, Vb, b.gxe, b.gye, b.Hu, b.Hv, b.GU, b.GV,
-                       b.Un, b.Vn, b.accE, b.accU, b.accV, nsub, dtau, p.grav);
+                       b.Un, b.Vn, b.accE, b.accU, b.accV, nsub, dtau, p.grav, bs);
     }
 }
 
@@ -1833,7 +1833,7 @@ __global__ void __launch_bounds__(TPB) k_ens_correct(const EnsMember<R>* __restr
 
 }  // namespace
 
-EnsShape ens_shape() { return EnsShape{TPB, TX, TY, BRX - 2 * BS, BRY - 2 * BS, BS, CORR_SLAB}; }
+EnsShape ens_shape() { return EnsShape{TPB, TX, TY, BRX, BRY, BS, CORR_SLAB}; }
 
 template <typename R>
 int ens_blocks_per_sm(int kind) {
@@ -1857,7 +1857,7 @@ int ens_blocks_per_sm(int kind) {
 
 template <typename R>
 void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwork, int grid,
-                int* counter, int odd, int nsub, cudaStream_t s) {
+                int* counter, int odd, int nsub, int bs, cudaStream_t s) {
     if (nwork <= 0 || grid <= 0) return;
     const dim3 tile(TX, TY);
     switch (kind) {
@@ -1867,7 +1867,7 @@ void launch_ens(int kind, const EnsMember<R>* mem, const EnsItem* work, int nwor
         case ENS_BARO_BEGIN: k_ens_baro_begin<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
         case ENS_BARO_PASS:
             k_ens_baro_pass<R><<<grid, BNT, baro_smem<R>(), s>>>(
-                mem, work, nwork, counter, odd, nsub);
+                mem, work, nwork, counter, odd, nsub, bs);
             break;
         case ENS_BARO_END: k_ens_baro_end<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
         case ENS_CORRECT: k_ens_correct<R><<<grid, TPB, 0, s>>>(mem, work, nwork, counter); break;
@@ -1920,7 +1920,7 @@ int tile_wait_failed() {
                                         cudaStream_t);                \
     template int ens_blocks_per_sm<R>(int);                                                 \
     template void launch_ens<R>(int, const EnsMember<R>*, const EnsItem*, int, int, int*,   \
-                                int, int, cudaStream_t);
+                                int, int, int, cudaStream_t);
 
 OC_INST(double)
 OC_INST(float)

@@ -148,6 +148,10 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_ensemble_step": (c_int, [pv, c_int]),
             "ocean_ensemble_step_async": (c_int, [pv, c_int]),
             "ocean_ensemble_autotune": (c_int, [pv, c_int, POINTER(c_int)]),
+            "ocean_ensemble_autotune_regions": (c_int, [pv, c_int, POINTER(c_int)]),
+            "ocean_ensemble_region_substeps": (c_int, [pv]),
+            "ocean_ensemble_set_region_substeps": (c_int, [pv, c_int]),
+            "ocean_ensemble_region_times": (c_int, [pv, POINTER(ctypes.c_float)]),
             "ocean_ensemble_launch_shapes": (c_int, [pv, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
             "ocean_ensemble_kernel_launches": (c_long, [pv]),
             "ocean_ensemble_kind_times": (c_int, [pv, pd]),
@@ -648,6 +652,27 @@ class Ensemble:
         n = c_int()
         _check(load().ocean_ensemble_autotune(self._h, int(reps), ctypes.byref(n)))
         return n.value
+
+    def autotune_regions(self, reps: int = 1) -> int:
+        """Tune the barotropic region's halo width (substeps per pass: 4, 6 or 8) on real
+        steps; returns the number of steps taken."""
+        n = c_int()
+        _check(load().ocean_ensemble_autotune_regions(self._h, int(reps), ctypes.byref(n)))
+        return n.value
+
+    @property
+    def region_substeps(self) -> int:
+        return load().ocean_ensemble_region_substeps(self._h)
+
+    @region_substeps.setter
+    def region_substeps(self, bs: int) -> None:
+        _check(load().ocean_ensemble_set_region_substeps(self._h, int(bs)))
+
+    def region_times(self):
+        """Sub-cycle ms per step measured by autotune_regions for halo widths 4, 6, 8."""
+        ms = (ctypes.c_float * 3)()
+        _check(load().ocean_ensemble_region_times(self._h, ms))
+        return dict(zip((4, 6, 8), [float(x) for x in ms]))
 
     def launch_shapes(self):
         g, d, w = ((c_int * len(ENS_KINDS))() for _ in range(3))

@@ -117,3 +117,43 @@ def test_member_diagnostics_and_checkpoint():
             assert np.array_equal(a.get(f), b.get(f)), f
     E.close()
     E2.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_region_halo_widths_agree_to_rounding(precision):
+    # the barotropic regions cut for 4 and 8 substeps per pass against the default 6: the
+    # same sub-cycle, with the FP32 partial averages added into the FP64 accumulators at
+    # other substeps (in FP64 the groupings differ only in the last bits)
+    cases = _cases(count=5, seed=45)
+    D = ocean.Ensemble(cases, precision=precision)
+    assert D.region_substeps == 6
+    D.step(6)
+    tol = 1e-5 if precision == ocean.OCEAN_MIXED else 1e-13
+    for bs in (4, 8):
+        E = ocean.Ensemble(cases, precision=precision)
+        E.region_substeps = bs
+        assert E.region_substeps == bs
+        E.step(6)
+        assert E.launches == 6 * (6 + -(-30 // bs))
+        for a, b in zip(E.members, D.members):
+            for f in FIELDS:
+                assert max_rel(a.get(f), b.get(f)) <= tol, (bs, f)
+        E.close()
+    D.close()
+
+
+@pytest.mark.gpu
+def test_region_autotuner_keeps_the_fastest_halo_width():
+    cases = _cases(count=5, seed=46)
+    E = ocean.Ensemble(cases)
+    n = E.autotune_regions(reps=2)
+    assert n == 6
+    times = E.region_times()
+    assert all(t > 0 for t in times.values()), times
+    assert E.region_substeps == min(times, key=times.get)
+    E.step(2)
+    assert not any(m.diagnostics()["nonfinite"] for m in E.members)
+    with pytest.raises(ocean.OceanError):
+        E.region_substeps = 5
+    E.close()
