@@ -637,9 +637,14 @@ bool build_tile_maps(ocean_t m) {
                                         (unsigned long long)m->nz};
     const unsigned long long strides[2] = {(unsigned long long)m->pitch * m->esz,
                                            (unsigned long long)m->plane * m->esz};
-    const unsigned boxTS[3] = {40, 14, 1}, boxU[3] = {36, 8, 1}, boxV[3] = {32, 9, 1},
-                   boxMU[3] = {40, 14, 1}, boxMV[3] = {40, 13, 1}, boxC[3] = {36, 9, 1},
-                   boxO[3] = {32, 8, 1};
+    // boxes of one level: the tracer's T, S with a 3-cell halo read from i0 - 4 (a 16-byte
+    // aligned start), its u- and v-face velocities; the momentum's u (rows j0-3 ..), v
+    // (rows j0-2 ..), the centred p, w, nu (rows j0-1 ..); the block's own columns
+    const unsigned TXu = OC_TX, TYu = OC_TY;
+    const unsigned boxTS[3] = {TXu + 8, TYu + 6, 1}, boxU[3] = {TXu + 4, TYu, 1},
+                   boxV[3] = {TXu, TYu + 1, 1}, boxMU[3] = {TXu + 8, TYu + 6, 1},
+                   boxMV[3] = {TXu + 8, TYu + 5, 1}, boxC[3] = {TXu + 4, TYu + 1, 1},
+                   boxO[3] = {TXu, TYu, 1};
     const CUtensorMapSwizzle no = CU_TENSOR_MAP_SWIZZLE_NONE;
     for (int c = 0; c < 2; ++c) {
         TileMaps& t = m->tmaps[c];

@@ -13,6 +13,10 @@
 // Horizontal halo width of every padded field: five-point WENO stencils reach three
 // cells beyond a face, staggered averages one more.
 #define OC_H 4
+// Columns of one block of the 2.5-D tracer and momentum tiles (x by y); the host's tensor
+// maps use the same numbers for their boxes.
+#define OC_TX 32
+#define OC_TY 8
 // Largest number of levels the column kernels accept.
 #define OC_NZMAX 192
 

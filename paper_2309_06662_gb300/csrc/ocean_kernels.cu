@@ -176,17 +176,25 @@ __global__ void __launch_bounds__(TPB) k_diag(KP<R> p, const R* __restrict__ u,
 // stencils use a per-thread register window.  The Thomas coefficients of the implicit
 // solve go to global scratch (one value per level and column, written and read back by
 // the same thread, so they stay in L2).
-constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int TX = OC_TX, TY = OC_TY, NT = TX * TY;
+// rows of the momentum's centred tiles (TY + 1 used), a multiple of 8 so that each slot
+// (rows x (TX + 4) FP32 values) is a multiple of 128 bytes
+constexpr int PROWS = (TY + 1 + 7) / 8 * 8;
+static_assert(TX == 32 && (TY == 8 || TY == 16), "tile shapes the kernels are written for");
+static_assert((TY + 8) * (TX + 8) * 4 % 128 == 0 && TY * (TX + 4) * 4 % 128 == 0 &&
+              (TY + 1) * TX * 4 % 128 == 0 && TY * TX * 4 % 128 == 0 &&
+              PROWS * (TX + 4) * 4 % 128 == 0, "tensor-copy slots on 128-byte boundaries");
 // The tracer block has one more warp: its 8 x 33 x-faces and 9 x 32 y-faces (552 WENO
 // pairs per level) then take two per thread of 288 instead of up to three of 256; the
 // extra warp owns no column and only computes faces.
 constexpr int TTY = TY + 1, NTT = TX * TTY;
 // resident blocks per SM the register budget is sized for: the FP32 momentum and tracer
 // tiles fit 64 and 56 registers (four blocks per SM); the FP64 tiles need far more
-template <typename R> struct Occ4 { static constexpr int value = 4; };
+template <typename R> struct Occ4 { static constexpr int value = TY == 8 ? 4 : 2; };
 template <> struct Occ4<double> { static constexpr int value = 1; };
 // the variants with the optional vertical schemes keep more registers: 3 blocks per SM
-template <typename R, bool X> struct OccX { static constexpr int value = X ? 3 : Occ4<R>::value; };
+// of the 32 x 8 tiles
+template <typename R, bool X> struct OccX { static constexpr int value = X ? (TY == 8 ? 3 : 1) : Occ4<R>::value; };
 template <bool X> struct OccX<double, X> { static constexpr int value = 1; };
 
 // padded index of (i, j), clamped into the allocated halo: tiles at the ragged edge of
@@ -333,7 +341,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     // triple buffered, as tensor copies one thread issues per level (rows and columns
     // beyond the arrays arrive as zeros and feed only threads outside the domain)
     constexpr unsigned STAGE_BYTES =
-        (unsigned)sizeof(R) * (2u * 14u * 40u + (unsigned)TY * 36u + (unsigned)(TY + 1) * TX);
+        (unsigned)sizeof(R) * (2u * (TY + 6) * (TX + 8) + (unsigned)TY * (TX + 4) + (unsigned)(TY + 1) * TX);
     constexpr unsigned OWN_BYTES = (unsigned)sizeof(R) * TY * TX;
     if (tid == 0) {
         bar_init(&sm.bar[0]);
@@ -632,9 +640,9 @@ template <typename R>
 struct __align__(128) MomentumSmem {
     R u[3][TY + 8][TX + 8];   // u at i in [i0-2, i0+TX+3), j in [j0-3, j0+TY+3)
     R v[3][TY + 8][TX + 8];   // v at i in [i0-3, i0+TX+3), j in [j0-2, j0+TY+3)
-    R p[3][2 * TY][TX + 4];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
-    R w[3][2 * TY][TX + 4];   // w on the level's bottom faces, same centres
-    R nu[3][2 * TY][TX + 4];  // nu on those faces
+    R p[3][PROWS][TX + 4];   // pressure anomaly at centres i in [i0-1, i0+TX), j in [j0-1, j0+TY)
+    R w[3][PROWS][TX + 4];   // w on the level's bottom faces, same centres
+    R nu[3][PROWS][TX + 4];  // nu on those faces
     R gu[3][TY][TX], gv[3][TY][TX];   // own columns' G_u, G_v of the previous step
     unsigned long long bar[3];        // slot s's copies have landed
     // corner vorticity, i in [i0-2, i0+TX+3), j in [j0-2, j0+TY+3), and the kinetic energy
@@ -691,7 +699,8 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
     // Level k's own cells read its slot and level k+1's (a.u, a.v above, a.w and a.nu on the top
     // face).
     constexpr int TC = (TY + 1) * (TX + 1);   // centres of the pressure / a.w / a.nu tiles
-    constexpr unsigned TILES = (unsigned)sizeof(R) * (40u * 14u + 40u * 13u + 3u * 36u * 9u);
+    constexpr unsigned TILES = (unsigned)sizeof(R) * ((TX + 8) * (TY + 6) + (TX + 8) * (TY + 5) +
+                                                      3u * (TX + 4) * (TY + 1));
     constexpr unsigned OWN = (unsigned)sizeof(R) * TY * TX;
     const int yu = j0 + OC_H - 3, yv = j0 + OC_H - 2, yc = j0 + OC_H - 1;
     auto stage = [&](int k, int sl) {
@@ -1646,9 +1655,44 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     }
 }
 
+// One block merges FIN_TH consecutive partials (of the first nblk) into partial blockIdx.x
+// of `merged`, with compensation, in a fixed tree: the FP64 work of the merge spread over
+// the GPU instead of one SM.
+constexpr int FIN_TH = 256;
+__global__ void __launch_bounds__(FIN_TH) k_diag_merge(const double* __restrict__ partials,
+                                                       int nblk, double* __restrict__ merged) {
+    __shared__ CSum red[5][FIN_TH];
+    __shared__ double rc[FIN_TH], rb[FIN_TH];
+    const int t = threadIdx.x;
+    const long b = (long)blockIdx.x * FIN_TH + t;
+    for (int q = 0; q < 5; ++q) red[q][t] = CSum{0, 0};
+    rc[t] = 0.0;
+    rb[t] = 0.0;
+    if (b < nblk) {
+        const double* o = partials + b * 12;
+        for (int q = 0; q < 5; ++q) red[q][t] = CSum{o[2 * q], o[2 * q + 1]};
+        rc[t] = o[10];
+        rb[t] = o[11];
+    }
+    __syncthreads();
+    for (int h = FIN_TH / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int q = 0; q < 5; ++q) cs_merge(red[q][t], red[q][t + h]);
+            rc[t] = fmax(rc[t], rc[t + h]);
+            rb[t] = fmax(rb[t], rb[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double* o = merged + (long)blockIdx.x * 12;
+        for (int q = 0; q < 5; ++q) { o[2 * q] = red[q][0].s; o[2 * q + 1] = red[q][0].c; }
+        o[10] = rc[0];
+        o[11] = rb[0];
+    }
+}
+
 // the per-block partial sums merged in a fixed tree: each of 256 threads merges
 // nblk / 256 consecutive partials, then pairs of threads halve the set
-constexpr int FIN_TH = 256;
 __global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict__ partials,
                                                        int nblk, double* out) {
     __shared__ CSum red[5][FIN_TH];
@@ -1689,7 +1733,9 @@ __global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict_
 }  // namespace
 
 size_t diag_partials_bytes(long ncol) {
-    return (size_t)((ncol + OC_DIAG_THREADS - 1) / OC_DIAG_THREADS) * 12 * sizeof(double);
+    const long nblk = (ncol + OC_DIAG_THREADS - 1) / OC_DIAG_THREADS;
+    const long nmrg = (nblk + FIN_TH - 1) / FIN_TH;
+    return (size_t)(nblk + nmrg) * 12 * sizeof(double);
 }
 
 template <typename R>
@@ -1702,7 +1748,11 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
         k_diag_sums<R, unsigned><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
     else
         k_diag_sums<R, long><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
-    k_diag_final<<<1, FIN_TH, 0, s>>>(partials, nblk, out);
+    // the block partials merged by blocks of FIN_TH, then those by one block
+    const int nmrg = (nblk + FIN_TH - 1) / FIN_TH;
+    double* merged = partials + (long)nblk * 12;
+    k_diag_merge<<<nmrg, FIN_TH, 0, s>>>(partials, nblk, merged);
+    k_diag_final<<<1, FIN_TH, 0, s>>>(merged, nmrg, out);
 }
 
 // ------------------------------------------------------------------ batched ensemble
