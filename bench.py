@@ -618,7 +618,7 @@ def learned_main(args, case, wname, rank, world, local, dist, with_cpu=True):
             "sypd": metrics.sypd(p["dt"], ms / 1e3),
             "richardson_only": {"ms_per_step": res["richardson"]["ms"],
                                 "closure_overhead_ms": ms - res["richardson"]["ms"]},
-            "roofline": {"bound": "tensor", "kernel": "k_gemm_nt_pers (4-GEMM chain)",
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_fused (whole network per 128-column tile)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "algorithmic_flops_per_chain": flops, "ms_per_chain": ms_net,

@@ -791,6 +791,282 @@ void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int 
     gemm_nt(A, lda, B, ldb, M, N, K, e, s);
 }
 
+// ------------------------------------------------------------------ fused forward pass
+//
+// The whole network on one 128-column tile without leaving the SM: the hidden activations
+// stay in shared memory, written by the epilogue in the 128-byte-swizzled K-major layout
+// the next layer's MMAs read as their A operand, so HBM sees only the features in and the
+// outputs out (the four separate GEMMs move every hidden layer through HBM twice).  Per
+// tile and layer: warp 0 streams the layer's weight K-blocks (64 inputs x up to 256
+// outputs, BF16, from L2: the same weights serve every tile) and, for the first layer,
+// the tile's feature K-blocks into a ring of FM_S stages; warp 1 issues the MMAs
+// (M 128, N the layer's width, K 16) into one TMEM accumulator of up to 256 columns;
+// warps 2..9 drain it (bias + SiLU to BF16 into the activation tile, or bias to FP32 rows
+// of Y for the last layer).  Barriers: full/empty per stage; accf (the layer's MMAs
+// done), acce (its eight epilogue warps done: TMEM drained and the activation tile
+// written).  Every wait is bounded as in k_gemm_nt_pers.
+constexpr int FM_S = 3, FM_EW = 8, FM_TH = (2 + FM_EW) * 32;
+constexpr int FM_ACT = 4 * TILE_BYTES;                 // 128 rows x 256 BF16: four K-blocks
+constexpr int FM_B = 256 * TBK * 2;                    // up to 256 weight rows x 64 BF16
+constexpr int FM_STAGE = TILE_BYTES + FM_B;            // feature block + weight block
+constexpr size_t FM_SMEM = 1024 + FM_ACT + FM_S * (size_t)FM_STAGE + 4 * 256 * 4 + 256;
+static_assert(FM_SMEM <= 227 * 1024, "fused network's shared memory");
+
+struct FusedMaps {
+    CUtensorMap X, W[4];   // features [M][K0] (boxes 64 x 128), W_l^T [N_l][K_l] (64 x NB_l)
+};
+struct FusedArgs {
+    const float* bias[4];
+    float* Y;
+    int ldY, M, K0, H, N4;
+};
+
+__device__ __forceinline__ unsigned fm_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(TBM >> 4) << 24);
+}
+
+// byte offset of (row r, column c) of a BF16 tile in the 128-byte-swizzled K-major layout
+// of K-blocks of 64 columns: 8-row atoms of 1024 bytes, the 16-byte chunk of each row
+// rotated by the row within its atom (the layout TMA writes with SWIZZLE_128B)
+__device__ __forceinline__ unsigned sw128_offset(int r, int c) {
+    const int kb = c >> 6, j = (c & 63) >> 3;
+    return (unsigned)(kb * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) +
+                      (c & 7) * 2);
+}
+
+__global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ FusedMaps tm,
+                                                        FusedArgs a) {
+    extern __shared__ unsigned char fm_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        ((unsigned long long)fm_raw + 1023) & ~1023ull);
+    unsigned char* act = base;
+    auto sA = [&](int st) { return base + FM_ACT + st * FM_STAGE; };
+    auto sB = [&](int st) { return base + FM_ACT + st * FM_STAGE + TILE_BYTES; };
+    float* sbias = reinterpret_cast<float*>(base + FM_ACT + FM_S * FM_STAGE);   // [4][256]
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sbias + 4 * 256);
+    unsigned long long* empty = full + FM_S;
+    unsigned long long* accf = empty + FM_S;
+    unsigned long long* acce = accf + 1;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(acce + 1);
+    volatile int* abandon = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // layer shapes: inputs K_l, outputs N_l (the MMA width NB_l rounded up to 16)
+    const int Kl[4] = {a.K0, a.H, a.H, a.H}, Nl[4] = {a.H, a.H, a.H, a.N4};
+    int NB[4], nkb[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        NB[l] = (Nl[l] + 15) & ~15;
+        nkb[l] = (Kl[l] + TBK - 1) / TBK;
+    }
+    const int ntiles = (a.M + TBM - 1) / TBM;
+
+    for (int q = tid; q < 4 * 256; q += FM_TH) {
+        const int l = q >> 8, c = q & 255;
+        sbias[q] = c < Nl[l] ? a.bias[l][c] : 0.f;
+    }
+    // the activation tile's columns at and beyond H are never written: zero them once
+    for (int q = tid; q < FM_ACT / 16; q += FM_TH)
+        reinterpret_cast<uint4*>(act)[q] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int st = 0; st < FM_S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(acce)),
+                     "r"((unsigned)FM_EW));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abandon = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // the zeroed activation tile is read by the tensor cores (the async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---- copies: per tile and layer the weight (and feature) K-blocks
+            int g = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x) {
+                const int m0 = t * TBM;
+                for (int l = 0; l < 4 && !*abandon; ++l)
+                    for (int kb = 0; kb < nkb[l]; ++kb, ++g) {
+                        const int st = g % FM_S, use = g / FM_S;
+                        if (g >= FM_S &&
+                            !pg_wait(smem_u32(&empty[st]), (unsigned)(use - 1) & 1u, abandon))
+                            break;
+                        const unsigned bytes = (unsigned)NB[l] * TBK * 2 + (l == 0 ? (unsigned)TILE_BYTES : 0u);
+                        mbar_expect(smem_u32(&full[st]), bytes);
+                        if (l == 0) tma_load_2d(smem_u32(sA(st)), &tm.X, kb * TBK, m0, smem_u32(&full[st]));
+                        tma_load_2d(smem_u32(sB(st)), &tm.W[l], kb * TBK, 0, smem_u32(&full[st]));
+                    }
+            }
+            // copies still in flight when the block gave up: wait (bounded) for them
+            if (*abandon)
+                for (int gg = (g > FM_S ? g - FM_S : 0); gg < g; ++gg) {
+                    const long long t0 = clock64();
+                    unsigned ok = 0;
+                    while (!ok && clock64() - t0 < 2000000000LL)
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                            " selp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(ok)
+                            : "r"(smem_u32(&full[gg % FM_S])), "r"((unsigned)(gg / FM_S) & 1u)
+                            : "memory");
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---- MMAs: layer l of tile t is accumulator use u = 4 t' + l
+            int g = 0, u = 0;
+            bool fine = true;
+            for (int t = blockIdx.x; t < ntiles && fine; t += gridDim.x)
+                for (int l = 0; l < 4 && fine; ++l, ++u) {
+                    // the epilogue of the previous use has drained TMEM and, for l > 0,
+                    // written this layer's input into the activation tile
+                    if (u >= 1 && !pg_wait(smem_u32(acce), (unsigned)(u - 1) & 1u, abandon)) {
+                        fine = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned idesc = fm_idesc(NB[l]);
+                    for (int kb = 0; kb < nkb[l]; ++kb, ++g) {
+                        const int st = g % FM_S;
+                        if (!pg_wait(smem_u32(&full[st]), (unsigned)(g / FM_S) & 1u, abandon)) {
+                            fine = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const unsigned long long ad =
+                            sw128_desc(smem_u32(l == 0 ? sA(st) : act + kb * TILE_BYTES));
+                        const unsigned long long bd = sw128_desc(smem_u32(sB(st)));
+#pragma unroll
+                        for (int k = 0; k < TBK / 16; ++k) {
+                            const unsigned acc = (kb > 0 || k > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                "l"(ad + 2ull * k), "l"(bd + 2ull * k), "r"(idesc), "r"(acc));
+                        }
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                smem_u32(&empty[st]))
+                            : "memory");
+                    }
+                    if (!fine) break;
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                            smem_u32(accf))
+                        : "memory");
+                }
+        }
+    } else {   // ---- epilogue: warps 2..9, TMEM lanes 32 (warp % 4) .., alternate 32-column chunks
+        const int quarter = warp & 3, row = quarter * 32 + lane, half = (warp - 2) / 4;
+        int u = 0;
+        bool fine = true;
+        for (int t = blockIdx.x; t < ntiles && fine; t += gridDim.x) {
+            const int m = t * TBM + row;
+            for (int l = 0; l < 4; ++l, ++u) {
+                if (!pg_wait(smem_u32(accf), (unsigned)u & 1u, abandon)) {
+                    fine = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const float* bl = sbias + l * 256;
+                for (int ci = half; ci * 32 < NB[l]; ci += 2) {
+                    const int c0 = ci * 32;
+                    unsigned r[32];
+                    tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
+                    if (l < 3) {   // bias + SiLU, BF16, into the activation tile (0 beyond H)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            unsigned pk[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int c = c0 + 8 * q + 2 * j;
+                                const float z0 = __uint_as_float(r[8 * q + 2 * j]) + bl[c];
+                                const float z1 = __uint_as_float(r[8 * q + 2 * j + 1]) + bl[c + 1];
+                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(
+                                    c < a.H ? silu_bf16(z0) : 0.f, c + 1 < a.H ? silu_bf16(z1) : 0.f);
+                                pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+                            }
+                            if (c0 + 8 * q < FM_ACT / (TBM * 2))   // within the tile's 256 columns
+                                *reinterpret_cast<uint4*>(act + sw128_offset(row, c0 + 8 * q)) =
+                                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        }
+                    } else if (m < a.M) {   // bias, FP32 rows of Y
+                        float* y = a.Y + (long)m * a.ldY;
+                        if (c0 + 32 <= a.N4) {   // ldY is a multiple of 4: 16-byte vectors
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                reinterpret_cast<float4*>(y + c0)[q] = make_float4(
+                                    __uint_as_float(r[4 * q]) + bl[c0 + 4 * q],
+                                    __uint_as_float(r[4 * q + 1]) + bl[c0 + 4 * q + 1],
+                                    __uint_as_float(r[4 * q + 2]) + bl[c0 + 4 * q + 2],
+                                    __uint_as_float(r[4 * q + 3]) + bl[c0 + 4 * q + 3]);
+                        } else {
+                            for (int j = 0; j < 32; ++j)
+                                if (c0 + j < a.N4) y[c0 + j] = __uint_as_float(r[j]) + bl[c0 + j];
+                        }
+                    }
+                }
+                // the activation tile's new contents are read by the next layer's MMAs (the
+                // async proxy); the accumulator is free for them
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce))
+                                 : "memory");
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256u));
+}
+
+// tensor map of a row-major BF16 matrix [rows][ld], K columns, boxes of 64 columns x
+// box_rows rows, 128-byte swizzle; false if the driver refuses it
+bool fused_tensor_map(CUtensorMap* map, const bf16* ptr, int rows, int K, int ld, int box_rows) {
+    const unsigned long long dims[2] = {(unsigned long long)K, (unsigned long long)rows};
+    const unsigned long long strides[1] = {(unsigned long long)ld * sizeof(bf16)};
+    const unsigned box[2] = {(unsigned)TBK, (unsigned)box_rows};
+    return oc_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box,
+                           CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// the fused forward pass for M columns, when the shapes allow it (hidden width and output
+// width at most 256, multiples of 16 and of 4 for the widths, the FP32 rows of Y 16-byte
+// aligned) and the driver encodes the tensor maps; false to fall back to four GEMMs
+bool mlp_fused_forward(const bf16* X, int M, const void* const* Wt, const float* const* b,
+                       const int* dims, float* Y, cudaStream_t s) {
+    const int K0 = dims[0], H = dims[1], N4 = dims[4];
+    if (H > 256 || H % 16 || dims[2] != H || dims[3] != H || N4 > 256 || N4 % 4 || K0 % 8 || M < 1)
+        return false;
+    FusedMaps tm;
+    const int nb[4] = {H, H, H, (N4 + 15) & ~15};
+    if (!fused_tensor_map(&tm.X, X, M, K0, K0, TBM)) return false;
+    for (int l = 0; l < 4; ++l)
+        if (!fused_tensor_map(&tm.W[l], reinterpret_cast<const bf16*>(Wt[l]), dims[l + 1], dims[l],
+                              dims[l], nb[l]))
+            return false;
+    FusedArgs fa{{b[0], b[1], b[2], b[3]}, Y, N4, M, K0, H, N4};
+    const int tiles = (M + TBM - 1) / TBM;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_mlp_fused<<<tiles < sms ? tiles : sms, FM_TH, FM_SMEM, s>>>(tm, fa);
+    return true;
+}
+
 // ------------------------------------------------------------------ elementwise kernels
 
 // fp32 [M][C] -> bf16 [M][ldo] (and, if T, bf16 transpose [C][ldt])
@@ -951,6 +1227,9 @@ int closure_gemm_setup() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gemm_nt_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)PG_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FM_SMEM);
     return (int)e;
 }
 
@@ -987,6 +1266,7 @@ int closure_gemm_failed() {
 void closure_forward(const void* Xb, int M, const void* const* Wt, const float* const* b,
                      const int* dims, void* H0, void* H1, float* Y, cudaStream_t s) {
     const bf16* a = reinterpret_cast<const bf16*>(Xb);
+    if (mlp_fused_forward(a, M, Wt, b, dims, Y, s)) return;
     int lda = dims[0];
     bf16* H[2] = {reinterpret_cast<bf16*>(H0), reinterpret_cast<bf16*>(H1)};
     for (int l = 0; l < 4; ++l) {
