@@ -133,6 +133,10 @@ int validate(const ocean_grid* g, const ocean_params* p) {
         return fail(nullptr, OCEAN_ERR_ARG, "grid sizes must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz);
     if (g->nz > OC_NZMAX) return fail(nullptr, OCEAN_ERR_ARG, "nz = %d exceeds the maximum %d", g->nz, OC_NZMAX);
     if ((long)g->nx * g->ny > (1L << 30)) return fail(nullptr, OCEAN_ERR_ARG, "too many columns");
+    // the tile kernels address a 3-D array (halo and padding included) with 32-bit offsets
+    if ((long)((g->nx + 2 * OC_H + 31) & ~31) * (g->ny + 2 * OC_H) * g->nz >= (1L << 31))
+        return fail(nullptr, OCEAN_ERR_ARG, "%d x %d x %d cells exceed the 2^31 of a 3-D array",
+                    g->nx, g->ny, g->nz);
     if (g->periodic_x && g->nx < OC_H) return fail(nullptr, OCEAN_ERR_ARG, "periodic x needs nx >= %d", OC_H);
     if (g->periodic_y && g->ny < OC_H) return fail(nullptr, OCEAN_ERR_ARG, "periodic y needs ny >= %d", OC_H);
     if (g->periodic_y && g->kind == 1) return fail(nullptr, OCEAN_ERR_ARG, "lat-lon grids cannot be periodic in y");

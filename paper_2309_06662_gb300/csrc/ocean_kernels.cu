@@ -287,19 +287,21 @@ struct __align__(128) TracerSmem {
 // vertical ones reconstruct full values, since the reference varies along the column.
 // tile (bx, by): columns [bx TX, bx TX + TX) x [by TY, by TY + TY)
 // SV: the vertical reconstructions take the stretched-level coefficients of p.vw.
-template <typename R, bool STEP, bool SV>
+template <typename R, bool STEP, bool SV, typename Off = unsigned>
 __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, const int bx,
                                             const int by, const TracerArgs<R>& a) {
     using R2 = typename Vec2<R>::type;
     __shared__ TracerSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
-    const long P = g.plane;
+    // cell offsets: 32-bit by default (a 3-D array holds fewer than 2^31 cells, checked
+    // at creation); the ensemble's tiles keep 64-bit ones, which need fewer registers there
+    const Off P = (Off)g.plane;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool mine = ty < TY && i < g.nx && j < g.ny;
-    const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
+    const Off c2 = (Off)ix2(g, mine ? i : 0, mine ? j : 0);
     // ---- 2-D masks of the patch, and the lowest wet level of the whole patch
     if (tid == 0) sm.kmin = nz;
     for (int q = tid; q < (TY + 6) * (TX + 6); q += NTT) {
@@ -379,16 +381,16 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     for (int q = 0; q < 6; ++q) {
         const int kk = kstart - 2 + q;
         const bool ok = mine && kk >= kb && kk < nz;
-        wT[q] = ok ? a.T[kk * P + c2] + p.Tref[kk] : R(0);
-        wS[q] = ok ? a.S[kk * P + c2] + p.Sref[kk] : R(0);
+        wT[q] = ok ? a.T[(Off)kk * P + c2] + p.Tref[kk] : R(0);
+        wS[q] = ok ? a.S[(Off)kk * P + c2] + p.Sref[kk] : R(0);
     }
     // anomalies of level kstart+4, the next to enter the window
     R nT, nS;
     {
         const int kk = kstart + 4;
         const bool ok = mine && kk >= kb && kk < nz;
-        nT = ok ? a.T[kk * P + c2] : R(0);
-        nS = ok ? a.S[kk * P + c2] : R(0);
+        nT = ok ? a.T[(Off)kk * P + c2] : R(0);
+        nS = ok ? a.S[(Off)kk * P + c2] : R(0);
     }
     R fzT = R(0), fzS = R(0), cprev = R(0), dTprev = R(0), dSprev = R(0);
     R kcarry = R(0);   // diffusivity on the top face of the previous level
@@ -399,8 +401,10 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
     // warp that has finished level k-1 computes level k's faces while others still read
     // level k-1's; the barrier after the faces publishes them and frees the staging
     // buffer of level k-1 (read by every thread before it), which takes level k+2.
+    // the y-faces' row metric: row ty (row TY for the extra warp) on every level
+    const R dxv = p.dxv[j0 + (ty < TY ? ty : TY) + OC_H];
     for (int k = kstart; k < nz; ++k) {
-        const long Pk = k * P;
+        const Off Pk = (Off)k * P;
         const int fb = (k - kstart) & 1;
         bar_wait(&sm.bar[cb], (phase >> cb) & 1u);
         phase ^= 1u << cb;
@@ -462,7 +466,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
                 }
                 R rT, rS;
                 WenoPair<R>::run(qT, qS, in, in, p.eps, p.linear, rT, rS);
-                fV = vt * p.dxv[j0 + a + OC_H] * dzk;
+                fV = vt * dxv * dzk;
                 fT = fV * rT;
                 fS = fV * rS;
             }
@@ -486,7 +490,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         // level k+3, issued after the next level's barrier); the diffusivity on the bottom
         // face is the previous level's top one
         const bool live = mine && k >= kb;
-        const long ck = Pk + c2;
+        const Off ck = Pk + c2;
         R wt = R(0), k0 = kcarry, k1 = R(0), gT0 = R(0), gS0 = R(0), T0 = R(0), S0 = R(0);
         if (live) {
             if (k + 1 < nz) {
@@ -589,8 +593,8 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
             wT[5] = ok ? nT + p.Tref[kk] : R(0);
             wS[5] = ok ? nS + p.Sref[kk] : R(0);
             const bool ok5 = mine && kk + 1 >= kb && kk + 1 < nz;
-            nT = ok5 ? a.T[(kk + 1) * P + c2] : R(0);
-            nS = ok5 ? a.S[(kk + 1) * P + c2] : R(0);
+            nT = ok5 ? a.T[(Off)(kk + 1) * P + c2] : R(0);
+            nS = ok5 ? a.S[(Off)(kk + 1) * P + c2] : R(0);
         }
     }
     __syncthreads();   // every copy waited for: the barriers can be retired
@@ -607,7 +611,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
         R cc[4], tq[4], sq[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const long ck = (long)(k - q) * P + c2;
+            const Off ck = (Off)(k - q) * P + c2;
             const bool in = k - q >= kb;
             cc[q] = in ? a.kap[ck] : R(0);
             tq[q] = in ? a.Tn[ck] : R(0);
@@ -616,7 +620,7 @@ __device__ __forceinline__ void tracer_tile(const KP<R>& p, const TileMaps& tm, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (k - q < kb) break;
-            const long ck = (long)(k - q) * P + c2;
+            const Off ck = (Off)(k - q) * P + c2;
             xT = tq[q] - cc[q] * xT;
             xS = sq[q] - cc[q] * xS;
             a.Tn[ck] = xT;
@@ -660,18 +664,20 @@ struct __align__(128) MomentumSmem {
 // sum of the solved column Su = sum dz u**.  VA: the vertical advection in the WENO flux
 // form (own-column windows of u and v over levels k-2 .. k+3 in registers, the bottom
 // face's flux carried up from the level below), else centred.
-template <typename R, bool STEP, bool VA>
+template <typename R, bool STEP, bool VA, typename Off = unsigned>
 __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm, const int bx,
                                               const int by, const MomentumArgs<R>& a) {
     __shared__ MomentumSmem<R> sm;
     const GeoD& g = p.g;
     const int nz = g.nz;
-    const long P = g.plane;
+    // cell offsets: 32-bit by default (a 3-D array holds fewer than 2^31 cells, checked
+    // at creation); the ensemble's tiles keep 64-bit ones, which need fewer registers there
+    const Off P = (Off)g.plane;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool mine = i < g.nx && j < g.ny;
-    const long c2 = ix2(g, mine ? i : 0, mine ? j : 0);
+    const Off c2 = (Off)ix2(g, mine ? i : 0, mine ? j : 0);
     if (tid == 0) sm.kmin = nz;
     for (int q = tid; q < (TY + 5) * (TX + 5); q += NT) {
         const int a = q / (TX + 5), b = q % (TX + 5);
@@ -763,8 +769,8 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const int kk = kstart - 2 + q;
-            wu[q] = mine && kk >= ku && kk < nz ? a.u[kk * P + c2] : R(0);
-            wv[q] = mine && kk >= kv && kk < nz ? a.v[kk * P + c2] : R(0);
+            wu[q] = mine && kk >= ku && kk < nz ? a.u[(Off)kk * P + c2] : R(0);
+            wv[q] = mine && kk >= kv && kk < nz ? a.v[(Off)kk * P + c2] : R(0);
         }
     }
     int r3 = 0, q3 = 0;   // (k - kstart) mod 3 and div 3
@@ -773,7 +779,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
     // level k-1's; the barrier after them publishes them and frees the slot of level k-1
     // (read by every thread before it), which takes level k+2.
     for (int k = kstart; k < nz; ++k) {
-        const long Pk = k * P;
+        const Off Pk = (Off)k * P;
         // slots of levels k, k+1, k+2 and the parities of their completions, from the
         // running quotient and remainder of (k - kstart) / 3
         const int sc = r3, sn = r3 == 2 ? 0 : r3 + 1, s2 = r3 == 0 ? 2 : r3 - 1, fb = (k - kstart) & 1;
@@ -908,7 +914,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
                 }
                 const R wind = k == nz - 1 ? a.taux_s[c2] : R(0);
                 const R G = (ztu + fu) * vh - dK - vadv - dP + wind;
-                const long ck = Pk + c2;
+                const Off ck = Pk + c2;
                 if (!STEP) {
                     a.un[ck] = G;
                 } else {
@@ -942,7 +948,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
                 }
                 const R wind = k == nz - 1 ? a.tauy_s[c2] : R(0);
                 const R G = -(ztv + fv) * uh - dK - vadv - dP + wind;
-                const long ck = Pk + c2;
+                const Off ck = Pk + c2;
                 if (!STEP) {
                     a.vn[ck] = G;
                 } else {
@@ -970,8 +976,8 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
                 wv[q] = wv[q + 1];
             }
             const int kk = k + 4;
-            wu[5] = mine && kk >= ku && kk < nz ? a.u[kk * P + c2] : R(0);
-            wv[5] = mine && kk >= kv && kk < nz ? a.v[kk * P + c2] : R(0);
+            wu[5] = mine && kk >= ku && kk < nz ? a.u[(Off)kk * P + c2] : R(0);
+            wv[5] = mine && kk >= kv && kk < nz ? a.v[(Off)kk * P + c2] : R(0);
         }
         if (++r3 == 3) {
             r3 = 0;
@@ -994,7 +1000,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
         R cuq[4], duq[4], cvq[4], dvq[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const long ck = (long)(k - q) * P + c2;
+            const Off ck = (Off)(k - q) * P + c2;
             const bool inu = k - q >= ku, inv = k - q >= kv;
             cuq[q] = inu ? a.cu[ck] : R(0);
             duq[q] = inu ? a.un[ck] : R(0);
@@ -1003,7 +1009,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const long ck = (long)(k - q) * P + c2;
+            const Off ck = (Off)(k - q) * P + c2;
             if (k - q >= ku) {
                 xu = duq[q] - cuq[q] * xu;
                 a.un[ck] = xu;
@@ -1801,7 +1807,7 @@ __global__ void __launch_bounds__(NTT, (OccX<R, true>::value)) k_ens_tracer(
     for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
         const EnsItem e = work[it];
         const StepBuffers<R>& b = mem[e.m].b;
-        tracer_tile<R, true, false>(mem[e.m].k, b.tm, e.a, e.b, tracer_args(b));
+        tracer_tile<R, true, false, long>(mem[e.m].k, b.tm, e.a, e.b, tracer_args(b));
     }
 }
 
@@ -1813,7 +1819,7 @@ __global__ void __launch_bounds__(NT, (OccX<R, true>::value)) k_ens_momentum(
     for (int it = ens_first(counter, &s_next); it < nwork; it = ens_next(counter, &s_next, it)) {
         const EnsItem e = work[it];
         const StepBuffers<R>& b = mem[e.m].b;
-        momentum_tile<R, true, false>(mem[e.m].k, b.tm, e.a, e.b, momentum_args(b));
+        momentum_tile<R, true, false, long>(mem[e.m].k, b.tm, e.a, e.b, momentum_args(b));
     }
 }
 

@@ -796,20 +796,29 @@ void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int 
 // The whole network on one 128-column tile without leaving the SM: the hidden activations
 // stay in shared memory, written by the epilogue in the 128-byte-swizzled K-major layout
 // the next layer's MMAs read as their A operand, so HBM sees only the features in and the
-// outputs out (the four separate GEMMs move every hidden layer through HBM twice).  Per
-// tile and layer: warp 0 streams the layer's weight K-blocks (64 inputs x up to 256
-// outputs, BF16, from L2: the same weights serve every tile) and, for the first layer,
-// the tile's feature K-blocks into a ring of FM_S stages; warp 1 issues the MMAs
-// (M 128, N the layer's width, K 16) into one TMEM accumulator of up to 256 columns;
-// warps 2..9 drain it (bias + SiLU to BF16 into the activation tile, or bias to FP32 rows
-// of Y for the last layer).  Barriers: full/empty per stage; accf (the layer's MMAs
-// done), acce (its eight epilogue warps done: TMEM drained and the activation tile
-// written).  Every wait is bounded as in k_gemm_nt_pers.
-constexpr int FM_S = 3, FM_EW = 8, FM_TH = (2 + FM_EW) * 32;
+// outputs out (the four separate GEMMs move every hidden layer through HBM twice).
+// Roles, per tile and layer (use u = 4 n + l of the block's n-th tile):
+// - warp 0 streams the layer's weight K-blocks (64 inputs x up to 256 outputs, BF16, from
+//   L2: the same weights serve every tile) and, for the first layer, the tile's feature
+//   K-blocks into a ring of FM_S stages;
+// - warp 1 issues the MMAs (M 128, N the layer's width, K 16) into TMEM accumulator u mod 2
+//   (two of 256 columns: the next layer's sums build up while the epilogue still drains
+//   this one);
+// - warps 2..17 drain the accumulator (two TMEM loads of 32 columns per warp), release
+//   it once both are in registers, and write bias + SiLU as BF16 into the activation tile,
+//   each K-block announced on its own barrier: the next layer's MMAs start on K-blocks 0
+//   and 1 while the others are still being written.  The last layer's bias-added sums
+//   go to FP32 rows of Y.
+// Barriers: full/empty per stage; accf[b] (the MMAs of the accumulator's use done);
+// acce[b] (its sixteen epilogue warps have read it); actf[kb] (the eight epilogue warps
+// that write K-block kb of the next layer's input have written it).  Every wait is bounded as in
+// k_gemm_nt_pers.
+constexpr int FM_S = 3, FM_EW = 16, FM_TH = (2 + FM_EW) * 32;
 constexpr int FM_ACT = 4 * TILE_BYTES;                 // 128 rows x 256 BF16: four K-blocks
 constexpr int FM_B = 256 * TBK * 2;                    // up to 256 weight rows x 64 BF16
 constexpr int FM_STAGE = TILE_BYTES + FM_B;            // feature block + weight block
-constexpr size_t FM_SMEM = 1024 + FM_ACT + FM_S * (size_t)FM_STAGE + 4 * 256 * 4 + 256;
+constexpr int FM_NBAR = 2 * FM_S + 2 + 2 + 4;          // full, empty, accf, acce, actf
+constexpr size_t FM_SMEM = 1024 + FM_ACT + FM_S * (size_t)FM_STAGE + 4 * 256 * 4 + FM_NBAR * 8 + 16;
 static_assert(FM_SMEM <= 227 * 1024, "fused network's shared memory");
 
 struct FusedMaps {
@@ -834,6 +843,43 @@ __device__ __forceinline__ unsigned sw128_offset(int r, int c) {
                       (c & 7) * 2);
 }
 
+// 32 columns of this thread's TMEM lane into r, without waiting (tcgen05.wait::ld follows)
+__device__ __forceinline__ void tmem_ld32_async(unsigned taddr, unsigned* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// SiLU of eight sums z = acc + b as BF16, in the half-argument form: with h = z / 2,
+// SiLU(z) = z (1 + tanh(z / 2)) / 2 = h + h tanh(h); hb holds b / 2, so h = acc / 2 + hb
+// is one packed FMA per pair; tanh is the special-function unit's approximation (the
+// result is rounded to BF16)
+__device__ __forceinline__ uint4 silu8_bf16(const unsigned* r, const float* hb) {
+    const float4 b0 = *reinterpret_cast<const float4*>(hb);
+    const float4 b1 = *reinterpret_cast<const float4*>(hb + 4);
+    const float hbv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    unsigned pk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 h = __ffma2_rn(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
+                                    make_float2(0.5f, 0.5f), make_float2(hbv[2 * j], hbv[2 * j + 1]));
+        float2 t;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(t.x) : "f"(h.x));
+        asm("tanh.approx.f32 %0, %1;" : "=f"(t.y) : "f"(h.y));
+        const float2 s = __ffma2_rn(h, t, h);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(s.x, s.y);
+        pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+    }
+    return make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
 __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ FusedMaps tm,
                                                         FusedArgs a) {
     extern __shared__ unsigned char fm_raw[];
@@ -842,27 +888,28 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
     unsigned char* act = base;
     auto sA = [&](int st) { return base + FM_ACT + st * FM_STAGE; };
     auto sB = [&](int st) { return base + FM_ACT + st * FM_STAGE + TILE_BYTES; };
-    float* sbias = reinterpret_cast<float*>(base + FM_ACT + FM_S * FM_STAGE);   // [4][256]
+    // [4][256]: b / 2 of the hidden layers (the SiLU's half argument), b of the last
+    float* sbias = reinterpret_cast<float*>(base + FM_ACT + FM_S * FM_STAGE);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(sbias + 4 * 256);
     unsigned long long* empty = full + FM_S;
     unsigned long long* accf = empty + FM_S;
-    unsigned long long* acce = accf + 1;
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(acce + 1);
+    unsigned long long* acce = accf + 2;
+    unsigned long long* actf = acce + 2;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(actf + 4);
     volatile int* abandon = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // layer shapes: inputs K_l, outputs N_l (the MMA width NB_l rounded up to 16)
-    const int Kl[4] = {a.K0, a.H, a.H, a.H}, Nl[4] = {a.H, a.H, a.H, a.N4};
-    int NB[4], nkb[4];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        NB[l] = (Nl[l] + 15) & ~15;
-        nkb[l] = (Kl[l] + TBK - 1) / TBK;
-    }
+    // layer shapes: K-blocks of the inputs (K0, then H), MMA widths (H, then N4 rounded up
+    // to 16; H is a multiple of 16)
+    const int nkb0 = (a.K0 + TBK - 1) / TBK, nact = (a.H + TBK - 1) / TBK;
+    const int nb3 = (a.N4 + 15) & ~15;
+    auto NB = [&](int l) { return l < 3 ? a.H : nb3; };
+    auto nkb = [&](int l) { return l == 0 ? nkb0 : nact; };
     const int ntiles = (a.M + TBM - 1) / TBM;
 
     for (int q = tid; q < 4 * 256; q += FM_TH) {
         const int l = q >> 8, c = q & 255;
-        sbias[q] = c < Nl[l] ? a.bias[l][c] : 0.f;
+        const float* bp = l == 0 ? a.bias[0] : l == 1 ? a.bias[1] : l == 2 ? a.bias[2] : a.bias[3];
+        sbias[q] = c < (l < 3 ? a.H : a.N4) ? (l < 3 ? 0.5f : 1.f) * bp[c] : 0.f;
     }
     // the activation tile's columns at and beyond H are never written: zero them once
     for (int q = tid; q < FM_ACT / 16; q += FM_TH)
@@ -872,16 +919,21 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(accf)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(acce)),
-                     "r"((unsigned)FM_EW));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&accf[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acce[b])),
+                         "r"((unsigned)FM_EW));
+        }
+        for (int kb = 0; kb < 4; ++kb)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&actf[kb])),
+                         "r"((unsigned)FM_EW / 2));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         *abandon = 0;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(256u));
+                     "r"(512u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     // the zeroed activation tile is read by the tensor cores (the async proxy)
@@ -897,12 +949,12 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
             for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x) {
                 const int m0 = t * TBM;
                 for (int l = 0; l < 4 && !*abandon; ++l)
-                    for (int kb = 0; kb < nkb[l]; ++kb, ++g) {
+                    for (int kb = 0; kb < nkb(l); ++kb, ++g) {
                         const int st = g % FM_S, use = g / FM_S;
                         if (g >= FM_S &&
                             !pg_wait(smem_u32(&empty[st]), (unsigned)(use - 1) & 1u, abandon))
                             break;
-                        const unsigned bytes = (unsigned)NB[l] * TBK * 2 + (l == 0 ? (unsigned)TILE_BYTES : 0u);
+                        const unsigned bytes = (unsigned)NB(l) * TBK * 2 + (l == 0 ? (unsigned)TILE_BYTES : 0u);
                         mbar_expect(smem_u32(&full[st]), bytes);
                         if (l == 0) tma_load_2d(smem_u32(sA(st)), &tm.X, kb * TBK, m0, smem_u32(&full[st]));
                         tma_load_2d(smem_u32(sB(st)), &tm.W[l], kb * TBK, 0, smem_u32(&full[st]));
@@ -923,22 +975,29 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                 }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // ---- MMAs: layer l of tile t is accumulator use u = 4 t' + l
+        if (lane == 0) {   // ---- MMAs: layer l of the n-th tile is use u = 4 n + l
             int g = 0, u = 0;
             bool fine = true;
-            for (int t = blockIdx.x; t < ntiles && fine; t += gridDim.x)
+            for (int t = blockIdx.x, n = 0; t < ntiles && fine; t += gridDim.x, ++n)
                 for (int l = 0; l < 4 && fine; ++l, ++u) {
-                    // the epilogue of the previous use has drained TMEM and, for l > 0,
-                    // written this layer's input into the activation tile
-                    if (u >= 1 && !pg_wait(smem_u32(acce), (unsigned)(u - 1) & 1u, abandon)) {
+                    const int b = u & 1;
+                    // accumulator b drained by the epilogue of use u - 2
+                    if (u >= 2 && !pg_wait(smem_u32(&acce[b]), (unsigned)((u >> 1) - 1) & 1u, abandon)) {
                         fine = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const unsigned idesc = fm_idesc(NB[l]);
-                    for (int kb = 0; kb < nkb[l]; ++kb, ++g) {
+                    const unsigned idesc = fm_idesc(NB(l));
+                    const unsigned dt = tmem + (unsigned)(b * 256);
+                    for (int kb = 0; kb < nkb(l); ++kb, ++g) {
                         const int st = g % FM_S;
                         if (!pg_wait(smem_u32(&full[st]), (unsigned)(g / FM_S) & 1u, abandon)) {
+                            fine = false;
+                            break;
+                        }
+                        // layers 1..3: K-block kb of the input, written by the epilogue of
+                        // layer l - 1 of this tile (the (3 n + l - 1)-th phase of actf[kb])
+                        if (l > 0 && !pg_wait(smem_u32(&actf[kb]), (unsigned)(3 * n + l - 1) & 1u, abandon)) {
                             fine = false;
                             break;
                         }
@@ -951,7 +1010,7 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                             const unsigned acc = (kb > 0 || k > 0) ? 1u : 0u;
                             asm volatile(
                                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
                                 "l"(ad + 2ull * k), "l"(bd + 2ull * k), "r"(idesc), "r"(acc));
                         }
                         asm volatile(
@@ -962,75 +1021,90 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                     if (!fine) break;
                     asm volatile(
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                            smem_u32(accf))
+                            smem_u32(&accf[b]))
                         : "memory");
                 }
         }
-    } else {   // ---- epilogue: warps 2..9, TMEM lanes 32 (warp % 4) .., alternate 32-column chunks
-        const int quarter = warp & 3, row = quarter * 32 + lane, half = (warp - 2) / 4;
+    } else {   // ---- epilogue: warps 2..17, TMEM lanes 32 (warp % 4) ..
+        // warp group g = (warp - 2) / 4 owns the 32-column chunks g and g + 4: chunk g lies in
+        // K-block g / 2 (0 or 1), chunk g + 4 in K-block g / 2 + 2, so the sixteen warps
+        // complete K-blocks 0 and 1 first; eight warps write each K-block
+        const int quarter = warp & 3, row = quarter * 32 + lane, grp = (warp - 2) >> 2;
+        const unsigned lanes = (unsigned)(quarter * 32) << 16;
+        const int ch[2] = {grp, grp + 4};
         int u = 0;
         bool fine = true;
         for (int t = blockIdx.x; t < ntiles && fine; t += gridDim.x) {
             const int m = t * TBM + row;
             for (int l = 0; l < 4; ++l, ++u) {
-                if (!pg_wait(smem_u32(accf), (unsigned)u & 1u, abandon)) {
+                const int b = u & 1;
+                if (!pg_wait(smem_u32(&accf[b]), (unsigned)(u >> 1) & 1u, abandon)) {
                     fine = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const float* bl = sbias + l * 256;
-                for (int ci = half; ci * 32 < NB[l]; ci += 2) {
-                    const int c0 = ci * 32;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c0 = ch[h] * 32, kb = ch[h] >> 1;
+                    const bool valid = c0 < NB(l);
                     unsigned r[32];
-                    tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0, r);
+                    if (valid) {
+                        tmem_ld32_async(tmem + lanes + (unsigned)(b * 256 + c0), r);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    }
+                    if (h == 1) {   // both chunks read: accumulator b is free for use u + 2
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(
+                                             smem_u32(&acce[b]))
+                                         : "memory");
+                    }
                     if (l < 3) {   // bias + SiLU, BF16, into the activation tile (0 beyond H)
+                        if (kb < nact) {
+                            if (valid) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            unsigned pk[4];
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const int c = c0 + 8 * q + 2 * j;
-                                const float z0 = __uint_as_float(r[8 * q + 2 * j]) + bl[c];
-                                const float z1 = __uint_as_float(r[8 * q + 2 * j + 1]) + bl[c + 1];
-                                const __nv_bfloat162 h2 = __floats2bfloat162_rn(
-                                    c < a.H ? silu_bf16(z0) : 0.f, c + 1 < a.H ? silu_bf16(z1) : 0.f);
-                                pk[j] = *reinterpret_cast<const unsigned*>(&h2);
+                                for (int q = 0; q < 4; ++q) {
+                                    const int c = c0 + 8 * q;
+                                    const uint4 v = c < a.H ? silu8_bf16(&r[8 * q], bl + c)
+                                                            : make_uint4(0u, 0u, 0u, 0u);
+                                    *reinterpret_cast<uint4*>(act + sw128_offset(row, c)) = v;
+                                }
                             }
-                            if (c0 + 8 * q < FM_ACT / (TBM * 2))   // within the tile's 256 columns
-                                *reinterpret_cast<uint4*>(act + sw128_offset(row, c0 + 8 * q)) =
-                                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            // this warp's part of K-block kb of the next layer's input is in
+                            // shared memory, for the tensor cores (the async proxy)
+                            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0)
+                                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(
+                                                 smem_u32(&actf[kb]))
+                                             : "memory");
                         }
-                    } else if (m < a.M) {   // bias, FP32 rows of Y
+                    } else if (valid && m < a.M) {   // bias, FP32 rows of Y
                         float* y = a.Y + (long)m * a.ldY;
                         if (c0 + 32 <= a.N4) {   // ldY is a multiple of 4: 16-byte vectors
 #pragma unroll
-                            for (int q = 0; q < 8; ++q)
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 bb = *reinterpret_cast<const float4*>(bl + c0 + 4 * q);
                                 reinterpret_cast<float4*>(y + c0)[q] = make_float4(
-                                    __uint_as_float(r[4 * q]) + bl[c0 + 4 * q],
-                                    __uint_as_float(r[4 * q + 1]) + bl[c0 + 4 * q + 1],
-                                    __uint_as_float(r[4 * q + 2]) + bl[c0 + 4 * q + 2],
-                                    __uint_as_float(r[4 * q + 3]) + bl[c0 + 4 * q + 3]);
+                                    __uint_as_float(r[4 * q]) + bb.x, __uint_as_float(r[4 * q + 1]) + bb.y,
+                                    __uint_as_float(r[4 * q + 2]) + bb.z, __uint_as_float(r[4 * q + 3]) + bb.w);
+                            }
                         } else {
-                            for (int j = 0; j < 32; ++j)
-                                if (c0 + j < a.N4) y[c0 + j] = __uint_as_float(r[j]) + bl[c0 + j];
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj)
+                                if (c0 + jj < a.N4) y[c0 + jj] = __uint_as_float(r[jj]) + bl[c0 + jj];
                         }
                     }
                 }
-                // the activation tile's new contents are read by the next layer's MMAs (the
-                // async proxy); the accumulator is free for them
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                __syncwarp();
-                if (lane == 0)
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce))
-                                 : "memory");
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256u));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512u));
 }
 
 // tensor map of a row-major BF16 matrix [rows][ld], K columns, boxes of 64 columns x

@@ -1,13 +1,23 @@
-"""CPU model of the barrier protocol of the fused closure network (k_mlp_fused): a copy
-warp streaming the K-blocks of every layer (and the first layer's features) through a
-ring of stages, an MMA warp running the four layers of each tile into one TMEM
-accumulator, and eight epilogue warps that drain it and write the next layer's input into
-the shared activation tile.  Copies and MMA completions land asynchronously and the warps
-are scheduled at random.  The model follows the kernel's waits and arrivals and checks:
-no deadlock; an MMA reads the K-block the copies filled for it; a layer's MMAs read the
-activation tile only after all eight epilogue warps wrote the previous layer into it; the
-epilogue never writes the tile while MMAs still read it, nor overwrites an accumulator
-before it was drained.  Removing the MMA warp's wait on the epilogue makes it fail."""
+"""CPU model of the barrier protocol of the fused closure network (k_mlp_fused).
+
+The kernel's roles:
+- a copy warp streams the K-blocks of every layer's weights, and the first layer's
+  features, through a ring of stages;
+- an MMA warp runs use u = 4 n + l (tile n, layer l) into TMEM accumulator u mod 2;
+- sixteen epilogue warps drain an accumulator into registers, 32 columns at a time,
+  release it, and write the next layer's input into the shared activation tile; eight
+  warps write each K-block, announced on its own barrier, so that the next layer's MMAs
+  start on K-blocks 0 and 1 while the epilogue still writes the others.
+
+Copies and MMA completions land asynchronously and the warps are scheduled at random. The
+model follows the kernel's waits and arrivals (barrier counts, phase parities) and
+checks:
+- it never deadlocks;
+- an MMA reads the K-block the copies filled for it, and the activation K-block of the
+  layer before, once the eight epilogue warps that write it did;
+- the epilogue never writes an activation K-block while MMAs still read it;
+- no accumulator is overwritten before it was drained.
+Removing any one of the MMA warp's waits makes it fail."""
 import random
 
 import pytest
@@ -17,14 +27,24 @@ from tests.test_gemm_protocol_model import MBar
 LAYERS = 4
 
 
-def run(ntiles, nkb, stages, epi_warps, seed, skip_epilogue_wait=False):
+def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
+    """nkb[l]: K-blocks of layer l; layers 1..3 read the hidden width, nkb[1] K-blocks
+    of the activation tile."""
     rnd = random.Random(seed)
     full = [MBar(1) for _ in range(stages)]
     empty = [MBar(1) for _ in range(stages)]
-    accf, acce = MBar(1), MBar(epi_warps)
+    accf = [MBar(1) for _ in range(2)]
+    acce = [MBar(epi_warps) for _ in range(2)]
+    nact = nkb[1]
+    actf = [MBar(epi_warps // 2) for _ in range(nact)]
     stage_holds = [None] * stages        # (tile, layer, K-block) the copies put there
     mma_reads = [None] * stages
-    state = dict(acc=None, drained=0, act=None, act_parts=0, act_reads=0)
+    acc = [None, None]                   # (tile, layer) whose sums the accumulator holds
+    acc_busy = [False, False]            # MMAs in flight into it
+    drained = [0, 0]
+    act = [None] * nact                  # (tile, layer) whose output the K-block holds
+    act_parts = [0] * nact
+    act_reads = [0] * nact
     events = []
 
     def copies():
@@ -43,57 +63,72 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip_epilogue_wait=False):
                     yield
 
     def mmas():
-        g = u = 0
+        g = 0
         for t in range(ntiles):
             for l in range(LAYERS):
-                if u >= 1 and not skip_epilogue_wait:
-                    while not acce.done((u - 1) & 1):
+                u = 4 * t + l
+                b = u & 1
+                if u >= 2 and skip != "acce":
+                    while not acce[b].done(((u >> 1) - 1) & 1):
                         yield
-                assert state["acc"] is None, "accumulator overwritten before it was drained"
-                if l > 0:
-                    assert state["act"] == (t, l - 1) and state["act_parts"] == epi_warps, \
-                        "layer input read before the epilogue wrote it"
+                assert acc[b] is None and not acc_busy[b], \
+                    "accumulator overwritten before it was drained"
+                acc_busy[b] = True
                 for kb in range(nkb[l]):
                     st = g % stages
                     while not full[st].done((g // stages) & 1):
                         yield
                     assert stage_holds[st] == (t, l, kb)
-                    mma_reads[st] = (t, l, kb)
                     if l > 0:
-                        state["act_reads"] += 1
-                    events.append(("mma", st, l > 0))
+                        if skip != "actf":
+                            while not actf[kb].done((3 * t + l - 1) & 1):
+                                yield
+                        assert act[kb] == (t, l - 1) and act_parts[kb] == epi_warps // 2, \
+                            "layer input read before the epilogue wrote it"
+                        act_reads[kb] += 1
+                    mma_reads[st] = (t, l, kb)
+                    events.append(("mma", st, kb if l > 0 else None))
                     g += 1
                     yield
-                events.append(("acc", None, (t, l)))
-                u += 1
+                events.append(("acc", b, (t, l)))
 
-    def epilogue():
-        u = 0
+    def epilogue(e):
+        # warp group e // 4 writes its chunks' K-blocks e // 8 and e // 8 + 2, the first
+        # before it reads its second chunk out of the accumulator
+        kbs = [e // 8, e // 8 + 2]
         for t in range(ntiles):
             for l in range(LAYERS):
-                while not accf.done(u & 1):
+                u = 4 * t + l
+                b = u & 1
+                while not accf[b].done((u >> 1) & 1):
                     yield
-                assert state["acc"] == (t, l)
-                yield
-                if l < LAYERS - 1:   # this warp's part of the next layer's input
-                    assert state["act_reads"] == 0, "activation tile written while MMAs read it"
-                    if state["act"] != (t, l):
-                        state["act"], state["act_parts"] = (t, l), 0
-                    state["act_parts"] += 1
-                state["drained"] += 1
-                if state["drained"] == epi_warps:
-                    state["acc"], state["drained"] = None, 0
-                acce.arrive()
-                u += 1
+                assert acc[b] == (t, l)
+                for h in range(2):
+                    yield                 # one chunk of the accumulator into registers
+                    assert acc[b] == (t, l), "accumulator overwritten while being read"
+                    if h == 1:
+                        drained[b] += 1
+                        if drained[b] == epi_warps:
+                            acc[b], drained[b] = None, 0
+                        acce[b].arrive()
+                    kb = kbs[h]
+                    if l < LAYERS - 1 and kb < nact:   # the next layer's input
+                        yield
+                        assert act_reads[kb] == 0, "activation K-block written while MMAs read it"
+                        if act[kb] != (t, l):
+                            assert act_parts[kb] in (0, epi_warps // 2)
+                            act[kb], act_parts[kb] = (t, l), 0
+                        act_parts[kb] += 1
+                        actf[kb].arrive()
                 yield
 
-    warps = [copies(), mmas()] + [epilogue() for _ in range(epi_warps)]
+    warps = [copies(), mmas()] + [epilogue(e) for e in range(epi_warps)]
     alive = set(range(len(warps)))
-    for _ in range(3_000_000):
+    for _ in range(5_000_000):
         if not alive and not events:
             return
         if events and (not alive or rnd.random() < 0.3):
-            # copies land in any order; the MMAs complete in issue order
+            # copies land in any order; MMA completions in issue order
             k = rnd.randrange(len(events))
             if events[k][0] != "copy":
                 k = next(q for q, ev in enumerate(events) if ev[0] != "copy")
@@ -103,12 +138,12 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip_epilogue_wait=False):
                 full[a].complete(1)
             elif kind == "mma":
                 mma_reads[a] = None
-                if val:
-                    state["act_reads"] -= 1
+                if val is not None:
+                    act_reads[val] -= 1
                 empty[a].arrive()
             else:
-                state["acc"] = val
-                accf.arrive()
+                acc[a], acc_busy[a] = val, False
+                accf[a].arrive()
             continue
         if alive:
             w = rnd.choice(sorted(alive))
@@ -119,17 +154,21 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip_epilogue_wait=False):
     raise AssertionError("deadlock")
 
 
+def _shapes(r):
+    h = r.randint(1, 4)
+    return [r.randint(1, 5), h, h, h]
+
+
 @pytest.mark.parametrize("stages", [2, 3])
 def test_fused_network_protocol(stages):
-    for seed in range(120):
+    for seed in range(150):
         r = random.Random(seed)
-        nkb = [r.randint(1, 5)] + [r.randint(1, 4)] * 3
-        run(r.randint(1, 4), nkb, stages, 8, seed)
+        run(r.randint(1, 4), _shapes(r), stages, 16, seed)
 
 
-def test_the_model_catches_a_missing_epilogue_wait():
+@pytest.mark.parametrize("skip", ["acce", "actf"])
+def test_the_model_catches_a_missing_wait(skip):
     with pytest.raises(AssertionError):
-        for seed in range(120):
+        for seed in range(150):
             r = random.Random(seed)
-            nkb = [r.randint(1, 5)] + [r.randint(1, 4)] * 3
-            run(r.randint(2, 4), nkb, 3, 8, seed, skip_epilogue_wait=True)
+            run(r.randint(2, 4), _shapes(r), 3, 16, seed, skip=skip)
