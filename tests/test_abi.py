@@ -53,6 +53,12 @@ def test_arena_size_and_argument_errors_without_gpu():
     prm.n_substeps = 0
     assert L.ocean_arena_bytes(ctypes.byref(g), ctypes.byref(prm), ctypes.byref(nb)) == -1
     prm.n_substeps = 30
+    # a padded 3-D array of 2^31 cells or more is refused (32-bit cell offsets): 30000 x
+    # 30000 columns pass the column limit, 30000 x 30000 x 8 cells do not
+    huge = ocean.OceanGrid(g.kind, 30000, 30000, g.nz, 0, 0, 0.0, 1.0, 0.0, 1.0, g.z_faces)
+    assert L.ocean_arena_bytes(ctypes.byref(huge), ctypes.byref(prm), ctypes.byref(nb)) == -1
+    assert b"2^31" in L.ocean_last_error(None)
+    prm.n_substeps = 30
     h = ctypes.c_void_p()
     assert L.ocean_create(ctypes.byref(g), None, ctypes.byref(prm), ctypes.byref(h)) == -1
     assert L.ocean_step(None, 1) == -1
