@@ -798,9 +798,11 @@ void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int 
 // the next layer's MMAs read as their A operand, so HBM sees only the features in and the
 // outputs out (the four separate GEMMs move every hidden layer through HBM twice).
 // Roles, per tile and layer (use u = 4 n + l of the block's n-th tile):
-// - warp 0 streams the layer's weight K-blocks (64 inputs x up to 256 outputs, BF16, from
-//   L2: the same weights serve every tile) and, for the first layer, the tile's feature
-//   K-blocks into a ring of FM_S stages;
+// - warp 0 streams per tile and layer the weight K-blocks (64 inputs x up to 256 outputs,
+//   BF16, from L2: the same weights serve every tile) through a ring of FM_S stages;
+// - warp 18 streams the tiles' feature K-blocks (128 columns x 64 features) from HBM
+//   through a ring of their own (FM_SX stages), so that the next tile's features load
+//   while this tile's later layers run;
 // - warp 1 issues the MMAs (M 128, N the layer's width, K 16) into TMEM accumulator u mod 2
 //   (two of 256 columns: the next layer's sums build up while the epilogue still drains
 //   this one);
@@ -809,16 +811,17 @@ void gemm_nt_forward(const bf16* A, int lda, const bf16* B, int ldb, int M, int 
 //   each K-block announced on its own barrier: the next layer's MMAs start on K-blocks 0
 //   and 1 while the others are still being written.  The last layer's bias-added sums
 //   go to FP32 rows of Y.
-// Barriers: full/empty per stage; accf[b] (the MMAs of the accumulator's use done);
+// Barriers: full/empty per weight stage, fullx/emptyx per feature stage; accf[b] (the MMAs of the accumulator's use done);
 // acce[b] (its sixteen epilogue warps have read it); actf[kb] (the eight epilogue warps
 // that write K-block kb of the next layer's input have written it).  Every wait is bounded as in
 // k_gemm_nt_pers.
-constexpr int FM_S = 3, FM_EW = 16, FM_TH = (2 + FM_EW) * 32;
+constexpr int FM_S = 3, FM_SX = 3, FM_EW = 16, FM_TH = (3 + FM_EW) * 32;
+constexpr int FM_XW = 2 + FM_EW;                       // the feature-copy warp
 constexpr int FM_ACT = 4 * TILE_BYTES;                 // 128 rows x 256 BF16: four K-blocks
 constexpr int FM_B = 256 * TBK * 2;                    // up to 256 weight rows x 64 BF16
-constexpr int FM_STAGE = TILE_BYTES + FM_B;            // feature block + weight block
-constexpr int FM_NBAR = 2 * FM_S + 2 + 2 + 4;          // full, empty, accf, acce, actf
-constexpr size_t FM_SMEM = 1024 + FM_ACT + FM_S * (size_t)FM_STAGE + 4 * 256 * 4 + FM_NBAR * 8 + 16;
+constexpr int FM_NBAR = 2 * FM_S + 2 * FM_SX + 2 + 2 + 4;   // full, empty, fullx, emptyx, accf, acce, actf
+constexpr size_t FM_SMEM = 1024 + FM_ACT + FM_S * (size_t)FM_B + FM_SX * (size_t)TILE_BYTES +
+                           4 * 256 * 4 + FM_NBAR * 8 + 16;
 static_assert(FM_SMEM <= 227 * 1024, "fused network's shared memory");
 
 struct FusedMaps {
@@ -886,13 +889,15 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
     unsigned char* base = reinterpret_cast<unsigned char*>(
         ((unsigned long long)fm_raw + 1023) & ~1023ull);
     unsigned char* act = base;
-    auto sA = [&](int st) { return base + FM_ACT + st * FM_STAGE; };
-    auto sB = [&](int st) { return base + FM_ACT + st * FM_STAGE + TILE_BYTES; };
+    auto sB = [&](int st) { return base + FM_ACT + st * FM_B; };                      // weights
+    auto sX = [&](int st) { return base + FM_ACT + FM_S * FM_B + st * TILE_BYTES; };  // features
     // [4][256]: b / 2 of the hidden layers (the SiLU's half argument), b of the last
-    float* sbias = reinterpret_cast<float*>(base + FM_ACT + FM_S * FM_STAGE);
+    float* sbias = reinterpret_cast<float*>(base + FM_ACT + FM_S * FM_B + FM_SX * TILE_BYTES);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(sbias + 4 * 256);
     unsigned long long* empty = full + FM_S;
-    unsigned long long* accf = empty + FM_S;
+    unsigned long long* fullx = empty + FM_S;
+    unsigned long long* emptyx = fullx + FM_SX;
+    unsigned long long* accf = emptyx + FM_SX;
     unsigned long long* acce = accf + 2;
     unsigned long long* actf = acce + 2;
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(actf + 4);
@@ -919,6 +924,10 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])));
         }
+        for (int st = 0; st < FM_SX; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&fullx[st])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&emptyx[st])));
+        }
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&accf[b])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acce[b])),
@@ -943,40 +952,53 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
+    // copies still in flight when the block gave up: wait (bounded) for them; the g-th
+    // copy of a ring of ns stages completes phase g / ns of stage g mod ns
+    auto drain = [&](unsigned long long* bars, int ns, int g) {
+        for (int gg = (g > ns ? g - ns : 0); gg < g; ++gg) {
+            const long long t0 = clock64();
+            unsigned ok = 0;
+            while (!ok && clock64() - t0 < 2000000000LL)
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(ok)
+                    : "r"(smem_u32(&bars[gg % ns])), "r"((unsigned)(gg / ns) & 1u)
+                    : "memory");
+        }
+    };
     if (warp == 0) {
-        if (lane == 0) {   // ---- copies: per tile and layer the weight (and feature) K-blocks
+        if (lane == 0) {   // ---- weight copies: per tile and layer its K-blocks
             int g = 0;
-            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x) {
-                const int m0 = t * TBM;
+            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x)
                 for (int l = 0; l < 4 && !*abandon; ++l)
                     for (int kb = 0; kb < nkb(l); ++kb, ++g) {
                         const int st = g % FM_S, use = g / FM_S;
                         if (g >= FM_S &&
                             !pg_wait(smem_u32(&empty[st]), (unsigned)(use - 1) & 1u, abandon))
                             break;
-                        const unsigned bytes = (unsigned)NB(l) * TBK * 2 + (l == 0 ? (unsigned)TILE_BYTES : 0u);
-                        mbar_expect(smem_u32(&full[st]), bytes);
-                        if (l == 0) tma_load_2d(smem_u32(sA(st)), &tm.X, kb * TBK, m0, smem_u32(&full[st]));
+                        mbar_expect(smem_u32(&full[st]), (unsigned)NB(l) * TBK * 2);
                         tma_load_2d(smem_u32(sB(st)), &tm.W[l], kb * TBK, 0, smem_u32(&full[st]));
                     }
-            }
-            // copies still in flight when the block gave up: wait (bounded) for them
-            if (*abandon)
-                for (int gg = (g > FM_S ? g - FM_S : 0); gg < g; ++gg) {
-                    const long long t0 = clock64();
-                    unsigned ok = 0;
-                    while (!ok && clock64() - t0 < 2000000000LL)
-                        asm volatile(
-                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                            " selp.u32 %0, 1, 0, p;\n}\n"
-                            : "=r"(ok)
-                            : "r"(smem_u32(&full[gg % FM_S])), "r"((unsigned)(gg / FM_S) & 1u)
-                            : "memory");
+            if (*abandon) drain(full, FM_S, g);
+        }
+    } else if (warp == FM_XW) {
+        if (lane == 0) {   // ---- feature copies: per tile its K-blocks
+            int g = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abandon; t += gridDim.x)
+                for (int kb = 0; kb < nkb0; ++kb, ++g) {
+                    const int st = g % FM_SX, use = g / FM_SX;
+                    if (g >= FM_SX &&
+                        !pg_wait(smem_u32(&emptyx[st]), (unsigned)(use - 1) & 1u, abandon))
+                        break;
+                    mbar_expect(smem_u32(&fullx[st]), (unsigned)TILE_BYTES);
+                    tma_load_2d(smem_u32(sX(st)), &tm.X, kb * TBK, t * TBM, smem_u32(&fullx[st]));
                 }
+            if (*abandon) drain(fullx, FM_SX, g);
         }
     } else if (warp == 1) {
         if (lane == 0) {   // ---- MMAs: layer l of the n-th tile is use u = 4 n + l
-            int g = 0, u = 0;
+            int g = 0, gx = 0, u = 0;
             bool fine = true;
             for (int t = blockIdx.x, n = 0; t < ntiles && fine; t += gridDim.x, ++n)
                 for (int l = 0; l < 4 && fine; ++l, ++u) {
@@ -995,15 +1017,18 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                             fine = false;
                             break;
                         }
-                        // layers 1..3: K-block kb of the input, written by the epilogue of
-                        // layer l - 1 of this tile (the (3 n + l - 1)-th phase of actf[kb])
-                        if (l > 0 && !pg_wait(smem_u32(&actf[kb]), (unsigned)(3 * n + l - 1) & 1u, abandon)) {
+                        // layer 0: the tile's feature K-block; layers 1..3: K-block kb of
+                        // the input, written by the epilogue of layer l - 1 of this tile (the
+                        // (3 n + l - 1)-th phase of actf[kb])
+                        const int sx = gx % FM_SX;
+                        if (l == 0 ? !pg_wait(smem_u32(&fullx[sx]), (unsigned)(gx / FM_SX) & 1u, abandon)
+                                   : !pg_wait(smem_u32(&actf[kb]), (unsigned)(3 * n + l - 1) & 1u, abandon)) {
                             fine = false;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const unsigned long long ad =
-                            sw128_desc(smem_u32(l == 0 ? sA(st) : act + kb * TILE_BYTES));
+                            sw128_desc(smem_u32(l == 0 ? sX(sx) : act + kb * TILE_BYTES));
                         const unsigned long long bd = sw128_desc(smem_u32(sB(st)));
 #pragma unroll
                         for (int k = 0; k < TBK / 16; ++k) {
@@ -1017,6 +1042,13 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                 smem_u32(&empty[st]))
                             : "memory");
+                        if (l == 0) {
+                            asm volatile(
+                                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                    smem_u32(&emptyx[sx]))
+                                : "memory");
+                            ++gx;
+                        }
                     }
                     if (!fine) break;
                     asm volatile(
@@ -1025,7 +1057,7 @@ __global__ void __launch_bounds__(FM_TH, 1) k_mlp_fused(const __grid_constant__ 
                         : "memory");
                 }
         }
-    } else {   // ---- epilogue: warps 2..17, TMEM lanes 32 (warp % 4) ..
+    } else if (warp < FM_XW) {   // ---- epilogue: warps 2..17, TMEM lanes 32 (warp % 4) ..
         // warp group g = (warp - 2) / 4 owns the 32-column chunks g and g + 4: chunk g lies in
         // K-block g / 2 (0 or 1), chunk g + 4 in K-block g / 2 + 2, so the sixteen warps
         // complete K-blocks 0 and 1 first; eight warps write each K-block

@@ -1,8 +1,9 @@
 """CPU model of the barrier protocol of the fused closure network (k_mlp_fused).
 
 The kernel's roles:
-- a copy warp streams the K-blocks of every layer's weights, and the first layer's
-  features, through a ring of stages;
+- a copy warp streams the K-blocks of every layer's weights through a ring of stages,
+  and another the tiles' feature K-blocks (the first layer's input) through a ring of
+  their own;
 - an MMA warp runs use u = 4 n + l (tile n, layer l) into TMEM accumulator u mod 2;
 - sixteen epilogue warps drain an accumulator into registers, 32 columns at a time,
   release it, and write the next layer's input into the shared activation tile; eight
@@ -13,8 +14,9 @@ Copies and MMA completions land asynchronously and the warps are scheduled at ra
 model follows the kernel's waits and arrivals (barrier counts, phase parities) and
 checks:
 - it never deadlocks;
-- an MMA reads the K-block the copies filled for it, and the activation K-block of the
-  layer before, once the eight epilogue warps that write it did;
+- an MMA reads the weight and feature K-blocks the copies filled for it, and the
+  activation K-block of the layer before, once the eight epilogue warps that write it
+  did;
 - the epilogue never writes an activation K-block while MMAs still read it;
 - no accumulator is overwritten before it was drained.
 Removing any one of the MMA warp's waits makes it fail."""
@@ -27,7 +29,7 @@ from tests.test_gemm_protocol_model import MBar
 LAYERS = 4
 
 
-def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
+def run(ntiles, nkb, stages, epi_warps, seed, skip=None, xstages=3):
     """nkb[l]: K-blocks of layer l; layers 1..3 read the hidden width, nkb[1] K-blocks
     of the activation tile."""
     rnd = random.Random(seed)
@@ -37,8 +39,12 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
     acce = [MBar(epi_warps) for _ in range(2)]
     nact = nkb[1]
     actf = [MBar(epi_warps // 2) for _ in range(nact)]
+    fullx = [MBar(1) for _ in range(xstages)]
+    emptyx = [MBar(1) for _ in range(xstages)]
     stage_holds = [None] * stages        # (tile, layer, K-block) the copies put there
     mma_reads = [None] * stages
+    xstage_holds = [None] * xstages      # (tile, K-block) of the features
+    xmma_reads = [None] * xstages
     acc = [None, None]                   # (tile, layer) whose sums the accumulator holds
     acc_busy = [False, False]            # MMAs in flight into it
     drained = [0, 0]
@@ -62,8 +68,22 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
                     g += 1
                     yield
 
-    def mmas():
+    def xcopies():
         g = 0
+        for t in range(ntiles):
+            for kb in range(nkb[0]):
+                st, use = g % xstages, g // xstages
+                if g >= xstages:
+                    while not emptyx[st].done((use - 1) & 1):
+                        yield
+                assert xmma_reads[st] is None, "feature stage refilled while the MMAs read it"
+                fullx[st].expect(1)
+                events.append(("xcopy", st, (t, kb)))
+                g += 1
+                yield
+
+    def mmas():
+        g = gx = 0
         for t in range(ntiles):
             for l in range(LAYERS):
                 u = 4 * t + l
@@ -79,6 +99,13 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
                     while not full[st].done((g // stages) & 1):
                         yield
                     assert stage_holds[st] == (t, l, kb)
+                    sx = gx % xstages
+                    if l == 0:
+                        if skip != "fullx":
+                            while not fullx[sx].done((gx // xstages) & 1):
+                                yield
+                        assert xstage_holds[sx] == (t, kb), "features read before they landed"
+                        xmma_reads[sx] = (t, kb)
                     if l > 0:
                         if skip != "actf":
                             while not actf[kb].done((3 * t + l - 1) & 1):
@@ -87,8 +114,10 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
                             "layer input read before the epilogue wrote it"
                         act_reads[kb] += 1
                     mma_reads[st] = (t, l, kb)
-                    events.append(("mma", st, kb if l > 0 else None))
+                    events.append(("mma", st, kb if l > 0 else None, sx if l == 0 else None))
                     g += 1
+                    if l == 0:
+                        gx += 1
                     yield
                 events.append(("acc", b, (t, l)))
 
@@ -122,7 +151,7 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
                         actf[kb].arrive()
                 yield
 
-    warps = [copies(), mmas()] + [epilogue(e) for e in range(epi_warps)]
+    warps = [copies(), xcopies(), mmas()] + [epilogue(e) for e in range(epi_warps)]
     alive = set(range(len(warps)))
     for _ in range(5_000_000):
         if not alive and not events:
@@ -130,17 +159,23 @@ def run(ntiles, nkb, stages, epi_warps, seed, skip=None):
         if events and (not alive or rnd.random() < 0.3):
             # copies land in any order; MMA completions in issue order
             k = rnd.randrange(len(events))
-            if events[k][0] != "copy":
-                k = next(q for q, ev in enumerate(events) if ev[0] != "copy")
-            kind, a, val = events.pop(k)
+            if events[k][0] not in ("copy", "xcopy"):
+                k = next(q for q, ev in enumerate(events) if ev[0] not in ("copy", "xcopy"))
+            kind, a, val, *rest = events.pop(k)
             if kind == "copy":
                 stage_holds[a] = val
                 full[a].complete(1)
+            elif kind == "xcopy":
+                xstage_holds[a] = val
+                fullx[a].complete(1)
             elif kind == "mma":
                 mma_reads[a] = None
                 if val is not None:
                     act_reads[val] -= 1
                 empty[a].arrive()
+                if rest[0] is not None:
+                    xmma_reads[rest[0]] = None
+                    emptyx[rest[0]].arrive()
             else:
                 acc[a], acc_busy[a] = val, False
                 accf[a].arrive()
@@ -159,14 +194,14 @@ def _shapes(r):
     return [r.randint(1, 5), h, h, h]
 
 
-@pytest.mark.parametrize("stages", [2, 3])
-def test_fused_network_protocol(stages):
+@pytest.mark.parametrize("stages,xstages", [(2, 2), (3, 3), (3, 2)])
+def test_fused_network_protocol(stages, xstages):
     for seed in range(150):
         r = random.Random(seed)
-        run(r.randint(1, 4), _shapes(r), stages, 16, seed)
+        run(r.randint(1, 4), _shapes(r), stages, 16, seed, xstages=xstages)
 
 
-@pytest.mark.parametrize("skip", ["acce", "actf"])
+@pytest.mark.parametrize("skip", ["acce", "actf", "fullx"])
 def test_the_model_catches_a_missing_wait(skip):
     with pytest.raises(AssertionError):
         for seed in range(150):
