@@ -193,7 +193,10 @@ constexpr int TTY = TY + 1, NTT = TX * TTY;
 template <typename R> struct Occ4 { static constexpr int value = TY == 8 ? 4 : 2; };
 template <> struct Occ4<double> { static constexpr int value = 1; };
 // the variants with the optional vertical schemes keep more registers: 3 blocks per SM
-// of the 32 x 8 tiles
+// of the 32 x 8 tiles.  The momentum tile takes that budget in every form: at 3 blocks
+// per SM its FP32 step needs 73 registers and spills none (4.92 -> 4.87 ms at 1/12
+// degree, against 4 blocks with 64 registers and a spill); the tracer tile stays at 4
+// (6.37 ms against 6.51 at 3 blocks)
 template <typename R, bool X> struct OccX { static constexpr int value = X ? (TY == 8 ? 3 : 1) : Occ4<R>::value; };
 template <bool X> struct OccX<double, X> { static constexpr int value = 1; };
 
@@ -1035,7 +1038,7 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
 }
 
 template <typename R, bool STEP, bool VA>
-__global__ void __launch_bounds__(NT, (OccX<R, VA>::value)) k_momentum(
+__global__ void __launch_bounds__(NT, (OccX<R, true>::value)) k_momentum(
     KP<R> p, const __grid_constant__ TileMaps tm, const __grid_constant__ MomentumArgs<R> a) {
     momentum_tile<R, STEP, VA>(p, tm, blockIdx.x, blockIdx.y, a);
 }
