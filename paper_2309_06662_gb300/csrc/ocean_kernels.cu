@@ -750,14 +750,23 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
         kzu = max(kzu, (int)sm.kbzin[ty + n][tx + 2]);
         kzv = max(kzv, (int)sm.kbzin[ty + 2][tx + n]);
     }
-    // corner slot: lowest active level << 16 | row << 8 | column (-1: none); centre slot:
-    // row << 8 | column (-1: none)
+    // corner slot (-1: none): its offset in a level's u / v tile (row a, column b) in bits
+    // 0..9, in the vorticity buffer in bits 10..18, the row a in bits 19..22 and its lowest
+    // active level from bit 23; centre slot (-1: none): the offset of u(row a + 2, column
+    // b + 3) in a u / v tile in bits 0..9, of the centre in the kinetic-energy buffer from
+    // bit 10
+    static_assert((TY + 4) * (TX + 8) + TX + 4 < 1024 && (TY + 5) * (TX + 5) < 512 && TY + 5 <= 16 &&
+                  OC_NZMAX < 256 && (TY + 1) * (TX + 1) < (1 << 20), "slot fields");
     auto zslot = [&](int q) {
         if (q >= NCR) return -1;
         const int a = q / (TX + 5), b = q % (TX + 5);
-        return ((int)sm.kbz[a][b] << 16) | (a << 8) | b;
+        return (a * (TX + 8) + b) | ((a * (TX + 5) + b) << 10) | (a << 19) | ((int)sm.kbz[a][b] << 23);
     };
-    auto kslot = [&](int q) { return q < TC ? ((q / (TX + 1)) << 8) | (q % (TX + 1)) : -1; };
+    auto kslot = [&](int q) {
+        if (q >= TC) return -1;
+        const int a = q / (TX + 1), b = q % (TX + 1);
+        return ((a + 2) * (TX + 8) + b + 3) | ((a * (TX + 1) + b) << 10);
+    };
     const int zs0 = zslot(tid), zs1 = zslot(tid + NT), ko0 = kslot(tid), ko1 = kslot(tid + NT);
     R sUn = 0, sGU = 0, sVn = 0, sGV = 0;
     R cuk = 0, duk = 0, cvk = 0, dvk = 0;
@@ -789,28 +798,31 @@ __device__ __forceinline__ void momentum_tile(const KP<R>& p, const TileMaps& tm
         const unsigned pc = (unsigned)q3 & 1u, pn = (unsigned)(r3 == 2 ? q3 + 1 : q3) & 1u;
         bar_wait(&sm.bar[sc], pc);
         // ---- corner vorticity (zero unless all four cells are wet) and kinetic energy
+        const R* const ul = &sm.u[sc][0][0];
+        const R* const vl = &sm.v[sc][0][0];
         auto corner = [&](const int zsr) {
-            const int a = (zsr >> 8) & 255, b = zsr & 255;
-            const R* us = &sm.u[sc][a][b];
-            const R* vs = &sm.v[sc][a][b];
+            const int a = (zsr >> 19) & 15;
+            const R* us = ul + (zsr & 1023);
+            const R* vs = vl + (zsr & 1023);
             R zz = R(0);
-            if (k >= (zsr >> 16)) {
+            if (k >= (zsr >> 23)) {
                 // a.u(i, jc) = a.u[a + 1][b], a.u(i, jc-1) = a.u[a][b]; a.v(i, jc) = a.v[a][b + 1],
                 // a.v(i-1, jc) = a.v[a][b]  (tile columns offset by 2 for a.u, 1 for a.v)
                 const R circ = p.dy * (vs[2] - vs[1])
                              - (sm.zdxN[a] * us[(TX + 8) + 2] - sm.zdxS[a] * us[2]);
                 zz = circ * sm.zrA[a];
             }
-            sm.z[fb][a][b] = zz;
+            (&sm.z[fb][0][0])[(zsr >> 10) & 511] = zz;
         };
         corner(zs0);
         if (zs1 >= 0) corner(zs1);
         auto centre = [&](const int kor) {
-            const int a = kor >> 8, b = kor & 255;
-            // centre (i0-1+b, j0-1+a): a.u at cols b+1, b+2 of row a+2; a.v at col b+2, rows a+1, a+2
-            const R ua = sm.u[sc][a + 2][(b + 1) + 2], ub = sm.u[sc][a + 2][(b + 2) + 2];
-            const R va = sm.v[sc][a + 1][(b + 2) + 1], vb = sm.v[sc][a + 2][(b + 2) + 1];
-            sm.K[fb][a][b] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
+            // centre (i0-1+b, j0-1+a): a.u at cols b+1, b+2 of row a+2; a.v at col b+2, rows
+            // a+1, a+2 (tile columns offset by 2 for a.u, 1 for a.v: the same tile offset)
+            const int o = kor & 1023;
+            const R ua = ul[o], ub = ul[o + 1];
+            const R va = vl[o - (TX + 8)], vb = vl[o];
+            (&sm.K[fb][0][0])[kor >> 10] = R(0.25) * (ua * ua + ub * ub) + R(0.25) * (va * va + vb * vb);
         };
         centre(ko0);
         if (ko1 >= 0) centre(ko1);
