@@ -70,22 +70,22 @@ __device__ __forceinline__ void diag_col(const KP<R>& p, const long c, const R* 
     const int kb = g.kb[c2], nz = g.nz;
     if (kb >= nz) return;
     const long P = g.plane;
-    // pressure anomaly, integrated downward from the surface (T and S of four levels
+    // pressure anomaly, integrated downward from the surface (T and S of eight levels
     // loaded at once; the recurrence is serial)
     R bup = buoy_anom(p, T[(nz - 1) * P + c2], S[(nz - 1) * P + c2]);
     R pk = -rmul(bup, p.ptop);
     pr[(nz - 1) * P + c2] = pk;
 #pragma unroll 1
-    for (int k4 = nz - 2; k4 >= kb; k4 -= 4) {
-        R tq[4], sq[4];
+    for (int k4 = nz - 2; k4 >= kb; k4 -= 8) {
+        R tq[8], sq[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const bool in = k4 - q >= kb;
             tq[q] = in ? T[(long)(k4 - q) * P + c2] : R(0);
             sq[q] = in ? S[(long)(k4 - q) * P + c2] : R(0);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const int k = k4 - q;
             if (k < kb) break;
             R bk = buoy_anom(p, tq[q], sq[q]);
