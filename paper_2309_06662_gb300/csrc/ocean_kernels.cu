@@ -1600,30 +1600,46 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
         R ku2 = R(0), kv2 = R(0);
         const int k0 = __reduce_min_sync(__activemask(), min(kb, min(ku, kv)));   // warp-uniform
         const IDX plane = (IDX)g.plane, pitch = (IDX)g.pitch;
-        IDX ck = (IDX)k0 * plane + (IDX)c2;
-#pragma unroll 4
-        for (int k = k0; k < g.nz; ++k, ck += plane) {
-            const R tq = T[ck], sq = S[ck], uq = u[ck], vq = v[ck];
-            // one test for the four values (a NaN or infinity in any makes the sum
-            // non-finite; physical values are far from overflowing it)
-            bad = bad || !isfinite(tq + sq + uq + vq);
-            const R dzr = (R)m.dz[k];
-            if (k >= kb) {
-                tcol = fma(tq, dzr, tcol);
-                scol = fma(sq, dzr, scol);
-                cflr = fmax(cflr, fabs(wk) * (R)m.dtdz[k]);   // w on the level's floor
-                if (k < g.nz - 1) {
-                    const R div = dyr * dzr * (u[ck + 1] - uq) + dzr * (dxvN * v[ck + pitch] - dxvS * vq);
-                    wk = wk - div * rac;
+        IDX ck0 = (IDX)k0 * plane + (IDX)c2;
+        // four levels' operands loaded at once (24 loads in flight per column), then used
+        for (int k4 = k0; k4 < g.nz; k4 += 4, ck0 += 4 * plane) {
+            R tq[4], sq[4], uq[4], vq[4], ueq[4], vnq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const IDX ck = ck0 + (IDX)q * plane;
+                const bool in = k4 + q < g.nz;
+                tq[q] = in ? T[ck] : R(0);
+                sq[q] = in ? S[ck] : R(0);
+                uq[q] = in ? u[ck] : R(0);
+                vq[q] = in ? v[ck] : R(0);
+                ueq[q] = in ? u[ck + 1] : R(0);
+                vnq[q] = in ? v[ck + pitch] : R(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = k4 + q;
+                if (k >= g.nz) break;
+                // one test for the four values (a NaN or infinity in any makes the sum
+                // non-finite; physical values are far from overflowing it)
+                bad = bad || !isfinite(tq[q] + sq[q] + uq[q] + vq[q]);
+                const R dzr = (R)m.dz[k];
+                if (k >= kb) {
+                    tcol = fma(tq[q], dzr, tcol);
+                    scol = fma(sq[q], dzr, scol);
+                    cflr = fmax(cflr, fabs(wk) * (R)m.dtdz[k]);   // w on the level's floor
+                    if (k < g.nz - 1) {
+                        const R div = dyr * dzr * (ueq[q] - uq[q]) + dzr * (dxvN * vnq[q] - dxvS * vq[q]);
+                        wk = wk - div * rac;
+                    }
                 }
-            }
-            if (k >= ku) {
-                ku2 += uq * uq * dzr;
-                cflr = fmax(cflr, fabs(uq) * dtr * rdx);
-            }
-            if (k >= kv) {
-                kv2 += vq * vq * dzr;
-                cflr = fmax(cflr, fabs(vq) * dtr * rdyr);
+                if (k >= ku) {
+                    ku2 += uq[q] * uq[q] * dzr;
+                    cflr = fmax(cflr, fabs(uq[q]) * dtr * rdx);
+                }
+                if (k >= kv) {
+                    kv2 += vq[q] * vq[q] * dzr;
+                    cflr = fmax(cflr, fabs(vq[q]) * dtr * rdyr);
+                }
             }
         }
         if (kb < g.nz) {
