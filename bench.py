@@ -559,8 +559,8 @@ def learned_main(args, case, wname, rank, world, local, dist, with_cpu=True):
         if closure == ocean.OCEAN_CLOSURE_LEARNED:
             # end to end through the C ABI, per step: the wind stress from pinned host
             # memory, one step with the network in the loop, the diagnostics back
-            taux = torch.from_numpy(np.ascontiguousarray(case.taux)).pin_memory().numpy()
-            tauy = torch.from_numpy(np.ascontiguousarray(case.tauy)).pin_memory().numpy()
+            taux = torch.from_numpy(np.ascontiguousarray(case.taux, dtype=np.float32)).pin_memory().numpy()
+            tauy = torch.from_numpy(np.ascontiguousarray(case.tauy, dtype=np.float32)).pin_memory().numpy()
             barrier()
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
@@ -572,8 +572,8 @@ def learned_main(args, case, wname, rank, world, local, dist, with_cpu=True):
             res[name]["e2e"] = {"value": cells / e2e_s * world, "unit": "cell-updates/s",
                                 "h2d_bytes_per_step": int(taux.nbytes + tauy.nbytes),
                                 "d2h_bytes_per_step": 8 * 8, "healthy": not d["nonfinite"],
-                                "what": "per step: wind stress host->device, one step with "
-                                        "the network, diagnostics device->host"}
+                                "what": "per step: wind stress (FP32) host->device, one step "
+                                        "with the network, diagnostics device->host"}
         m.close()
         del m
         torch.cuda.empty_cache()
@@ -686,8 +686,9 @@ def ensemble_main(args, cases, wname, rank, world, local, dist, with_cpu=True):
         roofline.barotropic_bytes_per_column(esz, 30) * wet_cols
     # end to end: per step every member's wind stress from pinned host memory, the
     # ensemble step, and every member's diagnostics read back
-    winds = [(torch.from_numpy(np.ascontiguousarray(c.taux)).pin_memory().numpy(),
-              torch.from_numpy(np.ascontiguousarray(c.tauy)).pin_memory().numpy()) for c in cases]
+    winds = [(torch.from_numpy(np.ascontiguousarray(c.taux, dtype=np.float32)).pin_memory().numpy(),
+              torch.from_numpy(np.ascontiguousarray(c.tauy, dtype=np.float32)).pin_memory().numpy())
+             for c in cases]
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -854,8 +855,9 @@ def main():
                                 "kernels": -(-int(p["n_substeps"]) // 6) + 2}
 
     # ---------------------------------------------------------------- end to end, host buffers
-    taux = torch.from_numpy(np.ascontiguousarray(case.taux)).pin_memory().numpy()
-    tauy = torch.from_numpy(np.ascontiguousarray(case.tauy)).pin_memory().numpy()
+    # the mixed model takes its wind in FP32 (ocean_set_wind_stress_f32: half the bytes)
+    taux = torch.from_numpy(np.ascontiguousarray(case.taux, dtype=np.float32)).pin_memory().numpy()
+    tauy = torch.from_numpy(np.ascontiguousarray(case.tauy, dtype=np.float32)).pin_memory().numpy()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -926,7 +928,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "cell-updates/s",
                     "h2d_bytes_per_step": int(taux.nbytes + tauy.nbytes),
                     "d2h_bytes_per_step": 8 * 8, "healthy": healthy,
-                    "what": "per step: wind stress host->device, one step, diagnostics "
+                    "what": "per step: wind stress (FP32) host->device, one step, diagnostics "
                             "(conservation sums, CFL, NaN check) device->host"},
             "gpu_launches": launches,
             "clocks": clk.summary(),

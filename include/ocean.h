@@ -200,6 +200,12 @@ int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref);
  * reuse the arrays at once.  Errors: OCEAN_ERR_ARG (null handle), OCEAN_ERR_CUDA. */
 int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy);
 
+/* The same from FP32 host arrays: half the bytes over the host link.  Each value is
+ * widened to FP64 before the scaling, so a float array gives the fields that the double
+ * array of the same values gives (in either precision of the model; an FP64 model then
+ * sees the float values).  Errors: OCEAN_ERR_ARG (null handle), OCEAN_ERR_CUDA. */
+int ocean_set_wind_stress_f32(ocean_t h, const float* taux, const float* tauy);
+
 /* Advance n >= 0 steps and wait for them; runs the health check when check_every > 0.
  * One step n -> n+1 is the sequence of the paper's Sec. "New numerical methods for finite
  * volume fluid dynamics on the sphere" and Sec. "Optimization of ocean free surface

@@ -502,27 +502,27 @@ int build_geometry(ocean_t m, const double* depth) {
 
 // The host arrays go to a device staging area by two copies on the model's stream; a
 // kernel scales them by 1 / (rho0 dz_top) and writes them into the padded fields.
-// Returns once the host arrays have been read.
-int set_wind(ocean_t m, const double* taux, const double* tauy) {
+// Returns once the host arrays have been read.  W: double, or float (half the bytes).
+template <typename W>
+int set_wind(ocean_t m, const W* taux, const W* tauy) {
     const size_t n = (size_t)m->nx * m->ny;
-    double* raw = m->wind_raw;
+    W* raw = reinterpret_cast<W*>(m->wind_raw);   // room for 2 n doubles
     if (taux)
-        OC_CUDA(m, cudaMemcpyAsync(raw, taux, n * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+        OC_CUDA(m, cudaMemcpyAsync(raw, taux, n * sizeof(W), cudaMemcpyHostToDevice, m->stream));
     if (tauy)
-        OC_CUDA(m, cudaMemcpyAsync(raw + n, tauy, n * sizeof(double), cudaMemcpyHostToDevice,
-                                   m->stream));
+        OC_CUDA(m, cudaMemcpyAsync(raw + n, tauy, n * sizeof(W), cudaMemcpyHostToDevice, m->stream));
     const double s = 1.0 / (m->prm.rho0 * m->dz[m->nz - 1]);
     GeoD g{};
     g.nx = m->nx; g.ny = m->ny; g.nz = m->nz; g.px = m->px; g.py = m->py; g.pitch = m->pitch;
     g.plane = m->plane;
     if (m->prec == OCEAN_FP64)
-        launch_wind<double>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
-                            reinterpret_cast<double*>(m->taux_s), reinterpret_cast<double*>(m->tauy_s),
-                            m->stream);
+        launch_wind<double, W>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
+                               reinterpret_cast<double*>(m->taux_s),
+                               reinterpret_cast<double*>(m->tauy_s), m->stream);
     else
-        launch_wind<float>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
-                           reinterpret_cast<float*>(m->taux_s), reinterpret_cast<float*>(m->tauy_s),
-                           m->stream);
+        launch_wind<float, W>(g, taux ? raw : nullptr, tauy ? raw + n : nullptr, s,
+                              reinterpret_cast<float*>(m->taux_s),
+                              reinterpret_cast<float*>(m->tauy_s), m->stream);
     OC_CUDA(m, cudaGetLastError());
     OC_CUDA(m, cudaStreamSynchronize(m->stream));
     return OCEAN_OK;
@@ -872,7 +872,7 @@ int create_common(const ocean_grid* grid, const double* depth, const ocean_param
         return fail(nullptr, OCEAN_ERR_CUDA, "the driver refused the tile kernels' tensor maps");
     }
     rc = build_geometry(m, depth);
-    if (rc == OCEAN_OK) rc = set_wind(m, params->taux, params->tauy);
+    if (rc == OCEAN_OK) rc = set_wind<double>(m, params->taux, params->tauy);
     if (rc != OCEAN_OK) {
         ocean_destroy(m);
         return rc;
@@ -1159,7 +1159,12 @@ int ocean_set_reference(ocean_t h, const double* Tref, const double* Sref) {
 
 int ocean_set_wind_stress(ocean_t h, const double* taux, const double* tauy) {
     if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
-    return set_wind(h, taux, tauy);
+    return set_wind<double>(h, taux, tauy);
+}
+
+int ocean_set_wind_stress_f32(ocean_t h, const float* taux, const float* tauy) {
+    if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
+    return set_wind<float>(h, taux, tauy);
 }
 
 int ocean_step_async(ocean_t h, int n) {

@@ -482,9 +482,9 @@ void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s);
 template <typename R>
 void launch_halo2(const GeoD& g, R* f, cudaStream_t s);
 // surface wind stress: o[x|y][column] = (R)(t[x|y][j nx + i] * scale) on the padded
-// plane (zero where t is null)
-template <typename R>
-void launch_wind(const GeoD& g, const double* tx, const double* ty, double scale, R* ox, R* oy,
+// plane (zero where t is null); t is double or float, the product is taken in FP64
+template <typename R, typename W>
+void launch_wind(const GeoD& g, const W* tx, const W* ty, double scale, R* ox, R* oy,
                  cudaStream_t s);
 template <typename R>
 int setup_kernel_attributes(int nz);

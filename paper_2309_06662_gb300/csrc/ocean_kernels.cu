@@ -1469,14 +1469,16 @@ template <typename R> struct PtrPack { R* f[4]; };
 // periodic copies: x halo columns of the interior rows, then y halo rows of the full
 // padded width (so the corners come out right)
 
-template <typename R>
-__global__ void k_wind(GeoD g, const double* __restrict__ tx, const double* __restrict__ ty,
+// W: the host arrays' type (double, or float); the scaling is in FP64 either way, so a
+// float array and the double array of the same values give the same fields
+template <typename R, typename W>
+__global__ void k_wind(GeoD g, const W* __restrict__ tx, const W* __restrict__ ty,
                        double scale, R* __restrict__ ox, R* __restrict__ oy) {
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const long c2 = ix2(g, (int)(c % g.nx), (int)(c / g.nx));
-    ox[c2] = tx ? (R)(tx[c] * scale) : R(0);
-    oy[c2] = ty ? (R)(ty[c] * scale) : R(0);
+    ox[c2] = tx ? (R)((double)tx[c] * scale) : R(0);
+    oy[c2] = ty ? (R)((double)ty[c] * scale) : R(0);
 }
 
 template <typename R>
@@ -1531,11 +1533,11 @@ void launch_halo3(const GeoD& g, R* const* f, int nf, cudaStream_t s) {
     for (int q = 0; q < nf; q += 4) halo_pack<R>(g, f + q, nf - q < 4 ? nf - q : 4, g.nz, s);
 }
 
-template <typename R>
-void launch_wind(const GeoD& g, const double* tx, const double* ty, double scale, R* ox, R* oy,
+template <typename R, typename W>
+void launch_wind(const GeoD& g, const W* tx, const W* ty, double scale, R* ox, R* oy,
                  cudaStream_t s) {
     const long n = (long)g.nx * g.ny;
-    k_wind<R><<<nblocks(n, TPB), TPB, 0, s>>>(g, tx, ty, scale, ox, oy);
+    k_wind<R, W><<<nblocks(n, TPB), TPB, 0, s>>>(g, tx, ty, scale, ox, oy);
 }
 
 template <typename R>
@@ -2000,8 +2002,10 @@ int tile_wait_failed() {
     template void launch_correct<R>(const KP<R>&, const StepBuffers<R>&, cudaStream_t);     \
     template void launch_halo3<R>(const GeoD&, R* const*, int, cudaStream_t);               \
     template void launch_halo2<R>(const GeoD&, R*, cudaStream_t);                           \
-    template void launch_wind<R>(const GeoD&, const double*, const double*, double, R*, R*,  \
-                                 cudaStream_t);                                             \
+    template void launch_wind<R, double>(const GeoD&, const double*, const double*, double, \
+                                         R*, R*, cudaStream_t);                             \
+    template void launch_wind<R, float>(const GeoD&, const float*, const float*, double, R*, \
+                                        R*, cudaStream_t);                                  \
     template void launch_diagnostics<R>(const GeoD&, const DiagMetrics&, const R*, const R*, \
                                         const R*, const R*, const double*, double*, double*, \
                                         cudaStream_t);                \

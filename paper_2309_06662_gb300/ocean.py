@@ -94,7 +94,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         if not os.path.exists(path):
             raise RuntimeError(f"libocean.so not built ({path}); run paper_2309_06662_gb300.build")
         L = ctypes.CDLL(path)
-        pv, pd = c_void_p, POINTER(c_double)
+        pv, pd, pf = c_void_p, POINTER(c_double), POINTER(ctypes.c_float)
         sig = {
             "ocean_arena_bytes": (c_int, [POINTER(OceanGrid), POINTER(OceanParams), POINTER(c_size_t)]),
             "ocean_create": (c_int, [POINTER(OceanGrid), pd, POINTER(OceanParams), POINTER(pv)]),
@@ -105,6 +105,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
             "ocean_set_field": (c_int, [pv, c_int, pd, c_size_t]),
             "ocean_get_field": (c_int, [pv, c_int, pd, c_size_t]),
             "ocean_set_wind_stress": (c_int, [pv, pd, pd]),
+            "ocean_set_wind_stress_f32": (c_int, [pv, pf, pf]),
             "ocean_get_reference": (c_int, [pv, pd, pd]),
             "ocean_set_reference": (c_int, [pv, pd, pd]),
             "ocean_step": (c_int, [pv, c_int]),
@@ -406,7 +407,13 @@ class Ocean:
         return t
 
     def set_wind_stress(self, taux, tauy) -> None:
-        """Replace the surface wind stress ([ny][nx], N/m^2); the arrays are copied."""
+        """Replace the surface wind stress ([ny][nx], N/m^2); the arrays are copied.
+        Two float32 arrays go through ocean_set_wind_stress_f32 (half the bytes), anything
+        else as float64."""
+        if getattr(taux, "dtype", None) == np.float32 and getattr(tauy, "dtype", None) == np.float32:
+            tx, ty = np.ascontiguousarray(taux), np.ascontiguousarray(tauy)
+            _check(load().ocean_set_wind_stress_f32(self._h, _fp(tx), _fp(ty)), self._h)
+            return
         tx = np.ascontiguousarray(taux, dtype=np.float64)
         ty = np.ascontiguousarray(tauy, dtype=np.float64)
         _check(load().ocean_set_wind_stress(self._h, _dp(tx), _dp(ty)), self._h)

@@ -327,3 +327,22 @@ def test_wind_stress_replaced_after_creation_matches_the_oracle_built_with_it():
     o.step(10)
     errs = state_errors(g, o)
     assert all(e <= FP64_TOL for e in errs.values()), errs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [ocean.OCEAN_FP64, ocean.OCEAN_MIXED])
+def test_wind_stress_from_float_arrays_is_bitwise_the_double_upload(precision):
+    # ocean_set_wind_stress_f32 widens each value to FP64 before scaling it, so float
+    # arrays and the double arrays of the same values give the same model, bit for bit
+    a = _moving_state(inputs.latlon_small_case())
+    rng = np.random.default_rng(5)
+    tx = rng.normal(0.0, 0.1, a.taux.shape).astype(np.float32)
+    ty = rng.normal(0.0, 0.1, a.tauy.shape).astype(np.float32)
+    f = ocean.Ocean(a, precision=precision)
+    d = ocean.Ocean(a, precision=precision)
+    f.set_wind_stress(tx, ty)                                       # the float32 entry point
+    d.set_wind_stress(tx.astype(np.float64), ty.astype(np.float64))
+    f.step(5)
+    d.step(5)
+    for name in ("u", "v", "T_anom", "S_anom", "eta"):
+        assert np.array_equal(f.get(name), d.get(name)), name
