@@ -52,9 +52,20 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, 
         ubp = ub;
         vbp = vb;
         // T and S are stored as anomalies from the level reference, which is close to
-        // the feature mean: (T' + (Tref - mu)) keeps the resolution (T - mu) would lose
-        const float cT = w ? (float)((double)T[ck] + ((double)p.Tref[k] - (double)mu[k])) : 0.f;
-        const float cS = w ? (float)((double)S[ck] + ((double)p.Sref[k] - (double)mu[nz + k])) : 0.f;
+        // the feature mean: (T' + (Tref - mu)) keeps the resolution (T - mu) would lose.
+        // In FP32 the difference Tref - mu of two nearby values is exact, so one rounding
+        // of the sum gives what the FP64 sum rounded to FP32 gives, without FP64
+        // arithmetic (GB300's FP64 rate is a small fraction of its FP32 rate)
+        float cT = 0.f, cS = 0.f;
+        if (w) {
+            if constexpr (sizeof(R) == sizeof(float)) {
+                cT = (float)T[ck] + ((float)p.Tref[k] - mu[k]);
+                cS = (float)S[ck] + ((float)p.Sref[k] - mu[nz + k]);
+            } else {
+                cT = (float)((double)T[ck] + ((double)p.Tref[k] - (double)mu[k]));
+                cS = (float)((double)S[ck] + ((double)p.Sref[k] - (double)mu[nz + k]));
+            }
+        }
         const float raw[6] = {cT, cS, ub - mu[2 * nz + k], vb - mu[3 * nz + k],
                               n2 - mu[4 * nz + k], sh2 - mu[5 * nz + k]};
         const bool use[6] = {w, w, w, w, f, f};
