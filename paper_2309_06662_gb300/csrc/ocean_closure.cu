@@ -53,9 +53,11 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, 
         vbp = vb;
         // T and S are stored as anomalies from the level reference, which is close to
         // the feature mean: (T' + (Tref - mu)) keeps the resolution (T - mu) would lose.
-        // In FP32 the difference Tref - mu of two nearby values is exact, so one rounding
-        // of the sum gives what the FP64 sum rounded to FP32 gives, without FP64
-        // arithmetic (GB300's FP64 rate is a small fraction of its FP32 rate)
+        // In FP32 the difference Tref - mu is exact when the two lie within a factor of
+        // two of each other (Sterbenz), so one rounding of the sum gives what the FP64 sum
+        // rounded to FP32 gives; otherwise one more FP32 rounding, far below the BF16
+        // rounding of the feature.  No FP64 arithmetic (GB300's FP64 rate is a small
+        // fraction of its FP32 rate)
         float cT = 0.f, cS = 0.f;
         if (w) {
             if constexpr (sizeof(R) == sizeof(float)) {
