@@ -45,8 +45,8 @@ extern "C" {
 #define OCEAN_ERR_STATE (-6)     /* call not valid in the handle's current state */
 
 #define OCEAN_FP64 0             /* every field and stencil in FP64 */
-#define OCEAN_MIXED 1            /* FP32 fields and stencils, FP64 free surface,
-                                    barotropic averages and conservation sums */
+#define OCEAN_MIXED 1            /* FP32 fields and stencils, FP64 free surface and
+                                    conservation sums */
 
 #define OCEAN_CLOSURE_RI 0       /* Richardson-number closure */
 #define OCEAN_CLOSURE_LEARNED 1  /* column MLP, with the Ri closure as fallback */

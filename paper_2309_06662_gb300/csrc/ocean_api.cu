@@ -73,6 +73,13 @@ struct ocean_s {
     void* levm = nullptr;   // 8 level arrays of nz elements
     void* lvt = nullptr;    // per-level rows of OC_LVROW constants of the tile kernels
     double *drow = nullptr, *dlev = nullptr;
+    // FP32 metrics of the mixed form's conservation reduction: dz, dt/dz (nz each), Ac
+    // (ny + 2H); and the reference part of the totals (sum over wet columns of the
+    // reference profiles' content, and the wet volume), formed on the host in FP64
+    float* dgf = nullptr;
+    double dconst[3] = {0.0, 0.0, 0.0};
+    bool dconst_ok = false;
+    std::vector<double> h_colT, h_colS, h_colV;
     double *diag_part = nullptr, *diag_out = nullptr;
     // host-side copies
     std::vector<short> h_kb, h_kbu, h_kbv;
@@ -215,6 +222,7 @@ size_t layout(ocean_t m, char* base) {
     m->lvt = c.take<char>((size_t)OC_LVROW * m->nz * e);
     m->drow = c.take<double>(3 * nr);
     m->dlev = c.take<double>(4 * (size_t)m->nz + 3 * ((size_t)m->nz + 1));
+    m->dgf = c.take<float>(2 * (size_t)m->nz + nr);
     m->diag_part = reinterpret_cast<double*>(c.take<char>(diag_partials_bytes((long)m->nx * m->ny)));
     m->diag_out = c.take<double>(8);
     m->cl_mu = c.take<float>(6 * (size_t)m->nz);
@@ -366,6 +374,16 @@ void upload_levels(ocean_t m) {
     }
     upload_real(m, lv, m->levm);
     upload_bytes(m, m->dlev, dl.data(), dl.size() * sizeof(double));
+    std::vector<float> fl(2 * (size_t)nz);
+    for (int k = 0; k < nz; ++k) {
+        fl[k] = (float)m->dz[k];
+        fl[nz + k] = (float)(m->prm.dt / m->dz[k]);
+    }
+    upload_bytes(m, m->dgf, fl.data(), fl.size() * sizeof(float));
+    m->h_colT.assign(cT, cT + nz + 1);
+    m->h_colS.assign(cS, cS + nz + 1);
+    m->h_colV.assign(cV, cV + nz + 1);
+    m->dconst_ok = false;
     // rows of the tile kernels (KP::lvt): dz, 1/dz, dt/(dz dzf) below and above, Tref,
     // Sref, and those factors times the reference profiles' level differences
     std::vector<double> rows((size_t)OC_LVROW * nz, 0.0);
@@ -440,6 +458,9 @@ int build_geometry(ocean_t m, const double* depth) {
         drow[2 * nr + jj] = m->h_rows[1][jj];
     }
     upload_bytes(m, m->drow, drow.data(), drow.size() * sizeof(double));
+    std::vector<float> acf((size_t)nr);
+    for (int jj = 0; jj < nr; ++jj) acf[jj] = (float)m->h_rows[7][jj];
+    upload_bytes(m, m->dgf + 2 * (size_t)m->nz, acf.data(), acf.size() * sizeof(float));
     upload_levels(m);
     // ---- averaging weights of the sub-cycle
     std::vector<double> fw((size_t)p.n_substeps);
@@ -793,6 +814,29 @@ void enqueue_tendencies(ocean_t m) {
     m->tend_valid = true;
 }
 
+// The reference profiles' part of the tracer totals and the wet volume: sums over the
+// wet columns of (sum from the column's lowest wet level to the top of Tref dz, Sref dz,
+// dz) times the column's area, in FP64 with Neumaier compensation.  They change only with
+// the reference profiles, so the mixed form's reduction adds them as constants.
+void reference_totals(ocean_t m) {
+    double s[3] = {0.0, 0.0, 0.0}, cmp[3] = {0.0, 0.0, 0.0};
+    const std::vector<double>* cols[3] = {&m->h_colT, &m->h_colS, &m->h_colV};
+    for (int j = 0; j < m->ny; ++j) {
+        const double ac = m->h_rows[7][j + OC_H];
+        for (int i = 0; i < m->nx; ++i) {
+            const int kb = m->h_kb[(size_t)(j + OC_H) * m->pitch + (i + OC_H)];
+            if (kb >= m->nz) continue;
+            for (int q = 0; q < 3; ++q) {
+                const double x = (*cols[q])[kb] * ac, t = s[q] + x;
+                cmp[q] += std::fabs(s[q]) >= std::fabs(x) ? (s[q] - t) + x : (x - t) + s[q];
+                s[q] = t;
+            }
+        }
+    }
+    for (int q = 0; q < 3; ++q) m->dconst[q] = s[q] + cmp[q];
+    m->dconst_ok = true;
+}
+
 template <typename R>
 void enqueue_diagnostics(ocean_t m) {
     const KP<R> k = make_kp<R>(m, m->nstep == 0);
@@ -803,6 +847,22 @@ void enqueue_diagnostics(ocean_t m) {
     DiagMetrics dm{m->drow, m->drow + nr, m->drow + 2 * nr, m->dlev, m->dlev + nz,
                    m->dlev + 2 * nz, m->dlev + 3 * nz, cols, cols + nz + 1, cols + 2 * (nz + 1),
                    m->dy, 1.0 / m->dy, m->prm.dt};
+    if (sizeof(R) == sizeof(float)) {   // the mixed form's FP32 metrics and constant parts
+        if (!m->dconst_ok) reference_totals(m);
+        const float* rows = reinterpret_cast<const float*>(m->rowm);
+        dm.fdz = m->dgf;
+        dm.fdtdz = m->dgf + nz;
+        dm.fAc = m->dgf + 2 * nz;
+        dm.frdxc = rows + nr;
+        dm.fdxv = rows + 2 * nr;
+        dm.frAc = rows + 3 * nr;
+        dm.fdy = (float)m->dy;
+        dm.frdy = (float)(1.0 / m->dy);
+        dm.fdt = (float)m->prm.dt;
+        dm.cT = m->dconst[0];
+        dm.cS = m->dconst[1];
+        dm.cV = m->dconst[2];
+    }
     launch_diagnostics<R>(k.g, dm, b.u, b.v, b.T, b.S, m->eta, m->diag_part, m->diag_out,
                           m->stream);
 }

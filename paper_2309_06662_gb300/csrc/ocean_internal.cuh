@@ -495,6 +495,13 @@ int setup_kernel_attributes(int nz);
 struct DiagMetrics {
     const double *Ac, *dxv, *rdxc, *dz, *Tref, *Sref, *dtdz, *colT, *colS, *colV;
     double dy, rdy, dt;
+    // the mixed form's reduction: FP32 copies of the metrics (per level dz, dt/dz; per row
+    // Ac, 1/dx_c, dxv, 1/A_c) and the reference part of the totals (sum T dV, sum S dV of
+    // the reference profiles, the wet volume), which it adds as constants
+    const float *fdz = nullptr, *fdtdz = nullptr, *fAc = nullptr, *frdxc = nullptr,
+                *fdxv = nullptr, *frAc = nullptr;
+    float fdy = 0.f, frdy = 0.f, fdt = 0.f;
+    double cT = 0.0, cS = 0.0, cV = 0.0;
 };
 
 // Conservation/health reduction; `partials` is device scratch of at least

@@ -1059,6 +1059,23 @@ __global__ void __launch_bounds__(NT, (OccX<R, true>::value)) k_momentum(
 
 // start of the sub-cycle: U^0 = U^n, deta^0 = 0, accumulators cleared, the gradient of
 // the FP64 free surface eta^n formed once (in R)
+// The sub-cycle's sums over all passes, per column: FP64 words in the FP64 form; in the
+// mixed form FP32 words in the first half of the same storage (half the accumulators'
+// DRAM traffic per pass; the sums are of deviations from the step's start, O(1e-3) of
+// the state, so FP32's 24 bits over ten passes stay far below the mixed form's error)
+__device__ __forceinline__ void acc_add(double* a, long c, double p) { atomicAdd(a + c, p); }
+__device__ __forceinline__ void acc_add(double* a, long c, float p) {
+    atomicAdd(reinterpret_cast<float*>(a) + c, p);
+}
+template <typename R> __device__ __forceinline__ void acc_zero(double* a, long c) {
+    if (sizeof(R) == sizeof(float)) reinterpret_cast<float*>(a)[c] = 0.f;
+    else a[c] = 0.0;
+}
+template <typename R> __device__ __forceinline__ double acc_get(const double* a, long c) {
+    if (sizeof(R) == sizeof(float)) return (double)reinterpret_cast<const float*>(a)[c];
+    return a[c];
+}
+
 template <typename R>
 __device__ __forceinline__ void baro_begin_col(const KP<R>& p, const long c,
                                                const R* __restrict__ Un, const R* __restrict__ Vn,
@@ -1077,9 +1094,9 @@ __device__ __forceinline__ void baro_begin_col(const KP<R>& p, const long c,
     paccE[c2] = R(0);
     paccU[c2] = R(0);
     paccV[c2] = R(0);
-    accE[c2] = 0.0;
-    accU[c2] = 0.0;
-    accV[c2] = 0.0;
+    acc_zero<R>(accE, c2);
+    acc_zero<R>(accU, c2);
+    acc_zero<R>(accV, c2);
     gxe[c2] = Hu[c2] > R(0) ? R(eta[c2] - eta[c2 - 1]) : R(0);
     gye[c2] = Hv[c2] > R(0) ? R(eta[c2] - eta[c2 - g.pitch]) : R(0);
 }
@@ -1267,9 +1284,9 @@ __device__ __forceinline__ void baro_region(
         Vb[c] = vv[r];
         // one thread owns each cell: a reduction in memory is the plain FP64 add, issued
         // without waiting for the old value
-        atomicAdd(&accE[c], widen(pE[r]));
-        atomicAdd(&accU[c], widen(pU[r]));
-        atomicAdd(&accV[c], widen(pV[r]));
+        acc_add(accE, c, pE[r]);
+        acc_add(accU, c, pU[r]);
+        acc_add(accV, c, pV[r]);
     }
 }
 
@@ -1301,9 +1318,9 @@ __device__ __forceinline__ void baro_end_col(const KP<R>& p, const long c, doubl
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j);
-    if (g.kb[c2] < g.nz) eta[c2] = eta[c2] + accE[c2] * rns;
-    corrU[c2] = rHu[c2] > R(0) ? (R(accU[c2] * rns) + (Un[c2] - Su[c2])) * rHu[c2] : R(0);
-    corrV[c2] = rHv[c2] > R(0) ? (R(accV[c2] * rns) + (Vn[c2] - Sv[c2])) * rHv[c2] : R(0);
+    if (g.kb[c2] < g.nz) eta[c2] = eta[c2] + acc_get<R>(accE, c2) * rns;
+    corrU[c2] = rHu[c2] > R(0) ? (R(acc_get<R>(accU, c2) * rns) + (Un[c2] - Su[c2])) * rHu[c2] : R(0);
+    corrV[c2] = rHv[c2] > R(0) ? (R(acc_get<R>(accV, c2) * rns) + (Vn[c2] - Sv[c2])) * rHv[c2] : R(0);
 }
 
 template <typename R>
@@ -1709,6 +1726,122 @@ __global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums(
     }
 }
 
+// The mixed form of the same reduction without FP64 arithmetic per cell (GB300's FP64
+// unit runs conversions and adds at a small fraction of the FP32 rate, and the FP64
+// reduction spent most of its time there): the metrics come as FP32 copies, each
+// column's anomaly content and kinetic energy are formed in FP32 and summed over the warp
+// by the same pairwise tree in FP32, and only then widened, per warp, into the block's
+// FP64 tree.  The reference profiles' part of the tracer totals and the wet volume do
+// not change with the state: the host forms them once in FP64 and the final merge adds
+// them.  sum eta dA stays FP64 per column (eta is the FP64 state).
+template <typename IDX>
+__global__ void __launch_bounds__(OC_DIAG_THREADS) k_diag_sums_f32(
+    GeoD g, DiagMetrics m, const float* __restrict__ u, const float* __restrict__ v,
+    const float* __restrict__ T, const float* __restrict__ S, const double* __restrict__ eta,
+    double* __restrict__ partials) {
+    float fT = 0.f, fS = 0.f, fK = 0.f, cflr = 0.f;
+    double vE = 0.0;
+    bool bad = false;
+    const long ncol = (long)g.nx * g.ny;
+    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncol) {
+        const int i = (int)(c % g.nx), j = (int)(c / g.nx), jr = j + OC_H;
+        const long c2 = ix2(g, i, j);
+        const int kb = g.kb[c2], ku = g.kbu[c2], kv = g.kbv[c2];
+        const float ac = m.fAc[jr], av = m.fdxv[jr] * m.fdy, rdx = m.frdxc[jr];
+        const float dyr = m.fdy, dxvS = m.fdxv[jr], dxvN = m.fdxv[jr + 1], rac = m.frAc[jr];
+        const float dtr = m.fdt, rdyr = m.frdy;
+        // w for the CFL number, integrated up from the sea floor as in the FP64 form
+        float wk = 0.f, tcol = 0.f, scol = 0.f, ku2 = 0.f, kv2 = 0.f;
+        const int k0 = __reduce_min_sync(__activemask(), min(kb, min(ku, kv)));   // warp-uniform
+        const IDX plane = (IDX)g.plane, pitch = (IDX)g.pitch;
+        IDX ck0 = (IDX)k0 * plane + (IDX)c2;
+        // four levels' operands loaded at once (24 loads in flight per column), then used
+        for (int k4 = k0; k4 < g.nz; k4 += 4, ck0 += 4 * plane) {
+            float tq[4], sq[4], uq[4], vq[4], ueq[4], vnq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const IDX ck = ck0 + (IDX)q * plane;
+                const bool in = k4 + q < g.nz;
+                tq[q] = in ? T[ck] : 0.f;
+                sq[q] = in ? S[ck] : 0.f;
+                uq[q] = in ? u[ck] : 0.f;
+                vq[q] = in ? v[ck] : 0.f;
+                ueq[q] = in ? u[ck + 1] : 0.f;
+                vnq[q] = in ? v[ck + pitch] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = k4 + q;
+                if (k >= g.nz) break;
+                bad = bad || !isfinite(tq[q] + sq[q] + uq[q] + vq[q]);
+                const float dzr = m.fdz[k];
+                if (k >= kb) {
+                    tcol = fmaf(tq[q], dzr, tcol);
+                    scol = fmaf(sq[q], dzr, scol);
+                    cflr = fmaxf(cflr, fabsf(wk) * m.fdtdz[k]);   // w on the level's floor
+                    if (k < g.nz - 1) {
+                        const float div = dyr * dzr * (ueq[q] - uq[q]) + dzr * (dxvN * vnq[q] - dxvS * vq[q]);
+                        wk = wk - div * rac;
+                    }
+                }
+                if (k >= ku) {
+                    ku2 += uq[q] * uq[q] * dzr;
+                    cflr = fmaxf(cflr, fabsf(uq[q]) * dtr * rdx);
+                }
+                if (k >= kv) {
+                    kv2 += vq[q] * vq[q] * dzr;
+                    cflr = fmaxf(cflr, fabsf(vq[q]) * dtr * rdyr);
+                }
+            }
+        }
+        if (kb < g.nz) {
+            fT = tcol * ac;
+            fS = scol * ac;
+            vE = eta[c2] * m.Ac[jr];
+        }
+        fK = 0.5f * (ku2 * ac + kv2 * av);
+        bad = bad || !isfinite(eta[c2]);
+    }
+    int nb = bad ? 1 : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        fT += __shfl_down_sync(0xffffffffu, fT, off);
+        fS += __shfl_down_sync(0xffffffffu, fS, off);
+        fK += __shfl_down_sync(0xffffffffu, fK, off);
+        vE += __shfl_down_sync(0xffffffffu, vE, off);
+        cflr = fmaxf(cflr, __shfl_down_sync(0xffffffffu, cflr, off));
+        nb |= __shfl_down_sync(0xffffffffu, nb, off);
+    }
+    constexpr int NW = OC_DIAG_THREADS / 32;
+    __shared__ double ws[7][NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        ws[0][wid] = (double)fT; ws[1][wid] = (double)fS; ws[2][wid] = vE; ws[3][wid] = (double)fK;
+        ws[4][wid] = 0.0;   // the wet volume is a constant of the grid (added at the end)
+        ws[5][wid] = (double)cflr; ws[6][wid] = (double)nb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* o = partials + (long)blockIdx.x * 12;
+        for (int q = 0; q < 5; ++q) {
+            double a[NW];
+            for (int w = 0; w < NW; ++w) a[w] = ws[q][w];
+            for (int h = NW / 2; h > 0; h >>= 1)
+                for (int w = 0; w < h; ++w) a[w] += a[w + h];
+            o[2 * q] = a[0];
+            o[2 * q + 1] = 0.0;
+        }
+        double cm = 0.0, bm = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            cm = fmax(cm, ws[5][w]);
+            bm = fmax(bm, ws[6][w]);
+        }
+        o[10] = cm;
+        o[11] = bm;
+    }
+}
+
 // One block merges FIN_TH consecutive partials (of the first nblk) into partial blockIdx.x
 // of `merged`, with compensation, in a fixed tree: the FP64 work of the merge spread over
 // the GPU instead of one SM.
@@ -1748,7 +1881,8 @@ __global__ void __launch_bounds__(FIN_TH) k_diag_merge(const double* __restrict_
 // the per-block partial sums merged in a fixed tree: each of 256 threads merges
 // nblk / 256 consecutive partials, then pairs of threads halve the set
 __global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict__ partials,
-                                                       int nblk, double* out) {
+                                                       int nblk, double* out, double cT,
+                                                       double cS, double cV) {
     __shared__ CSum red[5][FIN_TH];
     __shared__ double rc[FIN_TH], rb[FIN_TH];
     const int t = threadIdx.x;
@@ -1773,13 +1907,15 @@ __global__ void __launch_bounds__(FIN_TH) k_diag_final(const double* __restrict_
         __syncthreads();
     }
     if (t == 0) {
-        out[0] = red[0][0].s + red[0][0].c;
-        out[1] = red[1][0].s + red[1][0].c;
+        // cT, cS, cV: the reference part of the totals when the blocks summed anomalies
+        // only (the mixed form), else 0
+        out[0] = cT + (red[0][0].s + red[0][0].c);
+        out[1] = cS + (red[1][0].s + red[1][0].c);
         out[2] = red[2][0].s + red[2][0].c;
         out[3] = red[3][0].s + red[3][0].c;
         out[4] = rc[0];
         out[5] = rb[0];
-        out[6] = red[4][0].s + red[4][0].c;
+        out[6] = cV + (red[4][0].s + red[4][0].c);
         out[7] = 0.0;
     }
 }
@@ -1798,15 +1934,24 @@ void launch_diagnostics(const GeoD& g, const DiagMetrics& m, const R* u, const R
                         cudaStream_t s) {
     const long ncol = (long)g.nx * g.ny;
     const int nblk = (int)((ncol + OC_DIAG_THREADS - 1) / OC_DIAG_THREADS);
-    if ((unsigned long long)g.plane * g.nz < (1ull << 32))
+    const bool small = (unsigned long long)g.plane * g.nz < (1ull << 32);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (small)
+            k_diag_sums_f32<unsigned><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
+        else
+            k_diag_sums_f32<long><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
+    } else if (small) {
         k_diag_sums<R, unsigned><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
-    else
+    } else {
         k_diag_sums<R, long><<<nblk, OC_DIAG_THREADS, 0, s>>>(g, m, u, v, T, S, eta, partials);
+    }
     // the block partials merged by blocks of FIN_TH, then those by one block
     const int nmrg = (nblk + FIN_TH - 1) / FIN_TH;
     double* merged = partials + (long)nblk * 12;
     k_diag_merge<<<nmrg, FIN_TH, 0, s>>>(partials, nblk, merged);
-    k_diag_final<<<1, FIN_TH, 0, s>>>(merged, nmrg, out);
+    const bool f32 = sizeof(R) == sizeof(float);
+    k_diag_final<<<1, FIN_TH, 0, s>>>(merged, nmrg, out, f32 ? m.cT : 0.0, f32 ? m.cS : 0.0,
+                                      f32 ? m.cV : 0.0);
 }
 
 // ------------------------------------------------------------------ batched ensemble

@@ -37,13 +37,15 @@ KERNEL_WORDS = {
 def barotropic_bytes_per_column(esz: int, n_substeps: int, per_pass: int = 6) -> float:
     """Bytes the split-explicit sub-cycle moves per wet column and step, as written: the
     begin kernel (U^n, V^n, H_u, H_v and FP64 eta^n in; U, V, deta, partial sums and the
-    eta gradients out, FP64 accumulators cleared), one temporally blocked pass per
+    eta gradients out, the three accumulators cleared), one temporally blocked pass per
     `per_pass` substeps (state deta, U, V, the six read-only terms and U^n, V^n in; the
-    state out and the three FP64 accumulators read and written), and the end kernel."""
+    state out and the three accumulators read and written), and the end kernel (the
+    accumulators and FP64 eta in, eta and the corrections out).  The accumulators have
+    the path's precision (esz bytes: FP32 in the mixed form, FP64 in the FP64 form)."""
     passes = -(-n_substeps // per_pass)
-    begin = 12 * esz + 8 + 24
-    one_pass = 14 * esz + 48
-    end = 8 * esz + 40
+    begin = 12 * esz + 8 + 3 * esz
+    one_pass = 14 * esz + 6 * esz
+    end = 8 * esz + 16 + 3 * esz
     return begin + passes * one_pass + end
 
 

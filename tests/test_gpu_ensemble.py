@@ -123,8 +123,8 @@ def test_member_diagnostics_and_checkpoint():
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_region_halo_widths_agree_to_rounding(precision):
     # the barotropic regions cut for 4 and 8 substeps per pass against the default 6: the
-    # same sub-cycle, with the FP32 partial averages added into the FP64 accumulators at
-    # other substeps (in FP64 the groupings differ only in the last bits)
+    # same sub-cycle, with the partial averages added into the accumulators at other
+    # substeps (in FP64 the groupings differ only in the last bits)
     cases = _cases(count=5, seed=45)
     D = ocean.Ensemble(cases, precision=precision)
     assert D.region_substeps == 6

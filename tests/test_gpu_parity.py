@@ -346,3 +346,22 @@ def test_wind_stress_from_float_arrays_is_bitwise_the_double_upload(precision):
     d.step(5)
     for name in ("u", "v", "T_anom", "S_anom", "eta"):
         assert np.array_equal(f.get(name), d.get(name)), name
+
+
+@pytest.mark.gpu
+def test_mixed_diagnostics_agree_with_the_fp64_reduction():
+    # the mixed form's reduction (FP32 metrics and column sums, the reference profiles'
+    # part of the totals and the wet volume formed once on the host) against the FP64
+    # reduction of the same state: the mixed model's fields, widened, set into an FP64
+    # model of the same case
+    c = _moving_state(inputs.latlon_small_case())
+    g = ocean.Ocean(c, precision=ocean.OCEAN_MIXED)
+    g.step(3)
+    h = ocean.Ocean(c, precision=ocean.OCEAN_FP64)
+    for name in ("u", "v", "T", "S", "eta"):
+        h.set(name, g.get(name))
+    dm, dd = g.diagnostics(), h.diagnostics()
+    for k, tol in (("tracer_T", 1e-6), ("tracer_S", 1e-6), ("wet_volume", 1e-12),
+                   ("ke", 1e-5), ("max_cfl", 1e-5)):
+        assert abs(dm[k] - dd[k]) <= tol * abs(dd[k]), (k, dm[k], dd[k])
+    assert not dm["nonfinite"] and not dd["nonfinite"]
