@@ -1145,21 +1145,6 @@ __device__ __forceinline__ long wrap_ix(const GeoD& g, int i, int j, int& jw) {
     return ix2(g, i, j);
 }
 
-// An FP32 value as the FP64 value it equals, by integer operations: the exponent is
-// rebiased (127 -> 1023) and the 23-bit fraction moves to the top of the 52-bit one.
-// Zeros and subnormals (below 1.2e-38) become a signed zero, infinities and NaNs keep
-// their class.  The FP64 conversion instruction runs on GB300's FP64 unit, whose rate is
-// a small fraction of the integer rate; three of them per cell and pass cost more than
-// the rest of the pass.
-__device__ __forceinline__ double widen(float x) {
-    const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu, f = b & 0x7fffffu;
-    const unsigned s = b & 0x80000000u;
-    const unsigned e64 = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
-    const unsigned fx = e == 0u ? 0u : f;
-    return __hiloint2double((int)(s | (e64 << 20) | (fx >> 3)), (int)(fx << 29));
-}
-__device__ __forceinline__ double widen(double x) { return x; }
-
 // region (bx, by): the interior [bx IX, bx IX + IX) x [by IY, by IY + IY) and its halo.
 // WEIGHTED: the partial sums take substep m with the filter's weight fw[m] (the pass's own
 // weights), else with weight 1 (equal weights, scaled by 1/N_s at the end)
