@@ -1071,9 +1071,10 @@ template <typename R> __device__ __forceinline__ void acc_zero(double* a, long c
     if (sizeof(R) == sizeof(float)) reinterpret_cast<float*>(a)[c] = 0.f;
     else a[c] = 0.0;
 }
-template <typename R> __device__ __forceinline__ double acc_get(const double* a, long c) {
-    if (sizeof(R) == sizeof(float)) return (double)reinterpret_cast<const float*>(a)[c];
-    return a[c];
+// an accumulator times s, in the path's precision (FP32 in the mixed form: no FP64 unit)
+template <typename R> __device__ __forceinline__ R acc_scaled(const double* a, long c, double s) {
+    if (sizeof(R) == sizeof(float)) return (R)(reinterpret_cast<const float*>(a)[c] * (float)s);
+    return (R)(a[c] * s);
 }
 
 template <typename R>
@@ -1303,9 +1304,9 @@ __device__ __forceinline__ void baro_end_col(const KP<R>& p, const long c, doubl
     if (c >= (long)g.nx * g.ny) return;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx);
     const long c2 = ix2(g, i, j);
-    if (g.kb[c2] < g.nz) eta[c2] = eta[c2] + acc_get<R>(accE, c2) * rns;
-    corrU[c2] = rHu[c2] > R(0) ? (R(acc_get<R>(accU, c2) * rns) + (Un[c2] - Su[c2])) * rHu[c2] : R(0);
-    corrV[c2] = rHv[c2] > R(0) ? (R(acc_get<R>(accV, c2) * rns) + (Vn[c2] - Sv[c2])) * rHv[c2] : R(0);
+    if (g.kb[c2] < g.nz) eta[c2] = eta[c2] + (double)acc_scaled<R>(accE, c2, rns);
+    corrU[c2] = rHu[c2] > R(0) ? (acc_scaled<R>(accU, c2, rns) + (Un[c2] - Su[c2])) * rHu[c2] : R(0);
+    corrV[c2] = rHv[c2] > R(0) ? (acc_scaled<R>(accV, c2, rns) + (Vn[c2] - Sv[c2])) * rHv[c2] : R(0);
 }
 
 template <typename R>
