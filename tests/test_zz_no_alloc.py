@@ -62,3 +62,39 @@ def test_static_variant_rejects_oversize_before_launching():
         assert rc == -1
         assert b"exceeds the static scratch" in L.ocean_last_error(None)
     assert L.ocean_tridiag_batched_static(*fake, 0, 10, ocean.OCEAN_FP64, None) == -1
+
+
+@pytest.mark.gpu
+def test_static_variant_inside_a_captured_cuda_graph():
+    # the use the entry point exists for: after one eager call (which looks up its
+    # scratch array), a call captured into a CUDA graph and replayed on new inputs copied
+    # into the captured buffers solves each new system
+    import torch
+    L = ocean.load()
+    precision, dt = ocean.OCEAN_FP64, torch.float64
+    rng = np.random.default_rng(29)
+    n, nsys = 40, 700
+    sysm = [torch.tensor(t, dtype=dt, device="cuda") for t in _system(rng, n, nsys)]
+    x = torch.empty((n, nsys), dtype=dt, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert _call(L.ocean_tridiag_batched_static, sysm, x, n, nsys, precision,
+                     s.cuda_stream) == 0
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        rc = _call(L.ocean_tridiag_batched_static, sysm, x, n, nsys, precision, s.cuda_stream)
+    assert rc == 0, L.ocean_last_error(None)
+    for _ in range(2):
+        new = [torch.tensor(t, dtype=dt, device="cuda") for t in _system(rng, n, nsys)]
+        for dst, src in zip(sysm, new):
+            dst.copy_(src)
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = torch.empty_like(x)
+        assert _call(L.ocean_tridiag_batched, new, ref, n, nsys, precision,
+                     torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        err = (x - ref).abs().max().item()
+        assert err <= 1e-14 * max(1.0, ref.abs().max().item()), err
