@@ -3,7 +3,7 @@
 
 Workload (default): the 1/12-degree lat-lon configuration, 4320 x 1680 x 48 cells
 (70S-70N), dt = 180 s, 60 barotropic substeps, in the mixed-precision form (FP32 fields
-and stencils; FP64 free surface, barotropic averages and conservation sums).
+and stencils; FP64 free surface and conservation sums).
 `--workload ensemble96` times the batched ensemble instead: 96 closed basins of seeded
 uneven sizes (32-512 x 32-512 x 8-48), stepped together.  `--workload learned_half` times
 the 1/2-degree step with the learned column closure (network 288-256-256-256-144 on every
@@ -909,7 +909,7 @@ def main():
             "data": "synthetic (seeded random-field bathymetry, stratified T/S with noise, "
                     "zonal wind 0.1 cos(3 lat); stands in for the ECCO2-forced domains)",
             "config": config_block(case, wname, "mixed (FP32 fields and stencils; FP64 free "
-                                                 "surface, barotropic averages, sums)"),
+                                                 "surface and sums)"),
             "sypd": metrics.sypd(p["dt"], ms_all / 1e3),
             "sim_days_per_day": metrics.sim_days_per_day(p["dt"], ms_all / 1e3),
             "wet_cells": wet,
