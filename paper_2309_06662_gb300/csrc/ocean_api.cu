@@ -100,7 +100,7 @@ struct ocean_s {
     int cl_dims[5] = {};
     void *cl_X = nullptr, *cl_H0 = nullptr, *cl_H1 = nullptr, *cl_Wt[4] = {}, *cl_dGT = nullptr,
          *cl_dGS = nullptr;
-    float *cl_Y = nullptr, *cl_b[4] = {}, *cl_stage = nullptr, *cl_mu = nullptr, *cl_sigma = nullptr;
+    float *cl_Y = nullptr, *cl_b[4] = {}, *cl_stage = nullptr, *cl_mu = nullptr, *cl_sigma = nullptr;   // cl_sigma: 1/sigma
     double dy = 0;
     int cur = 0;
     long nstep = 0;
@@ -1299,6 +1299,14 @@ int ocean_diagnostics(ocean_t h, ocean_diag* out) {
     return OCEAN_OK;
 }
 
+// the features' scales go to the device as reciprocals: the kernels multiply (an FP32
+// division is a sequence of instructions; the BF16 features do not see the difference)
+void upload_rsigma(ocean_t h, const float* sigma) {
+    std::vector<float> r(6 * (size_t)h->nz);
+    for (size_t q = 0; q < r.size(); ++q) r[q] = (float)(1.0 / (double)sigma[q]);
+    upload_bytes(h, h->cl_sigma, r.data(), r.size() * sizeof(float));
+}
+
 int ocean_set_closure(ocean_t h, const float* params, size_t count, const float* mu,
                       const float* sigma, const ocean_closure_scales* sc) {
     if (!h) return fail(nullptr, OCEAN_ERR_ARG, "null handle");
@@ -1321,7 +1329,7 @@ int ocean_set_closure(ocean_t h, const float* params, size_t count, const float*
         p += out;
     }
     upload_bytes(h, h->cl_mu, mu, 6 * (size_t)h->nz * sizeof(float));
-    upload_bytes(h, h->cl_sigma, sigma, 6 * (size_t)h->nz * sizeof(float));
+    upload_rsigma(h, sigma);
     OC_CUDA(h, cudaGetLastError());
     OC_CUDA(h, cudaStreamSynchronize(h->stream));
     h->cl_sc = *sc;
@@ -1338,7 +1346,7 @@ int ocean_closure_features(ocean_t h, const float* mu, const float* sigma, float
     if (d_X && (!mu || !sigma)) return fail(h, OCEAN_ERR_ARG, "features need mu and sigma");
     if (d_X) {
         upload_bytes(h, h->cl_mu, mu, 6 * (size_t)h->nz * sizeof(float));
-        upload_bytes(h, h->cl_sigma, sigma, 6 * (size_t)h->nz * sizeof(float));
+        upload_rsigma(h, sigma);
     }
     if (h->prec == OCEAN_FP64) {
         const KP<double> k = make_kp<double>(h, false);

@@ -15,7 +15,7 @@ inline int cblocks(long n) { return (int)((n + CT - 1) / CT); }
 __device__ __forceinline__ float softplus_c(float z) { return z > 20.f ? z : log1pf(__expf(z)); }
 
 // Per interior column c = j nx + i: raw features (T, S, centre u, v on levels; N^2 and
-// shear^2 on bottom faces), z-scored with mu/sigma where the entry counts (wet level or
+// shear^2 on bottom faces), z-scored with mu and 1/sigma where the entry counts (wet level or
 // interior face), else 0, for the levels [k0, k1).  emit(fi, x, k, w, f, gT, gS) receives
 // feature fi = q nz + k, its value, and for q = 0 the level's masks and vertical
 // gradients.
@@ -25,7 +25,7 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, 
                                                 const R* __restrict__ v, const R* __restrict__ T,
                                                 const R* __restrict__ S,
                                                 const float* __restrict__ mu,
-                                                const float* __restrict__ sigma, Emit emit) {
+                                                const float* __restrict__ rsigma, Emit emit) {
     const GeoD& g = p.g;
     const int i = (int)(c % g.nx), j = (int)(c / g.nx), nz = g.nz;
     const long c2 = ix2(g, i, j), P = g.plane;
@@ -74,7 +74,7 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, 
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const int fi = q * nz + k;
-            emit(fi, use[q] ? raw[q] / sigma[fi] : 0.f, k, w, f, gT, gS);
+            emit(fi, use[q] ? raw[q] * rsigma[fi] : 0.f, k, w, f, gT, gS);
         }
     }
 }
@@ -84,7 +84,7 @@ __device__ __forceinline__ void column_features(const KP<R>& p, long c, int k0, 
 template <typename R>
 __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __restrict__ v,
                                    const R* __restrict__ T, const R* __restrict__ S,
-                                   const float* __restrict__ mu, const float* __restrict__ sigma,
+                                   const float* __restrict__ mu, const float* __restrict__ rsigma,
                                    float* __restrict__ Xf, __nv_bfloat16* __restrict__ Xb,
                                    unsigned char* __restrict__ face, unsigned char* __restrict__ wet,
                                    float* __restrict__ dzT, float* __restrict__ dzS) {
@@ -92,7 +92,7 @@ __global__ void k_closure_features(KP<R> p, const R* __restrict__ u, const R* __
     const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long)g.nx * g.ny) return;
     const int nz = g.nz;
-    column_features<R>(p, c, 0, nz, u, v, T, S, mu, sigma,
+    column_features<R>(p, c, 0, nz, u, v, T, S, mu, rsigma,
                        [&](int fi, float x, int k, bool w, bool f, float gT, float gS) {
                            if (Xf) Xf[c * 6 * nz + fi] = x;
                            if (Xb) Xb[c * 6 * nz + fi] = __float2bfloat16_rn(x);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(XC * XQ) k_closure_xb(KP<R> p, const R* __rest
                                                         const R* __restrict__ T,
                                                         const R* __restrict__ S,
                                                         const float* __restrict__ mu,
-                                                        const float* __restrict__ sigma,
+                                                        const float* __restrict__ rsigma,
                                                         __nv_bfloat16* __restrict__ Xb) {
     extern __shared__ __align__(16) unsigned char fx_raw[];
     __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(fx_raw);
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(XC * XQ) k_closure_xb(KP<R> p, const R* __rest
     const int L = (nz + XQ - 1) / XQ, k0 = tq * L, k1 = min(k0 + L, nz);
     if (c0 + tc < ncol && k0 < k1) {
         __nv_bfloat16* row = tile + (long)tc * ld;
-        column_features<R>(p, c0 + tc, k0, k1, u, v, T, S, mu, sigma,
+        column_features<R>(p, c0 + tc, k0, k1, u, v, T, S, mu, rsigma,
                            [&](int fi, float x, int, bool, bool, float, float) {
                                row[fi] = __float2bfloat16_rn(x);
                            });
@@ -322,18 +322,18 @@ __global__ void k_closure_targets(KP<R> p, const R* __restrict__ GcT, const R* _
 
 template <typename R>
 void launch_closure_features(const KP<R>& p, const R* u, const R* v, const R* T, const R* S,
-                             const float* mu, const float* sigma, float* Xf, void* Xb,
+                             const float* mu, const float* rsigma, float* Xf, void* Xb,
                              unsigned char* face, unsigned char* wet, float* dzT, float* dzS,
                              cudaStream_t s) {
     const long ncol = (long)p.g.nx * p.g.ny;
     if (Xb && !Xf && !face && !wet && !dzT && !dzS) {   // the step's BF16 features
         const size_t smem = (size_t)XC * (6 * p.g.nz + 2) * sizeof(__nv_bfloat16);
         k_closure_xb<R><<<(int)((ncol + XC - 1) / XC), XC * XQ, smem, s>>>(
-            p, u, v, T, S, mu, sigma, reinterpret_cast<__nv_bfloat16*>(Xb));
+            p, u, v, T, S, mu, rsigma, reinterpret_cast<__nv_bfloat16*>(Xb));
         return;
     }
     k_closure_features<R><<<cblocks(ncol), CT, 0, s>>>(
-        p, u, v, T, S, mu, sigma, Xf, reinterpret_cast<__nv_bfloat16*>(Xb), face, wet, dzT, dzS);
+        p, u, v, T, S, mu, rsigma, Xf, reinterpret_cast<__nv_bfloat16*>(Xb), face, wet, dzT, dzS);
 }
 
 template <typename R>
