@@ -256,3 +256,31 @@ def test_bounded_wait_gives_up_and_the_context_survives():
     Y = net.forward(X).cpu().numpy()
     ref, _ = C.mlp_forward(params, X.cpu().numpy().astype(np.float64), bf16=True)
     assert np.max(np.abs(Y - ref)) <= 1e-2 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad_output", [0, 5, 7, 100])
+def test_columns_with_a_non_finite_output_keep_the_richardson_closure(bad_output):
+    # one output of the network made NaN for every column (through the last layer's
+    # bias): no column's outputs are applied, so the learned step is bitwise the
+    # Richardson-number step.  The output's index decides which of the threads that
+    # test a column's outputs sees it.
+    c = inputs.latlon_small_case(seed=23)
+    c.u, c.v = seeded_velocity(c, 7, 0.05)
+    nz, hidden = c.nz, 32
+    o = oracle.OracleModel(c)
+    mu, sd = _stats(*_oracle_features(o, c))
+    params = inputs.mlp_seeded_params(19, [6 * nz, hidden, hidden, hidden, 3 * nz])
+    W, b = params[-1]
+    b = np.array(b, dtype=np.float64, copy=True)
+    b[bad_output % (3 * nz)] = np.nan
+    params = params[:-1] + [(W, b)]
+    sc = dict(kappa=2e-3, gT=2e-8, gS=2e-9, sFT=1, sFS=1, sGT=1, sGS=1)
+    g = ocean.Ocean(c, precision=ocean.OCEAN_MIXED, closure=ocean.OCEAN_CLOSURE_LEARNED,
+                    closure_hidden=hidden)
+    g.set_closure(params, mu, sd, sc)
+    r = ocean.Ocean(c, precision=ocean.OCEAN_MIXED)
+    g.step(3)
+    r.step(3)
+    for f in ("u", "v", "T", "S", "eta"):
+        assert np.array_equal(g.get(f), r.get(f)), f
