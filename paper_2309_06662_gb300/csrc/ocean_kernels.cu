@@ -1062,7 +1062,9 @@ __global__ void __launch_bounds__(NT, (OccX<R, true>::value)) k_momentum(
 // The sub-cycle's sums over all passes, per column: FP64 words in the FP64 form; in the
 // mixed form FP32 words in the first half of the same storage (half the accumulators'
 // DRAM traffic per pass; the sums are of deviations from the step's start, O(1e-3) of
-// the state, so FP32's 24 bits over ten passes stay far below the mixed form's error)
+// the state, so FP32's 24 bits over ten passes stay far below the mixed form's error).
+// A pass adds its partial sums by in-memory reductions: one thread owns each cell, so
+// the reduction is the plain add, issued without waiting for the old value.
 __device__ __forceinline__ void acc_add(double* a, long c, double p) { atomicAdd(a + c, p); }
 __device__ __forceinline__ void acc_add(double* a, long c, float p) {
     atomicAdd(reinterpret_cast<float*>(a) + c, p);
