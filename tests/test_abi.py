@@ -63,6 +63,9 @@ def test_arena_size_and_argument_errors_without_gpu():
     assert L.ocean_create(ctypes.byref(g), None, ctypes.byref(prm), ctypes.byref(h)) == -1
     assert L.ocean_step(None, 1) == -1
     assert L.ocean_get_step(None) == -1
+    assert L.ocean_set_wind_stress(None, None, None) == -1
+    assert L.ocean_set_wind_stress_f32(None, None, None) == -1
+    assert b"null handle" in L.ocean_last_error(None)
 
 
 def test_ensemble_argument_errors_without_gpu():
